@@ -1,0 +1,186 @@
+/*
+ * helm.h -- C ABI of libhelm, batched discrete 2D Helmholtz solves and the FWI /
+ * bilevel-hypergradient hot path of Downing, Gazzola, Graham, Spence, "Optimising
+ * seismic imaging design parameters via bilevel learning" (arXiv:2301.10762).
+ *
+ * Discretisation (Appendix "Numerical forward model"): P1 finite elements on a uniform
+ * nx x nz rectangular grid cut into right triangles, nodal quadrature,
+ *     A(m, w) = S - w^2 diag(d m) - i w diag(b sqrt(m)),
+ * S the five-point stiffness (interior edge couplings -hz/hx horizontally, -hx/hz
+ * vertically, halved on boundary edges, zero row sums), d the tensor-trapezoid lumped
+ * mass (hx hz, halved per boundary direction), b the lumped boundary length.
+ * The adjoint operator is A^H = S - w^2 diag(d m) + i w diag(b sqrt(m)).
+ *
+ * Layout conventions shared by every entry point:
+ *   - node (i, j) sits at (x, z) = (i hx, j hz), z = 0 the top row, hx = lx/(nx-1),
+ *     hz = lz/(nz-1); canonical node index k = i*nz + j (z fastest); N = nx*nz;
+ *   - complex numbers are interleaved FP64 pairs (helm_c128, the layout of
+ *     torch.complex128 / numpy complex128);
+ *   - right-hand-side and solution blocks are [n_omega][nrhs][N]: one contiguous
+ *     length-N column per (frequency, right-hand side);
+ *   - "_dev" pointers are device (HBM) pointers owned by the caller; everything else is
+ *     host memory owned by the caller.  Opaque handles (helm_op_t, helm_factor_t) and
+ *     the HBM behind them are owned by the library and released by helm_*_destroy.
+ *   - every call is asynchronous on the stream given to helm_assemble, except where a
+ *     result is returned through a host pointer (that call synchronises the stream).
+ *     A handle must not be used from two host threads or two streams at once.
+ *   - no entry point aborts, exits or throws; each returns a helm_status.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_EINVAL = 1,     /* invalid argument (sizes, NULL pointers, positions outside the grid) */
+    HELM_ENOMEM = 2,     /* device allocation failed */
+    HELM_ECUDA = 3,      /* a CUDA runtime call failed */
+    HELM_ENOCONV = 4,    /* iterative refinement or PCG did not reach its tolerance */
+    HELM_ESINGULAR = 5,  /* a zero or non-finite pivot was met in a line factorisation */
+    HELM_ETIMEOUT = 6    /* a bounded device-side wait gave up */
+} helm_status;
+
+typedef struct { double re, im; } helm_c128;
+
+/* Uniform grid: nx x nz nodes (both >= 4) on [0, lx] x [0, lz]. */
+typedef struct { int32_t nx, nz; double lx, lz; } helm_grid;
+
+/* Precision of the line factors.  HELM_FP64: complex FP64 factors and sweeps.
+ * HELM_MIXED: complex FP32 factors and sweeps, FP64 residuals and FP64 iterative
+ * refinement x += A~^{-1}(b - A x) until ||b - A x|| / ||b|| <= rtol per column. */
+typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_prec;
+
+/* Acquisition (Section 2, sets S and P): physical positions, host memory.
+ * Sources: on a node, the right-hand side is e_s (Appendix, "Computing the wavefield");
+ * off a node, the bilinear weights of the four surrounding nodes.
+ * Receivers: the sliding bicubic restriction R(P) of Section "Numerical restriction
+ * operator" (4 nearest nodes per direction, window clamped inside the grid).
+ * rec_w are receiver weights w_j multiplying the misfit (phi uses ||W eps||^2); NULL
+ * means w = 1, which is the paper's objective exactly. */
+typedef struct {
+    int32_t n_src, n_rec;
+    const double *src_xz;   /* [n_src][2] */
+    const double *src_amp;  /* [n_src] or NULL (amplitude 1) */
+    const double *rec_xz;   /* [n_rec][2] */
+    const double *rec_w;    /* [n_rec] or NULL (weight 1) */
+} helm_acq;
+
+typedef struct {
+    int32_t iters;        /* refinement sweeps used (1 for HELM_FP64) */
+    double max_relres;    /* max over columns of ||b - A x||_2 / ||b||_2, FP64; -1 if not computed */
+} helm_solve_info;
+
+typedef struct {
+    int32_t max_iter;     /* PCG iteration cap (Hessian products after the first) */
+    int32_t fixed_iters;  /* > 0: run exactly this many iterations, ignore rtol */
+    double rtol;          /* stop when ||r_n|| / ||r_0|| <= rtol */
+    double x0;            /* constant initial guess (the paper uses 1) */
+    double refine_rtol;   /* residual tolerance of every Helmholtz solve (mixed mode) */
+} helm_pcg_opts;
+
+typedef struct {
+    int32_t cg_matvecs;   /* Hessian-vector products of the last model (incl. initial residual) */
+    double cg_relres;     /* ||r|| / ||r_0|| reached, max over models */
+    int64_t solves;       /* Helmholtz right-hand-side solves of the hypergradient pass */
+    int64_t data_solves;  /* solves spent generating the data u(m') */
+    int32_t max_refine_iters;  /* largest refinement count of any solve (mixed) */
+} helm_hyper_info;
+
+typedef struct helm_op helm_op_t;
+typedef struct helm_factor helm_factor_t;
+
+const char *helm_status_string(helm_status s);
+/* Text of the last error detected on the calling thread (empty if none). */
+const char *helm_last_error(void);
+
+/* helm_assemble -- operator A(m, w) for every w in omega (Appendix "Numerical forward
+ * model", Eq. (matrices) with nodal quadrature).
+ *   grid:    grid description (host).
+ *   m_dev:   [N] squared slowness m = 1/c^2 > 0 (device, FP64); copied into the op.
+ *   omega:   [n_omega] angular frequencies (host), n_omega >= 1.
+ *   stream:  cudaStream_t used by every later call on this op and its factors
+ *            (NULL = the legacy default stream).
+ *   out:     receives the new handle.
+ * Errors: EINVAL (nx or nz < 4, n_omega < 1, NULL pointers), ENOMEM, ECUDA. */
+helm_status helm_assemble(const helm_grid *grid, const double *m_dev, const double *omega,
+                          int32_t n_omega, void *stream, helm_op_t **out);
+void helm_op_destroy(helm_op_t *op);
+
+/* helm_factor -- block-tridiagonal (line-by-line) factorisation of every A(m, w_q):
+ * with lines of constant i, A has diagonal blocks D_i (tridiagonal n_z x n_z) and
+ * diagonal couplings C_i; the factor stores G_i = S_i^{-1} with
+ * S_0 = D_0, S_i = D_i - C_i S_{i-1}^{-1} C_i.  This replaces the sparse direct
+ * (backslash) factorisation of the Appendix ("Computing the wavefield").
+ * Each S_i is inverted by block Gauss-Jordan with partial pivoting inside 16 x 16
+ * diagonal blocks.  Errors: ESINGULAR (zero / non-finite pivot), ENOMEM, ECUDA.
+ * The factor keeps a reference to op: destroy the factor before the op. */
+helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out);
+void helm_factor_destroy(helm_factor_t *f);
+
+/* helm_solve -- X = A(m, w_q)^{-1} B for every frequency q and column (Eq. (defu)
+ * discretised: u = A^{-1} e_s).  B_dev, X_dev: [n_omega][nrhs][N] complex (device);
+ * they may not alias.  rtol / max_iter drive the refinement of HELM_MIXED (ignored by
+ * HELM_FP64 except that info->max_relres is computed when info != NULL).
+ * Errors: EINVAL, ENOCONV (mixed: max_iter reached above rtol; X holds the last
+ * iterate), ECUDA. */
+helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
+                       double rtol, int32_t max_iter, helm_solve_info *info);
+
+/* helm_adjoint_solve -- X = (A^H)^{-1} B, the discrete adjoint solution operator
+ * S*_{m,w} of Definition def:solnop (Eq. (lambda)).  Since A is complex symmetric,
+ * it is computed from the same factor as conj(A^{-1} conj(B)).  Arguments as helm_solve. */
+helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
+                               helm_c128 *X_dev, double rtol, int32_t max_iter,
+                               helm_solve_info *info);
+
+/* helm_sources -- right-hand sides e_s (Appendix, "Computing the wavefield"),
+ * B_dev [n_omega][n_src][N] (identical for every frequency), amplitudes src_amp. */
+helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, helm_c128 *B_dev);
+
+/* helm_restrict -- Y = R(P) X (Eq. (Rv), sliding bicubic), X_dev [n_omega][ncol][N],
+ * Y_dev [n_omega][ncol][n_rec]. */
+helm_status helm_restrict(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
+                          const helm_c128 *X_dev, helm_c128 *Y_dev);
+
+/* fwi_misfit_grad -- phi and grad phi of Eq. (newphi) by the adjoint-state method
+ * (Algorithm alg:box1, Theorem th:grad):
+ *   u = A^{-1} e_s, eps = d - R u, lambda = (A^H)^{-1} R^T (W^2 eps),
+ *   phi = 1/2 sum |W eps|^2 + 1/2 m^T Gamma m,
+ *   grad_k = -Re sum_{s,w} g_k u_k conj(lambda_k) + (Gamma m)_k,
+ *   g_k = w^2 d_k + i w b_k / (2 sqrt(m_k)),  Gamma = alpha R + mu I (Eq. (Gamma)).
+ *   data_dev: [n_omega][n_src][n_rec] complex (device).
+ *   phi: host scalar (this call synchronises).  grad_dev: [N] FP64 (device).
+ *   u_out, lam_out: optional [n_omega][n_src][N] (device) or NULL. */
+helm_status fwi_misfit_grad(helm_factor_t *f, const helm_acq *acq, const helm_c128 *data_dev,
+                            double alpha, double mu, double rtol, double *phi, double *grad_dev,
+                            helm_c128 *u_out, helm_c128 *lam_out);
+
+/* bilevel_hypergrad -- upper-level objective and hypergradient (Algorithm alg:box,
+ * Theorems sogradt1 and sogradta), averaged over n_models training models:
+ *   per model: data u' = A(m')^{-1} e_s on the same grid; u, lambda at m_fwi;
+ *   rho = H^{-1}(m' - m_fwi) by PCG with preconditioner P2 = Gamma(alpha0, mu)
+ *   (Eq. (P2)), each Hessian product costing 2 solves per (s, w) (Discussion disc:Hess);
+ *   tau = A^{-1}(g u rho) (Eq. (tau_def));
+ *   psi = 1/(2 N_m') sum ||m' - m_fwi||^2, dpsi/dalpha = 1/N_m' sum m_fwi^T R rho,
+ *   dpsi/dp_{j,l} = 1/N_m' sum_{m',s,w} w_j^2 Re[conj((dR_l tau)_j)(R(u-u'))_j
+ *                                              + conj((R tau)_j)(dR_l(u-u'))_j],
+ *   dpsi/dw_j = -1/N_m' sum 2 w_j Re[conj((R tau)_j)(R(u'-u))_j].
+ *   grids[n_models], m_fwi[n_models], m_true[n_models]: per model (device vectors of
+ *   length nx*nz of that model's grid); acq and omega are shared by all models.
+ *   Outputs are host scalars / arrays (the call synchronises).  dpsi_dw may be NULL. */
+helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grids, const double *const *m_fwi,
+                              const double *const *m_true, const helm_acq *acq,
+                              const double *omega, int32_t n_omega, double alpha, double alpha0,
+                              double mu, helm_prec prec, const helm_pcg_opts *pcg, void *stream,
+                              double *psi, double *dpsi_dalpha, double *dpsi_dp, double *dpsi_dw,
+                              helm_hyper_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

@@ -1,0 +1,378 @@
+// extern "C" entry points of libhelm (declared in include/helm.h): handle management,
+// argument checks and orchestration of the kernels.  No computation of the path runs
+// on the host; the host only sequences launches and reads scalars back.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "helm.h"
+#include "kernels.h"
+#include "abi_internal.h"
+
+using namespace helm;
+
+static thread_local std::string g_last_error;
+
+void helm_set_error(const char *what, cudaError_t e) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s", what, e == cudaSuccess ? "ok" : cudaGetErrorString(e));
+    g_last_error = buf;
+}
+void helm_set_msg(const char *what) { g_last_error = what; }
+
+extern "C" const char *helm_status_string(helm_status s) {
+    switch (s) {
+        case HELM_OK: return "HELM_OK";
+        case HELM_EINVAL: return "HELM_EINVAL: invalid argument";
+        case HELM_ENOMEM: return "HELM_ENOMEM: device allocation failed";
+        case HELM_ECUDA: return "HELM_ECUDA: CUDA runtime error";
+        case HELM_ENOCONV: return "HELM_ENOCONV: iteration did not reach its tolerance";
+        case HELM_ESINGULAR: return "HELM_ESINGULAR: zero or non-finite pivot in a line factorisation";
+        case HELM_ETIMEOUT: return "HELM_ETIMEOUT: bounded device wait gave up";
+    }
+    return "HELM_?: unknown status";
+}
+
+extern "C" const char *helm_last_error(void) { return g_last_error.c_str(); }
+
+helm_status dev_alloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) return HELM_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        helm_set_error(what, e);
+        return e == cudaErrorMemoryAllocation ? HELM_ENOMEM : HELM_ECUDA;
+    }
+    return HELM_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------- operator
+
+extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev, const double *omega,
+                                     int32_t n_omega, void *stream, helm_op_t **out) {
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    if (!grid || !m_dev || !omega || n_omega < 1) { helm_set_msg("helm_assemble: NULL argument or n_omega < 1"); return HELM_EINVAL; }
+    if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0)) {
+        helm_set_msg("helm_assemble: need nx, nz >= 4 and positive lengths");
+        return HELM_EINVAL;
+    }
+    for (int w = 0; w < n_omega; ++w)
+        if (!isfinite(omega[w])) { helm_set_msg("helm_assemble: non-finite omega"); return HELM_EINVAL; }
+    helm_op *op = new (std::nothrow) helm_op();
+    if (!op) return HELM_ENOMEM;
+    op->g = GridGeom{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1)};
+    op->lx = grid->lx;
+    op->lz = grid->lz;
+    op->n_omega = n_omega;
+    op->omega.assign(omega, omega + n_omega);
+    op->st = (cudaStream_t)stream;
+    const size_t N = (size_t)grid->nx * grid->nz;
+    helm_status s;
+    if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "cudaMalloc(m)")) != HELM_OK ||
+        (s = dev_alloc((void **)&op->omega_dev, n_omega * sizeof(double), "cudaMalloc(omega)")) != HELM_OK ||
+        (s = dev_alloc((void **)&op->diag, (size_t)n_omega * N * sizeof(double2), "cudaMalloc(diag)")) != HELM_OK ||
+        (s = dev_alloc((void **)&op->status, sizeof(int), "cudaMalloc(status)")) != HELM_OK) {
+        helm_op_destroy(op);
+        return s;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(op->m, m_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, op->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(op->omega_dev, omega, n_omega * sizeof(double), cudaMemcpyHostToDevice, op->st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess ||
+        (e = launch_assemble(op->g, op->m, op->omega_dev, n_omega, op->diag, op->st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(op->st)) != cudaSuccess) {
+        helm_set_error("helm_assemble", e);
+        helm_op_destroy(op);
+        return HELM_ECUDA;
+    }
+    *out = op;
+    return HELM_OK;
+}
+
+extern "C" void helm_op_destroy(helm_op_t *op) {
+    if (!op) return;
+    dev_free(op->m);
+    dev_free(op->omega_dev);
+    dev_free(op->diag);
+    dev_free(op->status);
+    delete op;
+}
+
+// ------------------------------------------------------------------------ factor
+
+extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out) {
+    if (!out) return HELM_EINVAL;
+    *out = nullptr;
+    if (!op || (prec != HELM_FP64 && prec != HELM_MIXED)) { helm_set_msg("helm_factor: bad op or precision"); return HELM_EINVAL; }
+    helm_factor_t *f = new (std::nothrow) struct helm_factor();
+    if (!f) return HELM_ENOMEM;
+    f->op = op;
+    f->prec = prec;
+    const GridGeom &g = op->g;
+    f->cs = pick_cluster_size(g.nz);
+    const size_t esz = prec == HELM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t gelems = (size_t)op->n_omega * g.nx * g.nz * g.nz;
+    helm_status s;
+    if ((s = dev_alloc(&f->G, gelems * esz, "cudaMalloc(factor)")) != HELM_OK ||
+        (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "cudaMalloc(exchange)")) !=
+            HELM_OK) {
+        helm_factor_destroy(f);
+        return s;
+    }
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess) {
+        helm_set_error("helm_factor", e);
+        helm_factor_destroy(f);
+        return HELM_ECUDA;
+    }
+    if (prec == HELM_FP64)
+        e = launch_line_factor<double>(g, op->n_omega, op->diag, (double2 *)f->G, (double2 *)f->xch, op->status,
+                                       f->cs, op->st);
+    else
+        e = launch_line_factor<float>(g, op->n_omega, op->diag, (float2 *)f->G, (float2 *)f->xch, op->status,
+                                      f->cs, op->st);
+    int st_host = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) {
+        helm_set_error("helm_factor: launch", e);
+        helm_factor_destroy(f);
+        return HELM_ECUDA;
+    }
+    if (st_host & ST_SINGULAR) {
+        helm_set_msg("helm_factor: zero or non-finite pivot");
+        helm_factor_destroy(f);
+        return HELM_ESINGULAR;
+    }
+    *out = f;
+    return HELM_OK;
+}
+
+extern "C" void helm_factor_destroy(helm_factor_t *f) {
+    if (!f) return;
+    dev_free(f->G);
+    dev_free(f->xch);
+    dev_free(f->r);
+    dev_free(f->y);
+    dev_free(f->norms);
+    if (f->norms_host) cudaFreeHost(f->norms_host);
+    delete f;
+}
+
+helm_status factor_reserve(helm_factor_t *f, int nrhs) {
+    if (nrhs <= f->cap) return HELM_OK;
+    const helm_op *op = f->op;
+    const size_t cols = (size_t)op->n_omega * nrhs;
+    const size_t N = (size_t)op->g.nx * op->g.nz;
+    dev_free(f->r);
+    dev_free(f->y);
+    dev_free(f->norms);
+    if (f->norms_host) cudaFreeHost(f->norms_host);
+    f->r = nullptr;
+    f->y = nullptr;
+    f->norms = nullptr;
+    f->norms_host = nullptr;
+    f->cap = 0;
+    helm_status s;
+    if ((s = dev_alloc((void **)&f->r, cols * N * sizeof(double2), "cudaMalloc(residual)")) != HELM_OK) return s;
+    if (f->prec == HELM_MIXED &&
+        (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "cudaMalloc(work)")) != HELM_OK)
+        return s;
+    if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "cudaMalloc(norms)")) != HELM_OK) return s;
+    if (cudaMallocHost((void **)&f->norms_host, cols * 2 * sizeof(double)) != cudaSuccess) {
+        f->norms_host = nullptr;
+        helm_set_msg("cudaMallocHost(norms)");
+        return HELM_ENOMEM;
+    }
+    f->cap = nrhs;
+    return HELM_OK;
+}
+
+// max over columns of ||r|| / ||b|| from the norms buffer (synchronises)
+static helm_status read_relres(helm_factor_t *f, int nrhs, double *out) {
+    const helm_op *op = f->op;
+    const size_t cols = (size_t)op->n_omega * nrhs;
+    cudaError_t e = cudaMemcpyAsync(f->norms_host, f->norms, cols * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) { helm_set_error("read residual norms", e); return HELM_ECUDA; }
+    double mx = 0.0;
+    for (size_t c = 0; c < cols; ++c) {
+        const double rr = f->norms_host[2 * c], bb = f->norms_host[2 * c + 1];
+        const double rel = bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0);
+        if (!(rel <= mx)) mx = rel;  // propagates NaN
+    }
+    *out = mx;
+    return HELM_OK;
+}
+
+helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
+                       helm_solve_info *info, int conj) {
+    const helm_op *op = f->op;
+    const GridGeom &g = op->g;
+    const int n_sys = op->n_omega;
+    const size_t N = (size_t)g.nx * g.nz;
+    const int cs = pick_cluster_size(g.nz);
+    const int rchunk = 16;
+    cudaError_t e;
+    helm_status s;
+    if (info) { info->iters = 0; info->max_relres = -1.0; }
+    if (f->prec == HELM_FP64) {
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, cs, rchunk, op->st);
+        if (e != cudaSuccess) { helm_set_error("sweep fp64", e); return HELM_ECUDA; }
+        if (info) {
+            info->iters = 1;
+            if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
+            e = cudaMemsetAsync(f->norms, 0, (size_t)n_sys * nrhs * 2 * sizeof(double), op->st);
+            if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, f->norms, conj, op->st);
+            if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
+            if ((s = read_relres(f, nrhs, &info->max_relres)) != HELM_OK) return s;
+        }
+        return HELM_OK;
+    }
+    // mixed: x = A~^{-1} b, then x += A~^{-1}(b - A x) until ||b - A x|| / ||b|| <= rtol
+    if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
+    if (max_iter < 1) max_iter = 1;
+    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, cs, rchunk, op->st);
+    if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+    int it = 1;
+    double rel = INFINITY;
+    for (;;) {
+        e = cudaMemsetAsync(f->norms, 0, (size_t)n_sys * nrhs * 2 * sizeof(double), op->st);
+        if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, f->r, f->norms, conj, op->st);
+        if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
+        if ((s = read_relres(f, nrhs, &rel)) != HELM_OK) return s;
+        if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
+        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, f->r, X, f->y, conj, 1, cs, rchunk,
+                                     op->st);
+        if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+        ++it;
+    }
+    if (info) { info->iters = it; info->max_relres = rel; }
+    (void)N;
+    if (!(rel <= rtol)) { helm_set_msg("refinement did not reach rtol"); return HELM_ENOCONV; }
+    return HELM_OK;
+}
+
+static helm_status check_solve_args(helm_factor_t *f, int32_t nrhs, const helm_c128 *B, helm_c128 *X) {
+    if (!f || nrhs < 0 || (nrhs > 0 && (!B || !X)) || (const void *)B == (const void *)X) {
+        helm_set_msg("helm_solve: bad arguments (NULL, nrhs < 0 or B aliases X)");
+        return HELM_EINVAL;
+    }
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
+                                  double rtol, int32_t max_iter, helm_solve_info *info) {
+    helm_status s = check_solve_args(f, nrhs, B_dev, X_dev);
+    if (s != HELM_OK || nrhs == 0) return s;
+    return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 0);
+}
+
+extern "C" helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
+                                          helm_c128 *X_dev, double rtol, int32_t max_iter,
+                                          helm_solve_info *info) {
+    helm_status s = check_solve_args(f, nrhs, B_dev, X_dev);
+    if (s != HELM_OK || nrhs == 0) return s;
+    return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 1);
+}
+
+// ------------------------------------------------------------ acquisition helpers
+
+helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d) {
+    *d = DevAcq();
+    if (!acq || acq->n_src < 0 || acq->n_rec < 0 || (acq->n_src > 0 && !acq->src_xz) ||
+        (acq->n_rec > 0 && !acq->rec_xz)) {
+        helm_set_msg("acquisition: bad arguments");
+        return HELM_EINVAL;
+    }
+    for (int s = 0; s < acq->n_src; ++s) {
+        const double x = acq->src_xz[2 * s], z = acq->src_xz[2 * s + 1];
+        if (!(x >= 0 && x <= op->lx && z >= 0 && z <= op->lz)) { helm_set_msg("source outside the grid"); return HELM_EINVAL; }
+    }
+    for (int r = 0; r < acq->n_rec; ++r) {
+        const double x = acq->rec_xz[2 * r], z = acq->rec_xz[2 * r + 1];
+        if (!(x >= 0 && x <= op->lx && z >= 0 && z <= op->lz)) { helm_set_msg("receiver outside the grid"); return HELM_EINVAL; }
+    }
+    d->n_src = acq->n_src;
+    d->n_rec = acq->n_rec;
+    const int ns = std::max(1, acq->n_src), nr = std::max(1, acq->n_rec);
+    helm_status s;
+    if ((s = dev_alloc((void **)&d->src_xz, ns * 2 * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->src_amp, ns * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->rec_xz, nr * 2 * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->rec_w, nr * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_idx, nr * 16 * sizeof(int), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_w, nr * 16 * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_wx, nr * 16 * sizeof(double), "acq")) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_wz, nr * 16 * sizeof(double), "acq")) != HELM_OK) {
+        acq_free(d);
+        return s;
+    }
+    std::vector<double> amp(ns, 1.0), w(nr, 1.0);
+    if (acq->src_amp) std::copy(acq->src_amp, acq->src_amp + acq->n_src, amp.begin());
+    if (acq->rec_w) std::copy(acq->rec_w, acq->rec_w + acq->n_rec, w.begin());
+    cudaError_t e = cudaSuccess;
+    if (acq->n_src > 0) e = cudaMemcpyAsync(d->src_xz, acq->src_xz, acq->n_src * 2 * sizeof(double), cudaMemcpyHostToDevice, op->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d->src_amp, amp.data(), ns * sizeof(double), cudaMemcpyHostToDevice, op->st);
+    if (e == cudaSuccess && acq->n_rec > 0) e = cudaMemcpyAsync(d->rec_xz, acq->rec_xz, acq->n_rec * 2 * sizeof(double), cudaMemcpyHostToDevice, op->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d->rec_w, w.data(), nr * sizeof(double), cudaMemcpyHostToDevice, op->st);
+    if (e == cudaSuccess && acq->n_rec > 0)
+        e = launch_restriction_taps(op->g, acq->n_rec, d->rec_xz, d->tap_idx, d->tap_w, d->tap_wx, d->tap_wz, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);   // host vectors above go out of scope
+    if (e != cudaSuccess) {
+        helm_set_error("acquisition upload", e);
+        acq_free(d);
+        return HELM_ECUDA;
+    }
+    return HELM_OK;
+}
+
+void acq_free(DevAcq *d) {
+    dev_free(d->src_xz);
+    dev_free(d->src_amp);
+    dev_free(d->rec_xz);
+    dev_free(d->rec_w);
+    dev_free(d->tap_idx);
+    dev_free(d->tap_w);
+    dev_free(d->tap_wx);
+    dev_free(d->tap_wz);
+    *d = DevAcq();
+}
+
+extern "C" helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, helm_c128 *B_dev) {
+    if (!op || !acq || !B_dev) return HELM_EINVAL;
+    DevAcq d;
+    helm_status s = acq_upload(op, acq, &d);
+    if (s != HELM_OK) return s;
+    cudaError_t e = launch_sources(op->g, op->n_omega, d.n_src, d.src_xz, d.src_amp, (double2 *)B_dev, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    acq_free(&d);
+    if (e != cudaSuccess) { helm_set_error("helm_sources", e); return HELM_ECUDA; }
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_restrict(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
+                                     const helm_c128 *X_dev, helm_c128 *Y_dev) {
+    if (!op || !acq || ncol < 0 || (ncol > 0 && (!X_dev || !Y_dev))) return HELM_EINVAL;
+    DevAcq d;
+    helm_status s = acq_upload(op, acq, &d);
+    if (s != HELM_OK) return s;
+    cudaError_t e = launch_restrict(op->g, op->n_omega * ncol, d.n_rec, d.tap_idx, d.tap_w, (const double2 *)X_dev,
+                                    (double2 *)Y_dev, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    acq_free(&d);
+    if (e != cudaSuccess) { helm_set_error("helm_restrict", e); return HELM_ECUDA; }
+    return HELM_OK;
+}

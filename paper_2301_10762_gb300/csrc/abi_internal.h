@@ -1,0 +1,50 @@
+// Internal definitions of the opaque handles of include/helm.h (C++ only).
+#pragma once
+#include <vector>
+#include <cuda_runtime.h>
+#include "helm.h"
+#include "common.cuh"
+
+struct helm_op {
+    helm::GridGeom g;
+    double lx = 0, lz = 0;
+    int n_omega = 0;
+    std::vector<double> omega;
+    double *m = nullptr;          // [N] squared slowness (device copy)
+    double *omega_dev = nullptr;  // [n_omega]
+    double2 *diag = nullptr;      // [n_omega][N] diagonal of A(m, w)
+    int *status = nullptr;        // device status word
+    cudaStream_t st = nullptr;
+};
+
+struct helm_factor {
+    helm_op *op = nullptr;
+    helm_prec prec = HELM_FP64;
+    int cs = 1;
+    void *G = nullptr;     // [n_omega][nx][nz][nz] complex (FP64 or FP32)
+    void *xch = nullptr;   // factor exchange slots
+    // solve scratch, sized for `cap` right-hand sides per frequency
+    int cap = 0;
+    double2 *r = nullptr;  // FP64 residuals
+    float2 *y = nullptr;   // FP32 working vectors (mixed)
+    double *norms = nullptr;
+    double *norms_host = nullptr;
+};
+
+// acquisition on the device
+struct DevAcq {
+    int n_src = 0, n_rec = 0;
+    double *src_xz = nullptr, *src_amp = nullptr, *rec_xz = nullptr, *rec_w = nullptr;
+    int *tap_idx = nullptr;
+    double *tap_w = nullptr, *tap_wx = nullptr, *tap_wz = nullptr;
+};
+
+void helm_set_error(const char *what, cudaError_t e);
+void helm_set_msg(const char *what);
+helm_status dev_alloc(void **p, size_t bytes, const char *what);
+void dev_free(void *p);
+helm_status factor_reserve(helm_factor_t *f, int nrhs);
+helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
+                       helm_solve_info *info, int conj);
+helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d);
+void acq_free(DevAcq *d);

@@ -1,0 +1,78 @@
+// Shared device helpers for libhelm: complex arithmetic on interleaved pairs, the
+// grid coefficients of the discrete operator, and thread-block-cluster primitives.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace helm {
+
+// ------------------------------------------------------------------ complex types
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+template <typename T> using cx_t = typename cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx_t<T> mkc(T re, T im) {
+    cx_t<T> z; z.x = re; z.y = im; return z;
+}
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+    V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
+// acc += a * b
+template <typename V> __host__ __device__ __forceinline__ void cfma(V &acc, V a, V b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc -= a * b
+template <typename V> __host__ __device__ __forceinline__ void cfms(V &acc, V a, V b) {
+    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+
+__device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
+
+template <typename V> __device__ __forceinline__ V ldcg(const V *p);
+template <> __device__ __forceinline__ double2 ldcg<double2>(const double2 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float2 ldcg<float2>(const float2 *p) { return __ldcg(p); }
+
+// ----------------------------------------------------------- grid coefficients
+// Uniform grid, node (i, j) at (i hx, j hz), k = i*nz + j.  Edge couplings of the
+// five-point P1 stiffness: horizontal (i-1,j)-(i,j) is -(hz/hx) w_z(j), vertical
+// (i,j)-(i,j+1) is -(hx/hz) w_x(i), where the weight is 1/2 for an edge lying on the
+// boundary and 1 otherwise.
+struct GridGeom {
+    int nx, nz;
+    double hx, hz;
+};
+
+__host__ __device__ __forceinline__ double edge_w(int idx, int n) { return (idx == 0 || idx == n - 1) ? 0.5 : 1.0; }
+
+// coupling between line i-1 and line i at row j (i >= 1)
+__host__ __device__ __forceinline__ double coup_x(const GridGeom &g, int j) { return -(g.hz / g.hx) * edge_w(j, g.nz); }
+// coupling between rows j and j+1 of line i (j <= nz-2)
+__host__ __device__ __forceinline__ double coup_z(const GridGeom &g, int i) { return -(g.hx / g.hz) * edge_w(i, g.nx); }
+
+// ------------------------------------------------------------ cluster primitives
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r; asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r)); return r;
+}
+__device__ __forceinline__ unsigned cluster_id_x() {
+    unsigned r; asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r)); return r;
+}
+// Hardware cluster barrier with release/acquire ordering at cluster scope: global
+// stores made by any thread of the cluster before the barrier are visible to loads
+// of every thread of the cluster after it.  All threads of all CTAs must reach it.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// device status bits (OR-ed together)
+enum : int { ST_SINGULAR = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+}  // namespace helm

@@ -1,0 +1,272 @@
+// Line Schur factorisation of the block-tridiagonal Helmholtz matrix.
+//
+// With lines of constant i (n_z nodes each, z fastest), A(m, w) of the Appendix
+// ("Numerical forward model") is block tridiagonal: D_i tridiagonal (the five-point
+// stiffness along z plus the diagonal mass and boundary terms) and C_i = diag(c) the
+// couplings between lines i-1 and i.  Block LU without block pivoting gives
+//     S_0 = D_0,   S_i = D_i - C_i S_{i-1}^{-1} C_i,
+// and the factor stores G_i = S_i^{-1} for every line (used by the sweeps as dense
+// GEMM operands).  Because C_i is diagonal the Schur update is elementwise:
+// (C G C)_{ab} = c_a G_ab c_b.
+//
+// One thread-block cluster factors one system (one (model, frequency) pair); the
+// recurrence over lines is sequential, so parallelism inside a system comes from
+// splitting each line's n_z x n_z inversion over the CTAs of the cluster by column
+// blocks.  The inversion is an in-place block Gauss-Jordan sweep with 16 x 16 blocks:
+//   for k:  P = inv(W_kk)                       (partial pivoting inside the block)
+//           W_kJ <- P W_kJ,  W_IJ <- W_IJ - W_Ik W_kJ,  W_Ik <- -W_Ik P,  W_kk <- P.
+// The owner of column block k inverts W_kk and publishes P and the old column panel
+// W_:k through a double-buffered exchange slot in global memory (L2 resident); one
+// hardware cluster barrier per block step orders publish and use.  Each CTA only ever
+// touches its own columns of W, which lives in the factor storage itself (G_i slot).
+#include "kernels.h"
+
+namespace helm {
+
+constexpr int FAC_THREADS = 256;
+
+__host__ __device__ size_t factor_xch_elems(int nz) { return 2 * ((size_t)nz * NB + NB * NB); }
+
+template <typename T> __device__ __forceinline__ cx_t<T> from_c128(double2 a);
+template <> __device__ __forceinline__ double2 from_c128<double>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_c128<float>(double2 a) { return to_c64(a); }
+
+template <typename T> struct FactorArgs {
+    GridGeom g;
+    const double2 *diag;  // [n_sys][N]
+    cx_t<T> *G;           // [n_sys][nx][nz][nz]
+    cx_t<T> *xch;         // [n_sys][factor_xch_elems(nz)]
+    int *status;
+    int cs;
+};
+
+// In-place Gauss-Jordan inversion of the kb x kb block M (row stride NB, shared memory)
+// with partial pivoting; the inverse is written to out (row stride NB).  aug is a
+// kb x 2kb scratch (row stride 2*NB), fcol a length-NB scratch.
+template <typename T>
+__device__ void invert_block(const cx_t<T> *M, int kb, cx_t<T> *out, cx_t<T> *aug, cx_t<T> *fcol,
+                             int *s_piv, int *s_ok, int &bad) {
+    using V = cx_t<T>;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w2 = 2 * kb;
+    for (int e = tid; e < kb * w2; e += nt) {
+        int r = e / w2, c = e % w2;
+        aug[r * 2 * NB + c] = (c < kb) ? M[r * NB + c] : mkc<T>((c - kb) == r ? T(1) : T(0), T(0));
+    }
+    __syncthreads();
+    for (int q = 0; q < kb; ++q) {
+        if (tid < 32) {
+            T best = T(-1);
+            int bi = q;
+            for (int r = q + tid; r < kb; r += 32) {
+                V a = aug[r * 2 * NB + q];
+                T v = a.x * a.x + a.y * a.y;
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                T ob = __shfl_down_sync(0xffffffffu, best, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                *s_piv = bi;
+                *s_ok = (best > T(0) && isfinite(best)) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        const int piv = *s_piv;
+        const int ok = *s_ok;
+        if (!ok) bad = 1;
+        if (ok && piv != q && tid < w2) {
+            V t = aug[q * 2 * NB + tid];
+            aug[q * 2 * NB + tid] = aug[piv * 2 * NB + tid];
+            aug[piv * 2 * NB + tid] = t;
+        }
+        __syncthreads();
+        V pv = aug[q * 2 * NB + q];
+        if (tid < kb) fcol[tid] = aug[tid * 2 * NB + q];
+        __syncthreads();
+        if (ok && tid < w2) {
+            T den = pv.x * pv.x + pv.y * pv.y;
+            V inv = mkc<T>(pv.x / den, -pv.y / den);
+            aug[q * 2 * NB + tid] = cmul(aug[q * 2 * NB + tid], inv);
+        }
+        __syncthreads();
+        if (ok) {
+            for (int e = tid; e < kb * w2; e += nt) {
+                int r = e / w2, c = e % w2;
+                if (r != q) cfms(aug[r * 2 * NB + c], fcol[r], aug[q * 2 * NB + c]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kb * kb; e += nt) {
+        int r = e / kb, c = e % kb;
+        out[r * NB + c] = aug[r * 2 * NB + kb + c];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FAC_THREADS) line_factor_kernel(FactorArgs<T> a) {
+    using V = cx_t<T>;
+    const GridGeom g = a.g;
+    const int nx = g.nx, nz = g.nz, cs = a.cs;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rank = (int)cluster_ctarank();
+    const int sys = (int)cluster_id_x();
+    const int p = (nz + NB - 1) / NB;
+    const int bpc = (p + cs - 1) / cs;
+    const int kb_lo = rank * bpc, kb_hi = min(p, kb_lo + bpc);
+    const int c0 = min(nz, kb_lo * NB), c1 = min(nz, kb_hi * NB);
+    const int ncol = max(0, c1 - c0);
+    const int RS = bpc * NB;  // row stride of sR
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sPanel = reinterpret_cast<V *>(smem_raw);     // nz x NB
+    V *sP = sPanel + (size_t)nz * NB;                // NB x NB
+    V *sR = sP + NB * NB;                            // NB x RS
+    V *sAug = sR + NB * RS;                          // NB x 2NB
+    V *sF = sAug + 2 * NB * NB;                      // NB
+    __shared__ int s_piv, s_ok;
+
+    V *Gs = a.G + (size_t)sys * nx * nz * nz;
+    const double2 *dg = a.diag + (size_t)sys * nx * nz;
+    V *xch = a.xch + (size_t)sys * factor_xch_elems(nz);
+    const size_t slot_elems = (size_t)nz * NB + NB * NB;
+    int bad = 0;
+    int step = 0;
+
+    for (int i = 0; i < nx; ++i) {
+        V *W = Gs + (size_t)i * nz * nz;
+        const V *Wp = Gs + (size_t)(i - 1) * nz * nz;
+        const T cz = (T)coup_z(g, i);
+        // S_i = D_i - C_i G_{i-1} C_i on this CTA's columns
+        for (int e = tid; e < nz * ncol; e += nt) {
+            const int r = e / ncol, c = c0 + e % ncol;
+            V v = mkc<T>(T(0), T(0));
+            if (r == c) v = from_c128<T>(dg[(size_t)i * nz + r]);
+            else if (r == c + 1 || c == r + 1) v = mkc<T>(cz, T(0));
+            if (i > 0) {
+                const T s = (T)(coup_x(g, r) * coup_x(g, c));
+                V gp = Wp[(size_t)r * nz + c];
+                v.x -= s * gp.x;
+                v.y -= s * gp.y;
+            }
+            W[(size_t)r * nz + c] = v;
+        }
+        __syncthreads();
+
+        for (int k = 0; k < p; ++k, ++step) {
+            const int k0 = k * NB, kb = min(NB, nz - k0);
+            const int owner = k / bpc;
+            V *slot = xch + (size_t)(step & 1) * slot_elems;
+            V *slotPanel = slot;
+            V *slotP = slot + (size_t)nz * NB;
+            if (rank == owner) {
+                for (int e = tid; e < nz * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    sPanel[r * NB + q] = W[(size_t)r * nz + k0 + q];
+                }
+                __syncthreads();
+                invert_block<T>(sPanel + (size_t)k0 * NB, kb, sP, sAug, sF, &s_piv, &s_ok, bad);
+                for (int e = tid; e < nz * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    slotPanel[r * NB + q] = sPanel[r * NB + q];
+                }
+                for (int e = tid; e < kb * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    slotP[r * NB + q] = sP[r * NB + q];
+                }
+                // own column block k: W_Ik <- -W_Ik P, W_kk <- P
+                for (int e = tid; e < nz * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    V v;
+                    if (r >= k0 && r < k0 + kb) {
+                        v = sP[(r - k0) * NB + q];
+                    } else {
+                        V acc = mkc<T>(T(0), T(0));
+                        for (int t = 0; t < kb; ++t) cfma(acc, sPanel[r * NB + t], sP[t * NB + q]);
+                        v = mkc<T>(-acc.x, -acc.y);
+                    }
+                    W[(size_t)r * nz + k0 + q] = v;
+                }
+            }
+            cluster_sync_all();
+            if (rank != owner) {
+                for (int e = tid; e < nz * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    sPanel[r * NB + q] = ldcg(slotPanel + r * NB + q);
+                }
+                for (int e = tid; e < kb * kb; e += nt) {
+                    const int r = e / kb, q = e % kb;
+                    sP[r * NB + q] = ldcg(slotP + r * NB + q);
+                }
+            }
+            __syncthreads();
+            // Rk = P W[k rows, own columns != k block]
+            for (int e = tid; e < kb * ncol; e += nt) {
+                const int q = e / ncol, cc = e % ncol, c = c0 + cc;
+                if (c >= k0 && c < k0 + kb) continue;
+                V acc = mkc<T>(T(0), T(0));
+                for (int t = 0; t < kb; ++t) cfma(acc, sP[q * NB + t], W[(size_t)(k0 + t) * nz + c]);
+                sR[q * RS + cc] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < nz * ncol; e += nt) {
+                const int r = e / ncol, cc = e % ncol, c = c0 + cc;
+                if (c >= k0 && c < k0 + kb) continue;
+                if (r >= k0 && r < k0 + kb) {
+                    W[(size_t)r * nz + c] = sR[(r - k0) * RS + cc];
+                } else {
+                    V acc = W[(size_t)r * nz + c];
+                    for (int t = 0; t < kb; ++t) cfms(acc, sPanel[r * NB + t], sR[t * RS + cc]);
+                    W[(size_t)r * nz + c] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (bad && tid == 0) atomicOr(a.status, ST_SINGULAR);
+}
+
+template <typename T> static size_t factor_smem_bytes(int nz, int cs) {
+    const int p = (nz + NB - 1) / NB;
+    const int bpc = (p + cs - 1) / cs;
+    return sizeof(cx_t<T>) * ((size_t)nz * NB + NB * NB + (size_t)NB * bpc * NB + 2 * NB * NB + NB);
+}
+
+int pick_cluster_size(int nz) {
+    const int p = (nz + NB - 1) / NB;
+    return p >= 8 ? 8 : (p >= 4 ? 4 : (p >= 2 ? 2 : 1));
+}
+
+template <typename T>
+cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag, cx_t<T> *G, cx_t<T> *xch,
+                               int *status, int cs, cudaStream_t st) {
+    FactorArgs<T> a{g, diag, G, xch, status, cs};
+    const size_t smem = factor_smem_bytes<T>(g.nz, cs);
+    cudaError_t e = cudaFuncSetAttribute(line_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_sys * cs, 1, 1);
+    cfg.blockDim = dim3(FAC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, line_factor_kernel<T>, a);
+}
+
+template cudaError_t launch_line_factor<double>(const GridGeom &, int, const double2 *, double2 *, double2 *,
+                                                int *, int, cudaStream_t);
+template cudaError_t launch_line_factor<float>(const GridGeom &, int, const double2 *, float2 *, float2 *,
+                                               int *, int, cudaStream_t);
+
+}  // namespace helm

@@ -1,0 +1,285 @@
+"""Thin Python binding of libhelm (include/helm.h) over ctypes.
+
+Argument marshalling only: tensors are checked (device, dtype, contiguity, shape) and
+their device pointers passed to the C entry points, which run every step of the path
+in CUDA kernels.  There is no CPU fallback: if libhelm.so is missing or no GPU is
+visible, every call raises.
+
+Function names follow the C ABI: helm_assemble, helm_factor, helm_solve,
+helm_adjoint_solve, helm_sources, helm_restrict, fwi_misfit_grad, bilevel_hypergrad.
+Right-hand-side blocks are complex128 tensors of shape [n_omega, nrhs, N] with
+N = nx * nz and node index k = i * nz + j (z fastest).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelm.so")
+
+HELM_FP64, HELM_MIXED = 0, 1
+_STATUS = {0: "HELM_OK", 1: "HELM_EINVAL", 2: "HELM_ENOMEM", 3: "HELM_ECUDA", 4: "HELM_ENOCONV",
+           5: "HELM_ESINGULAR", 6: "HELM_ETIMEOUT"}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)} {detail}".strip())
+
+
+class helm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("lx", C.c_double), ("lz", C.c_double)]
+
+
+class helm_acq(C.Structure):
+    _fields_ = [("n_src", C.c_int32), ("n_rec", C.c_int32), ("src_xz", C.POINTER(C.c_double)),
+                ("src_amp", C.POINTER(C.c_double)), ("rec_xz", C.POINTER(C.c_double)),
+                ("rec_w", C.POINTER(C.c_double))]
+
+
+class helm_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("max_relres", C.c_double)]
+
+
+class helm_pcg_opts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("rtol", C.c_double), ("x0", C.c_double),
+                ("refine_rtol", C.c_double)]
+
+
+class helm_hyper_info(C.Structure):
+    _fields_ = [("cg_matvecs", C.c_int32), ("cg_relres", C.c_double), ("solves", C.c_int64),
+                ("data_solves", C.c_int64), ("max_refine_iters", C.c_int32)]
+
+
+EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
+            "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_sources", "helm_restrict",
+            "fwi_misfit_grad", "bilevel_hypergrad"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhelm.so (raises if it is missing; there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhelm.so not found at {path}; build it with __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, dbl = C.c_void_p, C.c_int32, C.c_double
+    P = C.POINTER
+    lib.helm_status_string.restype = C.c_char_p
+    lib.helm_status_string.argtypes = [C.c_int]
+    lib.helm_last_error.restype = C.c_char_p
+    lib.helm_last_error.argtypes = []
+    lib.helm_assemble.restype = C.c_int
+    lib.helm_assemble.argtypes = [P(helm_grid), vp, P(dbl), i32, vp, P(vp)]
+    lib.helm_op_destroy.restype = None
+    lib.helm_op_destroy.argtypes = [vp]
+    lib.helm_factor.restype = C.c_int
+    lib.helm_factor.argtypes = [vp, C.c_int, P(vp)]
+    lib.helm_factor_destroy.restype = None
+    lib.helm_factor_destroy.argtypes = [vp]
+    for name in ("helm_solve", "helm_adjoint_solve"):
+        fn = getattr(lib, name)
+        fn.restype = C.c_int
+        fn.argtypes = [vp, i32, vp, vp, dbl, i32, P(helm_solve_info)]
+    lib.helm_sources.restype = C.c_int
+    lib.helm_sources.argtypes = [vp, P(helm_acq), vp]
+    lib.helm_restrict.restype = C.c_int
+    lib.helm_restrict.argtypes = [vp, P(helm_acq), i32, vp, vp]
+    lib.fwi_misfit_grad.restype = C.c_int
+    lib.fwi_misfit_grad.argtypes = [vp, P(helm_acq), vp, dbl, dbl, dbl, P(dbl), vp, vp, vp]
+    lib.bilevel_hypergrad.restype = C.c_int
+    lib.bilevel_hypergrad.argtypes = [i32, P(helm_grid), P(vp), P(vp), P(helm_acq), P(dbl), i32, dbl, dbl,
+                                      dbl, C.c_int, P(helm_pcg_opts), vp, P(dbl), P(dbl), P(dbl), P(dbl),
+                                      P(helm_hyper_info)]
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != 0:
+        detail = _lib.helm_last_error().decode(errors="replace") if _lib is not None else ""
+        raise HelmError(status, where, detail)
+
+
+def _dev(t: torch.Tensor, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dbuf(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Acq:
+    """Host-side acquisition marshalled into a helm_acq struct (keeps the arrays alive)."""
+
+    def __init__(self, src_xz, rec_xz, src_amp=None, rec_w=None):
+        self._src, p_src = _dbuf(np.asarray(src_xz, dtype=np.float64).reshape(-1, 2))
+        self._rec, p_rec = _dbuf(np.asarray(rec_xz, dtype=np.float64).reshape(-1, 2))
+        self._amp = self._w = None
+        p_amp = p_w = C.POINTER(C.c_double)()
+        if src_amp is not None:
+            self._amp, p_amp = _dbuf(src_amp)
+        if rec_w is not None:
+            self._w, p_w = _dbuf(rec_w)
+        self.n_src, self.n_rec = self._src.shape[0], self._rec.shape[0]
+        self.struct = helm_acq(self.n_src, self.n_rec, p_src, p_amp, p_rec, p_w)
+
+    @classmethod
+    def from_workload(cls, acq):
+        return cls(acq.src_xz, acq.rec_xz, acq.src_amp, acq.rec_w)
+
+
+class Op:
+    def __init__(self, handle, nx, nz, lx, lz, omegas, stream):
+        self.handle, self.nx, self.nz, self.lx, self.lz = handle, nx, nz, lx, lz
+        self.omegas = np.asarray(omegas, dtype=np.float64)
+        self.n_omega = len(self.omegas)
+        self.N = nx * nz
+        self.stream = stream
+
+    def close(self):
+        if self.handle:
+            load().helm_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    def __init__(self, handle, op, prec):
+        self.handle, self.op, self.prec = handle, op, prec
+
+    def close(self):
+        if self.handle:
+            load().helm_factor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def helm_assemble(nx, nz, lx, lz, m: torch.Tensor, omegas, stream=None) -> Op:
+    lib = load()
+    pm = _dev(m, torch.float64, "m", (nx * nz,))
+    om, p_om = _dbuf(np.atleast_1d(omegas))
+    h = C.c_void_p()
+    g = helm_grid(nx, nz, lx, lz)
+    _check(lib.helm_assemble(C.byref(g), pm, p_om, len(om), _stream_ptr(stream), C.byref(h)), "helm_assemble")
+    return Op(h, nx, nz, lx, lz, om, stream)
+
+
+def helm_factor(op: Op, prec=HELM_FP64) -> Factor:
+    lib = load()
+    h = C.c_void_p()
+    _check(lib.helm_factor(op.handle, int(prec), C.byref(h)), "helm_factor")
+    return Factor(h, op, prec)
+
+
+def _solve(name, f: Factor, B, X, rtol, max_iter):
+    lib = load()
+    op = f.op
+    if B.dim() != 3 or B.shape[0] != op.n_omega or B.shape[2] != op.N:
+        raise ValueError(f"B must be [n_omega={op.n_omega}, nrhs, N={op.N}]")
+    nrhs = B.shape[1]
+    pb = _dev(B, torch.complex128, "B")
+    if X is None:
+        X = torch.empty_like(B)
+    px = _dev(X, torch.complex128, "X", B.shape)
+    info = helm_solve_info()
+    _check(getattr(lib, name)(f.handle, nrhs, pb, px, float(rtol), int(max_iter), C.byref(info)), name)
+    return X, {"iters": info.iters, "max_relres": info.max_relres}
+
+
+def helm_solve(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, rtol=1e-10, max_iter=8):
+    return _solve("helm_solve", f, B, X, rtol, max_iter)
+
+
+def helm_adjoint_solve(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, rtol=1e-10, max_iter=8):
+    return _solve("helm_adjoint_solve", f, B, X, rtol, max_iter)
+
+
+def helm_sources(op: Op, acq: Acq) -> torch.Tensor:
+    lib = load()
+    B = torch.empty((op.n_omega, acq.n_src, op.N), dtype=torch.complex128, device="cuda")
+    _check(lib.helm_sources(op.handle, C.byref(acq.struct), _dev(B, torch.complex128, "B")), "helm_sources")
+    return B
+
+
+def helm_restrict(op: Op, acq: Acq, X: torch.Tensor) -> torch.Tensor:
+    lib = load()
+    ncol = X.shape[1]
+    px = _dev(X, torch.complex128, "X", (op.n_omega, ncol, op.N))
+    Y = torch.empty((op.n_omega, ncol, acq.n_rec), dtype=torch.complex128, device="cuda")
+    _check(lib.helm_restrict(op.handle, C.byref(acq.struct), ncol, px, _dev(Y, torch.complex128, "Y")),
+           "helm_restrict")
+    return Y
+
+
+def fwi_misfit_grad(f: Factor, acq: Acq, data: torch.Tensor, alpha, mu, rtol=1e-10, want_fields=False):
+    lib = load()
+    op = f.op
+    pd = _dev(data, torch.complex128, "data", (op.n_omega, acq.n_src, acq.n_rec))
+    grad = torch.empty(op.N, dtype=torch.float64, device="cuda")
+    U = Lam = None
+    pu = pl = C.c_void_p()
+    if want_fields:
+        U = torch.empty((op.n_omega, acq.n_src, op.N), dtype=torch.complex128, device="cuda")
+        Lam = torch.empty_like(U)
+        pu, pl = C.c_void_p(U.data_ptr()), C.c_void_p(Lam.data_ptr())
+    phi = C.c_double()
+    _check(lib.fwi_misfit_grad(f.handle, C.byref(acq.struct), pd, float(alpha), float(mu), float(rtol),
+                               C.byref(phi), C.c_void_p(grad.data_ptr()), pu, pl), "fwi_misfit_grad")
+    return phi.value, grad, U, Lam
+
+
+def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
+                      cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
+                      stream=None):
+    """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors."""
+    lib = load()
+    n = len(grids)
+    G = (helm_grid * n)(*[helm_grid(*g) for g in grids])
+    pf = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_fwi", (g[0] * g[1],)).value for t, g in zip(m_fwi, grids)])
+    pt = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_true", (g[0] * g[1],)).value for t, g in zip(m_true, grids)])
+    om, p_om = _dbuf(np.atleast_1d(omegas))
+    opts = helm_pcg_opts(int(cg_max_iter), int(cg_fixed_iters), float(cg_rtol), float(x0), float(refine_rtol))
+    psi, dalpha = C.c_double(), C.c_double()
+    dp = np.zeros((acq.n_rec, 2))
+    dw = np.zeros(acq.n_rec)
+    info = helm_hyper_info()
+    _check(lib.bilevel_hypergrad(n, G, pf, pt, C.byref(acq.struct), p_om, len(om), float(alpha), float(alpha0),
+                                 float(mu), int(prec), C.byref(opts), _stream_ptr(stream), C.byref(psi),
+                                 C.byref(dalpha), dp.ctypes.data_as(C.POINTER(C.c_double)),
+                                 dw.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bilevel_hypergrad")
+    return {"psi": psi.value, "dpsi_dalpha": dalpha.value, "dpsi_dp": dp, "dpsi_dw": dw,
+            "cg_matvecs": info.cg_matvecs, "cg_relres": info.cg_relres, "solves": info.solves,
+            "data_solves": info.data_solves, "max_refine_iters": info.max_refine_iters}
