@@ -160,6 +160,21 @@ helm_status fwi_misfit_grad(helm_factor_t *f, const helm_acq *acq, const helm_c1
                             double alpha, double mu, double rtol, double *phi, double *grad_dev,
                             helm_c128 *u_out, helm_c128 *lam_out);
 
+/* fwi_hessian_vec -- Hessian-vector product of phi for a real direction m~ (Lemmas
+ * thm:H1 and thm:H2, Discussion disc:Hess): per (s, w) two new solves
+ *   v = A^{-1}(g u m~),  z = (A^H)^{-1}(R^T W^2 R v - m~ conj(g) lambda),
+ *   (H m~)_k = sum_{s,w} Re[g_k u_k conj(z_k)] - Re[g_k v_k conj(lambda_k)]
+ *              - Re[g'_k u_k conj(lambda_k)] m~_k + (Gamma m~)_k,   g'_k = -i w b_k / (4 m_k^{3/2}).
+ * (The second term uses G^* lambda = conj(g) lambda, as in the proof of Lemma thm:H2.)
+ *   u_dev, lam_dev: [n_omega][n_src][N] wavefields and adjoint fields at the factor's
+ *   model, e.g. the u_out / lam_out of fwi_misfit_grad (lam_dev may be NULL when
+ *   gauss_newton != 0).  mt_dev, hv_dev: [N] FP64 (device).
+ *   gauss_newton != 0: the Gauss-Newton part H1 m~ + Gamma m~ only (z without the
+ *   lambda term, no H2 terms). */
+helm_status fwi_hessian_vec(helm_factor_t *f, const helm_acq *acq, const helm_c128 *u_dev,
+                            const helm_c128 *lam_dev, const double *mt_dev, double alpha, double mu,
+                            double rtol, int32_t gauss_newton, double *hv_dev);
+
 /* bilevel_hypergrad -- upper-level objective and hypergradient (Algorithm alg:box,
  * Theorems sogradt1 and sogradta), averaged over n_models training models:
  *   per model: data u' = A(m')^{-1} e_s on the same grid; u, lambda at m_fwi;

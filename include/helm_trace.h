@@ -1,0 +1,41 @@
+/*
+ * helm_trace.h -- kernel tracing of libhelm (no counterpart in the paper; it measures
+ * the library itself).
+ *
+ * Every kernel launch of the library is counted.  When tracing is enabled, each launch
+ * is also bracketed by two CUDA events recorded on the launch's own stream, so that
+ * helm_trace_read can report the device time of every kernel by name.  Tracing adds
+ * two event records per launch; counting alone costs nothing measurable.
+ */
+#ifndef HELM_TRACE_H
+#define HELM_TRACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    char name[48];        /* kernel name */
+    int64_t launches;     /* launches since the last reset */
+    double total_ms;      /* summed device time of the traced launches (0 if tracing was off) */
+    int64_t timed;        /* launches that were timed */
+} helm_trace_entry;
+
+/* Enable (on != 0) or disable per-launch event timing.  Host only; not thread safe
+ * with concurrent library calls. */
+void helm_trace_enable(int on);
+/* Forget all counts and timings. */
+void helm_trace_reset(void);
+/* Synchronise the device, fold the recorded events into per-kernel totals and copy up
+ * to max entries (kernels with at least one launch) into out.  Returns the number of
+ * entries written, or -1 on a CUDA error. */
+int32_t helm_trace_read(helm_trace_entry *out, int32_t max);
+/* Total kernel launches since the last reset. */
+int64_t helm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_TRACE_H */

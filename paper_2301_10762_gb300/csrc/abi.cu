@@ -229,7 +229,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     helm_status s;
     if (info) { info->iters = 0; info->max_relres = -1.0; }
     if (f->prec == HELM_FP64) {
-        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, cs, rchunk, op->st);
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status, op->st);
         if (e != cudaSuccess) { helm_set_error("sweep fp64", e); return HELM_ECUDA; }
         if (info) {
             info->iters = 1;
@@ -244,7 +244,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     // mixed: x = A~^{-1} b, then x += A~^{-1}(b - A x) until ||b - A x|| / ||b|| <= rtol
     if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
     if (max_iter < 1) max_iter = 1;
-    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, cs, rchunk, op->st);
+    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, rchunk, op->status, op->st);
     if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
     int it = 1;
     double rel = INFINITY;
@@ -254,13 +254,18 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
         if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
         if ((s = read_relres(f, nrhs, &rel)) != HELM_OK) return s;
         if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
-        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, f->r, X, f->y, conj, 1, cs, rchunk,
-                                     op->st);
+        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, f->r, X, f->y, conj, 1, rchunk,
+                                     op->status, op->st);
         if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
         ++it;
     }
     if (info) { info->iters = it; info->max_relres = rel; }
     (void)N;
+    int st_host = 0;
+    e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) { helm_set_error("solve status", e); return HELM_ECUDA; }
+    if (st_host & ST_TIMEOUT) { helm_set_msg("a sweep kernel gave up waiting for its cluster"); return HELM_ETIMEOUT; }
     if (!(rel <= rtol)) { helm_set_msg("refinement did not reach rtol"); return HELM_ENOCONV; }
     return HELM_OK;
 }

@@ -1,6 +1,7 @@
 // Operator assembly, point-source right-hand sides and the sliding bicubic restriction.
 #include <math.h>
 #include "kernels.h"
+#include "trace.h"
 
 namespace helm {
 
@@ -33,7 +34,7 @@ __global__ void assemble_kernel(GridGeom g, const double *m, const double *omega
 cudaError_t launch_assemble(const GridGeom &g, const double *m, const double *omega_dev, int n_omega,
                             double2 *diag, cudaStream_t st) {
     const int N = g.nx * g.nz;
-    assemble_kernel<<<(N + 255) / 256, 256, 0, st>>>(g, m, omega_dev, n_omega, diag);
+    HELM_TRACED(K_ASSEMBLE, st, (assemble_kernel<<<(N + 255) / 256, 256, 0, st>>>(g, m, omega_dev, n_omega, diag)));
     return cudaGetLastError();
 }
 
@@ -67,7 +68,7 @@ cudaError_t launch_sources(const GridGeom &g, int n_omega, int n_src, const doub
     const int N = g.nx * g.nz;
     cudaError_t e = cudaMemsetAsync(B, 0, sizeof(double2) * (size_t)n_omega * n_src * N, st);
     if (e != cudaSuccess) return e;
-    sources_kernel<<<(n_src + 127) / 128, 128, 0, st>>>(g, n_omega, n_src, src_xz_dev, src_amp_dev, B);
+    HELM_TRACED(K_SOURCES, st, (sources_kernel<<<(n_src + 127) / 128, 128, 0, st>>>(g, n_omega, n_src, src_xz_dev, src_amp_dev, B)));
     return cudaGetLastError();
 }
 
@@ -111,7 +112,7 @@ __global__ void taps_kernel(GridGeom g, int n_rec, const double *rec_xz, int *id
 
 cudaError_t launch_restriction_taps(const GridGeom &g, int n_rec, const double *rec_xz_dev, int *tap_idx,
                                     double *tap_w, double *tap_wx, double *tap_wz, cudaStream_t st) {
-    taps_kernel<<<(n_rec + 63) / 64, 64, 0, st>>>(g, n_rec, rec_xz_dev, tap_idx, tap_w, tap_wx, tap_wz);
+    HELM_TRACED(K_TAPS, st, (taps_kernel<<<(n_rec + 63) / 64, 64, 0, st>>>(g, n_rec, rec_xz_dev, tap_idx, tap_w, tap_wx, tap_wz)));
     return cudaGetLastError();
 }
 
@@ -142,7 +143,7 @@ cudaError_t launch_restrict(const GridGeom &g, int n_cols, int n_rec, const int 
     const long warps = (long)n_cols * n_rec;
     const int blocks = (int)((warps * 32 + 255) / 256);
     if (blocks == 0) return cudaSuccess;
-    restrict_kernel<<<blocks, 256, 0, st>>>(N, n_cols, n_rec, tap_idx, tap_w, X, Y);
+    HELM_TRACED(K_RESTRICT, st, (restrict_kernel<<<blocks, 256, 0, st>>>(N, n_cols, n_rec, tap_idx, tap_w, X, Y)));
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 // hardware cluster barrier per block step orders publish and use.  Each CTA only ever
 // touches its own columns of W, which lives in the factor storage itself (G_i slot).
 #include "kernels.h"
+#include "trace.h"
 
 namespace helm {
 
@@ -136,11 +137,14 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_kernel(FactorArgs<T> 
     const size_t slot_elems = (size_t)nz * NB + NB * NB;
     int bad = 0;
     int step = 0;
+    // grid couplings, converted once (no FP64 work in the per-element loops)
+    const T cx_in = (T)coup_x(g, 1), cx_edge = (T)coup_x(g, 0);
+    const T cz_in = (T)coup_z(g, 1), cz_edge = (T)coup_z(g, 0);
 
     for (int i = 0; i < nx; ++i) {
         V *W = Gs + (size_t)i * nz * nz;
         const V *Wp = Gs + (size_t)(i - 1) * nz * nz;
-        const T cz = (T)coup_z(g, i);
+        const T cz = (i == 0 || i == nx - 1) ? cz_edge : cz_in;
         // S_i = D_i - C_i G_{i-1} C_i on this CTA's columns
         for (int e = tid; e < nz * ncol; e += nt) {
             const int r = e / ncol, c = c0 + e % ncol;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_kernel(FactorArgs<T> 
             if (r == c) v = from_c128<T>(dg[(size_t)i * nz + r]);
             else if (r == c + 1 || c == r + 1) v = mkc<T>(cz, T(0));
             if (i > 0) {
-                const T s = (T)(coup_x(g, r) * coup_x(g, c));
+                const T s = ((r == 0 || r == nz - 1) ? cx_edge : cx_in) * ((c == 0 || c == nz - 1) ? cx_edge : cx_in);
                 V gp = Wp[(size_t)r * nz + c];
                 v.x -= s * gp.x;
                 v.y -= s * gp.y;
@@ -261,7 +265,9 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, line_factor_kernel<T>, a);
+    cudaError_t le = cudaSuccess;
+    HELM_TRACED(sizeof(T) == 8 ? K_FACTOR64 : K_FACTOR32, st, (le = cudaLaunchKernelEx(&cfg, line_factor_kernel<T>, a)));
+    return le;
 }
 
 template cudaError_t launch_line_factor<double>(const GridGeom &, int, const double2 *, double2 *, double2 *,

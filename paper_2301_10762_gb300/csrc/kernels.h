@@ -27,7 +27,7 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
 // ---- sweep.cu
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int cs, int rchunk,
+                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
                               cudaStream_t st);
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
                             const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st);

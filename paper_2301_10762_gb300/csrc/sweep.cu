@@ -16,156 +16,283 @@
 // the input is an FP64 residual and the result is added to the FP64 iterate in the
 // final pass (x += A~^{-1} r).  TG = double is the plain FP64 path (Y aliases X).
 #include "kernels.h"
+#include "trace.h"
 
 namespace helm {
 
 constexpr int SW_THREADS = 256;
-constexpr int SW_KC = 32;      // K chunk (columns of G_i / rows of t) staged in shared memory
-constexpr int SW_MAXOPT = 4;   // outputs per thread (rows_per_cta * R <= 4 * 256)
+constexpr int SW_KC = 64;      // K chunk of the streamed (non-prefetched) G path
+constexpr int SW_MAXOPT = 2;   // outputs per thread (rows_per_cta * R <= 2 * 256)
+constexpr size_t SW_SMEM_MAX = 200 * 1024;
+constexpr uint32_t SW_WAIT_TRIES = 1u << 22;   // bounded mbarrier wait (seconds at worst)
 
 template <typename TG> struct SweepArgs {
     GridGeom g;
-    int nrhs, R, cs, n_chunks;
+    int nrhs, R, cs, n_chunks, prefetch;
     const cx_t<TG> *G;   // [n_sys][nx][nz][nz]
     const double2 *B;    // [n_sys][nrhs][N]
     double2 *X;          // [n_sys][nrhs][N]
-    cx_t<TG> *Y;         // working vector, [n_sys][nrhs][N] (== X for TG = double)
+    cx_t<TG> *Y;         // forward vectors y_i, [n_sys][nrhs][N] (== X for TG = double)
     int conj, accumulate;
+    int *status;
 };
 
 template <typename TG> __device__ __forceinline__ cx_t<TG> in_cast(double2 a);
 template <> __device__ __forceinline__ double2 in_cast<double>(double2 a) { return a; }
 template <> __device__ __forceinline__ float2 in_cast<float>(double2 a) { return to_c64(a); }
 
+// padded row stride (in complex elements) of the shared-memory operands: keeps 16-byte
+// alignment of every row and spreads consecutive rows over the banks
+template <typename TG> __host__ __device__ __forceinline__ int padded(int n) {
+    return sizeof(TG) == 4 ? ((n + 1) & ~1) + 2 : n + 1;
+}
+
+// sum_b g[b] t[b] over n complex entries (both 16-byte aligned), four independent chains
+__device__ __forceinline__ float2 dot_row(const float2 *g, const float2 *t, int n) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    int b = 0;
+    for (; b + 4 <= n; b += 4) {
+        const float4 gA = *reinterpret_cast<const float4 *>(g + b);
+        const float4 gB = *reinterpret_cast<const float4 *>(g + b + 2);
+        const float4 tA = *reinterpret_cast<const float4 *>(t + b);
+        const float4 tB = *reinterpret_cast<const float4 *>(t + b + 2);
+        cfma(a0, make_float2(gA.x, gA.y), make_float2(tA.x, tA.y));
+        cfma(a1, make_float2(gA.z, gA.w), make_float2(tA.z, tA.w));
+        cfma(a2, make_float2(gB.x, gB.y), make_float2(tB.x, tB.y));
+        cfma(a3, make_float2(gB.z, gB.w), make_float2(tB.z, tB.w));
+    }
+    for (; b < n; ++b) cfma(a0, g[b], t[b]);
+    return make_float2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+}
+__device__ __forceinline__ double2 dot_row(const double2 *g, const double2 *t, int n) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
+    int b = 0;
+    for (; b + 4 <= n; b += 4) {
+        cfma(a0, g[b], t[b]);
+        cfma(a1, g[b + 1], t[b + 1]);
+        cfma(a2, g[b + 2], t[b + 2]);
+        cfma(a3, g[b + 3], t[b + 3]);
+    }
+    for (; b < n; ++b) cfma(a0, g[b], t[b]);
+    return make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+}
+
+// line handled by global step s: forward s = 0..nx-1 -> line s; backward s = nx..2nx-2 -> line 2nx-2-s
+__device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 * nx - 2 - s; }
+
+// Persistent sweep: 2nx-1 dependent line steps.  Per step the critical path is: wait
+// (mbarrier, bounded) until every CTA of the cluster has pushed its rows of the previous
+// line vector into this CTA's shared memory (st.async with transaction-count
+// completion), t = b_i - C y_{i-1} (or C x_{i+1}) from shared memory, the
+// (rows x n_z) x (n_z x R) product with the G_i slab that cp.async brought in during the
+// previous step, and the push of the new rows to all CTAs.  Two exchange buffers
+// alternate; no CTA can overwrite a buffer before every CTA has consumed it, because
+// producing the data of step s+2 needs the data of step s+1 from every CTA, which each
+// CTA sends only after it has finished step s.
 template <typename TG>
 __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a) {
     using V = cx_t<TG>;
     const GridGeom g = a.g;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int tid = threadIdx.x;
+    const int cs = a.cs, R = a.R;
     const int rank = (int)cluster_ctarank();
     const int cid = (int)cluster_id_x();
     const int sys = cid / a.n_chunks, chunk = cid % a.n_chunks;
-    const int q0 = chunk * a.R;
-    const int Rc = min(a.R, a.nrhs - q0);
-    const int rpc = (nz + a.cs - 1) / a.cs;
+    const int q0 = chunk * R;
+    const int Rc = min(R, a.nrhs - q0);
+    const int rpc = (nz + cs - 1) / cs;
     const int r0 = min(nz, rank * rpc), r1 = min(nz, r0 + rpc);
     const int nrows = r1 - r0;
     const int nout = nrows * Rc;
+    const bool pf = a.prefetch != 0;
+    const int nzp = padded<TG>(nz);
+    const int kcp = padded<TG>(SW_KC);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *sG = reinterpret_cast<V *>(smem_raw);        // rpc x SW_KC
-    V *sT = sG + (size_t)rpc * SW_KC;               // SW_KC x R
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);           // [2]
+    V *sY = reinterpret_cast<V *>(smem_raw + 16);                       // [2][R][nzp]
+    V *sT = sY + 2 * (size_t)R * nzp;                                   // [R][nzp]
+    const size_t boff = (16 + sizeof(V) * 3 * (size_t)R * nzp + 15) & ~(size_t)15;
+    double2 *sB = reinterpret_cast<double2 *>(smem_raw + boff);         // [2][R][nz]
+    V *sG = reinterpret_cast<V *>(sB + 2 * (size_t)R * nz);             // pf: [2][rpc][nzp]; else [rpc][kcp]
+    __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
     const double2 *Bs = a.B + ((size_t)sys * a.nrhs + q0) * N;
     double2 *Xs = a.X + ((size_t)sys * a.nrhs + q0) * N;
     V *Ys = a.Y + ((size_t)sys * a.nrhs + q0) * N;
+    const int last = 2 * nx - 2;
+    const uint32_t phase_bytes = (uint32_t)(nz * Rc * sizeof(V));
+    // couplings between neighbouring lines (grid constants; an edge on the top/bottom
+    // boundary has half weight), converted once so the per-step loops do no FP64 work
+    const TG c_in = (TG)coup_x(g, 1), c_edge = (TG)coup_x(g, 0);
+    const int lane = tid & 31, wid = tid >> 5;   // division-free 2D loops: warp -> q, lane -> j
 
-    for (int pass = 0; pass < 2; ++pass) {
-        const int i_lo = (pass == 0) ? 0 : nx - 2;
-        const int i_hi = (pass == 0) ? nx : -1;
-        const int di = (pass == 0) ? 1 : -1;
-        for (int i = i_lo; i != i_hi; i += di) {
-            const V *Gi = Gs + (size_t)i * nz * nz;
-            V acc[SW_MAXOPT];
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init_cluster();
+        s_abort = 0;
+    }
+    __syncthreads();
+    cluster_sync_all();   // every mbarrier of the cluster is initialised before any push
+    if (tid == 0) {
+        if (last >= 1) mbar_arrive_expect_tx(&bars[1], phase_bytes);   // data of step 1
+        if (last >= 2) mbar_arrive_expect_tx(&bars[0], phase_bytes);   // data of step 2
+    }
+
+    auto prefetch = [&](int s) {
+        if (s > last) return;
+        const int i = step_line(s, nx);
+        const int buf = s & 1;
+        if (pf) {
+            const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
+            V *dst = sG + (size_t)buf * rpc * nzp;
+            if (sizeof(TG) == 4 && (nz & 1) == 0) {
+                for (int r = wid; r < nrows; r += SW_THREADS / 32)
+                    for (int b = 2 * lane; b < nz; b += 64)
+                        cp_async16(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
+            } else {
+                for (int r = wid; r < nrows; r += SW_THREADS / 32)
+                    for (int b = lane; b < nz; b += 32)
+                        cp_async_elem(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
+            }
+        }
+        if (s < nx) {
+            double2 *dst = sB + (size_t)buf * R * nz;
+            for (int q = wid; q < Rc; q += SW_THREADS / 32)
+                for (int j = lane; j < nz; j += 32)
+                    cp_async_elem(dst + (size_t)q * nz + j, Bs + (size_t)q * N + (size_t)i * nz + j);
+        }
+    };
+
+    prefetch(0);
+    cp_async_commit();
+    for (int s = 0; s <= last; ++s) {
+        const int i = step_line(s, nx);
+        const bool fwd = s < nx;
+        const int buf = s & 1;
+        if (s > 0 && tid == 0) {
+            if (!mbar_wait_bounded(&bars[buf], (uint32_t)(((s - 1) >> 1) & 1), SW_WAIT_TRIES)) {
+                atomicOr(a.status, ST_TIMEOUT);
+                s_abort = 1;
+            } else if (s + 2 <= last) {
+                mbar_arrive_expect_tx(&bars[buf], phase_bytes);   // re-arm for step s + 2
+            }
+        }
+        // operands of the epilogue, loaded early (own rows of line i)
+        V yown[SW_MAXOPT];
+        double2 xold[SW_MAXOPT];
+#pragma unroll
+        for (int u = 0; u < SW_MAXOPT; ++u) {
+            const int o = tid + u * SW_THREADS;
+            yown[u] = mkc<TG>(TG(0), TG(0));
+            xold[u] = make_double2(0.0, 0.0);
+            if (o < nout) {
+                const int r = o % nrows, q = o / nrows;
+                const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
+                if (!fwd) yown[u] = Ys[off];
+                if (a.accumulate && (!fwd || i == nx - 1)) xold[u] = Xs[off];
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();   // step s operands landed; every thread is done with step s - 1
+        if (s_abort) return;
+        // the other staging buffer is free now: prefetch the operands of step s + 1
+        prefetch(s + 1);
+        cp_async_commit();
+        // t = b_i - C_i y_{i-1} (forward) or C_{i+1} x_{i+1} (backward)
+        const V *yin = sY + (size_t)buf * R * nzp;
+        const double2 *bin = sB + (size_t)buf * R * nz;
+        for (int q = wid; q < Rc; q += SW_THREADS / 32)
+        for (int j = lane; j < nz; j += 32) {
+            const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
+            V t;
+            if (fwd) {
+                double2 bv = bin[(size_t)q * nz + j];
+                if (a.conj) bv.y = -bv.y;
+                t = in_cast<TG>(bv);
+                if (i > 0) {
+                    const V yp = yin[(size_t)q * nzp + j];
+                    t.x -= c * yp.x;
+                    t.y -= c * yp.y;
+                }
+            } else {
+                const V xn = yin[(size_t)q * nzp + j];
+                t = mkc<TG>(c * xn.x, c * xn.y);
+            }
+            sT[(size_t)q * nzp + j] = t;
+        }
+        __syncthreads();
+        V acc[SW_MAXOPT];
+        if (pf) {
+            const V *Gb = sG + (size_t)buf * rpc * nzp;
+#pragma unroll
+            for (int u = 0; u < SW_MAXOPT; ++u) {
+                const int o = tid + u * SW_THREADS;
+                acc[u] = mkc<TG>(TG(0), TG(0));
+                if (o < nout) acc[u] = dot_row(Gb + (size_t)(o % nrows) * nzp, sT + (size_t)(o / nrows) * nzp, nz);
+            }
+        } else {
 #pragma unroll
             for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
+            const V *Gi = Gs + (size_t)i * nz * nz;
             for (int kc = 0; kc < nz; kc += SW_KC) {
                 const int kw = min(SW_KC, nz - kc);
                 for (int e = tid; e < nrows * kw; e += SW_THREADS) {
                     const int r = e / kw, b = e % kw;
-                    sG[r * SW_KC + b] = Gi[(size_t)(r0 + r) * nz + kc + b];
-                }
-                for (int e = tid; e < kw * Rc; e += SW_THREADS) {
-                    const int b = e / Rc, q = e % Rc;
-                    const int j = kc + b;
-                    V t;
-                    if (pass == 0) {
-                        double2 bv = Bs[(size_t)q * N + (size_t)i * nz + j];
-                        if (a.conj) bv.y = -bv.y;
-                        t = in_cast<TG>(bv);
-                        if (i > 0) {
-                            const TG c = (TG)coup_x(g, j);
-                            V yp = ldcg(Ys + (size_t)q * N + (size_t)(i - 1) * nz + j);
-                            t.x -= c * yp.x;
-                            t.y -= c * yp.y;
-                        }
-                    } else {
-                        const TG c = (TG)coup_x(g, j);
-                        V xn = ldcg(Ys + (size_t)q * N + (size_t)(i + 1) * nz + j);
-                        t = mkc<TG>(c * xn.x, c * xn.y);
-                    }
-                    sT[b * a.R + q] = t;
+                    sG[(size_t)r * kcp + b] = Gi[(size_t)(r0 + r) * nz + kc + b];
                 }
                 __syncthreads();
 #pragma unroll
                 for (int u = 0; u < SW_MAXOPT; ++u) {
                     const int o = tid + u * SW_THREADS;
                     if (o < nout) {
-                        const int r = o / Rc, q = o % Rc;
-                        V s = acc[u];
-                        for (int b = 0; b < kw; ++b) cfma(s, sG[r * SW_KC + b], sT[b * a.R + q]);
-                        acc[u] = s;
+                        const V d = dot_row(sG + (size_t)(o % nrows) * kcp, sT + (size_t)(o / nrows) * nzp + kc, kw);
+                        acc[u].x += d.x;
+                        acc[u].y += d.y;
                     }
                 }
                 __syncthreads();
             }
+        }
+        // new rows: y_i (forward) or x_i = y_i - G_i C x_{i+1} (backward); push them to every
+        // CTA's exchange buffer for the next step, then store / finish own rows
+        const bool push = s < last;
+        V *ynext = sY + (size_t)((s + 1) & 1) * R * nzp;
+        const uint32_t lbar = smem_u32(&bars[(s + 1) & 1]);
 #pragma unroll
-            for (int u = 0; u < SW_MAXOPT; ++u) {
-                const int o = tid + u * SW_THREADS;
-                if (o < nout) {
-                    const int r = o / Rc, q = o % Rc;
-                    V *dst = Ys + (size_t)q * N + (size_t)i * nz + r0 + r;
-                    if (pass == 0) {
-                        *dst = acc[u];
-                    } else {
-                        V y = *dst;
-                        *dst = mkc<TG>(y.x - acc[u].x, y.y - acc[u].y);
-                    }
+        for (int u = 0; u < SW_MAXOPT; ++u) {
+            const int o = tid + u * SW_THREADS;
+            if (o < nout) {
+                const int r = o % nrows, q = o / nrows;
+                V v = fwd ? acc[u] : mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
+                if (push) {
+                    const uint32_t la = smem_u32(ynext + (size_t)q * nzp + r0 + r);
+                    for (int t = 0; t < cs; ++t) st_async(mapa_u32(la, (uint32_t)t), v, mapa_u32(lbar, (uint32_t)t));
+                }
+                const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
+                if (fwd && i < nx - 1) {
+                    Ys[off] = v;
+                } else {
+                    double2 d = make_double2((double)v.x, (double)v.y);
+                    if (a.conj) d.y = -d.y;
+                    if (a.accumulate) { d.x += xold[u].x; d.y += xold[u].y; }
+                    Xs[off] = d;
                 }
             }
-            cluster_sync_all();
         }
     }
-    // final pass over this CTA's rows: conjugate (adjoint) and, for the mixed path,
-    // promote to FP64 and add to the iterate
-    for (int e = tid; e < nx * nrows * Rc; e += SW_THREADS) {
-        const int q = e / (nx * nrows);
-        const int rem = e % (nx * nrows);
-        const int i = rem / nrows, r = rem % nrows;
-        const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
-        V y = Ys[off];
-        double2 d = make_double2((double)y.x, (double)y.y);
-        if (a.conj) d.y = -d.y;
-        if (a.accumulate) {
-            double2 x = Xs[off];
-            d.x += x.x;
-            d.y += x.y;
-        }
-        Xs[off] = d;
-    }
+    cp_async_wait<0>();
 }
 
-template <typename TG>
-cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int cs, int rchunk,
-                              cudaStream_t st) {
-    const int rpc = (g.nz + cs - 1) / cs;
-    int R = rchunk;
-    while (R > 1 && rpc * R > SW_MAXOPT * SW_THREADS) R /= 2;
-    if (R > nrhs) R = nrhs;
-    const int n_chunks = (nrhs + R - 1) / R;
-    SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, G, B, X, Y, conj, accumulate};
-    const size_t smem = sizeof(cx_t<TG>) * ((size_t)rpc * SW_KC + (size_t)SW_KC * R);
-    cudaError_t e = cudaFuncSetAttribute(line_sweep_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+// Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
+static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_sys * n_chunks * cs, 1, 1);
-    cfg.blockDim = dim3(SW_THREADS, 1, 1);
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cs;
@@ -173,13 +300,77 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, line_sweep_kernel<TG>, a);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <typename TG>
+cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
+                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
+                              cudaStream_t st) {
+    const void *fn = (const void *)line_sweep_kernel<TG>;
+    const int nz = g.nz;
+    const size_t vsz = sizeof(cx_t<TG>);
+    int cs = nz / 16;
+    cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
+    cudaError_t e;
+    for (;;) {
+        const int rpc = (nz + cs - 1) / cs;
+        const size_t nzp = (size_t)padded<TG>(nz), kcp = (size_t)padded<TG>(SW_KC);
+        auto smem_of = [&](int R, int pf) {
+            return ((16 + vsz * 3 * (size_t)R * nzp + 15) & ~(size_t)15) + sizeof(double2) * 2 * (size_t)nz * R +
+                   (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp);
+        };
+        int R = rchunk < 1 ? 1 : rchunk;
+        if (R > nrhs) R = nrhs;
+        while (R > 1 && rpc * R > SW_MAXOPT * SW_THREADS) R = (R + 1) / 2;
+        int pf = 1;
+        while (smem_of(R, pf) > SW_SMEM_MAX) {
+            if (pf && R <= 4) pf = 0;
+            else if (R > 1) R = (R + 1) / 2;
+            else if (pf) pf = 0;
+            else return cudaErrorInvalidConfiguration;
+        }
+        const size_t smem = smem_of(R, pf);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (cs > 8) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess || active_clusters(fn, cs, SW_THREADS, smem) == 0) {
+                cudaGetLastError();
+                cs = 8;
+                continue;
+            }
+        }
+        const int n_chunks = (nrhs + R - 1) / R;
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, G, B, X, Y, conj, accumulate, status};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(n_sys * n_chunks * cs, 1, 1);
+        cfg.blockDim = dim3(SW_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t le = cudaSuccess;
+        HELM_TRACED(sizeof(TG) == 8 ? K_SWEEP64 : K_SWEEP32, st,
+                    (le = cudaLaunchKernelEx(&cfg, line_sweep_kernel<TG>, a)));
+        return le;
+    }
 }
 
 template cudaError_t launch_line_sweep<double>(const GridGeom &, int, int, const double2 *, const double2 *,
-                                               double2 *, double2 *, int, int, int, int, cudaStream_t);
+                                               double2 *, double2 *, int, int, int, int *, cudaStream_t);
 template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const double2 *,
-                                              double2 *, float2 *, int, int, int, int, cudaStream_t);
+                                              double2 *, float2 *, int, int, int, int *, cudaStream_t);
 
 // ------------------------------------------------------------------ FP64 residual
 // R = B - A X (A^H X for conj = 1) with the five-point operator, and per column the
@@ -238,7 +429,7 @@ cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double
                             const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st) {
     const int N = g.nx * g.nz;
     dim3 grid((N + RES_THREADS - 1) / RES_THREADS, nrhs, n_sys);
-    residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R, norms, conj);
+    HELM_TRACED(K_RESIDUAL, st, (residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R, norms, conj)));
     return cudaGetLastError();
 }
 

@@ -1,0 +1,113 @@
+// Per-kernel launch counting and CUDA-event timing (include/helm_trace.h).
+#include <string.h>
+#include <mutex>
+#include <vector>
+
+#include "helm_trace.h"
+#include "trace.h"
+
+namespace helm {
+
+static const char *kNames[K_COUNT] = {
+    "assemble", "sources", "restriction_taps", "restrict", "line_factor_fp64", "line_factor_fp32",
+    "line_sweep_fp64", "line_sweep_fp32", "residual_fp64", "misfit", "scatter_adjoint_rhs", "grad_accumulate",
+    "g_u_p_rhs", "z_rhs_base", "hess_accumulate", "hyper_terms", "dot_partial", "sum_partials", "axpby",
+    "fill", "sub", "regR", "dct_matrix", "p2_scale", "dgemm_dct",
+};
+
+namespace {
+struct Rec {
+    int id;
+    cudaEvent_t a, b;
+};
+std::mutex g_mu;
+bool g_on = false;
+int64_t g_launch[K_COUNT] = {};
+int64_t g_timed[K_COUNT] = {};
+double g_ms[K_COUNT] = {};
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t get_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+TraceScope::TraceScope(int id, cudaStream_t st) : id_(id), st_(st), a_(nullptr) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    ++g_launch[id];
+    if (g_on) {
+        a_ = get_event();
+        if (a_) cudaEventRecord(a_, st_);
+    }
+}
+
+TraceScope::~TraceScope() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t b = get_event();
+    if (!b) return;
+    cudaEventRecord(b, st_);
+    g_recs.push_back(Rec{id_, a_, b});
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" void helm_trace_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_on = on != 0;
+}
+
+extern "C" void helm_trace_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &r : g_recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    memset(g_launch, 0, sizeof g_launch);
+    memset(g_timed, 0, sizeof g_timed);
+    memset(g_ms, 0, sizeof g_ms);
+}
+
+extern "C" int32_t helm_trace_read(helm_trace_entry *out, int32_t max) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    for (auto &r : g_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_ms[r.id] += ms;
+            ++g_timed[r.id];
+        }
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    int n = 0;
+    for (int i = 0; i < K_COUNT && n < max; ++i) {
+        if (g_launch[i] == 0) continue;
+        helm_trace_entry &e = out[n++];
+        memset(&e, 0, sizeof e);
+        strncpy(e.name, kNames[i], sizeof(e.name) - 1);
+        e.launches = g_launch[i];
+        e.total_ms = g_ms[i];
+        e.timed = g_timed[i];
+    }
+    return n;
+}
+
+extern "C" int64_t helm_launch_count(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int64_t t = 0;
+    for (int i = 0; i < K_COUNT; ++i) t += g_launch[i];
+    return t;
+}

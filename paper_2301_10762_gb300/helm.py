@@ -56,9 +56,15 @@ class helm_hyper_info(C.Structure):
                 ("data_solves", C.c_int64), ("max_refine_iters", C.c_int32)]
 
 
+class helm_trace_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("timed", C.c_int64)]
+
+
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
             "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_sources", "helm_restrict",
-            "fwi_misfit_grad", "bilevel_hypergrad"]
+            "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
+            # include/helm_trace.h
+            "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count"]
 
 _lib = None
 
@@ -95,10 +101,20 @@ def load(path: str = LIB_PATH):
     lib.helm_restrict.argtypes = [vp, P(helm_acq), i32, vp, vp]
     lib.fwi_misfit_grad.restype = C.c_int
     lib.fwi_misfit_grad.argtypes = [vp, P(helm_acq), vp, dbl, dbl, dbl, P(dbl), vp, vp, vp]
+    lib.fwi_hessian_vec.restype = C.c_int
+    lib.fwi_hessian_vec.argtypes = [vp, P(helm_acq), vp, vp, vp, dbl, dbl, dbl, i32, vp]
     lib.bilevel_hypergrad.restype = C.c_int
     lib.bilevel_hypergrad.argtypes = [i32, P(helm_grid), P(vp), P(vp), P(helm_acq), P(dbl), i32, dbl, dbl,
                                       dbl, C.c_int, P(helm_pcg_opts), vp, P(dbl), P(dbl), P(dbl), P(dbl),
                                       P(helm_hyper_info)]
+    lib.helm_trace_enable.restype = None
+    lib.helm_trace_enable.argtypes = [C.c_int]
+    lib.helm_trace_reset.restype = None
+    lib.helm_trace_reset.argtypes = []
+    lib.helm_trace_read.restype = C.c_int32
+    lib.helm_trace_read.argtypes = [P(helm_trace_entry), i32]
+    lib.helm_launch_count.restype = C.c_int64
+    lib.helm_launch_count.argtypes = []
     _lib = lib
     return lib
 
@@ -261,6 +277,20 @@ def fwi_misfit_grad(f: Factor, acq: Acq, data: torch.Tensor, alpha, mu, rtol=1e-
     return phi.value, grad, U, Lam
 
 
+def fwi_hessian_vec(f: Factor, acq: Acq, U: torch.Tensor, Lam: torch.Tensor | None, mt: torch.Tensor, alpha, mu,
+                    rtol=1e-10, gauss_newton=False):
+    lib = load()
+    op = f.op
+    shape = (op.n_omega, acq.n_src, op.N)
+    pu = _dev(U, torch.complex128, "U", shape)
+    pl = _dev(Lam, torch.complex128, "Lam", shape) if Lam is not None else C.c_void_p()
+    pm = _dev(mt, torch.float64, "mt", (op.N,))
+    hv = torch.empty(op.N, dtype=torch.float64, device="cuda")
+    _check(lib.fwi_hessian_vec(f.handle, C.byref(acq.struct), pu, pl, pm, float(alpha), float(mu), float(rtol),
+                               1 if gauss_newton else 0, C.c_void_p(hv.data_ptr())), "fwi_hessian_vec")
+    return hv
+
+
 def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
                       cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
                       stream=None):
@@ -283,3 +313,27 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu,
     return {"psi": psi.value, "dpsi_dalpha": dalpha.value, "dpsi_dp": dp, "dpsi_dw": dw,
             "cg_matvecs": info.cg_matvecs, "cg_relres": info.cg_relres, "solves": info.solves,
             "data_solves": info.data_solves, "max_refine_iters": info.max_refine_iters}
+
+
+# ------------------------------------------------------------------ tracing (helm_trace.h)
+
+def helm_trace_enable(on=True):
+    load().helm_trace_enable(1 if on else 0)
+
+
+def helm_trace_reset():
+    load().helm_trace_reset()
+
+
+def helm_trace_read():
+    """{kernel name: {"launches", "total_ms", "timed"}} since the last reset (synchronises)."""
+    buf = (helm_trace_entry * 64)()
+    n = load().helm_trace_read(buf, 64)
+    if n < 0:
+        raise HelmError(3, "helm_trace_read")
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
+                                   "timed": buf[i].timed} for i in range(n)}
+
+
+def helm_launch_count():
+    return int(load().helm_launch_count())

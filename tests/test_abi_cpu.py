@@ -7,12 +7,12 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "helm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("helm.h", "helm_trace.h")]
 LIB = os.path.join(ROOT, "paper_2301_10762_gb300", "libhelm.so")
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "\n".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\*?\s*([A-Za-z_][A-Za-z_0-9]*)\s*\(", src, re.M)
     return sorted(set(n for n in names if n not in ("if", "while", "return")))

@@ -1,0 +1,125 @@
+"""GPU parity of the FWI misfit/gradient and the bilevel hypergradient against the CPU
+oracle, through the C ABI (Algorithms alg:box1 and alg:box)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import helmholtz as H
+
+hm = pytest.importorskip("paper_2301_10762_gb300.helm")
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+@pytest.mark.parametrize("shape", [(24, 20), (50, 47)])
+def test_fwi_misfit_grad_matches_oracle(prec, tol, shape):
+    w = W.tiny_case(*shape, n_omega=2, n_src=5, n_rec=11, seed=21)
+    w.alpha, w.mu = 1e-3, 1e-6
+    rw = np.linspace(0.5, 1.5, 11)
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    data, _ = H.synthetic_data(g, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz)
+    phi_o, grad_o, fields = H.fwi_objective_gradient(g, w.m, w.omegas, w.acq.src_xz, w.acq.rec_xz, data,
+                                                     w.alpha, w.mu, rec_w=rw, return_fields=True)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
+    f = hm.helm_factor(op, prec)
+    acq = hm.Acq(w.acq.src_xz, w.acq.rec_xz, rec_w=rw)
+    phi, grad, U, Lam = hm.fwi_misfit_grad(f, acq, torch.tensor(data, device="cuda"), w.alpha, w.mu,
+                                           rtol=1e-12, want_fields=True)
+    assert abs(phi - phi_o) <= tol * abs(phi_o)
+    assert relerr(grad.cpu().numpy(), grad_o) <= tol
+    assert relerr(U.cpu().numpy(), fields["U"]) <= tol
+    assert relerr(Lam.cpu().numpy(), fields["Lam"]) <= tol
+
+
+def test_fwi_gradient_is_deterministic():
+    w = W.tiny_case(40, 33, n_omega=2, n_src=4, n_rec=7, seed=22)
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    data, _ = H.synthetic_data(g, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
+    f = hm.helm_factor(op, 0)
+    acq = hm.Acq.from_workload(w.acq)
+    d = torch.tensor(data, device="cuda")
+    p1, g1, _, _ = hm.fwi_misfit_grad(f, acq, d, 1e-3, 1e-6)
+    p2, g2, _, _ = hm.fwi_misfit_grad(f, acq, d, 1e-3, 1e-6)
+    assert p1 == p2 and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (1, 1e-7)])
+def test_hypergradient_fixed_iterations_matches_oracle(prec, tol):
+    """Two training models on different grids, fixed number of PCG iterations on both sides."""
+    rng = np.random.default_rng(3)
+    shapes = [(26, 22), (30, 30)]
+    om = np.array([4.0, 7.5])
+    src = np.array([[0.0, 0.2], [0.0, 0.5], [0.0, 0.8]])
+    rec = np.array([[0.9, 0.25], [0.93, 0.55], [0.88, 0.71], [0.95, 0.4]])
+    rw = np.array([1.0, 0.9, 1.1, 1.2])
+    # mu = 1e-2 keeps H well conditioned: with mu = 1e-4 a 1e-14 perturbation of the input
+    # already moves the oracle's own fixed-iteration PCG output by ~5e-8 (dpsi/dalpha)
+    alpha, alpha0, mu = 1e-3, 2e-3, 1e-2
+    ref = {"psi": 0.0, "dpsi_dalpha": 0.0, "dpsi_dp": 0.0, "dpsi_dw": 0.0}
+    grids, mf, mt = [], [], []
+    for (nx, nz) in shapes:
+        mtrue = W.layered_velocity(nx, nz, int(rng.integers(1000)))
+        mfwi = W.gaussian_smooth(mtrue.reshape(nx, nz), 2.0).reshape(-1)
+        g = H.Grid(nx, nz)
+        o = H.hypergradient(g, mfwi, mtrue, om, src, rec, alpha, alpha0, mu, rec_w=rw, cg_fixed_iters=6)
+        for k in ref:
+            ref[k] = ref[k] + o[k] / len(shapes)
+        grids.append((nx, nz, 1.0, 1.0))
+        mf.append(torch.tensor(mfwi, device="cuda"))
+        mt.append(torch.tensor(mtrue, device="cuda"))
+    acq = hm.Acq(src, rec, rec_w=rw)
+    out = hm.bilevel_hypergrad(grids, mf, mt, acq, om, alpha, alpha0, mu, prec=prec, cg_fixed_iters=6,
+                               refine_rtol=1e-13)
+    assert abs(out["psi"] - ref["psi"]) <= 1e-12 * abs(ref["psi"])
+    assert abs(out["dpsi_dalpha"] - ref["dpsi_dalpha"]) <= tol * abs(ref["dpsi_dalpha"])
+    assert relerr(out["dpsi_dp"], ref["dpsi_dp"]) <= tol
+    assert relerr(out["dpsi_dw"], ref["dpsi_dw"]) <= tol
+    assert out["cg_matvecs"] == 7
+    n_data = len(om) * len(src)
+    assert out["data_solves"] == len(shapes) * n_data
+    assert out["solves"] == len(shapes) * (2 + 2 * 7 + 1) * n_data
+
+
+def test_hypergradient_converged_pcg_matches_oracle():
+    nx, nz = 28, 24
+    mtrue = W.layered_velocity(nx, nz, 7)
+    mfwi = W.gaussian_smooth(mtrue.reshape(nx, nz), 2.0).reshape(-1)
+    om = np.array([3.0, 6.0])
+    src = np.array([[0.0, 0.3], [0.0, 0.7]])
+    rec = np.array([[1.0, 0.2], [1.0, 0.45], [0.97, 0.8]])
+    g = H.Grid(nx, nz)
+    o = H.hypergradient(g, mfwi, mtrue, om, src, rec, 1e-3, 1e-3, 1e-2, cg_rtol=1e-11)
+    out = hm.bilevel_hypergrad([(nx, nz, 1.0, 1.0)], [torch.tensor(mfwi, device="cuda")],
+                               [torch.tensor(mtrue, device="cuda")], hm.Acq(src, rec), om, 1e-3, 1e-3, 1e-2,
+                               cg_rtol=1e-11, refine_rtol=1e-13)
+    assert out["cg_relres"] <= 1e-11
+    assert relerr(out["dpsi_dp"], o["dpsi_dp"]) <= 1e-7
+    assert abs(out["dpsi_dalpha"] - o["dpsi_dalpha"]) <= 1e-7 * abs(o["dpsi_dalpha"])
+
+
+@pytest.mark.parametrize("gn", [False, True])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_hessian_vec_matches_oracle(gn, prec, tol):
+    w = W.tiny_case(30, 26, n_omega=2, n_src=4, n_rec=9, seed=31)
+    w.alpha, w.mu = 1e-3, 1e-5
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    data, _ = H.synthetic_data(g, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz)
+    _, _, fields = H.fwi_objective_gradient(g, w.m, w.omegas, w.acq.src_xz, w.acq.rec_xz, data, w.alpha, w.mu,
+                                            return_fields=True)
+    mt = np.random.default_rng(5).standard_normal(g.N)
+    ref = H.hessian_vec(g, w.m, w.omegas, fields, mt, w.alpha, w.mu, gauss_newton=gn)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
+    f = hm.helm_factor(op, prec)
+    acq = hm.Acq.from_workload(w.acq)
+    _, _, U, Lam = hm.fwi_misfit_grad(f, acq, torch.tensor(data, device="cuda"), w.alpha, w.mu, rtol=1e-12,
+                                      want_fields=True)
+    hv = hm.fwi_hessian_vec(f, acq, U, None if gn else Lam, torch.tensor(mt, device="cuda"), w.alpha, w.mu,
+                            rtol=1e-12, gauss_newton=gn)
+    assert relerr(hv.cpu().numpy(), ref) <= tol
