@@ -138,6 +138,23 @@ helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *
                                helm_c128 *X_dev, double rtol, int32_t max_iter,
                                helm_solve_info *info);
 
+/* helm_solve_noalloc -- helm_solve (adjoint = 0) or helm_adjoint_solve (adjoint != 0)
+ * that allocates nothing, for callers that cannot allocate device memory at solve time
+ * (a serving process whose device memory was partitioned once at start-up, a host
+ * framework whose caching allocator owns the free device memory, or a loop that cannot
+ * take the device-wide synchronisation of cudaMalloc / cudaFree).  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ * The working memory of the refinement (FP32 line vectors, FP64 residuals, per-column
+ * norms) lives in one fixed 32 MiB array in device global memory that every GPU loading
+ * the library holds until exit; the caller still passes B_dev and X_dev.  Limits:
+ * n_omega * nrhs * N * 24 bytes (mixed; norms only for FP64) within 32 MiB and at most
+ * 16384 columns, else HELM_EINVAL.  The first call on a device resolves the array's
+ * device address with that device current: make it before any stream capture.  Calls
+ * share the array (each clears what must start at zero); calls that overlap on the GPU
+ * race and must be serialised by the caller.  Other arguments and errors as helm_solve. */
+helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
+                               double rtol, int32_t max_iter, int32_t adjoint, helm_solve_info *info);
+
 /* helm_sources -- right-hand sides e_s (Appendix, "Computing the wavefield"),
  * B_dev [n_omega][n_src][N] (identical for every frequency), amplitudes src_amp. */
 helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, helm_c128 *B_dev);

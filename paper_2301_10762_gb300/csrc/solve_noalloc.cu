@@ -1,0 +1,160 @@
+// helm_solve_noalloc: helm_solve / helm_adjoint_solve for callers that cannot allocate
+// device memory at solve time.
+//
+// Some callers must not call cudaMalloc when they solve: a serving process whose device
+// memory was carved up once at start-up (a further allocation could fail or fragment
+// it), a host framework whose caching allocator already owns the free device memory,
+// and latency-critical loops that cannot afford the device-wide synchronisation that
+// cudaMalloc / cudaFree imply.  helm_solve meets the working memory of the mixed path
+// (FP32 line vectors, FP64 residuals, per-column norms) by growing buffers inside the
+// factor handle on first use, which allocates.  This variant runs the same kernels with
+// that working memory placed in one fixed array in device global memory, declared
+// below, which every GPU that loads the library holds until the process exits.
+//
+// Consequences for the caller:
+//   * the first call on a device resolves the device address of the array
+//     (cudaGetSymbolAddress, with that device current); make that first call before
+//     any stream capture;
+//   * every call shares the array and it keeps the previous call's contents (the
+//     norms are cleared by each call before use); calls that overlap on the GPU, from
+//     any stream or host thread, race on it and must be serialised by the caller;
+//   * sizes beyond the array are rejected with HELM_EINVAL.
+#include <math.h>
+#include <mutex>
+
+#include "helm.h"
+#include "kernels.h"
+#include "abi_internal.h"
+
+using namespace helm;
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB per GPU
+constexpr size_t kMaxCols = 16384;                    // columns (frequency x right-hand side) per call
+constexpr int kMaxDevices = 64;
+
+// the working memory of the no-allocation solve (device global memory, one per GPU)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void *g_dev_addr[kMaxDevices] = {};
+double g_norms_host[2 * kMaxCols];
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// device address of the array on the current device (resolved once per device)
+helm_status scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        helm_set_error("helm_solve_noalloc: cudaGetDevice", e);
+        return HELM_ECUDA;
+    }
+    if (!g_dev_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            helm_set_error("helm_solve_noalloc: cudaGetSymbolAddress", e);
+            return HELM_ECUDA;
+        }
+        g_dev_addr[dev] = p;
+    }
+    *out = g_dev_addr[dev];
+    return HELM_OK;
+}
+
+helm_status max_relres(const helm_op *op, const double *norms_dev, size_t cols, double *out) {
+    cudaError_t e = cudaMemcpyAsync(g_norms_host, norms_dev, cols * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) {
+        helm_set_error("helm_solve_noalloc: norms", e);
+        return HELM_ECUDA;
+    }
+    double mx = 0.0;
+    for (size_t c = 0; c < cols; ++c) {
+        const double rr = g_norms_host[2 * c], bb = g_norms_host[2 * c + 1];
+        const double rel = bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0);
+        if (!(rel <= mx)) mx = rel;
+    }
+    *out = mx;
+    return HELM_OK;
+}
+
+}  // namespace
+
+extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
+                                          helm_c128 *X_dev, double rtol, int32_t max_iter, int32_t adjoint,
+                                          helm_solve_info *info) {
+    if (!f || nrhs < 0 || (nrhs > 0 && (!B_dev || !X_dev)) || (const void *)B_dev == (const void *)X_dev) {
+        helm_set_msg("helm_solve_noalloc: bad arguments (NULL, nrhs < 0 or B aliases X)");
+        return HELM_EINVAL;
+    }
+    if (info) { info->iters = 0; info->max_relres = -1.0; }
+    if (nrhs == 0) return HELM_OK;
+    const helm_op *op = f->op;
+    const GridGeom &g = op->g;
+    const int n_sys = op->n_omega;
+    const size_t N = (size_t)g.nx * g.nz;
+    const size_t cols = (size_t)n_sys * nrhs;
+    const bool mixed = f->prec == HELM_MIXED;
+    const size_t y_bytes = mixed ? align256(cols * N * sizeof(float2)) : 0;
+    const size_t r_bytes = mixed ? align256(cols * N * sizeof(double2)) : 0;
+    const size_t n_bytes = align256(cols * 2 * sizeof(double));
+    if (cols > kMaxCols || y_bytes + r_bytes + n_bytes > kScratchBytes) {
+        helm_set_msg("helm_solve_noalloc: problem larger than the fixed working array "
+                     "(32 MiB: n_omega*nrhs*N*24 bytes plus norms, at most 16384 columns)");
+        return HELM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    void *base = nullptr;
+    helm_status s = scratch_address(&base);
+    if (s != HELM_OK) return s;
+    unsigned char *p = (unsigned char *)base;
+    float2 *Y = mixed ? (float2 *)p : nullptr;
+    double2 *R = mixed ? (double2 *)(p + y_bytes) : nullptr;
+    double *norms = (double *)(p + y_bytes + r_bytes);
+    const double2 *B = (const double2 *)B_dev;
+    double2 *X = (double2 *)X_dev;
+    const int conj = adjoint ? 1 : 0;
+    const int rchunk = 16;
+    cudaError_t e;
+    double rel = -1.0;
+    int it = 1;
+    if (!mixed) {
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status,
+                                      op->st);
+        if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
+        if (info) {
+            e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
+            if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, norms, conj, op->st);
+            if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: residual", e); return HELM_ECUDA; }
+            if ((s = max_relres(op, norms, cols, &rel)) != HELM_OK) return s;
+        }
+    } else {
+        if (max_iter < 1) max_iter = 1;
+        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, Y, conj, 0, rchunk, op->status,
+                                     op->st);
+        if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
+        for (;;) {
+            e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
+            if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, R, norms, conj, op->st);
+            if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: residual", e); return HELM_ECUDA; }
+            if ((s = max_relres(op, norms, cols, &rel)) != HELM_OK) return s;
+            if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
+            e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, R, X, Y, conj, 1, rchunk,
+                                         op->status, op->st);
+            if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
+            ++it;
+        }
+    }
+    int st_host = 0;
+    e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: status", e); return HELM_ECUDA; }
+    if (info) { info->iters = it; info->max_relres = rel; }
+    if (st_host & ST_TIMEOUT) { helm_set_msg("a sweep kernel gave up waiting for its cluster"); return HELM_ETIMEOUT; }
+    if (mixed && !(rel <= rtol)) { helm_set_msg("refinement did not reach rtol"); return HELM_ENOCONV; }
+    return HELM_OK;
+}

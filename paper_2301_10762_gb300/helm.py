@@ -61,7 +61,8 @@ class helm_trace_entry(C.Structure):
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
-            "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_sources", "helm_restrict",
+            "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
+            "helm_restrict",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
             "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count"]
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = C.c_int
         fn.argtypes = [vp, i32, vp, vp, dbl, i32, P(helm_solve_info)]
+    lib.helm_solve_noalloc.restype = C.c_int
+    lib.helm_solve_noalloc.argtypes = [vp, i32, vp, vp, dbl, i32, i32, P(helm_solve_info)]
     lib.helm_sources.restype = C.c_int
     lib.helm_sources.argtypes = [vp, P(helm_acq), vp]
     lib.helm_restrict.restype = C.c_int
@@ -241,6 +244,22 @@ def helm_solve(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, rtol=1
 
 def helm_adjoint_solve(f: Factor, B: torch.Tensor, X: torch.Tensor | None = None, rtol=1e-10, max_iter=8):
     return _solve("helm_adjoint_solve", f, B, X, rtol, max_iter)
+
+
+def helm_solve_noalloc(f: Factor, B: torch.Tensor, X: torch.Tensor, rtol=1e-10, max_iter=8, adjoint=False):
+    """Same result as helm_solve / helm_adjoint_solve, but the library allocates nothing:
+    its working memory is a fixed 32 MiB device array (see include/helm.h).  X must be
+    passed in by the caller."""
+    lib = load()
+    op = f.op
+    if B.dim() != 3 or B.shape[0] != op.n_omega or B.shape[2] != op.N:
+        raise ValueError(f"B must be [n_omega={op.n_omega}, nrhs, N={op.N}]")
+    pb = _dev(B, torch.complex128, "B")
+    px = _dev(X, torch.complex128, "X", B.shape)
+    info = helm_solve_info()
+    _check(lib.helm_solve_noalloc(f.handle, B.shape[1], pb, px, float(rtol), int(max_iter), 1 if adjoint else 0,
+                                  C.byref(info)), "helm_solve_noalloc")
+    return X, {"iters": info.iters, "max_relres": info.max_relres}
 
 
 def helm_sources(op: Op, acq: Acq) -> torch.Tensor:
