@@ -234,6 +234,229 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_kernel(FactorArgs<T> 
     if (bad && tid == 0) atomicOr(a.status, ST_SINGULAR);
 }
 
+// ----------------------------------------------------------------------------------
+// Shared-memory-resident variant (used whenever the slab fits): each CTA keeps its own
+// columns of S_i / G_i in shared memory for the whole line recurrence, so the Schur
+// update S_{i+1} = D_{i+1} - C G_i C of its columns is local.  Per 16-column block step
+// the owner inverts the diagonal block in one warp (registers and shuffles, partial
+// pivoting without row swaps: the pivot order is applied when the inverse is written)
+// and pushes the old column panel and the block inverse into every CTA's receive
+// buffer with distributed-shared-memory stores; one hardware cluster barrier per
+// block step publishes them.  Receive buffers alternate, so the owner of step t+1 never
+// overwrites data a slower CTA still reads at step t.
+
+// 16 x 16 inverse (kb x kb block padded with the identity) of M (shared, row stride ld)
+// by one warp; lane (r, h) holds row r, column half h of [M | I].  Writes the inverse to
+// P (row stride NB, shared).  Returns false in every lane if a pivot was zero or not
+// finite.
+template <typename T>
+__device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
+    using V = cx_t<T>;
+    const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4;
+    V a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (h == 0) a[j] = (r < kb && j < kb) ? M[r * ld + j] : mkc<T>(r == j ? T(1) : T(0), T(0));
+        else a[j] = mkc<T>(r == j ? T(1) : T(0), T(0));
+    }
+    unsigned used = 0;
+    int qinv = 0;   // step at which this lane's row was the pivot
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        T v = (h == 0 && !((used >> r) & 1u)) ? a[q].x * a[q].x + a[q].y * a[q].y : T(-1);
+        int idx = r;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, v, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        }
+        const int p = idx;
+        if (!(v > T(0)) || !isfinite(v)) ok = false;
+        used |= 1u << p;
+        if (r == p) qinv = q;
+        V pv;
+        pv.x = __shfl_sync(0xffffffffu, a[q].x, p);
+        pv.y = __shfl_sync(0xffffffffu, a[q].y, p);
+        const T den = pv.x * pv.x + pv.y * pv.y;
+        const V inv = ok ? mkc<T>(pv.x / den, -pv.y / den) : mkc<T>(T(1), T(0));
+        if (r == p) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = cmul(a[j], inv);
+        }
+        V f;
+        f.x = __shfl_sync(0xffffffffu, a[q].x, r);
+        f.y = __shfl_sync(0xffffffffu, a[q].y, r);
+        const int src = p + 16 * h;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            V pj;
+            pj.x = __shfl_sync(0xffffffffu, a[j].x, src);
+            pj.y = __shfl_sync(0xffffffffu, a[j].y, src);
+            if (r != p) cfms(a[j], f, pj);
+        }
+    }
+    // inverse row q = right half of the row chosen as pivot at step q
+    if (h == 1 && qinv < kb) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < kb) P[qinv * NB + j] = a[j];
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void st_cluster_c(uint32_t addr, float2 v) { st_cluster(addr, v); }
+__device__ __forceinline__ void st_cluster_c(uint32_t addr, double2 v) { st_cluster(addr, v); }
+
+template <typename T>
+__global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArgs<T> a) {
+    using V = cx_t<T>;
+    const GridGeom g = a.g;
+    const int nx = g.nx, nz = g.nz, cs = a.cs;
+    const int tid = threadIdx.x;
+    const int rank = (int)cluster_ctarank();
+    const int sys = (int)cluster_id_x();
+    const int p = (nz + NB - 1) / NB;
+    const int bpc = (p + cs - 1) / cs;
+    const int kb_lo = rank * bpc, kb_hi = min(p, kb_lo + bpc);
+    const int c0 = min(nz, kb_lo * NB), c1 = min(nz, kb_hi * NB);
+    const int ncol = max(0, c1 - c0);
+    const int ncb = (ncol + NB - 1) / NB;     // own column blocks
+    const int ldw = bpc * NB + 1;             // padded row stride of the slab
+    const int ldr = bpc * NB + 1;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sW = reinterpret_cast<V *>(smem_raw);                  // nz x ldw   own columns of S_i / G_i
+    V *sRecv = sW + (size_t)nz * ldw;                         // 2 x (nz*NB + NB*NB)
+    const size_t recv_elems = (size_t)nz * NB + NB * NB;
+    V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
+    V *sPst = sR + (size_t)NB * ldr;                          // NB x NB  owner's block inverse
+    __shared__ int s_bad;
+
+    V *Gs = a.G + (size_t)sys * nx * nz * nz;
+    const double2 *dg = a.diag + (size_t)sys * nx * nz;
+    const T cx_in = (T)coup_x(g, 1), cx_edge = (T)coup_x(g, 0);
+    const T cz_in = (T)coup_z(g, 1), cz_edge = (T)coup_z(g, 0);
+    const int cl = tid & (NB - 1), rw = tid >> 4;   // (row group, column) of the 2D loops
+    if (tid == 0) s_bad = 0;
+    int t = 0;
+
+    for (int i = 0; i < nx; ++i) {
+        const T cz = (i == 0 || i == nx - 1) ? cz_edge : cz_in;
+        // S_i = D_i - C G_{i-1} C on the own columns (G_{i-1} is the slab itself)
+        for (int cb = 0; cb < ncb; ++cb) {
+            const int cc = cb * NB + cl, c = c0 + cc;
+            if (c >= c1) continue;
+            const T cxc = (c == 0 || c == nz - 1) ? cx_edge : cx_in;
+            for (int r = rw; r < nz; r += FAC_THREADS / NB) {
+                const T cxr = (r == 0 || r == nz - 1) ? cx_edge : cx_in;
+                V v = mkc<T>(T(0), T(0));
+                if (i > 0) {
+                    const V gp = sW[(size_t)r * ldw + cc];
+                    const T s = cxr * cxc;
+                    v = mkc<T>(-s * gp.x, -s * gp.y);
+                }
+                if (r == c) {
+                    const V d = from_c128<T>(dg[(size_t)i * nz + r]);
+                    v.x += d.x;
+                    v.y += d.y;
+                } else if (r == c + 1 || c == r + 1) {
+                    v.x += cz;
+                }
+                sW[(size_t)r * ldw + cc] = v;
+            }
+        }
+        __syncthreads();
+
+        for (int k = 0; k < p; ++k, ++t) {
+            const int k0 = k * NB, kb = min(NB, nz - k0);
+            const int owner = k / bpc;
+            V *recvU = sRecv + (size_t)(t & 1) * recv_elems;   // nz x NB: old column panel W_:k
+            V *recvP = recvU + (size_t)nz * NB;                 // NB x NB: inverse of W_kk
+            if (rank == owner) {
+                const int kc = k0 - c0;
+                if (tid < 32) {
+                    if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, sPst) && tid == 0) s_bad = 1;
+                }
+                // push the old column panel to every CTA while warp 0 inverts
+                const uint32_t lu = smem_u32(recvU);
+                for (int r = rw; r < nz; r += FAC_THREADS / NB) {
+                    if (cl < kb) {
+                        const V v = sW[(size_t)r * ldw + kc + cl];
+                        const uint32_t off = (uint32_t)(((size_t)r * NB + cl) * sizeof(V));
+                        for (int dst = 0; dst < cs; ++dst) st_cluster_c(mapa_u32(lu + off, (uint32_t)dst), v);
+                    }
+                }
+                __syncthreads();
+                const uint32_t lp = smem_u32(recvP);
+                if (rw < kb && cl < kb) {
+                    const V v = sPst[rw * NB + cl];
+                    const uint32_t off = (uint32_t)((rw * NB + cl) * sizeof(V));
+                    for (int dst = 0; dst < cs; ++dst) st_cluster_c(mapa_u32(lp + off, (uint32_t)dst), v);
+                }
+            }
+            cluster_sync_all();
+            // Rk = P W[k rows, own columns outside block k]
+            for (int cb = 0; cb < ncb; ++cb) {
+                const int cc = cb * NB + cl, c = c0 + cc;
+                if (c >= c1 || (c >= k0 && c < k0 + kb)) continue;
+                for (int q = rw; q < kb; q += FAC_THREADS / NB) {
+                    V acc = mkc<T>(T(0), T(0));
+#pragma unroll 4
+                    for (int u = 0; u < kb; ++u) cfma(acc, recvP[q * NB + u], sW[(size_t)(k0 + u) * ldw + cc]);
+                    sR[q * ldr + cc] = acc;
+                }
+            }
+            __syncthreads();
+            for (int cb = 0; cb < ncb; ++cb) {
+                const int cc = cb * NB + cl, c = c0 + cc;
+                if (c >= c1) continue;
+                const bool inblk = (c >= k0 && c < k0 + kb);
+                for (int r = rw; r < nz; r += FAC_THREADS / NB) {
+                    const bool inrow = (r >= k0 && r < k0 + kb);
+                    V *w = sW + (size_t)r * ldw + cc;
+                    if (inblk) {
+                        // W_Ik <- -W_Ik P ; W_kk <- P
+                        if (inrow) {
+                            *w = recvP[(r - k0) * NB + (c - k0)];
+                        } else {
+                            V acc = mkc<T>(T(0), T(0));
+#pragma unroll 4
+                            for (int u = 0; u < kb; ++u) cfma(acc, recvU[(size_t)r * NB + u], recvP[u * NB + (c - k0)]);
+                            *w = mkc<T>(-acc.x, -acc.y);
+                        }
+                    } else if (inrow) {
+                        *w = sR[(r - k0) * ldr + cc];
+                    } else {
+                        V acc = *w;
+#pragma unroll 4
+                        for (int u = 0; u < kb; ++u) cfms(acc, recvU[(size_t)r * NB + u], sR[u * ldr + cc]);
+                        *w = acc;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // G_i (own columns) to the factor storage
+        V *W = Gs + (size_t)i * nz * nz;
+        for (int cb = 0; cb < ncb; ++cb) {
+            const int cc = cb * NB + cl, c = c0 + cc;
+            if (c >= c1) continue;
+            for (int r = rw; r < nz; r += FAC_THREADS / NB) W[(size_t)r * nz + c] = sW[(size_t)r * ldw + cc];
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
+}
+
+template <typename T> static size_t factor_smem_resident_bytes(int nz, int cs) {
+    const int p = (nz + NB - 1) / NB;
+    const int bpc = (p + cs - 1) / cs;
+    const size_t ld = (size_t)bpc * NB + 1;
+    return sizeof(cx_t<T>) * ((size_t)nz * ld + 2 * ((size_t)nz * NB + NB * NB) + NB * ld + NB * NB);
+}
+
 template <typename T> static size_t factor_smem_bytes(int nz, int cs) {
     const int p = (nz + NB - 1) / NB;
     const int bpc = (p + cs - 1) / cs;
@@ -249,9 +472,11 @@ template <typename T>
 cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag, cx_t<T> *G, cx_t<T> *xch,
                                int *status, int cs, cudaStream_t st) {
     FactorArgs<T> a{g, diag, G, xch, status, cs};
-    const size_t smem = factor_smem_bytes<T>(g.nz, cs);
-    cudaError_t e = cudaFuncSetAttribute(line_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem_res = factor_smem_resident_bytes<T>(g.nz, cs);
+    const bool resident = smem_res <= 200 * 1024;
+    const size_t smem = resident ? smem_res : factor_smem_bytes<T>(g.nz, cs);
+    auto kern = resident ? line_factor_smem_kernel<T> : line_factor_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_sys * cs, 1, 1);
@@ -266,7 +491,7 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t le = cudaSuccess;
-    HELM_TRACED(sizeof(T) == 8 ? K_FACTOR64 : K_FACTOR32, st, (le = cudaLaunchKernelEx(&cfg, line_factor_kernel<T>, a)));
+    HELM_TRACED(sizeof(T) == 8 ? K_FACTOR64 : K_FACTOR32, st, (le = cudaLaunchKernelEx(&cfg, kern, a)));
     return le;
 }
 

@@ -80,15 +80,77 @@ __device__ __forceinline__ double2 dot_row(const double2 *g, const double2 *t, i
 // line handled by global step s: forward s = 0..nx-1 -> line s; backward s = nx..2nx-2 -> line 2nx-2-s
 __device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 * nx - 2 - s; }
 
-// Persistent sweep: 2nx-1 dependent line steps.  Per step the critical path is: wait
-// (mbarrier, bounded) until every CTA of the cluster has pushed its rows of the previous
-// line vector into this CTA's shared memory (st.async with transaction-count
-// completion), t = b_i - C y_{i-1} (or C x_{i+1}) from shared memory, the
-// (rows x n_z) x (n_z x R) product with the G_i slab that cp.async brought in during the
-// previous step, and the push of the new rows to all CTAs.  Two exchange buffers
-// alternate; no CTA can overwrite a buffer before every CTA has consumed it, because
-// producing the data of step s+2 needs the data of step s+1 from every CTA, which each
-// CTA sends only after it has finished step s.
+// Pre-pass: Y_i = G_i b_i for every line i of every system at once (the half of the
+// forward sweep that does not depend on the recurrence), a batched complex GEMM over
+// (system, line, row tile, right-hand-side chunk).  b is the FP64 input (conjugated
+// for the adjoint), cast to TG.
+constexpr int PP_ROWS = 32;
+constexpr int PP_KC = 64;
+template <typename TG>
+__global__ void __launch_bounds__(SW_THREADS) line_gb_prepass_kernel(GridGeom g, int nrhs, int R, const cx_t<TG> *G,
+                                                                   const double2 *B, cx_t<TG> *Y, int conj) {
+    using V = cx_t<TG>;
+    const int nx = g.nx, nz = g.nz, N = nx * nz;
+    const int n_rt = (nz + PP_ROWS - 1) / PP_ROWS;
+    const int n_ch = (nrhs + R - 1) / R;
+    int bid = blockIdx.x;
+    const int ch = bid % n_ch; bid /= n_ch;
+    const int rt = bid % n_rt; bid /= n_rt;
+    const int i = bid % nx;
+    const int sys = bid / nx;
+    const int q0 = ch * R, Rc = min(R, nrhs - q0);
+    const int r0 = rt * PP_ROWS, nrows = min(PP_ROWS, nz - r0);
+    const int kcp = padded<TG>(PP_KC);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sb = reinterpret_cast<V *>(smem_raw);           // [R][kcp]
+    V *sg = sb + (size_t)R * kcp;                       // [PP_ROWS][kcp]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double2 *Bs = B + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz;
+    const V *Gi = G + ((size_t)sys * nx + i) * nz * nz + (size_t)r0 * nz;
+    V acc[SW_MAXOPT];
+#pragma unroll
+    for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
+    for (int kc = 0; kc < nz; kc += PP_KC) {
+        const int kw = min(PP_KC, nz - kc);
+        for (int q = wid; q < Rc; q += SW_THREADS / 32)
+            for (int j = lane; j < kw; j += 32) {
+                double2 bv = Bs[(size_t)q * N + kc + j];
+                if (conj) bv.y = -bv.y;
+                sb[(size_t)q * kcp + j] = in_cast<TG>(bv);
+            }
+        for (int r = wid; r < nrows; r += SW_THREADS / 32)
+            for (int j = lane; j < kw; j += 32) sg[(size_t)r * kcp + j] = Gi[(size_t)r * nz + kc + j];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < SW_MAXOPT; ++u) {
+            const int o = tid + u * SW_THREADS;
+            if (o < nrows * Rc) {
+                const V d = dot_row(sg + (size_t)(o % nrows) * kcp, sb + (size_t)(o / nrows) * kcp, kw);
+                acc[u].x += d.x;
+                acc[u].y += d.y;
+            }
+        }
+        __syncthreads();
+    }
+    V *Ys = Y + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz + r0;
+#pragma unroll
+    for (int u = 0; u < SW_MAXOPT; ++u) {
+        const int o = tid + u * SW_THREADS;
+        if (o < nrows * Rc) Ys[(size_t)(o / nrows) * N + (o % nrows)] = acc[u];
+    }
+}
+
+// Persistent sweep over 2nx-1 dependent line steps, after the pre-pass has stored
+// G_i b_i in Y.  Forward: y_i = G_i b_i - G_i (C y_{i-1}); backward:
+// x_i = y_i - G_i (C x_{i+1}).  Per step: wait (mbarrier, bounded) until every CTA of
+// the cluster has pushed its rows of the previous line vector, already multiplied by
+// the line coupling C, into this CTA's shared memory (st.async with transaction-count
+// completion); the (rows x n_z) x (n_z x R) product of the G_i slab (cp.async-prefetched
+// during the previous step) with that vector; subtract from the row values loaded
+// early from global memory; push the new rows (times C) to all CTAs.  Two exchange
+// buffers alternate; no CTA can overwrite a buffer before every CTA has consumed it,
+// because producing the data of step s+2 needs the data of step s+1 from every CTA,
+// which each CTA sends only after it has finished step s.
 template <typename TG>
 __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a) {
     using V = cx_t<TG>;
@@ -111,23 +173,17 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);           // [2]
-    V *sY = reinterpret_cast<V *>(smem_raw + 16);                       // [2][R][nzp]
-    V *sT = sY + 2 * (size_t)R * nzp;                                   // [R][nzp]
-    const size_t boff = (16 + sizeof(V) * 3 * (size_t)R * nzp + 15) & ~(size_t)15;
-    double2 *sB = reinterpret_cast<double2 *>(smem_raw + boff);         // [2][R][nz]
-    V *sG = reinterpret_cast<V *>(sB + 2 * (size_t)R * nz);             // pf: [2][rpc][nzp]; else [rpc][kcp]
+    V *sY = reinterpret_cast<V *>(smem_raw + 16);                       // [2][R][nzp]  C * (line vector)
+    V *sG = sY + 2 * (size_t)R * nzp;                                   // pf: [2][rpc][nzp]; else [rpc][kcp]
     __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
-    const double2 *Bs = a.B + ((size_t)sys * a.nrhs + q0) * N;
     double2 *Xs = a.X + ((size_t)sys * a.nrhs + q0) * N;
     V *Ys = a.Y + ((size_t)sys * a.nrhs + q0) * N;
     const int last = 2 * nx - 2;
     const uint32_t phase_bytes = (uint32_t)(nz * Rc * sizeof(V));
-    // couplings between neighbouring lines (grid constants; an edge on the top/bottom
-    // boundary has half weight), converted once so the per-step loops do no FP64 work
     const TG c_in = (TG)coup_x(g, 1), c_edge = (TG)coup_x(g, 0);
-    const int lane = tid & 31, wid = tid >> 5;   // division-free 2D loops: warp -> q, lane -> j
+    const int lane = tid & 31, wid = tid >> 5;
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -143,32 +199,19 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     }
 
     auto prefetch = [&](int s) {
-        if (s > last) return;
+        if (!pf || s > last || s == 0) return;   // step 0 needs no product
         const int i = step_line(s, nx);
-        const int buf = s & 1;
-        if (pf) {
-            const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
-            V *dst = sG + (size_t)buf * rpc * nzp;
-            if (sizeof(TG) == 4 && (nz & 1) == 0) {
-                for (int r = wid; r < nrows; r += SW_THREADS / 32)
-                    for (int b = 2 * lane; b < nz; b += 64)
-                        cp_async16(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
-            } else {
-                for (int r = wid; r < nrows; r += SW_THREADS / 32)
-                    for (int b = lane; b < nz; b += 32)
-                        cp_async_elem(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
-            }
-        }
-        if (s < nx) {
-            double2 *dst = sB + (size_t)buf * R * nz;
-            for (int q = wid; q < Rc; q += SW_THREADS / 32)
-                for (int j = lane; j < nz; j += 32)
-                    cp_async_elem(dst + (size_t)q * nz + j, Bs + (size_t)q * N + (size_t)i * nz + j);
+        const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
+        V *dst = sG + (size_t)(s & 1) * rpc * nzp;
+        if (sizeof(TG) == 4 && (nz & 1) == 0) {
+            for (int r = wid; r < nrows; r += SW_THREADS / 32)
+                for (int b = 2 * lane; b < nz; b += 64) cp_async16(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
+        } else {
+            for (int r = wid; r < nrows; r += SW_THREADS / 32)
+                for (int b = lane; b < nz; b += 32) cp_async_elem(dst + (size_t)r * nzp + b, src + (size_t)r * nz + b);
         }
     };
 
-    prefetch(0);
-    cp_async_commit();
     for (int s = 0; s <= last; ++s) {
         const int i = step_line(s, nx);
         const bool fwd = s < nx;
@@ -181,7 +224,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 mbar_arrive_expect_tx(&bars[buf], phase_bytes);   // re-arm for step s + 2
             }
         }
-        // operands of the epilogue, loaded early (own rows of line i)
+        // own rows of line i loaded early: G_i b_i (forward) or y_i (backward), and the
+        // FP64 iterate where the mixed epilogue accumulates
         V yown[SW_MAXOPT];
         double2 xold[SW_MAXOPT];
 #pragma unroll
@@ -192,73 +236,48 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             if (o < nout) {
                 const int r = o % nrows, q = o / nrows;
                 const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
-                if (!fwd) yown[u] = Ys[off];
+                yown[u] = Ys[off];
                 if (a.accumulate && (!fwd || i == nx - 1)) xold[u] = Xs[off];
             }
         }
-        cp_async_wait<0>();
+        if (s > 0) cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
         if (s_abort) return;
-        // the other staging buffer is free now: prefetch the operands of step s + 1
-        prefetch(s + 1);
+        prefetch(s + 1);   // into the staging buffer that step s - 1 used
         cp_async_commit();
-        // t = b_i - C_i y_{i-1} (forward) or C_{i+1} x_{i+1} (backward)
-        const V *yin = sY + (size_t)buf * R * nzp;
-        const double2 *bin = sB + (size_t)buf * R * nz;
-        for (int q = wid; q < Rc; q += SW_THREADS / 32)
-        for (int j = lane; j < nz; j += 32) {
-            const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
-            V t;
-            if (fwd) {
-                double2 bv = bin[(size_t)q * nz + j];
-                if (a.conj) bv.y = -bv.y;
-                t = in_cast<TG>(bv);
-                if (i > 0) {
-                    const V yp = yin[(size_t)q * nzp + j];
-                    t.x -= c * yp.x;
-                    t.y -= c * yp.y;
-                }
-            } else {
-                const V xn = yin[(size_t)q * nzp + j];
-                t = mkc<TG>(c * xn.x, c * xn.y);
-            }
-            sT[(size_t)q * nzp + j] = t;
-        }
-        __syncthreads();
         V acc[SW_MAXOPT];
-        if (pf) {
-            const V *Gb = sG + (size_t)buf * rpc * nzp;
 #pragma unroll
-            for (int u = 0; u < SW_MAXOPT; ++u) {
-                const int o = tid + u * SW_THREADS;
-                acc[u] = mkc<TG>(TG(0), TG(0));
-                if (o < nout) acc[u] = dot_row(Gb + (size_t)(o % nrows) * nzp, sT + (size_t)(o / nrows) * nzp, nz);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
-            const V *Gi = Gs + (size_t)i * nz * nz;
-            for (int kc = 0; kc < nz; kc += SW_KC) {
-                const int kw = min(SW_KC, nz - kc);
-                for (int e = tid; e < nrows * kw; e += SW_THREADS) {
-                    const int r = e / kw, b = e % kw;
-                    sG[(size_t)r * kcp + b] = Gi[(size_t)(r0 + r) * nz + kc + b];
-                }
-                __syncthreads();
+        for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
+        if (s > 0) {
+            const V *tin = sY + (size_t)buf * R * nzp;
+            if (pf) {
+                const V *Gb = sG + (size_t)buf * rpc * nzp;
 #pragma unroll
                 for (int u = 0; u < SW_MAXOPT; ++u) {
                     const int o = tid + u * SW_THREADS;
-                    if (o < nout) {
-                        const V d = dot_row(sG + (size_t)(o % nrows) * kcp, sT + (size_t)(o / nrows) * nzp + kc, kw);
-                        acc[u].x += d.x;
-                        acc[u].y += d.y;
-                    }
+                    if (o < nout) acc[u] = dot_row(Gb + (size_t)(o % nrows) * nzp, tin + (size_t)(o / nrows) * nzp, nz);
                 }
-                __syncthreads();
+            } else {
+                const V *Gi = Gs + (size_t)i * nz * nz;
+                for (int kc = 0; kc < nz; kc += SW_KC) {
+                    const int kw = min(SW_KC, nz - kc);
+                    for (int r = wid; r < nrows; r += SW_THREADS / 32)
+                        for (int b = lane; b < kw; b += 32) sG[(size_t)r * kcp + b] = Gi[(size_t)(r0 + r) * nz + kc + b];
+                    __syncthreads();
+#pragma unroll
+                    for (int u = 0; u < SW_MAXOPT; ++u) {
+                        const int o = tid + u * SW_THREADS;
+                        if (o < nout) {
+                            const V d = dot_row(sG + (size_t)(o % nrows) * kcp, tin + (size_t)(o / nrows) * nzp + kc, kw);
+                            acc[u].x += d.x;
+                            acc[u].y += d.y;
+                        }
+                    }
+                    __syncthreads();
+                }
             }
         }
-        // new rows: y_i (forward) or x_i = y_i - G_i C x_{i+1} (backward); push them to every
-        // CTA's exchange buffer for the next step, then store / finish own rows
+        // new rows v = own - product; push C v to every CTA, store / finish own rows
         const bool push = s < last;
         V *ynext = sY + (size_t)((s + 1) & 1) * R * nzp;
         const uint32_t lbar = smem_u32(&bars[(s + 1) & 1]);
@@ -267,12 +286,15 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             const int o = tid + u * SW_THREADS;
             if (o < nout) {
                 const int r = o % nrows, q = o / nrows;
-                V v = fwd ? acc[u] : mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
+                const int j = r0 + r;
+                const V v = mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
                 if (push) {
-                    const uint32_t la = smem_u32(ynext + (size_t)q * nzp + r0 + r);
-                    for (int t = 0; t < cs; ++t) st_async(mapa_u32(la, (uint32_t)t), v, mapa_u32(lbar, (uint32_t)t));
+                    const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
+                    const V cv = mkc<TG>(c * v.x, c * v.y);
+                    const uint32_t la = smem_u32(ynext + (size_t)q * nzp + j);
+                    for (int t = 0; t < cs; ++t) st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
                 }
-                const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
+                const size_t off = (size_t)q * N + (size_t)i * nz + j;
                 if (fwd && i < nx - 1) {
                     Ys[off] = v;
                 } else {
@@ -315,15 +337,25 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     const void *fn = (const void *)line_sweep_kernel<TG>;
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
+    const size_t nzp = (size_t)padded<TG>(nz), kcp = (size_t)padded<TG>(SW_KC);
     int cs = nz / 16;
     cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
     cudaError_t e;
+    // pre-pass Y_i = G_i b_i (all lines at once)
+    {
+        const int R = nrhs < 16 ? nrhs : 16;   // PP_ROWS * R <= SW_MAXOPT * SW_THREADS
+        const size_t smem = vsz * ((size_t)R + PP_ROWS) * (size_t)padded<TG>(PP_KC);
+        e = cudaFuncSetAttribute(line_gb_prepass_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + R - 1) / R);
+        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, SW_THREADS, smem, st>>>(g, nrhs, R, G, B, Y, conj)));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
-        const size_t nzp = (size_t)padded<TG>(nz), kcp = (size_t)padded<TG>(SW_KC);
         auto smem_of = [&](int R, int pf) {
-            return ((16 + vsz * 3 * (size_t)R * nzp + 15) & ~(size_t)15) + sizeof(double2) * 2 * (size_t)nz * R +
-                   (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp);
+            return (size_t)16 + vsz * 2 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp);
         };
         int R = rchunk < 1 ? 1 : rchunk;
         if (R > nrhs) R = nrhs;
