@@ -5,6 +5,7 @@
 // combined in index order), so results are bitwise reproducible run to run.
 #include <math.h>
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "helm.h"
@@ -562,22 +563,28 @@ extern "C" helm_status fwi_hessian_vec(helm_factor_t *f, const helm_acq *acq, co
 
 // --------------------------------------------------------------- fwi_misfit_grad
 
-// shared body: u = A^{-1} E, eps = d - R u, lambda = A^{-H} R^T(W^2 eps), grad, phi
-static helm_status misfit_grad_body(helm_factor_t *f, const DevAcq &da, const double2 *data, double alpha,
-                                    double mu, double rtol, double *phi_dev, double *grad, double2 *U, double2 *Lam,
-                                    Ws &ws, int64_t *count, int *max_it) {
+// forward part: u = A^{-1} E (E = point sources, scratch supplied by the caller)
+static helm_status forward_fields(helm_factor_t *f, const DevAcq &da, double rtol, double2 *E, double2 *U,
+                                  int64_t *count, int *max_it) {
+    const helm_op *op = f->op;
+    HK(launch_sources(op->g, op->n_omega, da.n_src, da.src_xz, da.src_amp, E, op->st));
+    HS(run_solve(f, da.n_src, E, U, rtol, 0, count, max_it));
+    return HELM_OK;
+}
+
+// adjoint part: eps = d - R u, lambda = A^{-H} R^T(W^2 eps), grad phi and phi (device)
+static helm_status adjoint_grad(helm_factor_t *f, const DevAcq &da, const double2 *data, double alpha, double mu,
+                                double rtol, double *phi_dev, double *grad, const double2 *U, double2 *Lam,
+                                double2 *E, Ws &ws, int64_t *count, int *max_it) {
     const helm_op *op = f->op;
     const GridGeom &g = op->g;
     const int N = g.nx * g.nz, ns = da.n_src, nr = da.n_rec, nw = op->n_omega;
     const size_t cols = (size_t)nw * ns;
     cudaStream_t st = op->st;
     helm_status s = HELM_OK;
-    double2 *E = ws.get<double2>(cols * N, &s);
     double2 *eps = ws.get<double2>(cols * std::max(1, nr), &s);
     double *phi_col = ws.get<double>(cols + nblk(N) + 2, &s);
     if (s != HELM_OK) return s;
-    HK(launch_sources(g, nw, ns, da.src_xz, da.src_amp, E, st));
-    HS(run_solve(f, ns, E, U, rtol, 0, count, max_it));
     HELM_TRACED(K_MISFIT, st, (misfit_kernel<<<(unsigned)cols, 256, 0, st>>>(N, nr, da.tap_idx, da.tap_w, da.rec_w, U, data, eps, phi_col)));
     HL();
     HK(cudaMemsetAsync(E, 0, cols * N * sizeof(double2), st));
@@ -589,6 +596,19 @@ static helm_status misfit_grad_body(helm_factor_t *f, const DevAcq &da, const do
     HL();
     HS(reduce_sum(phi_col, (int)(cols + nblk(N)), phi_dev, st));
     return HELM_OK;
+}
+
+// u = A^{-1} e_s, eps = d - R u, lambda = A^{-H} R^T(W^2 eps), grad, phi
+static helm_status misfit_grad_body(helm_factor_t *f, const DevAcq &da, const double2 *data, double alpha,
+                                    double mu, double rtol, double *phi_dev, double *grad, double2 *U, double2 *Lam,
+                                    Ws &ws, int64_t *count, int *max_it) {
+    const helm_op *op = f->op;
+    const size_t cols = (size_t)op->n_omega * da.n_src;
+    helm_status s = HELM_OK;
+    double2 *E = ws.get<double2>(cols * op->g.nx * op->g.nz, &s);
+    if (s != HELM_OK) return s;
+    HS(forward_fields(f, da, rtol, E, U, count, max_it));
+    return adjoint_grad(f, da, data, alpha, mu, rtol, phi_dev, grad, U, Lam, E, ws, count, max_it);
 }
 
 extern "C" helm_status fwi_misfit_grad(helm_factor_t *f, const helm_acq *acq, const helm_c128 *data_dev,
@@ -645,10 +665,41 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
                             double *acc_dev /*[2]: psi, dalpha*/, double *dp_dev, double *dw_dev,
                             helm_hyper_info *info) {
     ModelState ms;
-    HS(helm_assemble(grid, m_fwi, omega, n_omega, st, &ms.op_f));
-    HS(helm_assemble(grid, m_true, omega, n_omega, st, &ms.op_t));
-    HS(helm_factor(ms.op_f, prec, &ms.fac_f));
-    HS(helm_factor(ms.op_t, prec, &ms.fac_t));
+    // the data branch (A(m') assembled, factored, u' = A(m')^{-1} e_s, d = R u') runs on
+    // its own stream from a second host thread, concurrently with A(m_fwi) and u
+    cudaStream_t st2 = nullptr;
+    HK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { if (s) cudaStreamDestroy(s); } } sg{st2};
+    helm_status s = HELM_OK;
+    Ws ws(st);
+    Ws ws2(st2);
+    int64_t count = 0, dcount = 0;
+    int max_it = 0, max_it2 = 0;
+    DevAcq da2;
+    struct AcqGuard2 { DevAcq *d; ~AcqGuard2() { acq_free(d); } } ag2{&da2};
+    double2 *Ut = nullptr, *dtmp = nullptr;
+    helm_status s2 = HELM_OK;
+    std::thread data_branch([&]() {
+        s2 = helm_assemble(grid, m_true, omega, n_omega, st2, &ms.op_t);
+        if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &ms.fac_t);
+        if (s2 == HELM_OK) s2 = acq_upload(ms.op_t, acq, &da2);
+        if (s2 != HELM_OK) return;
+        const GridGeom &gt = ms.op_t->g;
+        const size_t ct = (size_t)n_omega * da2.n_src;
+        double2 *Et = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
+        Ut = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
+        dtmp = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
+        if (s2 != HELM_OK) return;
+        s2 = forward_fields(ms.fac_t, da2, po->refine_rtol, Et, Ut, &dcount, &max_it2);
+        if (s2 != HELM_OK) return;
+        cudaError_t e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_w, Ut, dtmp, st2);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st2);
+        if (e != cudaSuccess) { helm_set_error("data branch", e); s2 = HELM_ECUDA; }
+    });
+    struct Joiner { std::thread &t; ~Joiner() { if (t.joinable()) t.join(); } } joiner{data_branch};
+    s = helm_assemble(grid, m_fwi, omega, n_omega, st, &ms.op_f);
+    if (s == HELM_OK) s = helm_factor(ms.op_f, prec, &ms.fac_f);
+    if (s != HELM_OK) { data_branch.join(); return s; }
     helm_op *op = ms.op_f;
     const GridGeom &g = op->g;
     const int N = g.nx * g.nz;
@@ -658,31 +709,29 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     const int ns = da.n_src, nr = da.n_rec;
     const size_t cols = (size_t)n_omega * ns;
     const double rtol = po->refine_rtol;
-    helm_status s = HELM_OK;
-    Ws ws(st);
     double2 *E = ws.get<double2>(cols * N, &s);
-    double2 *Ut = ws.get<double2>(cols * N, &s);
     double2 *U = ws.get<double2>(cols * N, &s);
     double2 *Lam = ws.get<double2>(cols * N, &s);
     double2 *V = ws.get<double2>(cols * N, &s);
     double2 *Z = ws.get<double2>(cols * N, &s);
-    double2 *dtmp = ws.get<double2>(cols * std::max(1, nr), &s);
+    double2 *rtmp = ws.get<double2>(cols * std::max(1, nr), &s);
     double *phi_dev = ws.get<double>(1, &s);
     double *grad = ws.get<double>(N, &s);
     double *x = ws.get<double>(N, &s), *r = ws.get<double>(N, &s), *zz = ws.get<double>(N, &s);
     double *p = ws.get<double>(N, &s), *Hp = ws.get<double>(N, &s), *rhs = ws.get<double>(N, &s);
+    if (s != HELM_OK) { data_branch.join(); return s; }
+    // u at m_fwi while the data branch runs
+    s = forward_fields(ms.fac_f, da, rtol, E, U, &count, &max_it);
+    data_branch.join();
     if (s != HELM_OK) return s;
-    int64_t count = 0, dcount = 0;
-    int max_it = 0;
-    // data u' = A(m')^{-1} e_s and d = R u'
-    HK(launch_sources(g, n_omega, ns, da.src_xz, da.src_amp, E, st));
-    HS(run_solve(ms.fac_t, ns, E, Ut, rtol, 0, &dcount, &max_it));
-    HK(launch_restrict(g, (int)cols, nr, da.tap_idx, da.tap_w, Ut, dtmp, st));
-    // u, eps, lambda (and grad phi, unused here) at m_fwi
-    HS(misfit_grad_body(ms.fac_f, da, dtmp, alpha, mu, rtol, phi_dev, grad, U, Lam, ws, &count, &max_it));
+    if (s2 != HELM_OK) return s2;
+    max_it = std::max(max_it, max_it2);
+    // eps, lambda (and grad phi, unused here) at m_fwi
+    HS(adjoint_grad(ms.fac_f, da, dtmp, alpha, mu, rtol, phi_dev, grad, U, Lam, E, ws, &count, &max_it));
+    double2 *dbuf = rtmp;
 
     auto hess = [&](const double *pv, double *out) -> helm_status {
-        return hess_apply(ms.fac_f, da, U, Lam, pv, out, E, V, Z, dtmp, alpha, mu, rtol, 0, &count, &max_it);
+        return hess_apply(ms.fac_f, da, U, Lam, pv, out, E, V, Z, dbuf, alpha, mu, rtol, 0, &count, &max_it);
     };
 
     // PCG for H rho = m' - m_fwi with P2 = Gamma(alpha0, mu), x0 = const

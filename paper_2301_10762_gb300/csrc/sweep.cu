@@ -411,7 +411,8 @@ constexpr int RES_THREADS = 256;
 
 __global__ void __launch_bounds__(RES_THREADS) residual_kernel(GridGeom g, int nrhs, const double2 *diag,
                                                                const double2 *B, const double2 *X, double2 *R,
-                                                               double *norms, int conj) {
+                                                               double *norms, int conj, double cx_in, double cx_edge,
+                                                               double cz_in, double cz_edge) {
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int k = blockIdx.x * RES_THREADS + threadIdx.x;
     const int q = blockIdx.y, s = blockIdx.z;
@@ -424,7 +425,8 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(GridGeom g, int n
         if (conj) d.y = -d.y;
         double2 xv = x[k];
         double2 ax = cmul(d, xv);
-        const double cxj = coup_x(g, j), czi = coup_z(g, i);
+        const double cxj = (j == 0 || j == nz - 1) ? cx_edge : cx_in;   // grid couplings, precomputed
+        const double czi = (i == 0 || i == nx - 1) ? cz_edge : cz_in;
         if (i > 0) { double2 v = x[k - nz]; ax.x += cxj * v.x; ax.y += cxj * v.y; }
         if (i < nx - 1) { double2 v = x[k + nz]; ax.x += cxj * v.x; ax.y += cxj * v.y; }
         if (j > 0) { double2 v = x[k - 1]; ax.x += czi * v.x; ax.y += czi * v.y; }
@@ -461,7 +463,7 @@ cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double
                             const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st) {
     const int N = g.nx * g.nz;
     dim3 grid((N + RES_THREADS - 1) / RES_THREADS, nrhs, n_sys);
-    HELM_TRACED(K_RESIDUAL, st, (residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R, norms, conj)));
+    HELM_TRACED(K_RESIDUAL, st, (residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R, norms, conj, coup_x(g, 1), coup_x(g, 0), coup_z(g, 1), coup_z(g, 0))));
     return cudaGetLastError();
 }
 

@@ -1,0 +1,58 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+The FWI-step workload (128 x 128, omega in {5, 10, 15}, 16 sources) is solved with the
+same factor precision and refinement tolerance as the benchmark step, and every column is
+compared with the CPU oracle; the 256 x 256 mixed-precision workload (8 frequencies, 64
+sources) is compared on sampled frequencies.  Tolerances: 1e-9 (FP64 path), 1e-8 (mixed
+path), relative error per column."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import helmholtz as H
+
+hm = pytest.importorskip("paper_2301_10762_gb300.helm")
+
+pytestmark = pytest.mark.gpu
+
+# refinement tolerance of the benchmark step (bench.py)
+BENCH_RTOL = 1e-10
+
+
+def _colerr(X, ref):
+    return float(np.max(np.linalg.norm(X - ref, axis=-1) / np.linalg.norm(ref, axis=-1)))
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-8), (0, 1e-9)])
+def test_fwi_step_workload_every_column(prec, tol):
+    w = W.config_hyper_step(128)
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
+    f = hm.helm_factor(op, prec)
+    acq = hm.Acq.from_workload(w.acq)
+    B = hm.helm_sources(op, acq)
+    X, info = hm.helm_solve(f, B, rtol=BENCH_RTOL, max_iter=40)
+    Y, _ = hm.helm_adjoint_solve(f, B, rtol=BENCH_RTOL, max_iter=40)
+    E = H.source_vectors(g, w.acq.src_xz)
+    Xc, Yc = X.cpu().numpy(), Y.cpu().numpy()
+    for q, om in enumerate(w.omegas):
+        fo = H.Factor(H.helmholtz_matrix(g, w.m, om))
+        assert _colerr(Xc[q], fo.solve(E)) <= tol
+        assert _colerr(Yc[q], fo.adjoint_solve(E)) <= tol
+
+
+def test_mixed_256_workload_sampled_frequencies():
+    w = W.config_mixed(256)
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
+    f = hm.helm_factor(op, hm.HELM_MIXED)
+    B = hm.helm_sources(op, hm.Acq.from_workload(w.acq))
+    X, info = hm.helm_solve(f, B, rtol=1e-10, max_iter=40)
+    assert info["max_relres"] <= 1e-10
+    E = H.source_vectors(g, w.acq.src_xz)
+    Xc = X.cpu().numpy()
+    for q in (0, len(w.omegas) - 1):
+        fo = H.Factor(H.helmholtz_matrix(g, w.m, w.omegas[q]))
+        sel = np.arange(0, w.acq.n_src, 7)
+        assert _colerr(Xc[q][sel], fo.solve(E[sel])) <= 1e-8
