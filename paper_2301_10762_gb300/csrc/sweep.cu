@@ -15,12 +15,14 @@
 // Mixed precision: TG = float keeps the factor and the working vector in complex FP32;
 // the input is an FP64 residual and the result is added to the FP64 iterate in the
 // final pass (x += A~^{-1} r).  TG = double is the plain FP64 path (Y aliases X).
+#include <algorithm>
 #include "kernels.h"
 #include "trace.h"
 
 namespace helm {
 
 constexpr int SW_THREADS = 256;
+constexpr int PP_THREADS = 256;
 constexpr int SW_KC = 64;      // K chunk of the streamed (non-prefetched) G path
 constexpr int SW_MAXOPT = 2;   // outputs per thread (rows_per_cta * R <= 2 * 256)
 constexpr size_t SW_SMEM_MAX = 200 * 1024;
@@ -28,7 +30,7 @@ constexpr uint32_t SW_WAIT_TRIES = 1u << 22;   // bounded mbarrier wait (seconds
 
 template <typename TG> struct SweepArgs {
     GridGeom g;
-    int nrhs, R, cs, n_chunks, prefetch;
+    int nrhs, R, cs, n_chunks, prefetch, tpo;   // tpo: threads per output (K split), power of 2
     const cx_t<TG> *G;   // [n_sys][nx][nz][nz]
     const double2 *B;    // [n_sys][nrhs][N]
     double2 *X;          // [n_sys][nrhs][N]
@@ -77,6 +79,41 @@ __device__ __forceinline__ double2 dot_row(const double2 *g, const double2 *t, i
     return make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
 }
 
+// sum over the pairs p = part, part + tpo, ... of g[2p..2p+1] t[2p..2p+1] (complex FP32, both
+// operands 16-byte aligned; consecutive parts read adjacent 16-byte words, so the threads that
+// share an output never collide on a bank), plus the odd tail element for part 0
+__device__ __forceinline__ float2 dot_row_il(const float2 *g, const float2 *t, int n, int part, int tpo) {
+    const float4 *g4 = reinterpret_cast<const float4 *>(g);
+    const float4 *t4 = reinterpret_cast<const float4 *>(t);
+    const int np = n >> 1;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    int p = part;
+    for (; p + tpo < np; p += 2 * tpo) {
+        const float4 gA = g4[p], tA = t4[p], gB = g4[p + tpo], tB = t4[p + tpo];
+        cfma(a0, make_float2(gA.x, gA.y), make_float2(tA.x, tA.y));
+        cfma(a1, make_float2(gA.z, gA.w), make_float2(tA.z, tA.w));
+        cfma(a2, make_float2(gB.x, gB.y), make_float2(tB.x, tB.y));
+        cfma(a3, make_float2(gB.z, gB.w), make_float2(tB.z, tB.w));
+    }
+    if (p < np) {
+        const float4 gA = g4[p], tA = t4[p];
+        cfma(a0, make_float2(gA.x, gA.y), make_float2(tA.x, tA.y));
+        cfma(a1, make_float2(gA.z, gA.w), make_float2(tA.z, tA.w));
+    }
+    if ((n & 1) && part == 0) cfma(a2, g[n - 1], t[n - 1]);
+    return make_float2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+}
+__device__ __forceinline__ double2 dot_row_il(const double2 *g, const double2 *t, int n, int part, int tpo) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+    int b = part;
+    for (; b + tpo < n; b += 2 * tpo) {
+        cfma(a0, g[b], t[b]);
+        cfma(a1, g[b + tpo], t[b + tpo]);
+    }
+    if (b < n) cfma(a0, g[b], t[b]);
+    return make_double2(a0.x + a1.x, a0.y + a1.y);
+}
+
 // line handled by global step s: forward s = 0..nx-1 -> line s; backward s = nx..2nx-2 -> line 2nx-2-s
 __device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 * nx - 2 - s; }
 
@@ -87,7 +124,7 @@ __device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 
 constexpr int PP_ROWS = 32;
 constexpr int PP_KC = 64;
 template <typename TG>
-__global__ void __launch_bounds__(SW_THREADS) line_gb_prepass_kernel(GridGeom g, int nrhs, int R, const cx_t<TG> *G,
+__global__ void __launch_bounds__(PP_THREADS) line_gb_prepass_kernel(GridGeom g, int nrhs, int R, const cx_t<TG> *G,
                                                                    const double2 *B, cx_t<TG> *Y, int conj) {
     using V = cx_t<TG>;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
@@ -112,18 +149,18 @@ __global__ void __launch_bounds__(SW_THREADS) line_gb_prepass_kernel(GridGeom g,
     for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
     for (int kc = 0; kc < nz; kc += PP_KC) {
         const int kw = min(PP_KC, nz - kc);
-        for (int q = wid; q < Rc; q += SW_THREADS / 32)
+        for (int q = wid; q < Rc; q += PP_THREADS / 32)
             for (int j = lane; j < kw; j += 32) {
                 double2 bv = Bs[(size_t)q * N + kc + j];
                 if (conj) bv.y = -bv.y;
                 sb[(size_t)q * kcp + j] = in_cast<TG>(bv);
             }
-        for (int r = wid; r < nrows; r += SW_THREADS / 32)
+        for (int r = wid; r < nrows; r += PP_THREADS / 32)
             for (int j = lane; j < kw; j += 32) sg[(size_t)r * kcp + j] = Gi[(size_t)r * nz + kc + j];
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = tid + u * SW_THREADS;
+            const int o = tid + u * PP_THREADS;
             if (o < nrows * Rc) {
                 const V d = dot_row(sg + (size_t)(o % nrows) * kcp, sb + (size_t)(o / nrows) * kcp, kw);
                 acc[u].x += d.x;
@@ -135,7 +172,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_gb_prepass_kernel(GridGeom g,
     V *Ys = Y + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz + r0;
 #pragma unroll
     for (int u = 0; u < SW_MAXOPT; ++u) {
-        const int o = tid + u * SW_THREADS;
+        const int o = tid + u * PP_THREADS;
         if (o < nrows * Rc) Ys[(size_t)(o / nrows) * N + (o % nrows)] = acc[u];
     }
 }
@@ -175,6 +212,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);           // [2]
     V *sY = reinterpret_cast<V *>(smem_raw + 16);                       // [2][R][nzp]  C * (line vector)
     V *sG = sY + 2 * (size_t)R * nzp;                                   // pf: [2][rpc][nzp]; else [rpc][kcp]
+    V *sOwn = sG + (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp);   // [2][R][rpc]: own rows of line i
     __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
@@ -184,6 +222,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     const uint32_t phase_bytes = (uint32_t)(nz * Rc * sizeof(V));
     const TG c_in = (TG)coup_x(g, 1), c_edge = (TG)coup_x(g, 0);
     const int lane = tid & 31, wid = tid >> 5;
+    const int tpo = a.tpo, ngrp = SW_THREADS / tpo;
+    const int pr = tid / tpo, part = tid % tpo;       // output group, K part
+    const bool fp32 = sizeof(TG) == 4;
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -199,8 +240,15 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     }
 
     auto prefetch = [&](int s) {
-        if (!pf || s > last || s == 0) return;   // step 0 needs no product
+        if (s > last) return;
         const int i = step_line(s, nx);
+        {   // own rows of line i: G_i b_i (forward, from the pre-pass) or y_i (backward)
+            V *dst = sOwn + (size_t)(s & 1) * R * rpc;
+            for (int q = wid; q < Rc; q += SW_THREADS / 32)
+                for (int r = lane; r < nrows; r += 32)
+                    cp_async_elem(dst + (size_t)q * rpc + r, Ys + (size_t)q * N + (size_t)i * nz + r0 + r);
+        }
+        if (!pf || s == 0) return;   // step 0 needs no product
         const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
         V *dst = sG + (size_t)(s & 1) * rpc * nzp;
         if (sizeof(TG) == 4 && (nz & 1) == 0) {
@@ -212,6 +260,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
     };
 
+    prefetch(0);
+    cp_async_commit();
     for (int s = 0; s <= last; ++s) {
         const int i = step_line(s, nx);
         const bool fwd = s < nx;
@@ -226,23 +276,24 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
         // own rows of line i loaded early: G_i b_i (forward) or y_i (backward), and the
         // FP64 iterate where the mixed epilogue accumulates
-        V yown[SW_MAXOPT];
         double2 xold[SW_MAXOPT];
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = tid + u * SW_THREADS;
-            yown[u] = mkc<TG>(TG(0), TG(0));
+            const int o = pr + u * ngrp;
             xold[u] = make_double2(0.0, 0.0);
-            if (o < nout) {
-                const int r = o % nrows, q = o / nrows;
-                const size_t off = (size_t)q * N + (size_t)i * nz + r0 + r;
-                yown[u] = Ys[off];
-                if (a.accumulate && (!fwd || i == nx - 1)) xold[u] = Xs[off];
-            }
+            if (!fp32 && o < nout && a.accumulate && (!fwd || i == nx - 1))
+                xold[u] = Xs[(size_t)(o / nrows) * N + (size_t)i * nz + r0 + (o % nrows)];
         }
-        if (s > 0) cp_async_wait<0>();
+        cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
         if (s_abort) return;
+        V yown[SW_MAXOPT];
+#pragma unroll
+        for (int u = 0; u < SW_MAXOPT; ++u) {
+            const int o = pr + u * ngrp;
+            yown[u] = (o < nout) ? sOwn[(size_t)(s & 1) * R * rpc + (size_t)(o / nrows) * rpc + (o % nrows)]
+                                 : mkc<TG>(TG(0), TG(0));
+        }
         prefetch(s + 1);   // into the staging buffer that step s - 1 used
         cp_async_commit();
         V acc[SW_MAXOPT];
@@ -254,8 +305,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 const V *Gb = sG + (size_t)buf * rpc * nzp;
 #pragma unroll
                 for (int u = 0; u < SW_MAXOPT; ++u) {
-                    const int o = tid + u * SW_THREADS;
-                    if (o < nout) acc[u] = dot_row(Gb + (size_t)(o % nrows) * nzp, tin + (size_t)(o / nrows) * nzp, nz);
+                    const int o = pr + u * ngrp;
+                    if (o < nout)
+                        acc[u] = dot_row_il(Gb + (size_t)(o % nrows) * nzp, tin + (size_t)(o / nrows) * nzp, nz, part, tpo);
                 }
             } else {
                 const V *Gi = Gs + (size_t)i * nz * nz;
@@ -266,9 +318,10 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                     __syncthreads();
 #pragma unroll
                     for (int u = 0; u < SW_MAXOPT; ++u) {
-                        const int o = tid + u * SW_THREADS;
+                        const int o = pr + u * ngrp;
                         if (o < nout) {
-                            const V d = dot_row(sG + (size_t)(o % nrows) * kcp, tin + (size_t)(o / nrows) * nzp + kc, kw);
+                            const V d = dot_row_il(sG + (size_t)(o % nrows) * kcp, tin + (size_t)(o / nrows) * nzp + kc,
+                                                   kw, part, tpo);
                             acc[u].x += d.x;
                             acc[u].y += d.y;
                         }
@@ -277,13 +330,22 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 }
             }
         }
-        // new rows v = own - product; push C v to every CTA, store / finish own rows
+        // the K parts of every output meet in adjacent lanes
+        for (int m = 1; m < tpo; m <<= 1) {
+#pragma unroll
+            for (int u = 0; u < SW_MAXOPT; ++u) {
+                acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, m);
+                acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, m);
+            }
+        }
+        // new rows v = own - product; push C v to every CTA (targets split over the pair),
+        // store / finish own rows
         const bool push = s < last;
         V *ynext = sY + (size_t)((s + 1) & 1) * R * nzp;
         const uint32_t lbar = smem_u32(&bars[(s + 1) & 1]);
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = tid + u * SW_THREADS;
+            const int o = pr + u * ngrp;
             if (o < nout) {
                 const int r = o % nrows, q = o / nrows;
                 const int j = r0 + r;
@@ -292,21 +354,40 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                     const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
                     const V cv = mkc<TG>(c * v.x, c * v.y);
                     const uint32_t la = smem_u32(ynext + (size_t)q * nzp + j);
-                    for (int t = 0; t < cs; ++t) st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
+                    for (int t = part; t < cs; t += tpo)
+                        st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
                 }
-                const size_t off = (size_t)q * N + (size_t)i * nz + j;
-                if (fwd && i < nx - 1) {
-                    Ys[off] = v;
-                } else {
-                    double2 d = make_double2((double)v.x, (double)v.y);
-                    if (a.conj) d.y = -d.y;
-                    if (a.accumulate) { d.x += xold[u].x; d.y += xold[u].y; }
-                    Xs[off] = d;
+                if (part == 0) {
+                    const size_t off = (size_t)q * N + (size_t)i * nz + j;
+                    if (fp32 || (fwd && i < nx - 1)) {
+                        Ys[off] = v;   // mixed: the FP64 promotion runs in accumulate_kernel
+                    } else {
+                        double2 d = make_double2((double)v.x, (double)v.y);
+                        if (a.conj) d.y = -d.y;
+                        if (a.accumulate) { d.x += xold[u].x; d.y += xold[u].y; }
+                        Xs[off] = d;
+                    }
                 }
             }
         }
     }
     cp_async_wait<0>();
+}
+
+
+// Mixed path: X = (accumulate ? X : 0) + conj?(delta), delta the complex-FP32 solution of the
+// sweep (FP64 promotion kept out of the sweep's critical path).
+__global__ void accumulate_kernel(size_t n, const float2 *Y, double2 *X, int conj, int accumulate) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const float2 y = Y[e];
+        double2 d = make_double2((double)y.x, conj ? -(double)y.y : (double)y.y);
+        if (accumulate) {
+            const double2 x = X[e];
+            d.x += x.x;
+            d.y += x.y;
+        }
+        X[e] = d;
+    }
 }
 
 // Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
@@ -343,21 +424,26 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     cudaError_t e;
     // pre-pass Y_i = G_i b_i (all lines at once)
     {
-        const int R = nrhs < 16 ? nrhs : 16;   // PP_ROWS * R <= SW_MAXOPT * SW_THREADS
+        const int R = nrhs < 16 ? nrhs : 16;   // PP_ROWS * R <= SW_MAXOPT * PP_THREADS
         const size_t smem = vsz * ((size_t)R + PP_ROWS) * (size_t)padded<TG>(PP_KC);
         e = cudaFuncSetAttribute(line_gb_prepass_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + R - 1) / R);
-        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, SW_THREADS, smem, st>>>(g, nrhs, R, G, B, Y, conj)));
+        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, PP_THREADS, smem, st>>>(g, nrhs, R, G, B, Y, conj)));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
         auto smem_of = [&](int R, int pf) {
-            return (size_t)16 + vsz * 2 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp);
+            return (size_t)16 + vsz * 2 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp) +
+                   vsz * 2 * (size_t)R * rpc;
         };
-        int R = rchunk < 1 ? 1 : rchunk;
+        // right-hand sides per cluster: aim at ~64 outputs per CTA, so that a line step's
+        // product is spread over more clusters (the chain is latency bound, the GPU idle)
+        int R = 1;
+        while (R * 2 <= 16 && rpc * R * 2 <= 64) R *= 2;
+        if (rchunk > 0 && R > rchunk) R = rchunk;
         if (R > nrhs) R = nrhs;
         while (R > 1 && rpc * R > SW_MAXOPT * SW_THREADS) R = (R + 1) / 2;
         int pf = 1;
@@ -379,7 +465,9 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             }
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, G, B, X, Y, conj, accumulate, status};
+        int tpo = 1;
+        while (tpo < 8 && rpc * R * tpo * 2 <= SW_THREADS) tpo *= 2;
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, G, B, X, Y, conj, accumulate, status};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * cs, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);
@@ -395,7 +483,11 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         cudaError_t le = cudaSuccess;
         HELM_TRACED(sizeof(TG) == 8 ? K_SWEEP64 : K_SWEEP32, st,
                     (le = cudaLaunchKernelEx(&cfg, line_sweep_kernel<TG>, a)));
-        return le;
+        if (le != cudaSuccess || sizeof(TG) == 8) return le;
+        const size_t n = (size_t)n_sys * nrhs * g.nx * g.nz;
+        const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+        HELM_TRACED(K_ACCUM, st, (accumulate_kernel<<<blocks, 256, 0, st>>>(n, (const float2 *)Y, X, conj, accumulate)));
+        return cudaGetLastError();
     }
 }
 
