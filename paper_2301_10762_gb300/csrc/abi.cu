@@ -138,10 +138,10 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
     }
     if (prec == HELM_FP64)
         e = launch_line_factor<double>(g, op->n_omega, op->diag, (double2 *)f->G, (double2 *)f->xch, op->status,
-                                       f->cs, op->st);
+                                       f->cs, op->st, &f->mid);
     else
         e = launch_line_factor<float>(g, op->n_omega, op->diag, (float2 *)f->G, (float2 *)f->xch, op->status,
-                                      f->cs, op->st);
+                                      f->cs, op->st, &f->mid);
     int st_host = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
@@ -229,7 +229,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     helm_status s;
     if (info) { info->iters = 0; info->max_relres = -1.0; }
     if (f->prec == HELM_FP64) {
-        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status, op->st);
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status, op->st, f->mid);
         if (e != cudaSuccess) { helm_set_error("sweep fp64", e); return HELM_ECUDA; }
         if (info) {
             info->iters = 1;
@@ -244,7 +244,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     // mixed: x = A~^{-1} b, then x += A~^{-1}(b - A x) until ||b - A x|| / ||b|| <= rtol
     if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
     if (max_iter < 1) max_iter = 1;
-    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, rchunk, op->status, op->st);
+    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, rchunk, op->status, op->st, f->mid);
     if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
     int it = 1;
     double rel = INFINITY;
@@ -255,7 +255,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
         if ((s = read_relres(f, nrhs, &rel)) != HELM_OK) return s;
         if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
         e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, f->r, X, f->y, conj, 1, rchunk,
-                                     op->status, op->st);
+                                     op->status, op->st, f->mid);
         if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
         ++it;
     }

@@ -21,6 +21,7 @@ struct helm_factor {
     helm_op *op = nullptr;
     helm_prec prec = HELM_FP64;
     int cs = 1;
+    int mid = 0;           // middle line of the (twisted) line factorisation
     void *G = nullptr;     // [n_omega][nx][nz][nz] complex (FP64 or FP32)
     void *xch = nullptr;   // factor exchange slots
     // solve scratch, sized for `cap` right-hand sides per frequency

@@ -156,3 +156,15 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 }  // namespace helm
+
+namespace helm {
+// bulk copy (TMA engine) of `bytes` from this CTA's shared memory to another CTA's shared
+// memory (raddr, from mapa), completing `bytes` of the transaction count of the mbarrier at
+// remote address rbar.  bytes: multiple of 16; both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_copy_s2s(uint32_t raddr, uint32_t laddr, uint32_t bytes, uint32_t rbar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(raddr), "r"(laddr), "r"(bytes), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+}  // namespace helm

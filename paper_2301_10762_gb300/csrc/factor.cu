@@ -19,6 +19,7 @@
 // W_:k through a double-buffered exchange slot in global memory (L2 resident); one
 // hardware cluster barrier per block step orders publish and use.  Each CTA only ever
 // touches its own columns of W, which lives in the factor storage itself (G_i slot).
+#include <stdlib.h>
 #include "kernels.h"
 #include "trace.h"
 
@@ -38,7 +39,8 @@ template <typename T> struct FactorArgs {
     cx_t<T> *G;           // [n_sys][nx][nz][nz]
     cx_t<T> *xch;         // [n_sys][factor_xch_elems(nz)]
     int *status;
-    int cs;
+    int cs;               // CTAs per team (cluster = teams * cs)
+    int mid;              // middle line of the twisted factorisation (nx - 1: one-sided)
 };
 
 // In-place Gauss-Jordan inversion of the kb x kb block M (row stride NB, shared memory)
@@ -245,12 +247,19 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_kernel(FactorArgs<T> 
 // block step publishes them.  Receive buffers alternate, so the owner of step t+1 never
 // overwrites data a slower CTA still reads at step t.
 
+template <typename T> __device__ __forceinline__ T recip(T x);
+template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double recip<double>(double x) { return __drcp_rn(x); }
+
 // 16 x 16 inverse (kb x kb block padded with the identity) of M (shared, row stride ld)
-// by one warp; lane (r, h) holds row r, column half h of [M | I].  Writes the inverse to
-// P (row stride NB, shared).  Returns false in every lane if a pivot was zero or not
-// finite.
+// by one warp; lane (r, h) holds row r, column half h of [M | I].  Partial pivoting
+// without row swaps: the pivot of column q is found by one warp-wide max reduction over
+// a key (|a_rq|^2 with its low mantissa bits replaced by the row), the scaled pivot row is
+// broadcast through shared memory (srow, 32 entries), and the pivot order is applied when
+// the inverse is written to P (row stride NB, shared).  Returns false if a pivot was zero
+// or not finite.
 template <typename T>
-__device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
+__device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P, cx_t<T> *srow) {
     using V = cx_t<T>;
     const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4;
     V a[16];
@@ -264,40 +273,36 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
     bool ok = true;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        T v = (h == 0 && !((used >> r) & 1u)) ? a[q].x * a[q].x + a[q].y * a[q].y : T(-1);
-        int idx = r;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, v, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-        }
-        const int p = idx;
-        if (!(v > T(0)) || !isfinite(v)) ok = false;
+        const float mag = fminf((float)(a[q].x * a[q].x + a[q].y * a[q].y), 3.0e38f);
+        const unsigned key =
+            (h == 0 && !((used >> r) & 1u)) ? ((__float_as_uint(mag) & ~0xFu) | (unsigned)(15 - r)) : 0u;
+        const unsigned best = __reduce_max_sync(0xffffffffu, key);
+        const int p = 15 - (int)(best & 0xFu);
+        if ((best >> 4) == 0u || (best >> 23) >= 255u) ok = false;
         used |= 1u << p;
         if (r == p) qinv = q;
-        V pv;
+        V pv, f;
         pv.x = __shfl_sync(0xffffffffu, a[q].x, p);
         pv.y = __shfl_sync(0xffffffffu, a[q].y, p);
-        const T den = pv.x * pv.x + pv.y * pv.y;
-        const V inv = ok ? mkc<T>(pv.x / den, -pv.y / den) : mkc<T>(T(1), T(0));
-        if (r == p) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) a[j] = cmul(a[j], inv);
-        }
-        V f;
         f.x = __shfl_sync(0xffffffffu, a[q].x, r);
         f.y = __shfl_sync(0xffffffffu, a[q].y, r);
-        const int src = p + 16 * h;
+        const T rd = recip<T>(pv.x * pv.x + pv.y * pv.y);
+        const V inv = ok ? mkc<T>(pv.x * rd, -pv.y * rd) : mkc<T>(T(1), T(0));
+        if (r == p) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                a[j] = cmul(a[j], inv);
+                srow[h * 16 + j] = a[j];
+            }
+        }
+        __syncwarp();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            V pj;
-            pj.x = __shfl_sync(0xffffffffu, a[j].x, src);
-            pj.y = __shfl_sync(0xffffffffu, a[j].y, src);
+            const V pj = srow[h * 16 + j];
             if (r != p) cfms(a[j], f, pj);
         }
+        __syncwarp();
     }
-    // inverse row q = right half of the row chosen as pivot at step q
     if (h == 1 && qinv < kb) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -309,13 +314,23 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
 __device__ __forceinline__ void st_cluster_c(uint32_t addr, float2 v) { st_cluster(addr, v); }
 __device__ __forceinline__ void st_cluster_c(uint32_t addr, double2 v) { st_cluster(addr, v); }
 
+// Twisted variant: the cluster holds two teams of `cs` CTAs.  The left team runs the
+// Schur recurrence from the absorbing boundary x = 0 (S_0 = D_0, S_i = D_i - C G_{i-1} C,
+// i < m), the right team from x = L (S_{nx-1} = D_{nx-1}, S_i = D_i - C G_{i+1} C, i > m),
+// concurrently, and the left team then factors the middle line
+//     S_m = D_m - C G_{m-1} C - C G_{m+1} C.
+// The factor stores G_i = S_i^{-1} for every line (left inverses for i < m, right ones for
+// i > m).  With teams == 1 and m = nx - 1 this is the plain one-sided factorisation.
+// The two teams only meet at the middle line (G_{m+1} is read back from global memory);
+// the panel exchange of each block step stays inside a team.
 template <typename T>
 __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArgs<T> a) {
     using V = cx_t<T>;
     const GridGeom g = a.g;
     const int nx = g.nx, nz = g.nz, cs = a.cs;
     const int tid = threadIdx.x;
-    const int rank = (int)cluster_ctarank();
+    const int crank = (int)cluster_ctarank();
+    const int team = crank / cs, rank = crank % cs;
     const int sys = (int)cluster_id_x();
     const int p = (nz + NB - 1) / NB;
     const int bpc = (p + cs - 1) / cs;
@@ -325,46 +340,74 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArg
     const int ncb = (ncol + NB - 1) / NB;     // own column blocks
     const int ldw = bpc * NB + 1;             // padded row stride of the slab
     const int ldr = bpc * NB + 1;
+    const int m = a.mid;                      // middle line (nx - 1 without a right team)
+    const int lenR = nx - 1 - m;              // lines of the right team
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sW = reinterpret_cast<V *>(smem_raw);                  // nz x ldw   own columns of S_i / G_i
-    V *sRecv = sW + (size_t)nz * ldw;                         // 2 x (nz*NB + NB*NB)
+    const size_t recv_off = ((size_t)nz * ldw * sizeof(V) + 15) & ~(size_t)15;
+    V *sRecv = reinterpret_cast<V *>(smem_raw + recv_off);    // 2 x (nz*NB + NB*NB), 16-byte aligned
     const size_t recv_elems = (size_t)nz * NB + NB * NB;
     V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
-    V *sPst = sR + (size_t)NB * ldr;                          // NB x NB  owner's block inverse
     __shared__ int s_bad;
+    __shared__ __align__(8) uint64_t bars[2];                 // panel arrival, one per receive buffer
+    __shared__ __align__(16) V s_prow[32];                    // pivot row of the block inversion
 
     V *Gs = a.G + (size_t)sys * nx * nz * nz;
     const double2 *dg = a.diag + (size_t)sys * nx * nz;
     const T cx_in = (T)coup_x(g, 1), cx_edge = (T)coup_x(g, 0);
     const T cz_in = (T)coup_z(g, 1), cz_edge = (T)coup_z(g, 0);
     const int cl = tid & (NB - 1), rw = tid >> 4;   // (row group, column) of the 2D loops
-    if (tid == 0) s_bad = 0;
+    if (tid == 0) {
+        s_bad = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init_cluster();
+    }
+    __syncthreads();
+    const uint32_t panel_bytes = (uint32_t)(recv_elems * sizeof(V));
+    uint32_t ph0 = 0, ph1 = 0;   // completed panel phases per receive buffer (consumer side)
     int t = 0;
 
-    for (int i = 0; i < nx; ++i) {
-        const T cz = (i == 0 || i == nx - 1) ? cz_edge : cz_in;
-        // S_i = D_i - C G_{i-1} C on the own columns (G_{i-1} is the slab itself)
-        for (int cb = 0; cb < ncb; ++cb) {
-            const int cc = cb * NB + cl, c = c0 + cc;
-            if (c >= c1) continue;
-            const T cxc = (c == 0 || c == nz - 1) ? cx_edge : cx_in;
-            for (int r = rw; r < nz; r += FAC_THREADS / NB) {
-                const T cxr = (r == 0 || r == nz - 1) ? cx_edge : cx_in;
-                V v = mkc<T>(T(0), T(0));
-                if (i > 0) {
-                    const V gp = sW[(size_t)r * ldw + cc];
-                    const T s = cxr * cxc;
-                    v = mkc<T>(-s * gp.x, -s * gp.y);
+    for (int slot = 0; slot <= m; ++slot) {
+        // line of this team at this slot (-1: idle); the left team ends with the middle line
+        int i = -1, iprev = -1;
+        if (team == 0) { i = slot; iprev = slot - 1; }
+        else if (slot < lenR) { i = nx - 1 - slot; iprev = (slot == 0) ? -1 : i + 1; }
+        const bool active = i >= 0;
+        const bool middle = (team == 0 && slot == m && lenR > 0);
+        // the previous slot's G write-out of both teams is visible (the middle line reads G_{m+1})
+        cluster_sync_all();
+        if (active) {
+            const T cz = (i == 0 || i == nx - 1) ? cz_edge : cz_in;
+            const V *Gright = Gs + (size_t)(m + 1) * nz * nz;   // G_{m+1}, written by the right team
+            // S_i = D_i - C G_prev C (the slab holds G_prev), minus C G_{m+1} C on the middle line
+            for (int cb = 0; cb < ncb; ++cb) {
+                const int cc = cb * NB + cl, c = c0 + cc;
+                if (c >= c1) continue;
+                const T cxc = (c == 0 || c == nz - 1) ? cx_edge : cx_in;
+                for (int r = rw; r < nz; r += FAC_THREADS / NB) {
+                    const T cxr = (r == 0 || r == nz - 1) ? cx_edge : cx_in;
+                    const T sc = cxr * cxc;
+                    V v = mkc<T>(T(0), T(0));
+                    if (iprev >= 0) {
+                        const V gp = sW[(size_t)r * ldw + cc];
+                        v = mkc<T>(-sc * gp.x, -sc * gp.y);
+                    }
+                    if (middle) {
+                        const V gr = ldcg(Gright + (size_t)r * nz + c);
+                        v.x -= sc * gr.x;
+                        v.y -= sc * gr.y;
+                    }
+                    if (r == c) {
+                        const V d = from_c128<T>(dg[(size_t)i * nz + r]);
+                        v.x += d.x;
+                        v.y += d.y;
+                    } else if (r == c + 1 || c == r + 1) {
+                        v.x += cz;
+                    }
+                    sW[(size_t)r * ldw + cc] = v;
                 }
-                if (r == c) {
-                    const V d = from_c128<T>(dg[(size_t)i * nz + r]);
-                    v.x += d.x;
-                    v.y += d.y;
-                } else if (r == c + 1 || c == r + 1) {
-                    v.x += cz;
-                }
-                sW[(size_t)r * ldw + cc] = v;
             }
         }
         __syncthreads();
@@ -372,81 +415,95 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArg
         for (int k = 0; k < p; ++k, ++t) {
             const int k0 = k * NB, kb = min(NB, nz - k0);
             const int owner = k / bpc;
-            V *recvU = sRecv + (size_t)(t & 1) * recv_elems;   // nz x NB: old column panel W_:k
+            const int buf = t & 1;
+            V *recvU = sRecv + (size_t)buf * recv_elems;        // nz x NB: old column panel W_:k
             V *recvP = recvU + (size_t)nz * NB;                 // NB x NB: inverse of W_kk
-            if (rank == owner) {
-                const int kc = k0 - c0;
-                if (tid < 32) {
-                    if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, sPst) && tid == 0) s_bad = 1;
+            // every CTA of the cluster is done with step t - 1 (and so with this buffer's last use)
+            cluster_sync_all();
+            if (active) {
+                if (rank == owner) {
+                    const int kc = k0 - c0;
+                    // stage the old column panel and the block inverse contiguously, then let the
+                    // bulk-copy engine deliver them to the other CTAs of the team
+                    for (int r = rw; r < nz; r += FAC_THREADS / NB)
+                        if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
+                    if (tid < 32) {
+                        if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP, s_prow) && tid == 0) s_bad = 1;
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        fence_proxy_async_smem();
+                        const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
+                        for (int d = 0; d < cs; ++d)
+                            if (d != rank) {
+                                const uint32_t dst = (uint32_t)(team * cs + d);
+                                bulk_copy_s2s(mapa_u32(src, dst), src, panel_bytes, mapa_u32(lbar, dst));
+                            }
+                    }
+                } else {
+                    if (tid == 0) {
+                        mbar_arrive_expect_tx(&bars[buf], panel_bytes);
+                        const uint32_t par = buf ? ph1 : ph0;
+                        if (!mbar_wait_bounded(&bars[buf], par, 1u << 22)) atomicOr(a.status, ST_TIMEOUT);
+                    }
+                    if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+                    __syncthreads();
                 }
-                // push the old column panel to every CTA while warp 0 inverts
-                const uint32_t lu = smem_u32(recvU);
-                for (int r = rw; r < nz; r += FAC_THREADS / NB) {
-                    if (cl < kb) {
-                        const V v = sW[(size_t)r * ldw + kc + cl];
-                        const uint32_t off = (uint32_t)(((size_t)r * NB + cl) * sizeof(V));
-                        for (int dst = 0; dst < cs; ++dst) st_cluster_c(mapa_u32(lu + off, (uint32_t)dst), v);
+                // Rk = P W[k rows, own columns outside block k]
+                for (int cb = 0; cb < ncb; ++cb) {
+                    const int cc = cb * NB + cl, c = c0 + cc;
+                    if (c >= c1 || (c >= k0 && c < k0 + kb)) continue;
+                    for (int q = rw; q < kb; q += FAC_THREADS / NB) {
+                        V acc = mkc<T>(T(0), T(0));
+#pragma unroll 4
+                        for (int u = 0; u < kb; ++u) cfma(acc, recvP[q * NB + u], sW[(size_t)(k0 + u) * ldw + cc]);
+                        sR[q * ldr + cc] = acc;
                     }
                 }
                 __syncthreads();
-                const uint32_t lp = smem_u32(recvP);
-                if (rw < kb && cl < kb) {
-                    const V v = sPst[rw * NB + cl];
-                    const uint32_t off = (uint32_t)((rw * NB + cl) * sizeof(V));
-                    for (int dst = 0; dst < cs; ++dst) st_cluster_c(mapa_u32(lp + off, (uint32_t)dst), v);
-                }
-            }
-            cluster_sync_all();
-            // Rk = P W[k rows, own columns outside block k]
-            for (int cb = 0; cb < ncb; ++cb) {
-                const int cc = cb * NB + cl, c = c0 + cc;
-                if (c >= c1 || (c >= k0 && c < k0 + kb)) continue;
-                for (int q = rw; q < kb; q += FAC_THREADS / NB) {
-                    V acc = mkc<T>(T(0), T(0));
+                for (int cb = 0; cb < ncb; ++cb) {
+                    const int cc = cb * NB + cl, c = c0 + cc;
+                    if (c >= c1) continue;
+                    const bool inblk = (c >= k0 && c < k0 + kb);
+                    for (int r = rw; r < nz; r += FAC_THREADS / NB) {
+                        const bool inrow = (r >= k0 && r < k0 + kb);
+                        V *w = sW + (size_t)r * ldw + cc;
+                        if (inblk) {
+                            // W_Ik <- -W_Ik P ; W_kk <- P
+                            if (inrow) {
+                                *w = recvP[(r - k0) * NB + (c - k0)];
+                            } else {
+                                V acc = mkc<T>(T(0), T(0));
 #pragma unroll 4
-                    for (int u = 0; u < kb; ++u) cfma(acc, recvP[q * NB + u], sW[(size_t)(k0 + u) * ldw + cc]);
-                    sR[q * ldr + cc] = acc;
-                }
-            }
-            __syncthreads();
-            for (int cb = 0; cb < ncb; ++cb) {
-                const int cc = cb * NB + cl, c = c0 + cc;
-                if (c >= c1) continue;
-                const bool inblk = (c >= k0 && c < k0 + kb);
-                for (int r = rw; r < nz; r += FAC_THREADS / NB) {
-                    const bool inrow = (r >= k0 && r < k0 + kb);
-                    V *w = sW + (size_t)r * ldw + cc;
-                    if (inblk) {
-                        // W_Ik <- -W_Ik P ; W_kk <- P
-                        if (inrow) {
-                            *w = recvP[(r - k0) * NB + (c - k0)];
+                                for (int u = 0; u < kb; ++u) cfma(acc, recvU[(size_t)r * NB + u], recvP[u * NB + (c - k0)]);
+                                *w = mkc<T>(-acc.x, -acc.y);
+                            }
+                        } else if (inrow) {
+                            *w = sR[(r - k0) * ldr + cc];
                         } else {
-                            V acc = mkc<T>(T(0), T(0));
+                            V acc = *w;
 #pragma unroll 4
-                            for (int u = 0; u < kb; ++u) cfma(acc, recvU[(size_t)r * NB + u], recvP[u * NB + (c - k0)]);
-                            *w = mkc<T>(-acc.x, -acc.y);
+                            for (int u = 0; u < kb; ++u) cfms(acc, recvU[(size_t)r * NB + u], sR[u * ldr + cc]);
+                            *w = acc;
                         }
-                    } else if (inrow) {
-                        *w = sR[(r - k0) * ldr + cc];
-                    } else {
-                        V acc = *w;
-#pragma unroll 4
-                        for (int u = 0; u < kb; ++u) cfms(acc, recvU[(size_t)r * NB + u], sR[u * ldr + cc]);
-                        *w = acc;
                     }
                 }
             }
             __syncthreads();
         }
-        // G_i (own columns) to the factor storage
-        V *W = Gs + (size_t)i * nz * nz;
-        for (int cb = 0; cb < ncb; ++cb) {
-            const int cc = cb * NB + cl, c = c0 + cc;
-            if (c >= c1) continue;
-            for (int r = rw; r < nz; r += FAC_THREADS / NB) W[(size_t)r * nz + c] = sW[(size_t)r * ldw + cc];
+        if (active) {
+            // G_i (own columns) to the factor storage
+            V *W = Gs + (size_t)i * nz * nz;
+            for (int cb = 0; cb < ncb; ++cb) {
+                const int cc = cb * NB + cl, c = c0 + cc;
+                if (c >= c1) continue;
+                for (int r = rw; r < nz; r += FAC_THREADS / NB) W[(size_t)r * nz + c] = sW[(size_t)r * ldw + cc];
+            }
         }
     }
-    __syncthreads();
+    // no CTA leaves while the bulk-copy engine may still read its shared memory: every
+    // consumer has waited for the last panel before arriving here
+    cluster_sync_all();
     if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
 }
 
@@ -454,7 +511,8 @@ template <typename T> static size_t factor_smem_resident_bytes(int nz, int cs) {
     const int p = (nz + NB - 1) / NB;
     const int bpc = (p + cs - 1) / cs;
     const size_t ld = (size_t)bpc * NB + 1;
-    return sizeof(cx_t<T>) * ((size_t)nz * ld + 2 * ((size_t)nz * NB + NB * NB) + NB * ld + NB * NB);
+    const size_t v = sizeof(cx_t<T>);
+    return ((v * (size_t)nz * ld + 15) & ~(size_t)15) + v * (2 * ((size_t)nz * NB + NB * NB) + NB * ld);
 }
 
 template <typename T> static size_t factor_smem_bytes(int nz, int cs) {
@@ -470,22 +528,63 @@ int pick_cluster_size(int nz) {
 
 template <typename T>
 cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag, cx_t<T> *G, cx_t<T> *xch,
-                               int *status, int cs, cudaStream_t st) {
-    FactorArgs<T> a{g, diag, G, xch, status, cs};
+                               int *status, int cs, cudaStream_t st, int *mid_out) {
     const size_t smem_res = factor_smem_resident_bytes<T>(g.nz, cs);
     const bool resident = smem_res <= 200 * 1024;
+    int teams = 1;
+    cudaError_t e;
+    // HELM_FACTOR_TEAMS=1 forces the one-sided factorisation (for comparisons)
+    const char *force = getenv("HELM_FACTOR_TEAMS");
+    const bool allow_twisted = !(force && force[0] == '1');
+    if (resident) {
+        e = cudaFuncSetAttribute(line_factor_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res);
+        if (e != cudaSuccess) return e;
+    }
+    if (resident && allow_twisted) {
+        // two teams (twisted) when a cluster of 2 cs CTAs can be scheduled
+        if (2 * cs <= 16) {
+            bool ok = true;
+            if (2 * cs > 8) {
+                ok = cudaFuncSetAttribute(line_factor_smem_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                     cudaSuccess;
+                if (ok) {
+                    cudaLaunchConfig_t q = {};
+                    q.gridDim = dim3(2 * cs, 1, 1);
+                    q.blockDim = dim3(FAC_THREADS, 1, 1);
+                    q.dynamicSmemBytes = smem_res;
+                    cudaLaunchAttribute at[1];
+                    at[0].id = cudaLaunchAttributeClusterDimension;
+                    at[0].val.clusterDim.x = 2 * cs;
+                    at[0].val.clusterDim.y = 1;
+                    at[0].val.clusterDim.z = 1;
+                    q.attrs = at;
+                    q.numAttrs = 1;
+                    int n = 0;
+                    ok = cudaOccupancyMaxActiveClusters(&n, line_factor_smem_kernel<T>, &q) == cudaSuccess && n > 0;
+                }
+                cudaGetLastError();
+            }
+            if (ok) teams = 2;
+        }
+    }
+    const int mid = (teams == 2) ? g.nx / 2 : g.nx - 1;
+    if (mid_out) *mid_out = mid;
+    FactorArgs<T> a{g, diag, G, xch, status, cs, mid};
     const size_t smem = resident ? smem_res : factor_smem_bytes<T>(g.nz, cs);
     auto kern = resident ? line_factor_smem_kernel<T> : line_factor_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!resident) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int csz = teams * cs;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_sys * cs, 1, 1);
+    cfg.gridDim = dim3(n_sys * csz, 1, 1);
     cfg.blockDim = dim3(FAC_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.x = csz;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -496,8 +595,8 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
 }
 
 template cudaError_t launch_line_factor<double>(const GridGeom &, int, const double2 *, double2 *, double2 *,
-                                                int *, int, cudaStream_t);
+                                                int *, int, cudaStream_t, int *);
 template cudaError_t launch_line_factor<float>(const GridGeom &, int, const double2 *, float2 *, float2 *,
-                                               int *, int, cudaStream_t);
+                                               int *, int, cudaStream_t, int *);
 
 }  // namespace helm

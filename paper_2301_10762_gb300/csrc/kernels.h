@@ -22,13 +22,13 @@ cudaError_t launch_restrict(const GridGeom &g, int n_cols, int n_rec, const int 
 __host__ __device__ size_t factor_xch_elems(int nz);   // exchange-slot elements per system (both slots)
 template <typename T>
 cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag, cx_t<T> *G, cx_t<T> *xch,
-                               int *status, int cs, cudaStream_t st);
+                               int *status, int cs, cudaStream_t st, int *mid_out);
 
 // ---- sweep.cu
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
                               double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
-                              cudaStream_t st);
+                              cudaStream_t st, int mid);
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
                             const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st);
 

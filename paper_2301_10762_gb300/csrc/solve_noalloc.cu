@@ -124,7 +124,7 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     int it = 1;
     if (!mixed) {
         e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status,
-                                      op->st);
+                                      op->st, f->mid);
         if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
         if (info) {
             e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
@@ -135,7 +135,7 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     } else {
         if (max_iter < 1) max_iter = 1;
         e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, Y, conj, 0, rchunk, op->status,
-                                     op->st);
+                                     op->st, f->mid);
         if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
         for (;;) {
             e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
@@ -144,7 +144,7 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
             if ((s = max_relres(op, norms, cols, &rel)) != HELM_OK) return s;
             if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
             e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, R, X, Y, conj, 1, rchunk,
-                                         op->status, op->st);
+                                         op->status, op->st, f->mid);
             if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
             ++it;
         }

@@ -31,6 +31,7 @@ constexpr uint32_t SW_WAIT_TRIES = 1u << 22;   // bounded mbarrier wait (seconds
 template <typename TG> struct SweepArgs {
     GridGeom g;
     int nrhs, R, cs, n_chunks, prefetch, tpo;   // tpo: threads per output (K split), power of 2
+    int mid, teams;                             // twisted middle line and team count (factor layout)
     const cx_t<TG> *G;   // [n_sys][nx][nz][nz]
     const double2 *B;    // [n_sys][nrhs][N]
     double2 *X;          // [n_sys][nrhs][N]
@@ -177,25 +178,33 @@ __global__ void __launch_bounds__(PP_THREADS) line_gb_prepass_kernel(GridGeom g,
     }
 }
 
-// Persistent sweep over 2nx-1 dependent line steps, after the pre-pass has stored
-// G_i b_i in Y.  Forward: y_i = G_i b_i - G_i (C y_{i-1}); backward:
-// x_i = y_i - G_i (C x_{i+1}).  Per step: wait (mbarrier, bounded) until every CTA of
-// the cluster has pushed its rows of the previous line vector, already multiplied by
-// the line coupling C, into this CTA's shared memory (st.async with transaction-count
-// completion); the (rows x n_z) x (n_z x R) product of the G_i slab (cp.async-prefetched
-// during the previous step) with that vector; subtract from the row values loaded
-// early from global memory; push the new rows (times C) to all CTAs.  Two exchange
-// buffers alternate; no CTA can overwrite a buffer before every CTA has consumed it,
-// because producing the data of step s+2 needs the data of step s+1 from every CTA,
-// which each CTA sends only after it has finished step s.
+// Persistent twisted sweep, after the pre-pass has stored G_i b_i in Y.  The cluster holds
+// `teams` teams of `cs` CTAs; CTA rank%cs of a team owns a slab of rows of every line.
+//   left team:   y_i = G_i b_i - G_i C y_{i-1},  i = 0 .. m-1            (forward)
+//                x_m = G_m b_m - G_m (C y_{m-1} + C y_{m+1})              (middle)
+//                x_i = y_i - G_i C x_{i+1},      i = m-1 .. 0            (backward)
+//   right team:  y_i = G_i b_i - G_i C y_{i+1},  i = nx-1 .. m+1         (forward)
+//                x_i = y_i - G_i C x_{i-1},      i = m+1 .. nx-1         (backward)
+// with G_i the left inverses for i < m, the right ones for i > m and G_m the middle one
+// (factor.cu).  One team with m = nx - 1 is the plain one-sided block substitution.
+// Per step: wait (bounded mbarrier) until every CTA of the team has pushed its rows of the
+// previous line vector, already multiplied by the line coupling C, into this CTA's shared
+// memory (st.async with transaction-count completion); the (rows x n_z) x (n_z x R) product
+// with the G_i slab that cp.async brought in during the previous step; subtract from the
+// own rows (also prefetched); push the new rows.  The last forward rows of both teams go to
+// the left team's middle buffers, and the left team pushes C x_m to every CTA.  Exchange
+// buffers alternate; no CTA overwrites a buffer before every consumer is done with it,
+// because producing the data of step s+2 needs the data of step s+1 from every CTA of the
+// team, which each CTA sends only after it has finished step s.
 template <typename TG>
 __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a) {
     using V = cx_t<TG>;
     const GridGeom g = a.g;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int tid = threadIdx.x;
-    const int cs = a.cs, R = a.R;
-    const int rank = (int)cluster_ctarank();
+    const int cs = a.cs, R = a.R, teams = a.teams;
+    const int crank = (int)cluster_ctarank();
+    const int team = crank / cs, rank = crank % cs;
     const int cid = (int)cluster_id_x();
     const int sys = cid / a.n_chunks, chunk = cid % a.n_chunks;
     const int q0 = chunk * R;
@@ -207,48 +216,57 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     const bool pf = a.prefetch != 0;
     const int nzp = padded<TG>(nz);
     const int kcp = padded<TG>(SW_KC);
+    const int m = a.mid;
+    const int len = (team == 0) ? m : nx - 1 - m;      // forward lines of this team
+    const int nsteps = 2 * len + (team == 0 ? 1 : 0);   // forward, [middle], backward
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);           // [2]
-    V *sY = reinterpret_cast<V *>(smem_raw + 16);                       // [2][R][nzp]  C * (line vector)
-    V *sG = sY + 2 * (size_t)R * nzp;                                   // pf: [2][rpc][nzp]; else [rpc][kcp]
-    V *sOwn = sG + (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp);   // [2][R][rpc]: own rows of line i
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);           // [0,1] team ping-pong, [2] middle, [3] x_m
+    V *sY = reinterpret_cast<V *>(smem_raw + 32);                       // [2][R][nzp]  C * (line vector)
+    V *sMid = sY + 2 * (size_t)R * nzp;                                 // [2][R][nzp]  C y_{m-1}, C y_{m+1}
+    V *sX = sMid + 2 * (size_t)R * nzp;                                 // [R][nzp]     C x_m
+    V *sG = sX + (size_t)R * nzp;                                       // pf: [2][rpc][nzp]; else [rpc][kcp]
+    V *sOwn = sG + (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp);   // [2][R][rpc]: own rows of the line
     __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
     double2 *Xs = a.X + ((size_t)sys * a.nrhs + q0) * N;
     V *Ys = a.Y + ((size_t)sys * a.nrhs + q0) * N;
-    const int last = 2 * nx - 2;
-    const uint32_t phase_bytes = (uint32_t)(nz * Rc * sizeof(V));
+    const uint32_t vec_bytes = (uint32_t)(nz * Rc * sizeof(V));
     const TG c_in = (TG)coup_x(g, 1), c_edge = (TG)coup_x(g, 0);
     const int lane = tid & 31, wid = tid >> 5;
     const int tpo = a.tpo, ngrp = SW_THREADS / tpo;
-    const int pr = tid / tpo, part = tid % tpo;       // output group, K part
+    const int pr = tid / tpo, part = tid % tpo;        // output group, K part
     const bool fp32 = sizeof(TG) == 4;
 
+    // step kinds: 0 forward, 1 middle (left team), 2 backward
+    auto kind_of = [&](int s) { return s < len ? 0 : ((team == 0 && s == len) ? 1 : 2); };
+    auto line_of = [&](int s) {
+        if (s < len) return team == 0 ? s : nx - 1 - s;
+        if (team == 0) return s == len ? m : m - (s - len);
+        return m + 1 + (s - len);
+    };
+    auto bwd_index = [&](int s) { return team == 0 ? s - len - 1 : s - len; };   // 0 for the first backward step
+
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int b = 0; b < 4; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init_cluster();
         s_abort = 0;
     }
     __syncthreads();
     cluster_sync_all();   // every mbarrier of the cluster is initialised before any push
-    if (tid == 0) {
-        if (last >= 1) mbar_arrive_expect_tx(&bars[1], phase_bytes);   // data of step 1
-        if (last >= 2) mbar_arrive_expect_tx(&bars[0], phase_bytes);   // data of step 2
-    }
+    uint32_t ph0 = 0, ph1 = 0;
 
     auto prefetch = [&](int s) {
-        if (s > last) return;
-        const int i = step_line(s, nx);
-        {   // own rows of line i: G_i b_i (forward, from the pre-pass) or y_i (backward)
+        if (s >= nsteps) return;
+        const int i = line_of(s);
+        {   // own rows of line i: G_i b_i (forward, middle) or y_i (backward)
             V *dst = sOwn + (size_t)(s & 1) * R * rpc;
             for (int q = wid; q < Rc; q += SW_THREADS / 32)
                 for (int r = lane; r < nrows; r += 32)
                     cp_async_elem(dst + (size_t)q * rpc + r, Ys + (size_t)q * N + (size_t)i * nz + r0 + r);
         }
-        if (!pf || s == 0) return;   // step 0 needs no product
+        if (!pf || s == 0) return;   // the first forward line needs no product
         const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
         V *dst = sG + (size_t)(s & 1) * rpc * nzp;
         if (sizeof(TG) == 4 && (nz & 1) == 0) {
@@ -260,49 +278,79 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
     };
 
+    // rows computed in the previous step: the right team's first backward line is the line
+    // of its last forward step, whose values the prefetch (issued before they were stored)
+    // cannot see
+    V vlast[SW_MAXOPT];
+#pragma unroll
+    for (int u = 0; u < SW_MAXOPT; ++u) vlast[u] = mkc<TG>(TG(0), TG(0));
     prefetch(0);
     cp_async_commit();
-    for (int s = 0; s <= last; ++s) {
-        const int i = step_line(s, nx);
-        const bool fwd = s < nx;
-        const int buf = s & 1;
-        if (s > 0 && tid == 0) {
-            if (!mbar_wait_bounded(&bars[buf], (uint32_t)(((s - 1) >> 1) & 1), SW_WAIT_TRIES)) {
+    for (int s = 0; s < nsteps; ++s) {
+        const int kind = kind_of(s);
+        const int i = line_of(s);
+        const int bi = (kind == 2) ? bwd_index(s) : -1;
+        // input vector of the product: none (first forward line), the middle buffers, the
+        // x_m buffer (first backward line) or the team ping-pong buffer
+        const V *tin = nullptr;
+        const V *tin2 = nullptr;
+        if (tid == 0 && !(kind == 0 && s == 0)) {
+            uint64_t *bar;
+            uint32_t bytes = vec_bytes, par;
+            if (kind == 1) { bar = &bars[2]; bytes = vec_bytes * (uint32_t)teams; par = 0; }
+            else if (kind == 2 && bi == 0) { bar = &bars[3]; par = 0; }
+            else { bar = &bars[s & 1]; par = (s & 1) ? ph1 : ph0; }
+            mbar_arrive_expect_tx(bar, bytes);
+            if (!mbar_wait_bounded(bar, par, SW_WAIT_TRIES)) {
                 atomicOr(a.status, ST_TIMEOUT);
                 s_abort = 1;
-            } else if (s + 2 <= last) {
-                mbar_arrive_expect_tx(&bars[buf], phase_bytes);   // re-arm for step s + 2
             }
         }
-        // own rows of line i loaded early: G_i b_i (forward) or y_i (backward), and the
-        // FP64 iterate where the mixed epilogue accumulates
+        if (!(kind == 0 && s == 0) && kind != 1 && !(kind == 2 && bi == 0)) {
+            if (s & 1) ph1 ^= 1u; else ph0 ^= 1u;
+        }
+        if (kind == 1) { tin = sMid; tin2 = (teams == 2) ? sMid + (size_t)R * nzp : nullptr; }
+        else if (kind == 2 && bi == 0) tin = sX;
+        else if (!(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
         double2 xold[SW_MAXOPT];
+        const bool final_line = (kind != 0);
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
             const int o = pr + u * ngrp;
             xold[u] = make_double2(0.0, 0.0);
-            if (!fp32 && o < nout && a.accumulate && (!fwd || i == nx - 1))
+            if (!fp32 && o < nout && a.accumulate && final_line)
                 xold[u] = Xs[(size_t)(o / nrows) * N + (size_t)i * nz + r0 + (o % nrows)];
         }
         cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
         if (s_abort) return;
-        V yown[SW_MAXOPT];
+        prefetch(s + 1);   // into the staging buffers that step s - 1 used
+        cp_async_commit();
+        if (tin2) {
+            // middle line: t = C y_{m-1} + C y_{m+1}
+            V *tsum = const_cast<V *>(tin);
+            for (int q = wid; q < Rc; q += SW_THREADS / 32)
+                for (int j = lane; j < nz; j += 32) {
+                    const V u1 = tin2[(size_t)q * nzp + j];
+                    V &u0 = tsum[(size_t)q * nzp + j];
+                    u0.x += u1.x;
+                    u0.y += u1.y;
+                }
+            __syncthreads();
+        }
+        V yown[SW_MAXOPT], acc[SW_MAXOPT];
+        const bool same_line = (team == 1 && kind == 2 && bi == 0);
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
             const int o = pr + u * ngrp;
-            yown[u] = (o < nout) ? sOwn[(size_t)(s & 1) * R * rpc + (size_t)(o / nrows) * rpc + (o % nrows)]
+            yown[u] = (o < nout) ? (same_line ? vlast[u]
+                                              : sOwn[(size_t)(s & 1) * R * rpc + (size_t)(o / nrows) * rpc + (o % nrows)])
                                  : mkc<TG>(TG(0), TG(0));
+            acc[u] = mkc<TG>(TG(0), TG(0));
         }
-        prefetch(s + 1);   // into the staging buffer that step s - 1 used
-        cp_async_commit();
-        V acc[SW_MAXOPT];
-#pragma unroll
-        for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
-        if (s > 0) {
-            const V *tin = sY + (size_t)buf * R * nzp;
+        if (tin) {
             if (pf) {
-                const V *Gb = sG + (size_t)buf * rpc * nzp;
+                const V *Gb = sG + (size_t)(s & 1) * rpc * nzp;
 #pragma unroll
                 for (int u = 0; u < SW_MAXOPT; ++u) {
                     const int o = pr + u * ngrp;
@@ -331,18 +379,26 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             }
         }
         // the K parts of every output meet in adjacent lanes
-        for (int m = 1; m < tpo; m <<= 1) {
+        for (int mm = 1; mm < tpo; mm <<= 1) {
 #pragma unroll
             for (int u = 0; u < SW_MAXOPT; ++u) {
-                acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, m);
-                acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, m);
+                acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, mm);
+                acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, mm);
             }
         }
-        // new rows v = own - product; push C v to every CTA (targets split over the pair),
-        // store / finish own rows
-        const bool push = s < last;
-        V *ynext = sY + (size_t)((s + 1) & 1) * R * nzp;
-        const uint32_t lbar = smem_u32(&bars[(s + 1) & 1]);
+        // where the new rows go: the team's next buffer, the middle buffers of the left team
+        // (last forward line), or the x_m buffer of every CTA (middle line)
+        V *dstbuf = nullptr;
+        uint64_t *dstbar = nullptr;
+        int t_lo = team * cs, t_hi = team * cs + cs;
+        if (kind == 0 && s == len - 1) {
+            dstbuf = sMid + (size_t)team * R * nzp; dstbar = &bars[2]; t_lo = 0; t_hi = cs;
+        } else if (kind == 1) {
+            dstbuf = sX; dstbar = &bars[3]; t_lo = 0; t_hi = teams * cs;
+        } else if (s + 1 < nsteps) {
+            dstbuf = sY + (size_t)((s + 1) & 1) * R * nzp; dstbar = &bars[(s + 1) & 1];
+        }
+        const uint32_t lbar = dstbar ? smem_u32(dstbar) : 0u;
 #pragma unroll
         for (int u = 0; u < SW_MAXOPT; ++u) {
             const int o = pr + u * ngrp;
@@ -350,16 +406,17 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 const int r = o % nrows, q = o / nrows;
                 const int j = r0 + r;
                 const V v = mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
-                if (push) {
+                vlast[u] = v;
+                if (dstbuf) {
                     const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
                     const V cv = mkc<TG>(c * v.x, c * v.y);
-                    const uint32_t la = smem_u32(ynext + (size_t)q * nzp + j);
-                    for (int t = part; t < cs; t += tpo)
+                    const uint32_t la = smem_u32(dstbuf + (size_t)q * nzp + j);
+                    for (int t = t_lo + part; t < t_hi; t += tpo)
                         st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
                 }
                 if (part == 0) {
                     const size_t off = (size_t)q * N + (size_t)i * nz + j;
-                    if (fp32 || (fwd && i < nx - 1)) {
+                    if (fp32 || !final_line) {
                         Ys[off] = v;   // mixed: the FP64 promotion runs in accumulate_kernel
                     } else {
                         double2 d = make_double2((double)v.x, (double)v.y);
@@ -373,7 +430,6 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     }
     cp_async_wait<0>();
 }
-
 
 // Mixed path: X = (accumulate ? X : 0) + conj?(delta), delta the complex-FP32 solution of the
 // sweep (FP64 promotion kept out of the sweep's critical path).
@@ -414,13 +470,14 @@ static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
                               double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
-                              cudaStream_t st) {
+                              cudaStream_t st, int mid) {
     const void *fn = (const void *)line_sweep_kernel<TG>;
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
     const size_t nzp = (size_t)padded<TG>(nz), kcp = (size_t)padded<TG>(SW_KC);
+    const int teams = (mid < g.nx - 1) ? 2 : 1;
     int cs = nz / 16;
-    cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
+    cs = cs < 1 ? 1 : (cs > 16 / teams ? 16 / teams : cs);
     cudaError_t e;
     // pre-pass Y_i = G_i b_i (all lines at once)
     {
@@ -436,7 +493,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
         auto smem_of = [&](int R, int pf) {
-            return (size_t)16 + vsz * 2 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp) +
+            return (size_t)32 + vsz * 5 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp) +
                    vsz * 2 * (size_t)R * rpc;
         };
         // right-hand sides per cluster: aim at ~64 outputs per CTA, so that a line step's
@@ -456,26 +513,27 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         const size_t smem = smem_of(R, pf);
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (cs > 8) {
+        const int csz = teams * cs;
+        if (csz > 8) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess || active_clusters(fn, cs, SW_THREADS, smem) == 0) {
+            if (e != cudaSuccess || active_clusters(fn, csz, SW_THREADS, smem) == 0) {
                 cudaGetLastError();
-                cs = 8;
+                cs = 8 / teams;
                 continue;
             }
         }
         const int n_chunks = (nrhs + R - 1) / R;
         int tpo = 1;
         while (tpo < 8 && rpc * R * tpo * 2 <= SW_THREADS) tpo *= 2;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, G, B, X, Y, conj, accumulate, status};
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, accumulate, status};
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(n_sys * n_chunks * cs, 1, 1);
+        cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.x = csz;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
@@ -492,9 +550,9 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
 }
 
 template cudaError_t launch_line_sweep<double>(const GridGeom &, int, int, const double2 *, const double2 *,
-                                               double2 *, double2 *, int, int, int, int *, cudaStream_t);
+                                               double2 *, double2 *, int, int, int, int *, cudaStream_t, int);
 template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const double2 *,
-                                              double2 *, float2 *, int, int, int, int *, cudaStream_t);
+                                              double2 *, float2 *, int, int, int, int *, cudaStream_t, int);
 
 // ------------------------------------------------------------------ FP64 residual
 // R = B - A X (A^H X for conj = 1) with the five-point operator, and per column the
