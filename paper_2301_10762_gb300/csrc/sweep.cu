@@ -16,6 +16,7 @@
 // the input is an FP64 residual and the result is added to the FP64 iterate in the
 // final pass (x += A~^{-1} r).  TG = double is the plain FP64 path (Y aliases X).
 #include <algorithm>
+#include <stdlib.h>
 #include "kernels.h"
 #include "trace.h"
 
@@ -446,6 +447,18 @@ __global__ void accumulate_kernel(size_t n, const float2 *Y, double2 *X, int con
     }
 }
 
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 132;
+        cudaGetLastError();
+    }
+    return n;
+}
+
 // Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
 static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
     cudaLaunchConfig_t cfg = {};
@@ -478,6 +491,9 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     const int teams = (mid < g.nx - 1) ? 2 : 1;
     int cs = nz / 16;
     cs = cs < 1 ? 1 : (cs > 16 / teams ? 16 / teams : cs);
+    // tuning overrides: CTAs per team and right-hand sides per cluster
+    const char *env_cs = getenv("HELM_SWEEP_CS"), *env_r = getenv("HELM_SWEEP_R");
+    if (env_cs && atoi(env_cs) > 0) cs = std::min(atoi(env_cs), 16 / teams);
     cudaError_t e;
     // pre-pass Y_i = G_i b_i (all lines at once)
     {
@@ -496,12 +512,14 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             return (size_t)32 + vsz * 5 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp) +
                    vsz * 2 * (size_t)R * rpc;
         };
-        // right-hand sides per cluster: aim at ~64 outputs per CTA, so that a line step's
-        // product is spread over more clusters (the chain is latency bound, the GPU idle)
+        // right-hand sides per cluster (the chain is latency bound and the GPU otherwise
+        // idle, so more clusters with fewer outputs each; 128 outputs per CTA measured best)
         int R = 1;
-        while (R * 2 <= 16 && rpc * R * 2 <= 64) R *= 2;
+        while (R * 2 <= 16 && rpc * R * 2 <= 128) R *= 2;   // ~128 outputs per CTA (measured best)
         if (rchunk > 0 && R > rchunk) R = rchunk;
+        if (env_r && atoi(env_r) > 0) R = atoi(env_r);
         if (R > nrhs) R = nrhs;
+        if (R < 1) R = 1;
         while (R > 1 && rpc * R > SW_MAXOPT * SW_THREADS) R = (R + 1) / 2;
         int pf = 1;
         while (smem_of(R, pf) > SW_SMEM_MAX) {
