@@ -23,7 +23,6 @@
 namespace helm {
 
 constexpr int SW_THREADS = 256;
-constexpr int PP_THREADS = 256;
 constexpr int SW_KC = 64;      // K chunk of the streamed (non-prefetched) G path
 constexpr int SW_MAXOPT = 2;   // outputs per thread (rows_per_cta * R <= 2 * 256)
 constexpr size_t SW_SMEM_MAX = 200 * 1024;
@@ -45,10 +44,20 @@ template <typename TG> __device__ __forceinline__ cx_t<TG> in_cast(double2 a);
 template <> __device__ __forceinline__ double2 in_cast<double>(double2 a) { return a; }
 template <> __device__ __forceinline__ float2 in_cast<float>(double2 a) { return to_c64(a); }
 
-// padded row stride (in complex elements) of the shared-memory operands: keeps 16-byte
-// alignment of every row and spreads consecutive rows over the banks
-template <typename TG> __host__ __device__ __forceinline__ int padded(int n) {
-    return sizeof(TG) == 4 ? ((n + 1) & ~1) + 2 : n + 1;
+// Padded row stride (in complex elements) of the shared-memory operands of the sweep product.
+// A quarter-warp (the unit of a 16-byte shared load) reads 8/tpo rows x tpo adjacent 16-byte
+// K words; the stride is chosen so that those eight words fall on distinct banks:
+// 2*stride = 4*tpo (mod 32) words for complex FP32 (even stride keeps 16-byte alignment), and
+// 4*stride = 4*tpo (mod 32) words for complex FP64.
+template <typename TG> __host__ __device__ __forceinline__ int padded(int n, int tpo) {
+    if (sizeof(TG) == 4) {
+        int p = (n + 1) & ~1;
+        while (p % 16 != (2 * tpo) % 16) p += 2;
+        return p;
+    }
+    int p = n;
+    while (p % 8 != tpo % 8) ++p;
+    return p;
 }
 
 // sum_b g[b] t[b] over n complex entries (both 16-byte aligned), four independent chains
@@ -123,60 +132,75 @@ __device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 
 // forward sweep that does not depend on the recurrence), a batched complex GEMM over
 // (system, line, row tile, right-hand-side chunk).  b is the FP64 input (conjugated
 // for the adjoint), cast to TG.
-constexpr int PP_ROWS = 32;
-constexpr int PP_KC = 64;
+constexpr int PP_ROWS = 64;    // rows of G_i per CTA
+constexpr int PP_RHS = 16;     // right-hand sides per CTA
+constexpr int PP_KC = 32;      // K chunk
+// Register-blocked batched product: each thread computes 2 rows x 4 right-hand sides (64 rows
+// x 16 right-hand sides per CTA of 128 threads), so every two shared loads of G feed eight
+// complex MACs.  A warp shares its right-hand sides (broadcast reads) and takes rows tr and
+// tr + 32, whose padded stride keeps the G reads free of bank conflicts.
 template <typename TG>
-__global__ void __launch_bounds__(PP_THREADS) line_gb_prepass_kernel(GridGeom g, int nrhs, int R, const cx_t<TG> *G,
-                                                                   const double2 *B, cx_t<TG> *Y, int conj) {
+__global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nrhs, const cx_t<TG> *G,
+                                                             const double2 *B, cx_t<TG> *Y, int conj) {
     using V = cx_t<TG>;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int n_rt = (nz + PP_ROWS - 1) / PP_ROWS;
-    const int n_ch = (nrhs + R - 1) / R;
+    const int n_ch = (nrhs + PP_RHS - 1) / PP_RHS;
     int bid = blockIdx.x;
     const int ch = bid % n_ch; bid /= n_ch;
     const int rt = bid % n_rt; bid /= n_rt;
     const int i = bid % nx;
     const int sys = bid / nx;
-    const int q0 = ch * R, Rc = min(R, nrhs - q0);
+    const int q0 = ch * PP_RHS, Rc = min(PP_RHS, nrhs - q0);
     const int r0 = rt * PP_ROWS, nrows = min(PP_ROWS, nz - r0);
-    const int kcp = padded<TG>(PP_KC);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *sb = reinterpret_cast<V *>(smem_raw);           // [R][kcp]
-    V *sg = sb + (size_t)R * kcp;                       // [PP_ROWS][kcp]
+    constexpr int KP = PP_KC + 1;   // padded row stride (complex elements)
+    __shared__ V sg[PP_ROWS][KP];    // G_i rows x K chunk
+    __shared__ V sb[PP_RHS][KP];     // right-hand sides x K chunk
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tr = tid & 31, tq = tid >> 5;    // rows tr, tr + 32; right-hand sides 4 tq .. 4 tq + 3
     const double2 *Bs = B + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz;
     const V *Gi = G + ((size_t)sys * nx + i) * nz * nz + (size_t)r0 * nz;
-    V acc[SW_MAXOPT];
+    V acc[2][4];
 #pragma unroll
-    for (int u = 0; u < SW_MAXOPT; ++u) acc[u] = mkc<TG>(TG(0), TG(0));
+    for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) acc[a2][b2] = mkc<TG>(TG(0), TG(0));
     for (int kc = 0; kc < nz; kc += PP_KC) {
         const int kw = min(PP_KC, nz - kc);
-        for (int q = wid; q < Rc; q += PP_THREADS / 32)
-            for (int j = lane; j < kw; j += 32) {
-                double2 bv = Bs[(size_t)q * N + kc + j];
-                if (conj) bv.y = -bv.y;
-                sb[(size_t)q * kcp + j] = in_cast<TG>(bv);
+        for (int q = wid; q < PP_RHS; q += 4)
+            for (int j = lane; j < PP_KC; j += 32) {
+                V v = mkc<TG>(TG(0), TG(0));
+                if (q < Rc && j < kw) {
+                    double2 bv = Bs[(size_t)q * N + kc + j];
+                    if (conj) bv.y = -bv.y;
+                    v = in_cast<TG>(bv);
+                }
+                sb[q][j] = v;
             }
-        for (int r = wid; r < nrows; r += PP_THREADS / 32)
-            for (int j = lane; j < kw; j += 32) sg[(size_t)r * kcp + j] = Gi[(size_t)r * nz + kc + j];
+        for (int r = wid; r < PP_ROWS; r += 4)
+            for (int j = lane; j < PP_KC; j += 32)
+                sg[r][j] = (r < nrows && j < kw) ? Gi[(size_t)r * nz + kc + j] : mkc<TG>(TG(0), TG(0));
         __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < PP_KC; ++k) {
+            const V g0 = sg[tr][k], g1 = sg[tr + 32][k];
 #pragma unroll
-        for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = tid + u * PP_THREADS;
-            if (o < nrows * Rc) {
-                const V d = dot_row(sg + (size_t)(o % nrows) * kcp, sb + (size_t)(o / nrows) * kcp, kw);
-                acc[u].x += d.x;
-                acc[u].y += d.y;
+            for (int b2 = 0; b2 < 4; ++b2) {
+                const V bb = sb[4 * tq + b2][k];
+                cfma(acc[0][b2], g0, bb);
+                cfma(acc[1][b2], g1, bb);
             }
         }
         __syncthreads();
     }
     V *Ys = Y + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz + r0;
 #pragma unroll
-    for (int u = 0; u < SW_MAXOPT; ++u) {
-        const int o = tid + u * PP_THREADS;
-        if (o < nrows * Rc) Ys[(size_t)(o / nrows) * N + (o % nrows)] = acc[u];
-    }
+    for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) {
+            const int r = tr + 32 * a2, q = 4 * tq + b2;
+            if (r < nrows && q < Rc) Ys[(size_t)q * N + r] = acc[a2][b2];
+        }
 }
 
 // Persistent twisted sweep, after the pre-pass has stored G_i b_i in Y.  The cluster holds
@@ -215,8 +239,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     const int nrows = r1 - r0;
     const int nout = nrows * Rc;
     const bool pf = a.prefetch != 0;
-    const int nzp = padded<TG>(nz);
-    const int kcp = padded<TG>(SW_KC);
+    const int nzp = padded<TG>(nz, a.tpo);
+    const int kcp = padded<TG>(SW_KC, a.tpo);
     const int m = a.mid;
     const int len = (team == 0) ? m : nx - 1 - m;      // forward lines of this team
     const int nsteps = 2 * len + (team == 0 ? 1 : 0);   // forward, [middle], backward
@@ -487,7 +511,6 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     const void *fn = (const void *)line_sweep_kernel<TG>;
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
-    const size_t nzp = (size_t)padded<TG>(nz), kcp = (size_t)padded<TG>(SW_KC);
     const int teams = (mid < g.nx - 1) ? 2 : 1;
     int cs = nz / 16;
     cs = cs < 1 ? 1 : (cs > 16 / teams ? 16 / teams : cs);
@@ -497,18 +520,21 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     cudaError_t e;
     // pre-pass Y_i = G_i b_i (all lines at once)
     {
-        const int R = nrhs < 16 ? nrhs : 16;   // PP_ROWS * R <= SW_MAXOPT * PP_THREADS
-        const size_t smem = vsz * ((size_t)R + PP_ROWS) * (size_t)padded<TG>(PP_KC);
-        e = cudaFuncSetAttribute(line_gb_prepass_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + R - 1) / R);
-        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, PP_THREADS, smem, st>>>(g, nrhs, R, G, B, Y, conj)));
+        const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + PP_RHS - 1) / PP_RHS);
+        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj)));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
+        // threads per output (K split): as many as fit the CTA's 256 threads twice over
+        auto tpo_of = [&](int R) {
+            int t = 1;
+            while (t < 8 && rpc * R * t * 2 <= SW_THREADS) t *= 2;
+            return t;
+        };
         auto smem_of = [&](int R, int pf) {
+            const size_t nzp = (size_t)padded<TG>(nz, tpo_of(R)), kcp = (size_t)padded<TG>(SW_KC, tpo_of(R));
             return (size_t)32 + vsz * 5 * (size_t)R * nzp + (pf ? vsz * 2 * (size_t)rpc * nzp : vsz * (size_t)rpc * kcp) +
                    vsz * 2 * (size_t)R * rpc;
         };
@@ -541,8 +567,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             }
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        int tpo = 1;
-        while (tpo < 8 && rpc * R * tpo * 2 <= SW_THREADS) tpo *= 2;
+        const int tpo = tpo_of(R);
         SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, accumulate, status};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
