@@ -203,6 +203,42 @@ __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nr
         }
 }
 
+// ------------------------------------------------- tensor-pipe line product (complex FP32)
+// The product G t of a CTA's slab of G_i (rows x n_z, interleaved complex) with up to eight
+// right-hand sides is one real product on the tensor pipe: with k running over the
+// interleaved (re, im) columns of G,
+//     [Re(G t) | Im(G t)] = [G_re G_im ...] x [[Re t, Im t], [-Im t, Re t]] (row pairs),
+// an m16 x n8 tile for the real parts and one for the imaginary parts (mma.sync m16n8k8, TF32).
+// Each FP32 operand x is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the three
+// products hi*hi + hi*lo + lo*hi, accumulated in FP32, carry about 22 bits of each operand.
+// Thread (g, t) of a warp (g = lane / 4, t = lane % 4) holds the k columns 2t and 2t + 1 of an
+// 8-column block of complex entries as its two fragment slots, so A and B fragments come
+// from one 16-byte load each (any permutation of k shared by A and B leaves the product).
+constexpr int MMA_RHS = 8;   // right-hand sides per cluster on the tensor path (one n tile)
+// row stride of the shared-memory line vectors on the tensor path: the 16-byte B loads of a
+// quarter-warp (rows g, g + 1 at four 16-byte columns) fall on distinct banks
+__host__ __device__ __forceinline__ int padded_mma(int n) {
+    int p = (n + 1) & ~1;
+    while (p % 16 != 8) p += 2;
+    return p;
+}
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+// d += A (16 x 8, row) * B (8 x 8, col), TF32 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Persistent twisted sweep, after the pre-pass has stored G_i b_i in Y.  The cluster holds
 // `teams` teams of `cs` CTAs; CTA rank%cs of a team owns a slab of rows of every line.
 //   left team:   y_i = G_i b_i - G_i C y_{i-1},  i = 0 .. m-1            (forward)
@@ -221,7 +257,11 @@ __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nr
 // buffers alternate; no CTA overwrites a buffer before every consumer is done with it,
 // because producing the data of step s+2 needs the data of step s+1 from every CTA of the
 // team, which each CTA sends only after it has finished step s.
-template <typename TG>
+// MT > 0 selects the tensor-pipe product (complex FP32 only): MT m16 tiles of rows per CTA,
+// KP 8-column blocks of K per warp (the eight warps split K and meet in shared memory), the
+// G_i slab read from L2 straight into fragment registers one step ahead.  MT = 0 is the
+// CUDA-core product (FP64, or shapes the tensor tiles do not cover).
+template <typename TG, int MT, int KP>
 __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a) {
     using V = cx_t<TG>;
     const GridGeom g = a.g;
@@ -239,7 +279,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     const int nrows = r1 - r0;
     const int nout = nrows * Rc;
     const bool pf = a.prefetch != 0;
-    const int nzp = padded<TG>(nz, a.tpo);
+    const int nzp = MT > 0 ? padded_mma(nz) : padded<TG>(nz, a.tpo);
     const int kcp = padded<TG>(SW_KC, a.tpo);
     const int m = a.mid;
     const int len = (team == 0) ? m : nx - 1 - m;      // forward lines of this team
@@ -251,7 +291,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     V *sMid = sY + 2 * (size_t)R * nzp;                                 // [2][R][nzp]  C y_{m-1}, C y_{m+1}
     V *sX = sMid + 2 * (size_t)R * nzp;                                 // [R][nzp]     C x_m
     V *sG = sX + (size_t)R * nzp;                                       // pf: [2][rpc][nzp]; else [rpc][kcp]
-    V *sOwn = sG + (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp);   // [2][R][rpc]: own rows of the line
+    V *sOwn = sG + (MT > 0 ? 0 : (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp));   // [2][R][rpc]: own rows
+    constexpr int RP = 16 * (MT > 0 ? MT : 1) + 2;   // tensor path: padded row count of the partials
+    float2 *red = reinterpret_cast<float2 *>(sOwn + 2 * (size_t)R * rpc);   // [8 warps][MMA_RHS][RP]
     __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
@@ -291,7 +333,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 for (int r = lane; r < nrows; r += 32)
                     cp_async_elem(dst + (size_t)q * rpc + r, Ys + (size_t)q * N + (size_t)i * nz + r0 + r);
         }
-        if (!pf || s == 0) return;   // the first forward line needs no product
+        if (MT > 0 || !pf || s == 0) return;   // the first forward line needs no product
         const V *src = Gs + (size_t)i * nz * nz + (size_t)r0 * nz;
         V *dst = sG + (size_t)(s & 1) * rpc * nzp;
         if (sizeof(TG) == 4 && (nz & 1) == 0) {
@@ -303,12 +345,56 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
     };
 
+    // tensor path: this warp's fragments of the G_i slab, rows g and g + 8 of each m tile,
+    // complex columns 8j + 2t, 8j + 2t + 1 of the blocks j = wid, wid + 8, ...
+    const int fg = lane >> 2, ft = lane & 3;
+    const int NP = (nz + 7) >> 3;
+    float4 gfr[MT > 0 ? MT : 1][2][KP > 0 ? KP : 1];
+    auto load_g = [&](int s1) {
+        if constexpr (MT > 0) {
+            if (s1 >= nsteps) return;
+            const float2 *Gl = reinterpret_cast<const float2 *>(Gs) + ((size_t)line_of(s1) * nz + r0) * nz;
+#pragma unroll
+            for (int jj = 0; jj < KP; ++jj) {
+                const int j = wid + 8 * jj, kc = 8 * j + 2 * ft;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = 16 * mt + fg + 8 * h;
+                        gfr[mt][h][jj] = (j < NP && kc < nz && row < nrows)
+                                             ? __ldg(reinterpret_cast<const float4 *>(Gl + (size_t)row * nz + kc))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+            }
+        }
+    };
+
+    // this thread's outputs, fixed for the whole sweep: right-hand side oq and slab row orow of
+    // output o = pr + u * ngrp, the row's coupling to the next line, and its offsets
+    constexpr int NOPT = MT > 0 ? 1 : SW_MAXOPT;
+    bool ov[NOPT];
+    int oq[NOPT], orow[NOPT];
+    TG ocoef[NOPT];
+    uint32_t obyte[NOPT];   // byte offset of the output in a [R][nzp] line buffer
+    size_t ogl[NOPT];       // element offset of the output in Y / X, less i * nz
+#pragma unroll
+    for (int u = 0; u < NOPT; ++u) {
+        const int o = pr + u * ngrp;
+        ov[u] = o < nout;
+        oq[u] = ov[u] ? o / nrows : 0;
+        orow[u] = ov[u] ? o % nrows : 0;
+        const int j = r0 + orow[u];
+        ocoef[u] = (j == 0 || j == nz - 1) ? c_edge : c_in;
+        obyte[u] = (uint32_t)(((size_t)oq[u] * nzp + j) * sizeof(V));
+        ogl[u] = (size_t)oq[u] * N + j;
+    }
     // rows computed in the previous step: the right team's first backward line is the line
     // of its last forward step, whose values the prefetch (issued before they were stored)
     // cannot see
-    V vlast[SW_MAXOPT];
+    V vlast[NOPT];
 #pragma unroll
-    for (int u = 0; u < SW_MAXOPT; ++u) vlast[u] = mkc<TG>(TG(0), TG(0));
+    for (int u = 0; u < NOPT; ++u) vlast[u] = mkc<TG>(TG(0), TG(0));
     prefetch(0);
     cp_async_commit();
     for (int s = 0; s < nsteps; ++s) {
@@ -337,14 +423,12 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         if (kind == 1) { tin = sMid; tin2 = (teams == 2) ? sMid + (size_t)R * nzp : nullptr; }
         else if (kind == 2 && bi == 0) tin = sX;
         else if (!(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
-        double2 xold[SW_MAXOPT];
+        double2 xold[NOPT];
         const bool final_line = (kind != 0);
 #pragma unroll
-        for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = pr + u * ngrp;
+        for (int u = 0; u < NOPT; ++u) {
             xold[u] = make_double2(0.0, 0.0);
-            if (!fp32 && o < nout && a.accumulate && final_line)
-                xold[u] = Xs[(size_t)(o / nrows) * N + (size_t)i * nz + r0 + (o % nrows)];
+            if (!fp32 && ov[u] && a.accumulate && final_line) xold[u] = Xs[ogl[u] + (size_t)i * nz];
         }
         cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
@@ -363,24 +447,85 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 }
             __syncthreads();
         }
-        V yown[SW_MAXOPT], acc[SW_MAXOPT];
+        V yown[NOPT], acc[NOPT];
         const bool same_line = (team == 1 && kind == 2 && bi == 0);
 #pragma unroll
-        for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = pr + u * ngrp;
-            yown[u] = (o < nout) ? (same_line ? vlast[u]
-                                              : sOwn[(size_t)(s & 1) * R * rpc + (size_t)(o / nrows) * rpc + (o % nrows)])
-                                 : mkc<TG>(TG(0), TG(0));
+        for (int u = 0; u < NOPT; ++u) {
+            yown[u] = ov[u] ? (same_line ? vlast[u] : sOwn[(size_t)(s & 1) * R * rpc + oq[u] * rpc + orow[u]])
+                            : mkc<TG>(TG(0), TG(0));
             acc[u] = mkc<TG>(TG(0), TG(0));
         }
-        if (tin) {
+        if constexpr (MT > 0) {
+            if (tin) {
+                float accB[MT][2][4], accS[MT][2][4];   // hi*hi and the two cross terms
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int n = 0; n < 2; ++n)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) accB[mt][n][e] = accS[mt][n][e] = 0.f;
+                const float2 *tv = reinterpret_cast<const float2 *>(tin);
+#pragma unroll
+                for (int jj = 0; jj < KP; ++jj) {
+                    const int j = wid + 8 * jj, kc = 8 * j + 2 * ft;
+                    if (j >= NP) break;   // warp-uniform
+                    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (fg < Rc && kc < nz) xv = *reinterpret_cast<const float4 *>(tv + (size_t)fg * nzp + kc);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        uint32_t xr_h, xr_l, xi_h, xi_l;
+                        split_tf32(c ? xv.z : xv.x, xr_h, xr_l);
+                        split_tf32(c ? xv.w : xv.y, xi_h, xi_l);
+                        const uint32_t nxi_h = xi_h ^ 0x80000000u, nxi_l = xi_l ^ 0x80000000u;
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            const float4 ga = gfr[mt][0][jj], gb = gfr[mt][1][jj];
+                            uint32_t ah[4], al[4];
+                            split_tf32(c ? ga.z : ga.x, ah[0], al[0]);   // row g,     Re G
+                            split_tf32(c ? gb.z : gb.x, ah[1], al[1]);   // row g + 8, Re G
+                            split_tf32(c ? ga.w : ga.y, ah[2], al[2]);   // row g,     Im G
+                            split_tf32(c ? gb.w : gb.y, ah[3], al[3]);   // row g + 8, Im G
+                            mma_tf32(accB[mt][0], ah, xr_h, nxi_h);      // Re: Re G Re t - Im G Im t
+                            mma_tf32(accS[mt][0], ah, xr_l, nxi_l);
+                            mma_tf32(accS[mt][0], al, xr_h, nxi_h);
+                            mma_tf32(accB[mt][1], ah, xi_h, xr_h);       // Im: Re G Im t + Im G Re t
+                            mma_tf32(accS[mt][1], ah, xi_l, xr_l);
+                            mma_tf32(accS[mt][1], al, xi_h, xr_h);
+                        }
+                    }
+                }
+                // this warp's partial products (its K blocks) -> red[wid][rhs][row]
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int row = 16 * mt + fg + 8 * (e >> 1), q = 2 * ft + (e & 1);
+                        red[((size_t)wid * MMA_RHS + q) * RP + row] =
+                            make_float2(accB[mt][0][e] + accS[mt][0][e], accB[mt][1][e] + accS[mt][1][e]);
+                    }
+            }
+            load_g(s + 1);   // next line's fragments, in flight during the exchange
+            if (tin) {
+                __syncthreads();
+                if (ov[0]) {
+                    const int q = oq[0], r = orow[0], wpp = 8 / tpo;
+                    float2 sum = make_float2(0.f, 0.f);
+                    for (int w = part * wpp; w < (part + 1) * wpp; ++w) {
+                        const float2 v = red[((size_t)w * MMA_RHS + q) * RP + r];
+                        sum.x += v.x;
+                        sum.y += v.y;
+                    }
+                    acc[0].x = sum.x;
+                    acc[0].y = sum.y;
+                }
+            }
+        } else if (tin) {
             if (pf) {
                 const V *Gb = sG + (size_t)(s & 1) * rpc * nzp;
 #pragma unroll
-                for (int u = 0; u < SW_MAXOPT; ++u) {
-                    const int o = pr + u * ngrp;
-                    if (o < nout)
-                        acc[u] = dot_row_il(Gb + (size_t)(o % nrows) * nzp, tin + (size_t)(o / nrows) * nzp, nz, part, tpo);
+                for (int u = 0; u < NOPT; ++u) {
+                    if (ov[u])
+                        acc[u] = dot_row_il(Gb + (size_t)orow[u] * nzp, tin + (size_t)oq[u] * nzp, nz, part, tpo);
                 }
             } else {
                 const V *Gi = Gs + (size_t)i * nz * nz;
@@ -390,10 +535,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                         for (int b = lane; b < kw; b += 32) sG[(size_t)r * kcp + b] = Gi[(size_t)(r0 + r) * nz + kc + b];
                     __syncthreads();
 #pragma unroll
-                    for (int u = 0; u < SW_MAXOPT; ++u) {
-                        const int o = pr + u * ngrp;
-                        if (o < nout) {
-                            const V d = dot_row_il(sG + (size_t)(o % nrows) * kcp, tin + (size_t)(o / nrows) * nzp + kc,
+                    for (int u = 0; u < NOPT; ++u) {
+                        if (ov[u]) {
+                            const V d = dot_row_il(sG + (size_t)orow[u] * kcp, tin + (size_t)oq[u] * nzp + kc,
                                                    kw, part, tpo);
                             acc[u].x += d.x;
                             acc[u].y += d.y;
@@ -406,7 +550,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         // the K parts of every output meet in adjacent lanes
         for (int mm = 1; mm < tpo; mm <<= 1) {
 #pragma unroll
-            for (int u = 0; u < SW_MAXOPT; ++u) {
+            for (int u = 0; u < NOPT; ++u) {
                 acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, mm);
                 acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, mm);
             }
@@ -424,23 +568,20 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             dstbuf = sY + (size_t)((s + 1) & 1) * R * nzp; dstbar = &bars[(s + 1) & 1];
         }
         const uint32_t lbar = dstbar ? smem_u32(dstbar) : 0u;
+        const uint32_t lbuf = dstbuf ? smem_u32(dstbuf) : 0u;
 #pragma unroll
-        for (int u = 0; u < SW_MAXOPT; ++u) {
-            const int o = pr + u * ngrp;
-            if (o < nout) {
-                const int r = o % nrows, q = o / nrows;
-                const int j = r0 + r;
+        for (int u = 0; u < NOPT; ++u) {
+            if (ov[u]) {
                 const V v = mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
                 vlast[u] = v;
                 if (dstbuf) {
-                    const TG c = (j == 0 || j == nz - 1) ? c_edge : c_in;
-                    const V cv = mkc<TG>(c * v.x, c * v.y);
-                    const uint32_t la = smem_u32(dstbuf + (size_t)q * nzp + j);
+                    const V cv = mkc<TG>(ocoef[u] * v.x, ocoef[u] * v.y);
+                    const uint32_t la = lbuf + obyte[u];
                     for (int t = t_lo + part; t < t_hi; t += tpo)
                         st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
                 }
                 if (part == 0) {
-                    const size_t off = (size_t)q * N + (size_t)i * nz + j;
+                    const size_t off = ogl[u] + (size_t)i * nz;
                     if (fp32 || !final_line) {
                         Ys[off] = v;   // mixed: the FP64 promotion runs in accumulate_kernel
                     } else {
@@ -504,11 +645,22 @@ static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
     return n;
 }
 
+template <typename TG> using SweepFn = void (*)(SweepArgs<TG>);
+
+// kernel of the tensor-pipe product with MT m tiles and KP K blocks per warp (null if none)
+template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP) {
+    if constexpr (sizeof(TG) == 4) {
+        if (MT == 1 && KP == 1) return line_sweep_kernel<TG, 1, 1>;
+        if (MT == 1 && KP == 2) return line_sweep_kernel<TG, 1, 2>;
+        if (MT == 2 && KP == 4) return line_sweep_kernel<TG, 2, 4>;
+    }
+    return nullptr;
+}
+
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
                               double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
                               cudaStream_t st, int mid) {
-    const void *fn = (const void *)line_sweep_kernel<TG>;
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
     const int teams = (mid < g.nx - 1) ? 2 : 1;
@@ -516,6 +668,9 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     cs = cs < 1 ? 1 : (cs > 16 / teams ? 16 / teams : cs);
     // tuning overrides: CTAs per team and right-hand sides per cluster
     const char *env_cs = getenv("HELM_SWEEP_CS"), *env_r = getenv("HELM_SWEEP_R");
+    // HELM_SWEEP_CUDA_CORES=1 keeps complex-FP32 sweeps on the CUDA-core product
+    const char *env_cc = getenv("HELM_SWEEP_CUDA_CORES");
+    const bool allow_mma = !(env_cc && atoi(env_cc) > 0);
     if (env_cs && atoi(env_cs) > 0) cs = std::min(atoi(env_cs), 16 / teams);
     cudaError_t e;
     // pre-pass Y_i = G_i b_i (all lines at once)
@@ -554,7 +709,38 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             else if (pf) pf = 0;
             else return cudaErrorInvalidConfiguration;
         }
-        const size_t smem = smem_of(R, pf);
+        size_t smem = smem_of(R, pf);
+        int tpo = tpo_of(R);
+        SweepFn<TG> kfn = line_sweep_kernel<TG, 0, 0>;
+        // tensor-pipe product: complex FP32, even n_z (16-byte fragment loads), at most two m
+        // tiles of rows per CTA and K blocks that the kernels below cover; one n tile of eight
+        // right-hand sides per cluster
+        {
+            const int np = (nz + 7) / 8;
+            int MT = 0, KP = 0;
+            if (sizeof(TG) == 4 && allow_mma && (nz & 1) == 0) {
+                if (rpc <= 16 && np <= 8) { MT = 1; KP = 1; }
+                else if (rpc <= 16 && np <= 16) { MT = 1; KP = 2; }
+                else if (rpc <= 32 && np <= 32) { MT = 2; KP = 4; }
+            }
+            SweepFn<TG> mfn = MT > 0 ? sweep_mma_fn<TG>(MT, KP) : nullptr;
+            if (mfn) {
+                int Rm = std::min(nrhs, MMA_RHS);
+                if (rchunk > 0 && Rm > rchunk) Rm = rchunk;
+                if (env_r && atoi(env_r) > 0) Rm = std::min(atoi(env_r), MMA_RHS);
+                const size_t nzp = (size_t)padded_mma(nz);
+                const size_t sm = (size_t)32 + vsz * 5 * (size_t)Rm * nzp + vsz * 2 * (size_t)Rm * rpc +
+                                  sizeof(float2) * 8 * MMA_RHS * (size_t)(16 * MT + 2);
+                if (sm <= SW_SMEM_MAX) {
+                    kfn = mfn;
+                    R = Rm;
+                    smem = sm;
+                    tpo = MT == 1 ? 2 : 1;   // outputs of the K halves (warps 0-3, 4-7) meet by shuffle
+                    pf = 1;
+                }
+            }
+        }
+        const void *fn = (const void *)kfn;
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int csz = teams * cs;
@@ -567,7 +753,6 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             }
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        const int tpo = tpo_of(R);
         SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, accumulate, status};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
@@ -583,7 +768,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         cfg.numAttrs = 1;
         cudaError_t le = cudaSuccess;
         HELM_TRACED(sizeof(TG) == 8 ? K_SWEEP64 : K_SWEEP32, st,
-                    (le = cudaLaunchKernelEx(&cfg, line_sweep_kernel<TG>, a)));
+                    (le = cudaLaunchKernelEx(&cfg, kfn, a)));
         if (le != cudaSuccess || sizeof(TG) == 8) return le;
         const size_t n = (size_t)n_sys * nrhs * g.nx * g.nz;
         const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
