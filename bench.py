@@ -150,6 +150,8 @@ def kernel_cost(name, w, n_cols_per_solve):
         return flops, byts
     if name == "residual_fp64":
         return 40.0 * N * nrhs * n_sys, (48.0 * nrhs + 16.0) * N * n_sys
+    if name == "refine_update":   # x', r from x, delta, b (FP32 pairs) and the diagonal
+        return None, (64.0 * nrhs + 16.0) * N * n_sys
     return None, None
 
 

@@ -144,10 +144,10 @@ helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *
  * framework whose caching allocator owns the free device memory, or a loop that cannot
  * take the device-wide synchronisation of cudaMalloc / cudaFree).  The paper has no
  * counterpart: this is a property of the library, not of the method.
- * The working memory of the refinement (FP32 line vectors, FP64 residuals, per-column
- * norms) lives in one fixed 32 MiB array in device global memory that every GPU loading
- * the library holds until exit; the caller still passes B_dev and X_dev.  Limits:
- * n_omega * nrhs * N * 24 bytes (mixed; norms only for FP64) within 32 MiB and at most
+ * The working memory of the refinement (right-hand side and iterates as FP32 pairs, FP32
+ * line vectors, per-column norms) lives in one fixed 32 MiB array in device global memory
+ * that every GPU loading the library holds until exit; the caller still passes B_dev and
+ * X_dev.  Limits: n_omega * nrhs * N * 64 bytes (mixed; norms only for FP64) within 32 MiB and at most
  * 16384 columns, else HELM_EINVAL.  The first call on a device resolves the array's
  * device address with that device current: make it before any stream capture.  Calls
  * share the array (each clears what must start at zero); calls that overlap on the GPU

@@ -155,6 +155,18 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
         helm_factor_destroy(f);
         return HELM_ESINGULAR;
     }
+    if (prec == HELM_MIXED) {   // diagonal of A as FP32 pairs for the refinement residual
+        const size_t n = (size_t)op->n_omega * g.nx * g.nz;
+        if ((s = dev_alloc((void **)&f->diag2, n * sizeof(float4), "cudaMalloc(diag pairs)")) != HELM_OK) {
+            helm_factor_destroy(f);
+            return s;
+        }
+        if ((e = launch_split_diag(n, op->diag, f->diag2, op->st)) != cudaSuccess) {
+            helm_set_error("helm_factor: split diagonal", e);
+            helm_factor_destroy(f);
+            return HELM_ECUDA;
+        }
+    }
     *out = f;
     return HELM_OK;
 }
@@ -163,7 +175,11 @@ extern "C" void helm_factor_destroy(helm_factor_t *f) {
     if (!f) return;
     dev_free(f->G);
     dev_free(f->xch);
-    dev_free(f->r);
+    dev_free(f->diag2);
+    dev_free(f->bd);
+    dev_free(f->xa);
+    dev_free(f->xb);
+    dev_free(f->r32);
     dev_free(f->y);
     dev_free(f->norms);
     if (f->norms_host) cudaFreeHost(f->norms_host);
@@ -175,19 +191,25 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
     const helm_op *op = f->op;
     const size_t cols = (size_t)op->n_omega * nrhs;
     const size_t N = (size_t)op->g.nx * op->g.nz;
-    dev_free(f->r);
+    dev_free(f->bd);
+    dev_free(f->xa);
+    dev_free(f->xb);
+    dev_free(f->r32);
     dev_free(f->y);
     dev_free(f->norms);
     if (f->norms_host) cudaFreeHost(f->norms_host);
-    f->r = nullptr;
-    f->y = nullptr;
+    f->bd = f->xa = f->xb = nullptr;
+    f->r32 = f->y = nullptr;
     f->norms = nullptr;
     f->norms_host = nullptr;
     f->cap = 0;
     helm_status s;
-    if ((s = dev_alloc((void **)&f->r, cols * N * sizeof(double2), "cudaMalloc(residual)")) != HELM_OK) return s;
     if (f->prec == HELM_MIXED &&
-        (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "cudaMalloc(work)")) != HELM_OK)
+        ((s = dev_alloc((void **)&f->bd, cols * N * sizeof(float4), "cudaMalloc(rhs pairs)")) != HELM_OK ||
+         (s = dev_alloc((void **)&f->xa, cols * N * sizeof(float4), "cudaMalloc(iterate)")) != HELM_OK ||
+         (s = dev_alloc((void **)&f->xb, cols * N * sizeof(float4), "cudaMalloc(iterate)")) != HELM_OK ||
+         (s = dev_alloc((void **)&f->r32, cols * N * sizeof(float2), "cudaMalloc(residual)")) != HELM_OK ||
+         (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "cudaMalloc(work)")) != HELM_OK))
         return s;
     if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "cudaMalloc(norms)")) != HELM_OK) return s;
     if (cudaMallocHost((void **)&f->norms_host, cols * 2 * sizeof(double)) != cudaSuccess) {
@@ -199,21 +221,75 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
     return HELM_OK;
 }
 
-// max over columns of ||r|| / ||b|| from the norms buffer (synchronises)
-static helm_status read_relres(helm_factor_t *f, int nrhs, double *out) {
-    const helm_op *op = f->op;
-    const size_t cols = (size_t)op->n_omega * nrhs;
-    cudaError_t e = cudaMemcpyAsync(f->norms_host, f->norms, cols * 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                                    op->st);
+helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, double *norms_host, double *out) {
+    cudaError_t e = cudaMemcpyAsync(norms_host, norms_dev, cols * 2 * sizeof(double), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
     if (e != cudaSuccess) { helm_set_error("read residual norms", e); return HELM_ECUDA; }
     double mx = 0.0;
     for (size_t c = 0; c < cols; ++c) {
-        const double rr = f->norms_host[2 * c], bb = f->norms_host[2 * c + 1];
+        const double rr = norms_host[2 * c], bb = norms_host[2 * c + 1];
         const double rel = bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0);
         if (!(rel <= mx)) mx = rel;  // propagates NaN
     }
     *out = mx;
+    return HELM_OK;
+}
+
+// Iterative refinement with the complex-FP32 factor: x_1 = A~^{-1} b, then
+// x_{k+1} = x_k + A~^{-1}(b - A x_k) until ||b - A x|| / ||b|| <= rtol (every column) or max_iter
+// correction solves.  The iterate and the residual are FP32 pairs (refine.cu) down to
+// kPairFloor or until the pair residual stops falling; a tighter rtol continues with FP64
+// residuals on the FP64 iterate.
+helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, double2 *X, int conj, double rtol,
+                         int max_iter, const MixedWork &w, int *iters, double *relres) {
+    constexpr double kPairFloor = 1e-12;   // well above the pair residual's floor (about 1e-13)
+    const helm_op *op = f->op;
+    const GridGeom &g = op->g;
+    const int n_sys = op->n_omega;
+    const int cols = n_sys * nrhs;
+    const size_t n = (size_t)cols * g.nx * g.nz;
+    const int rchunk = 16;
+    if (max_iter < 1) max_iter = 1;
+    cudaError_t e = launch_refine_start(g, cols, B, conj, w.bd, w.r32, w.norms, op->st);
+    if (e != cudaSuccess) { helm_set_error("refinement start", e); return HELM_ECUDA; }
+    auto sweep = [&]() {
+        return launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, w.r32, nullptr, w.y, 0, rchunk,
+                                        op->status, op->st, f->mid);
+    };
+    const float4 *x_in = nullptr;
+    float4 *x_out = w.xa;
+    int it = 0;
+    double rel = INFINITY, prev = INFINITY;
+    helm_status s;
+    for (;;) {   // FP32-pair phase
+        if ((e = sweep()) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+        ++it;
+        e = launch_refine_update(g, n_sys, nrhs, f->diag2, w.bd, x_in, w.y, x_out, w.r32, w.norms, op->st);
+        if (e != cudaSuccess) { helm_set_error("refinement update", e); return HELM_ECUDA; }
+        if ((s = max_relres(op, (size_t)cols, w.norms, w.norms_host, &rel)) != HELM_OK) return s;
+        x_in = x_out;
+        x_out = (x_out == w.xa) ? w.xb : w.xa;
+        if (rel <= rtol || it >= max_iter || !isfinite(rel) || rel <= kPairFloor || rel > 0.25 * prev) break;
+        prev = rel;
+    }
+    e = launch_refine_finish(n, x_in, conj, X, op->st);
+    if (e != cudaSuccess) { helm_set_error("refinement finish", e); return HELM_ECUDA; }
+    if (!(rel <= rtol) && it < max_iter && isfinite(rel)) {
+        // FP64 phase: r = b - A x in FP64 on the FP64 iterate, correction conj?(A~^{-1} conj?(r))
+        for (;;) {
+            e = cudaMemsetAsync(w.norms, 0, (size_t)cols * 2 * sizeof(double), op->st);
+            if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, w.r32, w.norms, conj, op->st);
+            if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
+            if ((s = max_relres(op, (size_t)cols, w.norms, w.norms_host, &rel)) != HELM_OK) return s;
+            if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
+            if ((e = sweep()) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+            e = launch_refine_accumulate(n, w.y, conj, X, op->st);
+            if (e != cudaSuccess) { helm_set_error("refinement accumulate", e); return HELM_ECUDA; }
+            ++it;
+        }
+    }
+    *iters = it;
+    *relres = rel;
     return HELM_OK;
 }
 
@@ -222,45 +298,31 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     const helm_op *op = f->op;
     const GridGeom &g = op->g;
     const int n_sys = op->n_omega;
-    const size_t N = (size_t)g.nx * g.nz;
-    const int cs = pick_cluster_size(g.nz);
+    const size_t cols = (size_t)n_sys * nrhs;
     const int rchunk = 16;
     cudaError_t e;
     helm_status s;
     if (info) { info->iters = 0; info->max_relres = -1.0; }
     if (f->prec == HELM_FP64) {
-        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status, op->st, f->mid);
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, rchunk, op->status, op->st,
+                                      f->mid);
         if (e != cudaSuccess) { helm_set_error("sweep fp64", e); return HELM_ECUDA; }
         if (info) {
             info->iters = 1;
             if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
-            e = cudaMemsetAsync(f->norms, 0, (size_t)n_sys * nrhs * 2 * sizeof(double), op->st);
+            e = cudaMemsetAsync(f->norms, 0, cols * 2 * sizeof(double), op->st);
             if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, f->norms, conj, op->st);
             if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
-            if ((s = read_relres(f, nrhs, &info->max_relres)) != HELM_OK) return s;
+            if ((s = max_relres(op, cols, f->norms, f->norms_host, &info->max_relres)) != HELM_OK) return s;
         }
         return HELM_OK;
     }
-    // mixed: x = A~^{-1} b, then x += A~^{-1}(b - A x) until ||b - A x|| / ||b|| <= rtol
     if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
-    if (max_iter < 1) max_iter = 1;
-    e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, f->y, conj, 0, rchunk, op->status, op->st, f->mid);
-    if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
-    int it = 1;
+    const MixedWork w{f->bd, f->xa, f->xb, f->r32, f->y, f->norms, f->norms_host};
+    int it = 0;
     double rel = INFINITY;
-    for (;;) {
-        e = cudaMemsetAsync(f->norms, 0, (size_t)n_sys * nrhs * 2 * sizeof(double), op->st);
-        if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, f->r, f->norms, conj, op->st);
-        if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
-        if ((s = read_relres(f, nrhs, &rel)) != HELM_OK) return s;
-        if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
-        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, f->r, X, f->y, conj, 1, rchunk,
-                                     op->status, op->st, f->mid);
-        if (e != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
-        ++it;
-    }
+    if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;
     if (info) { info->iters = it; info->max_relres = rel; }
-    (void)N;
     int st_host = 0;
     e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);

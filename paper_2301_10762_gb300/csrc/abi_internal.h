@@ -24,12 +24,21 @@ struct helm_factor {
     int mid = 0;           // middle line of the (twisted) line factorisation
     void *G = nullptr;     // [n_omega][nx][nz][nz] complex (FP64 or FP32)
     void *xch = nullptr;   // factor exchange slots
+    float4 *diag2 = nullptr;   // mixed: [n_omega][N] diagonal of A as FP32 pairs
     // solve scratch, sized for `cap` right-hand sides per frequency
     int cap = 0;
-    double2 *r = nullptr;  // FP64 residuals
-    float2 *y = nullptr;   // FP32 working vectors (mixed)
+    float4 *bd = nullptr, *xa = nullptr, *xb = nullptr;   // mixed: b and the iterate (ping-pong), FP32 pairs
+    float2 *r32 = nullptr, *y = nullptr;                  // mixed: correction right-hand side and result
     double *norms = nullptr;
     double *norms_host = nullptr;
+};
+
+// working memory of one mixed-precision solve of n_omega x nrhs columns
+struct MixedWork {
+    float4 *bd, *xa, *xb;
+    float2 *r32, *y;
+    double *norms;        // device [cols][2]
+    double *norms_host;   // host [cols][2]
 };
 
 // acquisition on the device
@@ -47,5 +56,10 @@ void dev_free(void *p);
 helm_status factor_reserve(helm_factor_t *f, int nrhs);
 helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
                        helm_solve_info *info, int conj);
+// mixed-precision refinement (refine.cu kernels) to ||b - A x|| / ||b|| <= rtol per column
+helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, double2 *X, int conj, double rtol,
+                         int max_iter, const MixedWork &w, int *iters, double *relres);
+// max over columns of ||r|| / ||b|| from a device norms buffer (synchronises the op's stream)
+helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, double *norms_host, double *out);
 helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d);
 void acq_free(DevAcq *d);

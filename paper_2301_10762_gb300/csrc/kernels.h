@@ -25,13 +25,29 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
                                int *status, int cs, cudaStream_t st, int *mid_out);
 
 // ---- sweep.cu
+// B in the working precision; TG = double writes X (conjugated if conj), TG = float writes Y
 template <typename TG>
-cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
-                              cudaStream_t st, int mid);
+cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
+                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid);
+// FP64 residual B - A X (A^H X for conj), norms[col] += (||R||^2, ||B||^2); R32 = conj?(R) in FP32 if given
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
-                            const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st);
+                            const double2 *X, float2 *R32, double *norms, int conj, cudaStream_t st);
 
 int pick_cluster_size(int nz);
+
+// ---- refine.cu (mixed-precision refinement in FP32-pair arithmetic)
+// diag2[s][k] = (hi.re, hi.im, lo.re, lo.im) of the FP64 diagonal
+cudaError_t launch_split_diag(size_t n, const double2 *diag, float4 *diag2, cudaStream_t st);
+// bd = pair form of conj?(B), r32 = its leading part; norms[col][1] = ||B||^2, norms[col][0] = 0
+cudaError_t launch_refine_start(const GridGeom &g, int cols, const double2 *B, int conj, float4 *bd, float2 *r32,
+                                double *norms, cudaStream_t st);
+// x_out = x_in (none: 0) + delta; r32 = leading part of bd - A x_out; norms[col][0] += ||r||^2
+cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const float4 *diag2, const float4 *bd,
+                                 const float4 *x_in, const float2 *delta, float4 *x_out, float2 *r32, double *norms,
+                                 cudaStream_t st);
+// X = conj?(hi + lo) in FP64
+cudaError_t launch_refine_finish(size_t n, const float4 *x, int conj, double2 *X, cudaStream_t st);
+// X += conj?(delta) in FP64 (refinement tail with FP64 residuals)
+cudaError_t launch_refine_accumulate(size_t n, const float2 *delta, int conj, double2 *X, cudaStream_t st);
 
 }  // namespace helm

@@ -6,8 +6,8 @@
 // it), a host framework whose caching allocator already owns the free device memory,
 // and latency-critical loops that cannot afford the device-wide synchronisation that
 // cudaMalloc / cudaFree imply.  helm_solve meets the working memory of the mixed path
-// (FP32 line vectors, FP64 residuals, per-column norms) by growing buffers inside the
-// factor handle on first use, which allocates.  This variant runs the same kernels with
+// (FP32-pair right-hand side and iterates, FP32 line vectors, per-column norms) by growing
+// buffers inside the factor handle on first use, which allocates.  This variant runs the same kernels with
 // that working memory placed in one fixed array in device global memory, declared
 // below, which every GPU that loads the library holds until the process exits.
 //
@@ -64,24 +64,6 @@ helm_status scratch_address(void **out) {
     return HELM_OK;
 }
 
-helm_status max_relres(const helm_op *op, const double *norms_dev, size_t cols, double *out) {
-    cudaError_t e = cudaMemcpyAsync(g_norms_host, norms_dev, cols * 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                                    op->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
-    if (e != cudaSuccess) {
-        helm_set_error("helm_solve_noalloc: norms", e);
-        return HELM_ECUDA;
-    }
-    double mx = 0.0;
-    for (size_t c = 0; c < cols; ++c) {
-        const double rr = g_norms_host[2 * c], bb = g_norms_host[2 * c + 1];
-        const double rel = bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0);
-        if (!(rel <= mx)) mx = rel;
-    }
-    *out = mx;
-    return HELM_OK;
-}
-
 }  // namespace
 
 extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
@@ -99,12 +81,12 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     const size_t N = (size_t)g.nx * g.nz;
     const size_t cols = (size_t)n_sys * nrhs;
     const bool mixed = f->prec == HELM_MIXED;
-    const size_t y_bytes = mixed ? align256(cols * N * sizeof(float2)) : 0;
-    const size_t r_bytes = mixed ? align256(cols * N * sizeof(double2)) : 0;
+    const size_t p_bytes = mixed ? align256(cols * N * sizeof(float4)) : 0;   // bd, xa, xb
+    const size_t v_bytes = mixed ? align256(cols * N * sizeof(float2)) : 0;   // r32, y
     const size_t n_bytes = align256(cols * 2 * sizeof(double));
-    if (cols > kMaxCols || y_bytes + r_bytes + n_bytes > kScratchBytes) {
+    if (cols > kMaxCols || 3 * p_bytes + 2 * v_bytes + n_bytes > kScratchBytes) {
         helm_set_msg("helm_solve_noalloc: problem larger than the fixed working array "
-                     "(32 MiB: n_omega*nrhs*N*24 bytes plus norms, at most 16384 columns)");
+                     "(32 MiB: n_omega*nrhs*N*64 bytes plus norms, at most 16384 columns)");
         return HELM_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_mu);
@@ -112,9 +94,6 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     helm_status s = scratch_address(&base);
     if (s != HELM_OK) return s;
     unsigned char *p = (unsigned char *)base;
-    float2 *Y = mixed ? (float2 *)p : nullptr;
-    double2 *R = mixed ? (double2 *)(p + y_bytes) : nullptr;
-    double *norms = (double *)(p + y_bytes + r_bytes);
     const double2 *B = (const double2 *)B_dev;
     double2 *X = (double2 *)X_dev;
     const int conj = adjoint ? 1 : 0;
@@ -123,31 +102,26 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     double rel = -1.0;
     int it = 1;
     if (!mixed) {
-        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, 0, rchunk, op->status,
-                                      op->st, f->mid);
+        double *norms = (double *)p;
+        e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, rchunk, op->status, op->st,
+                                      f->mid);
         if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
         if (info) {
             e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
             if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, norms, conj, op->st);
             if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: residual", e); return HELM_ECUDA; }
-            if ((s = max_relres(op, norms, cols, &rel)) != HELM_OK) return s;
+            if ((s = max_relres(op, cols, norms, g_norms_host, &rel)) != HELM_OK) return s;
         }
     } else {
-        if (max_iter < 1) max_iter = 1;
-        e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, B, X, Y, conj, 0, rchunk, op->status,
-                                     op->st, f->mid);
-        if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
-        for (;;) {
-            e = cudaMemsetAsync(norms, 0, cols * 2 * sizeof(double), op->st);
-            if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, R, norms, conj, op->st);
-            if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: residual", e); return HELM_ECUDA; }
-            if ((s = max_relres(op, norms, cols, &rel)) != HELM_OK) return s;
-            if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
-            e = launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, R, X, Y, conj, 1, rchunk,
-                                         op->status, op->st, f->mid);
-            if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: sweep", e); return HELM_ECUDA; }
-            ++it;
-        }
+        MixedWork w;
+        w.bd = (float4 *)p;
+        w.xa = (float4 *)(p + p_bytes);
+        w.xb = (float4 *)(p + 2 * p_bytes);
+        w.r32 = (float2 *)(p + 3 * p_bytes);
+        w.y = (float2 *)(p + 3 * p_bytes + v_bytes);
+        w.norms = (double *)(p + 3 * p_bytes + 2 * v_bytes);
+        w.norms_host = g_norms_host;
+        if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;
     }
     int st_host = 0;
     e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);

@@ -4,17 +4,16 @@
 //   forward   y_0 = G_0 b_0,            y_i = G_i (b_i - C_i y_{i-1}),
 //   backward  x_{nx-1} = y_{nx-1},      x_i = y_i - G_i C_{i+1} x_{i+1},
 // two dense (n_z x n_z) x (n_z x R) products per line with all right-hand sides of a
-// chunk as the product's N dimension.  The adjoint solve of A^H uses the same factor:
-// A is complex symmetric, so (A^H)^{-1} b = conj(A^{-1} conj(b)).
+// chunk as the product's N dimension (the twisted variant runs both halves at once, see
+// line_sweep_kernel).  The adjoint solve of A^H uses the same factor: A is complex
+// symmetric, so (A^H)^{-1} b = conj(A^{-1} conj(b)).
 //
-// One thread-block cluster handles one (system, right-hand-side chunk); CTA r of the
-// cluster owns a slab of rows of every line.  Line i+1 needs all rows of line i, so
-// every line step ends with one hardware cluster barrier; the vector y_{i-1} (or
-// x_{i+1}) is read back from global memory (L2) by every CTA of the cluster.
+// One thread-block cluster handles one (system, right-hand-side chunk); CTA r of a team owns
+// a slab of rows of every line and pushes its new rows, scaled by the line coupling, into the
+// shared memory of every CTA of the team (st.async with mbarrier completion).
 //
-// Mixed precision: TG = float keeps the factor and the working vector in complex FP32;
-// the input is an FP64 residual and the result is added to the FP64 iterate in the
-// final pass (x += A~^{-1} r).  TG = double is the plain FP64 path (Y aliases X).
+// TG = float is the correction solve of the mixed-precision refinement (refine.cu): complex
+// FP32 factor, right-hand side and result.  TG = double is the plain FP64 path (Y aliases X).
 #include <algorithm>
 #include <stdlib.h>
 #include "kernels.h"
@@ -33,16 +32,12 @@ template <typename TG> struct SweepArgs {
     int nrhs, R, cs, n_chunks, prefetch, tpo;   // tpo: threads per output (K split), power of 2
     int mid, teams;                             // twisted middle line and team count (factor layout)
     const cx_t<TG> *G;   // [n_sys][nx][nz][nz]
-    const double2 *B;    // [n_sys][nrhs][N]
+    const cx_t<TG> *B;   // [n_sys][nrhs][N] right-hand sides in the working precision
     double2 *X;          // [n_sys][nrhs][N]
     cx_t<TG> *Y;         // forward vectors y_i, [n_sys][nrhs][N] (== X for TG = double)
-    int conj, accumulate;
+    int conj;            // FP64 path: B and X conjugated (adjoint solve)
     int *status;
 };
-
-template <typename TG> __device__ __forceinline__ cx_t<TG> in_cast(double2 a);
-template <> __device__ __forceinline__ double2 in_cast<double>(double2 a) { return a; }
-template <> __device__ __forceinline__ float2 in_cast<float>(double2 a) { return to_c64(a); }
 
 // Padded row stride (in complex elements) of the shared-memory operands of the sweep product.
 // A quarter-warp (the unit of a 16-byte shared load) reads 8/tpo rows x tpo adjacent 16-byte
@@ -130,8 +125,9 @@ __device__ __forceinline__ int step_line(int s, int nx) { return s < nx ? s : 2 
 
 // Pre-pass: Y_i = G_i b_i for every line i of every system at once (the half of the
 // forward sweep that does not depend on the recurrence), a batched complex GEMM over
-// (system, line, row tile, right-hand-side chunk).  b is the FP64 input (conjugated
-// for the adjoint), cast to TG.
+// (system, line, row tile, right-hand-side chunk).  b is the input in the working precision
+// (conjugated for the adjoint FP64 solve).  The CUDA-core sweep uses it; the tensor-path sweep
+// takes b_i into its own product instead.
 constexpr int PP_ROWS = 64;    // rows of G_i per CTA
 constexpr int PP_RHS = 16;     // right-hand sides per CTA
 constexpr int PP_KC = 32;      // K chunk
@@ -141,7 +137,7 @@ constexpr int PP_KC = 32;      // K chunk
 // tr + 32, whose padded stride keeps the G reads free of bank conflicts.
 template <typename TG>
 __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nrhs, const cx_t<TG> *G,
-                                                             const double2 *B, cx_t<TG> *Y, int conj) {
+                                                             const cx_t<TG> *B, cx_t<TG> *Y, int conj) {
     using V = cx_t<TG>;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int n_rt = (nz + PP_ROWS - 1) / PP_ROWS;
@@ -158,7 +154,7 @@ __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nr
     __shared__ V sb[PP_RHS][KP];     // right-hand sides x K chunk
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int tr = tid & 31, tq = tid >> 5;    // rows tr, tr + 32; right-hand sides 4 tq .. 4 tq + 3
-    const double2 *Bs = B + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz;
+    const V *Bs = B + ((size_t)sys * nrhs + q0) * N + (size_t)i * nz;
     const V *Gi = G + ((size_t)sys * nx + i) * nz * nz + (size_t)r0 * nz;
     V acc[2][4];
 #pragma unroll
@@ -171,9 +167,8 @@ __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nr
             for (int j = lane; j < PP_KC; j += 32) {
                 V v = mkc<TG>(TG(0), TG(0));
                 if (q < Rc && j < kw) {
-                    double2 bv = Bs[(size_t)q * N + kc + j];
-                    if (conj) bv.y = -bv.y;
-                    v = in_cast<TG>(bv);
+                    v = Bs[(size_t)q * N + kc + j];
+                    if (conj) v.y = -v.y;
                 }
                 sb[q][j] = v;
             }
@@ -327,7 +322,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     auto prefetch = [&](int s) {
         if (s >= nsteps) return;
         const int i = line_of(s);
-        {   // own rows of line i: G_i b_i (forward, middle) or y_i (backward)
+        if (MT == 0 || kind_of(s) == 2) {   // own rows of line i: G_i b_i (forward, middle) or y_i (backward)
             V *dst = sOwn + (size_t)(s & 1) * R * rpc;
             for (int q = wid; q < Rc; q += SW_THREADS / 32)
                 for (int r = lane; r < nrows; r += 32)
@@ -350,10 +345,15 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     const int fg = lane >> 2, ft = lane & 3;
     const int NP = (nz + 7) >> 3;
     float4 gfr[MT > 0 ? MT : 1][2][KP > 0 ? KP : 1];
+    float4 bfr[KP > 0 ? KP : 1];   // b_i (forward and middle lines): rhs fg, columns 8j + 2t, 8j + 2t + 1
+    const V *Bs = a.B + ((size_t)sys * a.nrhs + q0) * N;
     auto load_g = [&](int s1) {
         if constexpr (MT > 0) {
             if (s1 >= nsteps) return;
-            const float2 *Gl = reinterpret_cast<const float2 *>(Gs) + ((size_t)line_of(s1) * nz + r0) * nz;
+            const int i1 = line_of(s1);
+            const bool fwd1 = kind_of(s1) != 2;
+            const float2 *Gl = reinterpret_cast<const float2 *>(Gs) + ((size_t)i1 * nz + r0) * nz;
+            const float2 *Bl = reinterpret_cast<const float2 *>(Bs) + (size_t)fg * N + (size_t)i1 * nz;
 #pragma unroll
             for (int jj = 0; jj < KP; ++jj) {
                 const int j = wid + 8 * jj, kc = 8 * j + 2 * ft;
@@ -366,6 +366,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                                              ? __ldg(reinterpret_cast<const float4 *>(Gl + (size_t)row * nz + kc))
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
+                bfr[jj] = (fwd1 && j < NP && kc < nz && fg < Rc) ? __ldg(reinterpret_cast<const float4 *>(Bl + kc))
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
     };
@@ -397,6 +399,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     for (int u = 0; u < NOPT; ++u) vlast[u] = mkc<TG>(TG(0), TG(0));
     prefetch(0);
     cp_async_commit();
+    load_g(0);
     for (int s = 0; s < nsteps; ++s) {
         const int kind = kind_of(s);
         const int i = line_of(s);
@@ -423,13 +426,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         if (kind == 1) { tin = sMid; tin2 = (teams == 2) ? sMid + (size_t)R * nzp : nullptr; }
         else if (kind == 2 && bi == 0) tin = sX;
         else if (!(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
-        double2 xold[NOPT];
         const bool final_line = (kind != 0);
-#pragma unroll
-        for (int u = 0; u < NOPT; ++u) {
-            xold[u] = make_double2(0.0, 0.0);
-            if (!fp32 && ov[u] && a.accumulate && final_line) xold[u] = Xs[ogl[u] + (size_t)i * nz];
-        }
         cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
         if (s_abort) return;
@@ -451,12 +448,15 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         const bool same_line = (team == 1 && kind == 2 && bi == 0);
 #pragma unroll
         for (int u = 0; u < NOPT; ++u) {
-            yown[u] = ov[u] ? (same_line ? vlast[u] : sOwn[(size_t)(s & 1) * R * rpc + oq[u] * rpc + orow[u]])
-                            : mkc<TG>(TG(0), TG(0));
+            // the tensor path folds b_i into its forward product: v = 0 - G_i (t - b_i)
+            const bool own = MT == 0 || kind == 2;
+            yown[u] = (ov[u] && own) ? (same_line ? vlast[u] : sOwn[(size_t)(s & 1) * R * rpc + oq[u] * rpc + orow[u]])
+                                     : mkc<TG>(TG(0), TG(0));
             acc[u] = mkc<TG>(TG(0), TG(0));
         }
         if constexpr (MT > 0) {
-            if (tin) {
+            {
+                const bool fwd = kind != 2;
                 float accB[MT][2][4], accS[MT][2][4];   // hi*hi and the two cross terms
 #pragma unroll
                 for (int mt = 0; mt < MT; ++mt)
@@ -470,7 +470,10 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                     const int j = wid + 8 * jj, kc = 8 * j + 2 * ft;
                     if (j >= NP) break;   // warp-uniform
                     float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (fg < Rc && kc < nz) xv = *reinterpret_cast<const float4 *>(tv + (size_t)fg * nzp + kc);
+                    if (tin && fg < Rc && kc < nz) xv = *reinterpret_cast<const float4 *>(tv + (size_t)fg * nzp + kc);
+                    if (fwd) {   // product input t - b_i
+                        xv.x -= bfr[jj].x; xv.y -= bfr[jj].y; xv.z -= bfr[jj].z; xv.w -= bfr[jj].w;
+                    }
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         uint32_t xr_h, xr_l, xi_h, xi_l;
@@ -505,7 +508,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                     }
             }
             load_g(s + 1);   // next line's fragments, in flight during the exchange
-            if (tin) {
+            {
                 __syncthreads();
                 if (ov[0]) {
                     const int q = oq[0], r = orow[0], wpp = 8 / tpo;
@@ -583,11 +586,10 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 if (part == 0) {
                     const size_t off = ogl[u] + (size_t)i * nz;
                     if (fp32 || !final_line) {
-                        Ys[off] = v;   // mixed: the FP64 promotion runs in accumulate_kernel
+                        Ys[off] = v;   // complex FP32: the correction of the refinement
                     } else {
                         double2 d = make_double2((double)v.x, (double)v.y);
                         if (a.conj) d.y = -d.y;
-                        if (a.accumulate) { d.x += xold[u].x; d.y += xold[u].y; }
                         Xs[off] = d;
                     }
                 }
@@ -595,33 +597,6 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
     }
     cp_async_wait<0>();
-}
-
-// Mixed path: X = (accumulate ? X : 0) + conj?(delta), delta the complex-FP32 solution of the
-// sweep (FP64 promotion kept out of the sweep's critical path).
-__global__ void accumulate_kernel(size_t n, const float2 *Y, double2 *X, int conj, int accumulate) {
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const float2 y = Y[e];
-        double2 d = make_double2((double)y.x, conj ? -(double)y.y : (double)y.y);
-        if (accumulate) {
-            const double2 x = X[e];
-            d.x += x.x;
-            d.y += x.y;
-        }
-        X[e] = d;
-    }
-}
-
-static int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 132;
-        cudaGetLastError();
-    }
-    return n;
 }
 
 // Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
@@ -658,9 +633,8 @@ template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP) {
 }
 
 template <typename TG>
-cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const double2 *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int accumulate, int rchunk, int *status,
-                              cudaStream_t st, int mid) {
+cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
+                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid) {
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
     const int teams = (mid < g.nx - 1) ? 2 : 1;
@@ -668,18 +642,11 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     cs = cs < 1 ? 1 : (cs > 16 / teams ? 16 / teams : cs);
     // tuning overrides: CTAs per team and right-hand sides per cluster
     const char *env_cs = getenv("HELM_SWEEP_CS"), *env_r = getenv("HELM_SWEEP_R");
+    if (env_cs && atoi(env_cs) > 0) cs = std::min(atoi(env_cs), 16 / teams);
     // HELM_SWEEP_CUDA_CORES=1 keeps complex-FP32 sweeps on the CUDA-core product
     const char *env_cc = getenv("HELM_SWEEP_CUDA_CORES");
     const bool allow_mma = !(env_cc && atoi(env_cc) > 0);
-    if (env_cs && atoi(env_cs) > 0) cs = std::min(atoi(env_cs), 16 / teams);
     cudaError_t e;
-    // pre-pass Y_i = G_i b_i (all lines at once)
-    {
-        const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + PP_RHS - 1) / PP_RHS);
-        HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj)));
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
         // threads per output (K split): as many as fit the CTA's 256 threads twice over
@@ -696,7 +663,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         // right-hand sides per cluster (the chain is latency bound and the GPU otherwise
         // idle, so more clusters with fewer outputs each; 128 outputs per CTA measured best)
         int R = 1;
-        while (R * 2 <= 16 && rpc * R * 2 <= 128) R *= 2;   // ~128 outputs per CTA (measured best)
+        while (R * 2 <= 16 && rpc * R * 2 <= 128) R *= 2;
         if (rchunk > 0 && R > rchunk) R = rchunk;
         if (env_r && atoi(env_r) > 0) R = atoi(env_r);
         if (R > nrhs) R = nrhs;
@@ -712,6 +679,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         size_t smem = smem_of(R, pf);
         int tpo = tpo_of(R);
         SweepFn<TG> kfn = line_sweep_kernel<TG, 0, 0>;
+        bool mma = false;
         // tensor-pipe product: complex FP32, even n_z (16-byte fragment loads), at most two m
         // tiles of rows per CTA and K blocks that the kernels below cover; one n tile of eight
         // right-hand sides per cluster
@@ -733,6 +701,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
                                   sizeof(float2) * 8 * MMA_RHS * (size_t)(16 * MT + 2);
                 if (sm <= SW_SMEM_MAX) {
                     kfn = mfn;
+                    mma = true;
                     R = Rm;
                     smem = sm;
                     tpo = MT == 1 ? 2 : 1;   // outputs of the K halves (warps 0-3, 4-7) meet by shuffle
@@ -752,8 +721,14 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
                 continue;
             }
         }
+        if (!mma) {   // CUDA-core sweep: Y_i = G_i b_i for all lines first
+            const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + PP_RHS - 1) / PP_RHS);
+            HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj)));
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         const int n_chunks = (nrhs + R - 1) / R;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, accumulate, status};
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);
@@ -767,28 +742,26 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaError_t le = cudaSuccess;
-        HELM_TRACED(sizeof(TG) == 8 ? K_SWEEP64 : K_SWEEP32, st,
-                    (le = cudaLaunchKernelEx(&cfg, kfn, a)));
-        if (le != cudaSuccess || sizeof(TG) == 8) return le;
-        const size_t n = (size_t)n_sys * nrhs * g.nx * g.nz;
-        const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
-        HELM_TRACED(K_ACCUM, st, (accumulate_kernel<<<blocks, 256, 0, st>>>(n, (const float2 *)Y, X, conj, accumulate)));
-        return cudaGetLastError();
+        HELM_TRACED(sizeof(TG) == 8 ? K_SWEEP64 : K_SWEEP32, st, (le = cudaLaunchKernelEx(&cfg, kfn, a)));
+        return le;
     }
 }
 
 template cudaError_t launch_line_sweep<double>(const GridGeom &, int, int, const double2 *, const double2 *,
-                                               double2 *, double2 *, int, int, int, int *, cudaStream_t, int);
-template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const double2 *,
-                                              double2 *, float2 *, int, int, int, int *, cudaStream_t, int);
+                                               double2 *, double2 *, int, int, int *, cudaStream_t, int);
+template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const float2 *,
+                                              double2 *, float2 *, int, int, int *, cudaStream_t, int);
+
 
 // ------------------------------------------------------------------ FP64 residual
 // R = B - A X (A^H X for conj = 1) with the five-point operator, and per column the
 // squared norms ||R||^2 and ||B||^2 accumulated into norms[col][0..1] (pre-zeroed).
+// R32 (optional) receives conj?(R) in complex FP32: the right-hand side of the correction
+// solve A delta = conj?(R) of the FP64 refinement tail (refine.cu).
 constexpr int RES_THREADS = 256;
 
 __global__ void __launch_bounds__(RES_THREADS) residual_kernel(GridGeom g, int nrhs, const double2 *diag,
-                                                               const double2 *B, const double2 *X, double2 *R,
+                                                               const double2 *B, const double2 *X, float2 *R32,
                                                                double *norms, int conj, double cx_in, double cx_edge,
                                                                double cz_in, double cz_edge) {
     const int nx = g.nx, nz = g.nz, N = nx * nz;
@@ -811,7 +784,7 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(GridGeom g, int n
         if (j < nz - 1) { double2 v = x[k + 1]; ax.x += czi * v.x; ax.y += czi * v.y; }
         double2 b = B[col * N + k];
         double2 r = make_double2(b.x - ax.x, b.y - ax.y);
-        if (R) R[col * N + k] = r;
+        if (R32) R32[col * N + k] = make_float2((float)r.x, conj ? -(float)r.y : (float)r.y);
         rr = r.x * r.x + r.y * r.y;
         bb = b.x * b.x + b.y * b.y;
     }
@@ -838,10 +811,10 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(GridGeom g, int n
 }
 
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
-                            const double2 *X, double2 *R, double *norms, int conj, cudaStream_t st) {
+                            const double2 *X, float2 *R32, double *norms, int conj, cudaStream_t st) {
     const int N = g.nx * g.nz;
     dim3 grid((N + RES_THREADS - 1) / RES_THREADS, nrhs, n_sys);
-    HELM_TRACED(K_RESIDUAL, st, (residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R, norms, conj, coup_x(g, 1), coup_x(g, 0), coup_z(g, 1), coup_z(g, 0))));
+    HELM_TRACED(K_RESIDUAL, st, (residual_kernel<<<grid, RES_THREADS, 0, st>>>(g, nrhs, diag, B, X, R32, norms, conj, coup_x(g, 1), coup_x(g, 0), coup_z(g, 1), coup_z(g, 0))));
     return cudaGetLastError();
 }
 
