@@ -40,9 +40,10 @@ WORKLOAD = "hypergrad_step_128: 128x128, omega {5,10,15}, 16 sources, 32 receive
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 nominal of GB300 (vendor figure; the measured cuBLAS DGEMM reached 1.05)
 FP64_ALU_TFLOPS = 1.25
-# DRAM bytes per launch from an ncu capture of the same kernel build (None: not captured
-# for the current kernel).  Filled from the committed profile summaries.
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float] = {}
+# DRAM bytes (read + write) per launch from an ncu capture of the same kernel build, on this
+# workload (profiles/line_sweep_fp32_hypergrad_step_128.md); absent: not captured for the
+# current kernel.
+NCU_TRAFFIC_PER_LAUNCH: dict[str, float] = {"line_sweep_fp32": 56.71e6 + 0.63e6}
 
 
 def workload(rank=0, n=N_GRID):
@@ -141,7 +142,8 @@ def kernel_cost(name, w, n_cols_per_solve):
     if name.startswith("line_sweep"):
         esz = 8 if name.endswith("fp32") else 16
         flops = 16.0 * nx * nz * nz * nrhs * n_sys           # 2 sweeps x 8 flop per complex MAC
-        byts = 2.0 * n_sys * nx * nz * nz * esz + n_sys * nrhs * N * (16 + 16 + 2 * esz)
+        # factor read twice; b read, y written and read back, result written
+        byts = 2.0 * n_sys * nx * nz * nz * esz + n_sys * nrhs * N * 4.0 * esz
         return flops, byts
     if name.startswith("line_factor"):
         esz = 8 if name.endswith("fp32") else 16
@@ -167,7 +169,18 @@ def roofline(trace, w, peaks, prec):
     out = {"kernel": name, "share": st["total_ms"] / total_ms if total_ms else None,
            "avg_launch_us": avg_s * 1e6, "launches": st["timed"]}
     traffic = NCU_TRAFFIC_PER_LAUNCH.get(name)
-    if flops is not None and (name.startswith("line_sweep") or name.startswith("line_factor")):
+    if name.startswith("line_sweep") and byts is not None:
+        # the solve phase streams the factor: HBM-bound at these right-hand-side counts (its
+        # intensity, about nrhs/2 flop per byte, is far below the tensor ridge)
+        ach = byts / avg_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": traffic,
+                    "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else
+                                    "fallback 6800 GB/s"),
+                    "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops,
+                    "useful_tflops": flops / avg_s / 1e12})
+    elif flops is not None and name.startswith("line_factor"):
         fp32 = name.endswith("fp32")
         peak = FP32_ALU_TFLOPS if fp32 else FP64_ALU_TFLOPS
         ach = flops / avg_s / 1e12

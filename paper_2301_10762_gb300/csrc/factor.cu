@@ -254,12 +254,12 @@ template <> __device__ __forceinline__ double recip<double>(double x) { return _
 // 16 x 16 inverse (kb x kb block padded with the identity) of M (shared, row stride ld)
 // by one warp; lane (r, h) holds row r, column half h of [M | I].  Partial pivoting
 // without row swaps: the pivot of column q is found by one warp-wide max reduction over
-// a key (|a_rq|^2 with its low mantissa bits replaced by the row), the scaled pivot row is
-// broadcast through shared memory (srow, 32 entries), and the pivot order is applied when
-// the inverse is written to P (row stride NB, shared).  Returns false if a pivot was zero
-// or not finite.
+// a key (|a_rq|^2 with its low mantissa bits replaced by the row), the pivot row is
+// broadcast from the pivot lane's registers by shuffles and scaled by every lane, and the
+// pivot order is applied when the inverse is written to P (row stride NB, shared).  Returns
+// false if a pivot was zero or not finite.
 template <typename T>
-__device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P, cx_t<T> *srow) {
+__device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
     using V = cx_t<T>;
     const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4;
     V a[16];
@@ -288,20 +288,18 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P, cx_t
         f.y = __shfl_sync(0xffffffffu, a[q].y, r);
         const T rd = recip<T>(pv.x * pv.x + pv.y * pv.y);
         const V inv = ok ? mkc<T>(pv.x * rd, -pv.y * rd) : mkc<T>(T(1), T(0));
-        if (r == p) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                a[j] = cmul(a[j], inv);
-                srow[h * 16 + j] = a[j];
-            }
-        }
-        __syncwarp();
+        // pivot row of this lane's half, scaled by 1 / pivot, straight from the pivot lane's
+        // registers; the pivot row takes it, every other row subtracts f times it
+        const int src = p + 16 * h;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const V pj = srow[h * 16 + j];
-            if (r != p) cfms(a[j], f, pj);
+            V pj;
+            pj.x = __shfl_sync(0xffffffffu, a[j].x, src);
+            pj.y = __shfl_sync(0xffffffffu, a[j].y, src);
+            pj = cmul(pj, inv);
+            if (r == p) a[j] = pj;
+            else cfms(a[j], f, pj);
         }
-        __syncwarp();
     }
     if (h == 1 && qinv < kb) {
 #pragma unroll
@@ -351,7 +349,6 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArg
     V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
     __shared__ int s_bad;
     __shared__ __align__(8) uint64_t bars[2];                 // panel arrival, one per receive buffer
-    __shared__ __align__(16) V s_prow[32];                    // pivot row of the block inversion
 
     V *Gs = a.G + (size_t)sys * nx * nz * nz;
     const double2 *dg = a.diag + (size_t)sys * nx * nz;
@@ -428,7 +425,7 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArg
                     for (int r = rw; r < nz; r += FAC_THREADS / NB)
                         if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
                     if (tid < 32) {
-                        if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP, s_prow) && tid == 0) s_bad = 1;
+                        if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP) && tid == 0) s_bad = 1;
                     }
                     __syncthreads();
                     if (tid == 0) {

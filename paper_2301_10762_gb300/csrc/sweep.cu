@@ -397,6 +397,12 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     V vlast[NOPT];
 #pragma unroll
     for (int u = 0; u < NOPT; ++u) vlast[u] = mkc<TG>(TG(0), TG(0));
+    // tensor path with few fragments: the TF32 splits of this step's G_i fragments and the
+    // loads of the next step's are made at the top of the step, while the team's pushes are
+    // still in flight; larger tiles split inside the product (register budget)
+    constexpr bool kPreSplit = MT > 0 && MT * KP <= 2;
+    uint32_t ahs[kPreSplit ? MT : 1][kPreSplit ? KP : 1][2][4], als[kPreSplit ? MT : 1][kPreSplit ? KP : 1][2][4];
+    float4 bcur[KP > 0 ? KP : 1];
     prefetch(0);
     cp_async_commit();
     load_g(0);
@@ -404,6 +410,23 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         const int kind = kind_of(s);
         const int i = line_of(s);
         const int bi = (kind == 2) ? bwd_index(s) : -1;
+        if constexpr (kPreSplit) {
+#pragma unroll
+            for (int jj = 0; jj < KP; ++jj) {
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float4 ga = gfr[mt][0][jj], gb = gfr[mt][1][jj];
+                        split_tf32(c ? ga.z : ga.x, ahs[mt][jj][c][0], als[mt][jj][c][0]);
+                        split_tf32(c ? gb.z : gb.x, ahs[mt][jj][c][1], als[mt][jj][c][1]);
+                        split_tf32(c ? ga.w : ga.y, ahs[mt][jj][c][2], als[mt][jj][c][2]);
+                        split_tf32(c ? gb.w : gb.y, ahs[mt][jj][c][3], als[mt][jj][c][3]);
+                    }
+                bcur[jj] = bfr[jj];
+            }
+            load_g(s + 1);
+        }
         // input vector of the product: none (first forward line), the middle buffers, the
         // x_m buffer (first backward line) or the team ping-pong buffer
         const V *tin = nullptr;
@@ -472,7 +495,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                     float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (tin && fg < Rc && kc < nz) xv = *reinterpret_cast<const float4 *>(tv + (size_t)fg * nzp + kc);
                     if (fwd) {   // product input t - b_i
-                        xv.x -= bfr[jj].x; xv.y -= bfr[jj].y; xv.z -= bfr[jj].z; xv.w -= bfr[jj].w;
+                        const float4 bv = kPreSplit ? bcur[jj] : bfr[jj];
+                        xv.x -= bv.x; xv.y -= bv.y; xv.z -= bv.z; xv.w -= bv.w;
                     }
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
@@ -482,12 +506,20 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                         const uint32_t nxi_h = xi_h ^ 0x80000000u, nxi_l = xi_l ^ 0x80000000u;
 #pragma unroll
                         for (int mt = 0; mt < MT; ++mt) {
-                            const float4 ga = gfr[mt][0][jj], gb = gfr[mt][1][jj];
                             uint32_t ah[4], al[4];
-                            split_tf32(c ? ga.z : ga.x, ah[0], al[0]);   // row g,     Re G
-                            split_tf32(c ? gb.z : gb.x, ah[1], al[1]);   // row g + 8, Re G
-                            split_tf32(c ? ga.w : ga.y, ah[2], al[2]);   // row g,     Im G
-                            split_tf32(c ? gb.w : gb.y, ah[3], al[3]);   // row g + 8, Im G
+                            if constexpr (kPreSplit) {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    ah[e] = ahs[mt][jj][c][e];
+                                    al[e] = als[mt][jj][c][e];
+                                }
+                            } else {
+                                const float4 ga = gfr[mt][0][jj], gb = gfr[mt][1][jj];
+                                split_tf32(c ? ga.z : ga.x, ah[0], al[0]);   // row g,     Re G
+                                split_tf32(c ? gb.z : gb.x, ah[1], al[1]);   // row g + 8, Re G
+                                split_tf32(c ? ga.w : ga.y, ah[2], al[2]);   // row g,     Im G
+                                split_tf32(c ? gb.w : gb.y, ah[3], al[3]);   // row g + 8, Im G
+                            }
                             mma_tf32(accB[mt][0], ah, xr_h, nxi_h);      // Re: Re G Re t - Im G Im t
                             mma_tf32(accS[mt][0], ah, xr_l, nxi_l);
                             mma_tf32(accS[mt][0], al, xr_h, nxi_h);
@@ -507,7 +539,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                             make_float2(accB[mt][0][e] + accS[mt][0][e], accB[mt][1][e] + accS[mt][1][e]);
                     }
             }
-            load_g(s + 1);   // next line's fragments, in flight during the exchange
+            if constexpr (!kPreSplit) load_g(s + 1);   // next line's fragments, in flight during the exchange
             {
                 __syncthreads();
                 if (ov[0]) {
