@@ -164,6 +164,23 @@ helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, helm_c128 *B_
 helm_status helm_restrict(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
                           const helm_c128 *X_dev, helm_c128 *Y_dev);
 
+/* helm_restrict_adjoint -- X = R(P)^T Y, the transpose of helm_restrict (the discrete
+ * realisation of R* used for the adjoint right-hand side, Theorem th:grad).  Y_dev
+ * [n_omega][ncol][n_rec], X_dev [n_omega][ncol][N] (overwritten).  Sums run over the
+ * receivers in a fixed order (bitwise reproducible).  Synchronises the op's stream. */
+helm_status helm_restrict_adjoint(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
+                                  const helm_c128 *Y_dev, helm_c128 *X_dev);
+
+/* helm_field_grad -- gradient with respect to m of a real functional L of the wavefields
+ * U = A(m)^{-1} B, by the adjoint-state argument of Theorem th:grad (Eq. (I4)): for
+ * dL = Re sum conj(G) dU and Lam = (A^H)^{-1} G (helm_adjoint_solve),
+ *   grad_k = Re sum_{w,q} g_k(w) U_{w,q,k} conj(Lam_{w,q,k}),  g_k = w^2 d_k + i w b_k / (2 sqrt(m_k)),
+ * since dU/dm_k = A^{-1}(g_k e_k U_k) (Proposition prop:elem, Eq. (oneMgrad2a)).  U_dev, Lam_dev [n_omega][nrhs][N] (device),
+ * grad_dev [N] FP64 (device, overwritten; summed over frequencies and columns in a fixed
+ * order).  Asynchronous on the op's stream. */
+helm_status helm_field_grad(const helm_op_t *op, int32_t nrhs, const helm_c128 *U_dev, const helm_c128 *Lam_dev,
+                            double *grad_dev);
+
 /* fwi_misfit_grad -- phi and grad phi of Eq. (newphi) by the adjoint-state method
  * (Algorithm alg:box1, Theorem th:grad):
  *   u = A^{-1} e_s, eps = d - R u, lambda = (A^H)^{-1} R^T (W^2 eps),

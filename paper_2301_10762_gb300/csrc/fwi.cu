@@ -152,6 +152,29 @@ __global__ void grad_kernel(GridGeom g, int n_omega, int n_src, const double *om
     if (threadIdx.x == 0) reg_part[blockIdx.x] = t;
 }
 
+// grad_k = Re sum_{w,q} g_k(w) U_k conj(Lam_k): the m-gradient of a real functional of the
+// wavefields from its adjoint fields (helm_field_grad)
+__global__ void field_grad_kernel(GridGeom g, int n_omega, int nrhs, const double *omega, const double *m,
+                                  const double2 *U, const double2 *Lam, double *grad) {
+    const int N = g.nx * g.nz;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    double d, b;
+    node_db(g, k, d, b);
+    const double mk = m[k];
+    double acc = 0.0;
+    for (int w = 0; w < n_omega; ++w) {
+        const double2 gk = g_of(omega[w], d, b, mk);
+        for (int q = 0; q < nrhs; ++q) {
+            const size_t o = ((size_t)w * nrhs + q) * N + k;
+            const double2 gu = cmul(gk, U[o]);
+            const double2 l = Lam[o];
+            acc += gu.x * l.x + gu.y * l.y;   // Re(gu conj(l))
+        }
+    }
+    grad[k] = acc;
+}
+
 // out[w][s][k] = g_k(w) u_k p_k   (right-hand side of v, Eq. (defv), and of tau, Eq. (tau_def))
 __global__ void g_u_p_kernel(GridGeom g, int n_omega, int n_src, const double *omega, const double *m,
                              const double2 *U, const double *p, double2 *out) {
@@ -526,6 +549,44 @@ static helm_status hess_apply(helm_factor_t *f, const DevAcq &da, const double2 
     HS(run_solve(f, ns, E, Z, rtol, 1, count, max_it));
     HELM_TRACED(K_HESS, st, (hess_acc_kernel<<<nblk(N), 256, 0, st>>>(g, nw, ns, op->omega_dev, op->m, U, V, Z, Lam, pv, alpha, mu, gauss_newton, out)));
     HL();
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_field_grad(const helm_op_t *op, int32_t nrhs, const helm_c128 *U_dev,
+                                      const helm_c128 *Lam_dev, double *grad_dev) {
+    if (!op || nrhs < 0 || !grad_dev || (nrhs > 0 && (!U_dev || !Lam_dev))) {
+        helm_set_msg("helm_field_grad: bad arguments");
+        return HELM_EINVAL;
+    }
+    const int N = op->g.nx * op->g.nz;
+    HELM_TRACED(K_FIELDGRAD, op->st, (field_grad_kernel<<<(N + 255) / 256, 256, 0, op->st>>>(
+                                          op->g, op->n_omega, nrhs, op->omega_dev, op->m, (const double2 *)U_dev,
+                                          (const double2 *)Lam_dev, grad_dev)));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { helm_set_error("helm_field_grad", e); return HELM_ECUDA; }
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_restrict_adjoint(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
+                                             const helm_c128 *Y_dev, helm_c128 *X_dev) {
+    if (!op || !acq || ncol < 0 || (ncol > 0 && (!X_dev || !Y_dev))) {
+        helm_set_msg("helm_restrict_adjoint: bad arguments");
+        return HELM_EINVAL;
+    }
+    DevAcq d;
+    helm_status s = acq_upload(op, acq, &d);
+    if (s != HELM_OK) return s;
+    const size_t N = (size_t)op->g.nx * op->g.nz, cols = (size_t)op->n_omega * ncol;
+    cudaError_t e = cudaMemsetAsync(X_dev, 0, cols * N * sizeof(double2), op->st);
+    if (e == cudaSuccess && cols > 0 && d.n_rec > 0) {
+        HELM_TRACED(K_SCATTER, op->st, (scatter_kernel<<<(unsigned)cols, 32, 0, op->st>>>(
+                                           (int)N, d.n_rec, d.tap_idx, d.tap_w, nullptr, 0, (const double2 *)Y_dev,
+                                           (double2 *)X_dev)));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    acq_free(&d);
+    if (e != cudaSuccess) { helm_set_error("helm_restrict_adjoint", e); return HELM_ECUDA; }
     return HELM_OK;
 }
 

@@ -62,7 +62,7 @@ class helm_trace_entry(C.Structure):
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
             "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
-            "helm_restrict",
+            "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
             "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count"]
@@ -102,6 +102,10 @@ def load(path: str = LIB_PATH):
     lib.helm_sources.argtypes = [vp, P(helm_acq), vp]
     lib.helm_restrict.restype = C.c_int
     lib.helm_restrict.argtypes = [vp, P(helm_acq), i32, vp, vp]
+    lib.helm_restrict_adjoint.restype = C.c_int
+    lib.helm_restrict_adjoint.argtypes = [vp, P(helm_acq), i32, vp, vp]
+    lib.helm_field_grad.restype = C.c_int
+    lib.helm_field_grad.argtypes = [vp, i32, vp, vp, vp]
     lib.fwi_misfit_grad.restype = C.c_int
     lib.fwi_misfit_grad.argtypes = [vp, P(helm_acq), vp, dbl, dbl, dbl, P(dbl), vp, vp, vp]
     lib.fwi_hessian_vec.restype = C.c_int
@@ -277,6 +281,29 @@ def helm_restrict(op: Op, acq: Acq, X: torch.Tensor) -> torch.Tensor:
     _check(lib.helm_restrict(op.handle, C.byref(acq.struct), ncol, px, _dev(Y, torch.complex128, "Y")),
            "helm_restrict")
     return Y
+
+
+def helm_restrict_adjoint(op: Op, acq: Acq, Y: torch.Tensor) -> torch.Tensor:
+    """X = R(P)^T Y, Y [n_omega, ncol, n_rec] -> X [n_omega, ncol, N]."""
+    lib = load()
+    ncol = Y.shape[1]
+    py = _dev(Y, torch.complex128, "Y", (op.n_omega, ncol, acq.n_rec))
+    X = torch.empty((op.n_omega, ncol, op.N), dtype=torch.complex128, device="cuda")
+    _check(lib.helm_restrict_adjoint(op.handle, C.byref(acq.struct), ncol, py, _dev(X, torch.complex128, "X")),
+           "helm_restrict_adjoint")
+    return X
+
+
+def helm_field_grad(op: Op, U: torch.Tensor, Lam: torch.Tensor) -> torch.Tensor:
+    """grad_k = Re sum g_k U_k conj(Lam_k) over frequencies and columns (include/helm.h)."""
+    lib = load()
+    nrhs = U.shape[1]
+    shape = (op.n_omega, nrhs, op.N)
+    pu = _dev(U, torch.complex128, "U", shape)
+    pl = _dev(Lam, torch.complex128, "Lam", shape)
+    grad = torch.empty(op.N, dtype=torch.float64, device="cuda")
+    _check(lib.helm_field_grad(op.handle, nrhs, pu, pl, C.c_void_p(grad.data_ptr())), "helm_field_grad")
+    return grad
 
 
 def fwi_misfit_grad(f: Factor, acq: Acq, data: torch.Tensor, alpha, mu, rtol=1e-10, want_fields=False):
