@@ -81,10 +81,13 @@ typedef struct {
     double rtol;          /* stop when ||r_n|| / ||r_0|| <= rtol */
     double x0;            /* constant initial guess (the paper uses 1) */
     double refine_rtol;   /* residual tolerance of every Helmholtz solve (mixed mode) */
+    int32_t concurrent_models;  /* training models processed at once (own streams and host
+                                   threads); <= 0: library default (up to 3).  The results are
+                                   summed in model order, so they do not depend on it. */
 } helm_pcg_opts;
 
 typedef struct {
-    int32_t cg_matvecs;   /* Hessian-vector products of the last model (incl. initial residual) */
+    int32_t cg_matvecs;   /* Hessian-vector products, max over models (incl. initial residual) */
     double cg_relres;     /* ||r|| / ||r_0|| reached, max over models */
     int64_t solves;       /* Helmholtz right-hand-side solves of the hypergradient pass */
     int64_t data_solves;  /* solves spent generating the data u(m') */

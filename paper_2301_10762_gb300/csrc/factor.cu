@@ -534,7 +534,7 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     const char *force = getenv("HELM_FACTOR_TEAMS");
     const bool allow_twisted = !(force && force[0] == '1');
     if (resident) {
-        e = cudaFuncSetAttribute(line_factor_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res);
+        e = ensure_dyn_smem((const void *)line_factor_smem_kernel<T>, smem_res);
         if (e != cudaSuccess) return e;
     }
     if (resident && allow_twisted) {
@@ -570,7 +570,7 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     const size_t smem = resident ? smem_res : factor_smem_bytes<T>(g.nz, cs);
     auto kern = resident ? line_factor_smem_kernel<T> : line_factor_kernel<T>;
     if (!resident) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dyn_smem((const void *)kern, smem);
         if (e != cudaSuccess) return e;
     }
     const int csz = teams * cs;

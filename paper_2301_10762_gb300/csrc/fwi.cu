@@ -5,6 +5,7 @@
 // combined in index order), so results are bitwise reproducible run to run.
 #include <math.h>
 #include <algorithm>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -740,22 +741,27 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     struct AcqGuard2 { DevAcq *d; ~AcqGuard2() { acq_free(d); } } ag2{&da2};
     double2 *Ut = nullptr, *dtmp = nullptr;
     helm_status s2 = HELM_OK;
+    std::string msg2;   // error text of the data branch (set in its own thread)
     std::thread data_branch([&]() {
-        s2 = helm_assemble(grid, m_true, omega, n_omega, st2, &ms.op_t);
-        if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &ms.fac_t);
-        if (s2 == HELM_OK) s2 = acq_upload(ms.op_t, acq, &da2);
-        if (s2 != HELM_OK) return;
-        const GridGeom &gt = ms.op_t->g;
-        const size_t ct = (size_t)n_omega * da2.n_src;
-        double2 *Et = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
-        Ut = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
-        dtmp = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
-        if (s2 != HELM_OK) return;
-        s2 = forward_fields(ms.fac_t, da2, po->refine_rtol, Et, Ut, &dcount, &max_it2);
-        if (s2 != HELM_OK) return;
-        cudaError_t e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_w, Ut, dtmp, st2);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st2);
-        if (e != cudaSuccess) { helm_set_error("data branch", e); s2 = HELM_ECUDA; }
+        auto run = [&]() {
+            s2 = helm_assemble(grid, m_true, omega, n_omega, st2, &ms.op_t);
+            if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &ms.fac_t);
+            if (s2 == HELM_OK) s2 = acq_upload(ms.op_t, acq, &da2);
+            if (s2 != HELM_OK) return;
+            const GridGeom &gt = ms.op_t->g;
+            const size_t ct = (size_t)n_omega * da2.n_src;
+            double2 *Et = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
+            Ut = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
+            dtmp = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
+            if (s2 != HELM_OK) return;
+            s2 = forward_fields(ms.fac_t, da2, po->refine_rtol, Et, Ut, &dcount, &max_it2);
+            if (s2 != HELM_OK) return;
+            cudaError_t e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_w, Ut, dtmp, st2);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st2);
+            if (e != cudaSuccess) { helm_set_error("data branch", e); s2 = HELM_ECUDA; }
+        };
+        run();
+        if (s2 != HELM_OK) msg2 = helm_last_error();
     });
     struct Joiner { std::thread &t; ~Joiner() { if (t.joinable()) t.join(); } } joiner{data_branch};
     s = helm_assemble(grid, m_fwi, omega, n_omega, st, &ms.op_f);
@@ -785,7 +791,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     s = forward_fields(ms.fac_f, da, rtol, E, U, &count, &max_it);
     data_branch.join();
     if (s != HELM_OK) return s;
-    if (s2 != HELM_OK) return s2;
+    if (s2 != HELM_OK) { helm_set_msg(msg2.c_str()); return s2; }
     max_it = std::max(max_it, max_it2);
     // eps, lambda (and grad phi, unused here) at m_fwi
     HS(adjoint_grad(ms.fac_f, da, dtmp, alpha, mu, rtol, phi_dev, grad, U, Lam, E, ws, &count, &max_it));
@@ -884,34 +890,87 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
         return HELM_EINVAL;
     }
     keep_pool_memory();
-    helm_pcg_opts po = pcg ? *pcg : helm_pcg_opts{500, 0, 1e-13, 1.0, 1e-10};
+    helm_pcg_opts po = pcg ? *pcg : helm_pcg_opts{500, 0, 1e-13, 1.0, 1e-10, 0};
     cudaStream_t st = (cudaStream_t)stream;
     if (info) *info = helm_hyper_info{0, 0.0, 0, 0, 0};
     const int nr = acq->n_rec;
-    helm_status s = HELM_OK;
-    {
-        Ws ws(st);
-        double *acc = ws.get<double>(2, &s);
-        double *dp = ws.get<double>(2 * nr, &s);
-        double *dw = ws.get<double>(nr, &s);
-        if (s != HELM_OK) return s;
-        HK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-        HK(cudaMemsetAsync(dp, 0, 2 * nr * sizeof(double), st));
-        HK(cudaMemsetAsync(dw, 0, nr * sizeof(double), st));
-        for (int k = 0; k < n_models && s == HELM_OK; ++k)
-            s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], acq, omega, n_omega, alpha, alpha0, mu, prec, &po,
-                                st, 1.0 / n_models, acc, dp, dw, info);
-        if (s == HELM_OK || s == HELM_ENOCONV) {
-            double a2[2];
-            cudaError_t e = cudaMemcpyAsync(a2, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dpsi_dp, dp, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess && dpsi_dw)
-                e = cudaMemcpyAsync(dpsi_dw, dw, nr * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) { helm_set_error("bilevel_hypergrad", e); return HELM_ECUDA; }
-            *psi = a2[0];
-            *dpsi_dalpha = a2[1];
+    // Independent training models run concurrently, each on its own streams from its own host
+    // thread (the chain of one model is latency bound and leaves most of the GPU idle); every
+    // model writes its own partial results, which are summed here in model order.
+    constexpr int kDefaultConcurrent = 3;
+    const int K = std::max(1, std::min<int>(n_models, po.concurrent_models > 0 ? po.concurrent_models
+                                                                                : kDefaultConcurrent));
+    std::vector<double> acc_h(2 * (size_t)n_models, 0.0), dp_h(2 * (size_t)nr * n_models, 0.0),
+        dw_h((size_t)nr * n_models, 0.0);
+    std::vector<helm_hyper_info> infos(n_models, helm_hyper_info{0, 0.0, 0, 0, 0});
+    std::vector<helm_status> stat(n_models, HELM_OK);
+    std::vector<std::string> msg(n_models);
+    auto worker = [&](int w) {
+        cudaStream_t sw = st;
+        if (w > 0 && cudaStreamCreateWithFlags(&sw, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int k = w; k < n_models; k += K) { stat[k] = HELM_ECUDA; msg[k] = "bilevel_hypergrad: stream"; }
+            return;
         }
+        for (int k = w; k < n_models; k += K) {
+            helm_status s = HELM_OK;
+            {
+                Ws ws(sw);
+                double *acc = ws.get<double>(2, &s);
+                double *dp = ws.get<double>(2 * nr, &s);
+                double *dw = ws.get<double>(nr, &s);
+                cudaError_t e = cudaSuccess;
+                if (s == HELM_OK) e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), sw);
+                if (s == HELM_OK && e == cudaSuccess) e = cudaMemsetAsync(dp, 0, 2 * nr * sizeof(double), sw);
+                if (s == HELM_OK && e == cudaSuccess) e = cudaMemsetAsync(dw, 0, nr * sizeof(double), sw);
+                if (e != cudaSuccess) { helm_set_error("bilevel_hypergrad", e); s = HELM_ECUDA; }
+                if (s == HELM_OK)
+                    s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], acq, omega, n_omega, alpha, alpha0, mu, prec,
+                                        &po, sw, 1.0 / n_models, acc, dp, dw, &infos[k]);
+                if (s == HELM_OK || s == HELM_ENOCONV) {
+                    e = cudaMemcpyAsync(&acc_h[2 * (size_t)k], acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, sw);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(&dp_h[2 * (size_t)nr * k], dp, 2 * nr * sizeof(double),
+                                            cudaMemcpyDeviceToHost, sw);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(&dw_h[(size_t)nr * k], dw, nr * sizeof(double), cudaMemcpyDeviceToHost, sw);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(sw);
+                    if (e != cudaSuccess) { helm_set_error("bilevel_hypergrad", e); s = HELM_ECUDA; }
+                }
+            }
+            stat[k] = s;
+            if (s != HELM_OK) msg[k] = helm_last_error();
+        }
+        if (sw != st) cudaStreamDestroy(sw);
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int w = 1; w < K; ++w) pool.emplace_back(worker, w);
+        worker(0);
+        for (auto &t : pool) t.join();
     }
+    helm_status s = HELM_OK;
+    for (int k = 0; k < n_models; ++k)
+        if (stat[k] != HELM_OK && stat[k] != HELM_ENOCONV) { helm_set_msg(msg[k].c_str()); return stat[k]; }
+    double a0 = 0.0, a1 = 0.0;
+    for (int r = 0; r < 2 * nr; ++r) dpsi_dp[r] = 0.0;
+    if (dpsi_dw)
+        for (int r = 0; r < nr; ++r) dpsi_dw[r] = 0.0;
+    for (int k = 0; k < n_models; ++k) {   // model order
+        a0 += acc_h[2 * (size_t)k];
+        a1 += acc_h[2 * (size_t)k + 1];
+        for (int r = 0; r < 2 * nr; ++r) dpsi_dp[r] += dp_h[2 * (size_t)nr * k + r];
+        if (dpsi_dw)
+            for (int r = 0; r < nr; ++r) dpsi_dw[r] += dw_h[(size_t)nr * k + r];
+        if (info) {
+            info->cg_matvecs = std::max(info->cg_matvecs, infos[k].cg_matvecs);
+            info->cg_relres = std::max(info->cg_relres, infos[k].cg_relres);
+            info->solves += infos[k].solves;
+            info->data_solves += infos[k].data_solves;
+            info->max_refine_iters = std::max(info->max_refine_iters, infos[k].max_refine_iters);
+        }
+        if (stat[k] == HELM_ENOCONV && s == HELM_OK) { s = HELM_ENOCONV; helm_set_msg(msg[k].c_str()); }
+    }
+    *psi = a0;
+    *dpsi_dalpha = a1;
     return s;
 }

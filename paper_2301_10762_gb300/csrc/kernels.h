@@ -35,6 +35,10 @@ cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double
 
 int pick_cluster_size(int nz);
 
+// Raise the kernel's dynamic shared-memory limit to at least `bytes` (never lowers it), so
+// that host threads launching the same kernel with different sizes do not undo each other.
+cudaError_t ensure_dyn_smem(const void *fn, size_t bytes);
+
 // ---- refine.cu (mixed-precision refinement in FP32-pair arithmetic)
 // diag2[s][k] = (hi.re, hi.im, lo.re, lo.im) of the FP64 diagonal
 cudaError_t launch_split_diag(size_t n, const double2 *diag, float4 *diag2, cudaStream_t st);

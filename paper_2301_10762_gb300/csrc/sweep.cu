@@ -15,6 +15,8 @@
 // TG = float is the correction solve of the mixed-precision refinement (refine.cu): complex
 // FP32 factor, right-hand side and result.  TG = double is the plain FP64 path (Y aliases X).
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <stdlib.h>
 #include "kernels.h"
 #include "trace.h"
@@ -652,6 +654,20 @@ static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
     return n;
 }
 
+cudaError_t ensure_dyn_smem(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;   // (device, kernel) -> bytes set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 template <typename TG> using SweepFn = void (*)(SweepArgs<TG>);
 
 // kernel of the tensor-pipe product with MT m tiles and KP K blocks per warp (null if none)
@@ -742,7 +758,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             }
         }
         const void *fn = (const void *)kfn;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dyn_smem(fn, smem);
         if (e != cudaSuccess) return e;
         const int csz = teams * cs;
         if (csz > 8) {

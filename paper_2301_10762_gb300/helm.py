@@ -48,7 +48,7 @@ class helm_solve_info(C.Structure):
 
 class helm_pcg_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("rtol", C.c_double), ("x0", C.c_double),
-                ("refine_rtol", C.c_double)]
+                ("refine_rtol", C.c_double), ("concurrent_models", C.c_int32)]
 
 
 class helm_hyper_info(C.Structure):
@@ -339,7 +339,7 @@ def fwi_hessian_vec(f: Factor, acq: Acq, U: torch.Tensor, Lam: torch.Tensor | No
 
 def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
                       cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
-                      stream=None):
+                      stream=None, concurrent_models=0):
     """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors."""
     lib = load()
     n = len(grids)
@@ -347,7 +347,8 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu,
     pf = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_fwi", (g[0] * g[1],)).value for t, g in zip(m_fwi, grids)])
     pt = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_true", (g[0] * g[1],)).value for t, g in zip(m_true, grids)])
     om, p_om = _dbuf(np.atleast_1d(omegas))
-    opts = helm_pcg_opts(int(cg_max_iter), int(cg_fixed_iters), float(cg_rtol), float(x0), float(refine_rtol))
+    opts = helm_pcg_opts(int(cg_max_iter), int(cg_fixed_iters), float(cg_rtol), float(x0), float(refine_rtol),
+                         int(concurrent_models))
     psi, dalpha = C.c_double(), C.c_double()
     dp = np.zeros((acq.n_rec, 2))
     dw = np.zeros(acq.n_rec)
