@@ -23,7 +23,8 @@ typedef struct {
     int64_t timed;        /* launches that were timed */
 } helm_trace_entry;
 
-/* Enable (on != 0) or disable per-launch event timing.  Host only; not thread safe
+/* Enable (on != 0) or disable per-launch event timing.  Enabling creates a pool of CUDA
+ * events up front (16384), so that timed launches create none.  Host only; not thread safe
  * with concurrent library calls. */
 void helm_trace_enable(int on);
 /* Forget all counts and timings. */

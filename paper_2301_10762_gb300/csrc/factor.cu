@@ -540,27 +540,8 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     if (resident && allow_twisted) {
         // two teams (twisted) when a cluster of 2 cs CTAs can be scheduled
         if (2 * cs <= 16) {
-            bool ok = true;
-            if (2 * cs > 8) {
-                ok = cudaFuncSetAttribute(line_factor_smem_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                     cudaSuccess;
-                if (ok) {
-                    cudaLaunchConfig_t q = {};
-                    q.gridDim = dim3(2 * cs, 1, 1);
-                    q.blockDim = dim3(FAC_THREADS, 1, 1);
-                    q.dynamicSmemBytes = smem_res;
-                    cudaLaunchAttribute at[1];
-                    at[0].id = cudaLaunchAttributeClusterDimension;
-                    at[0].val.clusterDim.x = 2 * cs;
-                    at[0].val.clusterDim.y = 1;
-                    at[0].val.clusterDim.z = 1;
-                    q.attrs = at;
-                    q.numAttrs = 1;
-                    int n = 0;
-                    ok = cudaOccupancyMaxActiveClusters(&n, line_factor_smem_kernel<T>, &q) == cudaSuccess && n > 0;
-                }
-                cudaGetLastError();
-            }
+            const bool ok = max_active_clusters((const void *)line_factor_smem_kernel<T>, 2 * cs, FAC_THREADS,
+                                                smem_res) > 0;
             if (ok) teams = 2;
         }
     }

@@ -905,9 +905,25 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
     std::vector<helm_hyper_info> infos(n_models, helm_hyper_info{0, 0.0, 0, 0, 0});
     std::vector<helm_status> stat(n_models, HELM_OK);
     std::vector<std::string> msg(n_models);
+    // every worker runs on a non-blocking stream of its own that first waits for the caller's
+    // stream (the inputs are ready there); none of the model's work lands on the caller's stream,
+    // which may be the legacy default stream (work on it made the factorisations of the two
+    // branches of a model run one after the other in most steps)
+    cudaEvent_t ready = nullptr;
+    {
+        cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, st);
+        if (e != cudaSuccess) {
+            if (ready) cudaEventDestroy(ready);
+            helm_set_error("bilevel_hypergrad: event", e);
+            return HELM_ECUDA;
+        }
+    }
     auto worker = [&](int w) {
-        cudaStream_t sw = st;
-        if (w > 0 && cudaStreamCreateWithFlags(&sw, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStream_t sw = nullptr;
+        if (cudaStreamCreateWithFlags(&sw, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamWaitEvent(sw, ready, 0) != cudaSuccess) {
+            if (sw) cudaStreamDestroy(sw);
             for (int k = w; k < n_models; k += K) { stat[k] = HELM_ECUDA; msg[k] = "bilevel_hypergrad: stream"; }
             return;
         }
@@ -940,7 +956,7 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
             stat[k] = s;
             if (s != HELM_OK) msg[k] = helm_last_error();
         }
-        if (sw != st) cudaStreamDestroy(sw);
+        cudaStreamDestroy(sw);
     };
     {
         std::vector<std::thread> pool;
@@ -948,6 +964,7 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
         worker(0);
         for (auto &t : pool) t.join();
     }
+    cudaEventDestroy(ready);
     helm_status s = HELM_OK;
     for (int k = 0; k < n_models; ++k)
         if (stat[k] != HELM_OK && stat[k] != HELM_ENOCONV) { helm_set_msg(msg[k].c_str()); return stat[k]; }

@@ -38,6 +38,10 @@ int pick_cluster_size(int nz);
 // Raise the kernel's dynamic shared-memory limit to at least `bytes` (never lowers it), so
 // that host threads launching the same kernel with different sizes do not undo each other.
 cudaError_t ensure_dyn_smem(const void *fn, size_t bytes);
+// Allow cluster sizes above 8 for the kernel (set once per device and kernel).
+cudaError_t ensure_nonportable_clusters(const void *fn);
+// Co-resident clusters of csz CTAs of the kernel (0: cannot be scheduled); cached per shape.
+int max_active_clusters(const void *fn, int csz, int threads, size_t smem);
 
 // ---- refine.cu (mixed-precision refinement in FP32-pair arithmetic)
 // diag2[s][k] = (hi.re, hi.im, lo.re, lo.im) of the FP64 diagonal

@@ -16,6 +16,7 @@
 // FP32 factor, right-hand side and result.  TG = double is the plain FP64 path (Y aliases X).
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <stdlib.h>
 #include "kernels.h"
@@ -634,14 +635,39 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
 }
 
 // Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
-static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
+// Kernel attributes and occupancy queries are made once per (device, kernel, shape) and cached,
+// so that host threads launching the same kernels do not keep changing their attributes.
+cudaError_t ensure_nonportable_clusters(const void *fn) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, bool> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    bool &d = done[{dev, fn}];
+    if (d) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) d = true;
+    return e;
+}
+
+int max_active_clusters(const void *fn, int csz, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, int, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (csz > 8 && ensure_nonportable_clusters(fn) != cudaSuccess) { cudaGetLastError(); return 0; }
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, fn, csz, threads, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.gridDim = dim3(csz, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.x = csz;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -649,8 +675,9 @@ static int active_clusters(const void *fn, int cs, int threads, size_t smem) {
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        n = 0;
     }
+    cache[key] = n;
     return n;
 }
 
@@ -762,8 +789,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         if (e != cudaSuccess) return e;
         const int csz = teams * cs;
         if (csz > 8) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess || active_clusters(fn, csz, SW_THREADS, smem) == 0) {
+            if (max_active_clusters(fn, csz, SW_THREADS, smem) == 0) {
                 cudaGetLastError();
                 cs = 8 / teams;
                 continue;

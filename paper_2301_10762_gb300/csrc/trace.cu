@@ -66,6 +66,14 @@ using namespace helm;
 extern "C" void helm_trace_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_on = on != 0;
+    // events are created here, not at launch time: creating one while other host threads
+    // launch kernels can delay those launches
+    constexpr size_t kPool = 16384;
+    while (g_on && g_pool.size() + 2 * g_recs.size() < kPool) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); break; }
+        g_pool.push_back(e);
+    }
 }
 
 extern "C" void helm_trace_reset(void) {
