@@ -36,6 +36,20 @@ int32_t helm_trace_read(helm_trace_entry *out, int32_t max);
 /* Total kernel launches since the last reset. */
 int64_t helm_launch_count(void);
 
+typedef struct {
+    int32_t kernel;       /* kernel index (helm_trace_kernel_name) */
+    int32_t stream;       /* 0, 1, ...: order in which the launch's stream first appeared */
+    double start_ms;      /* device start / end of the launch, relative to the start of the */
+    double end_ms;        /* first timed launch since the last reset or read */
+} helm_trace_event;
+
+/* Synchronise the device and copy up to max timed launches recorded since the last
+ * reset or read, in launch order, into out (the records stay for helm_trace_read).
+ * Returns the number written, or -1 on a CUDA error. */
+int32_t helm_trace_timeline(helm_trace_event *out, int32_t max);
+/* Name of kernel index id, or NULL if out of range. */
+const char *helm_trace_kernel_name(int32_t id);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
 #include "helm.h"
 #include "kernels.h"
 #include "abi_internal.h"
@@ -38,10 +39,24 @@ extern "C" const char *helm_status_string(helm_status s) {
 
 extern "C" const char *helm_last_error(void) { return g_last_error.c_str(); }
 
-helm_status dev_alloc(void **p, size_t bytes, const char *what) {
+void keep_pool_memory() {
+    static std::once_flag once;
+    std::call_once(once, []() {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    });
+}
+
+helm_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return HELM_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
+    keep_pool_memory();
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -51,8 +66,8 @@ helm_status dev_alloc(void **p, size_t bytes, const char *what) {
     return HELM_OK;
 }
 
-void dev_free(void *p) {
-    if (p) cudaFree(p);
+void dev_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
 }
 
 // ---------------------------------------------------------------------- operator
@@ -78,10 +93,10 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     op->st = (cudaStream_t)stream;
     const size_t N = (size_t)grid->nx * grid->nz;
     helm_status s;
-    if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "cudaMalloc(m)")) != HELM_OK ||
-        (s = dev_alloc((void **)&op->omega_dev, n_omega * sizeof(double), "cudaMalloc(omega)")) != HELM_OK ||
-        (s = dev_alloc((void **)&op->diag, (size_t)n_omega * N * sizeof(double2), "cudaMalloc(diag)")) != HELM_OK ||
-        (s = dev_alloc((void **)&op->status, sizeof(int), "cudaMalloc(status)")) != HELM_OK) {
+    if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "allocate(m)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->omega_dev, n_omega * sizeof(double), "allocate(omega)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->diag, (size_t)n_omega * N * sizeof(double2), "allocate(diag)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->status, sizeof(int), "allocate(status)", op->st)) != HELM_OK) {
         helm_op_destroy(op);
         return s;
     }
@@ -102,10 +117,10 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
 
 extern "C" void helm_op_destroy(helm_op_t *op) {
     if (!op) return;
-    dev_free(op->m);
-    dev_free(op->omega_dev);
-    dev_free(op->diag);
-    dev_free(op->status);
+    dev_free(op->m, op->st);
+    dev_free(op->omega_dev, op->st);
+    dev_free(op->diag, op->st);
+    dev_free(op->status, op->st);
     delete op;
 }
 
@@ -124,8 +139,8 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
     const size_t esz = prec == HELM_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t gelems = (size_t)op->n_omega * g.nx * g.nz * g.nz;
     helm_status s;
-    if ((s = dev_alloc(&f->G, gelems * esz, "cudaMalloc(factor)")) != HELM_OK ||
-        (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "cudaMalloc(exchange)")) !=
+    if ((s = dev_alloc(&f->G, gelems * esz, "allocate(factor)", op->st)) != HELM_OK ||
+        (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "allocate(exchange)", op->st)) !=
             HELM_OK) {
         helm_factor_destroy(f);
         return s;
@@ -157,7 +172,7 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
     }
     if (prec == HELM_MIXED) {   // diagonal of A as FP32 pairs for the refinement residual
         const size_t n = (size_t)op->n_omega * g.nx * g.nz;
-        if ((s = dev_alloc((void **)&f->diag2, n * sizeof(float4), "cudaMalloc(diag pairs)")) != HELM_OK) {
+        if ((s = dev_alloc((void **)&f->diag2, n * sizeof(float4), "allocate(diag pairs)", op->st)) != HELM_OK) {
             helm_factor_destroy(f);
             return s;
         }
@@ -173,16 +188,16 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
 
 extern "C" void helm_factor_destroy(helm_factor_t *f) {
     if (!f) return;
-    dev_free(f->G);
-    dev_free(f->xch);
-    dev_free(f->diag2);
-    dev_free(f->bd);
-    dev_free(f->xa);
-    dev_free(f->xb);
-    dev_free(f->r32);
-    dev_free(f->y);
-    dev_free(f->norms);
-    if (f->norms_host) cudaFreeHost(f->norms_host);
+    cudaStream_t st = f->op ? f->op->st : nullptr;
+    dev_free(f->G, st);
+    dev_free(f->xch, st);
+    dev_free(f->diag2, st);
+    dev_free(f->bd, st);
+    dev_free(f->xa, st);
+    dev_free(f->xb, st);
+    dev_free(f->r32, st);
+    dev_free(f->y, st);
+    dev_free(f->norms, st);
     delete f;
 }
 
@@ -191,32 +206,27 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
     const helm_op *op = f->op;
     const size_t cols = (size_t)op->n_omega * nrhs;
     const size_t N = (size_t)op->g.nx * op->g.nz;
-    dev_free(f->bd);
-    dev_free(f->xa);
-    dev_free(f->xb);
-    dev_free(f->r32);
-    dev_free(f->y);
-    dev_free(f->norms);
-    if (f->norms_host) cudaFreeHost(f->norms_host);
+    const cudaStream_t st = op->st;
+    dev_free(f->bd, st);
+    dev_free(f->xa, st);
+    dev_free(f->xb, st);
+    dev_free(f->r32, st);
+    dev_free(f->y, st);
+    dev_free(f->norms, st);
     f->bd = f->xa = f->xb = nullptr;
     f->r32 = f->y = nullptr;
     f->norms = nullptr;
-    f->norms_host = nullptr;
     f->cap = 0;
     helm_status s;
     if (f->prec == HELM_MIXED &&
-        ((s = dev_alloc((void **)&f->bd, cols * N * sizeof(float4), "cudaMalloc(rhs pairs)")) != HELM_OK ||
-         (s = dev_alloc((void **)&f->xa, cols * N * sizeof(float4), "cudaMalloc(iterate)")) != HELM_OK ||
-         (s = dev_alloc((void **)&f->xb, cols * N * sizeof(float4), "cudaMalloc(iterate)")) != HELM_OK ||
-         (s = dev_alloc((void **)&f->r32, cols * N * sizeof(float2), "cudaMalloc(residual)")) != HELM_OK ||
-         (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "cudaMalloc(work)")) != HELM_OK))
+        ((s = dev_alloc((void **)&f->bd, cols * N * sizeof(float4), "allocate(rhs pairs)", st)) != HELM_OK ||
+         (s = dev_alloc((void **)&f->xa, cols * N * sizeof(float4), "allocate(iterate)", st)) != HELM_OK ||
+         (s = dev_alloc((void **)&f->xb, cols * N * sizeof(float4), "allocate(iterate)", st)) != HELM_OK ||
+         (s = dev_alloc((void **)&f->r32, cols * N * sizeof(float2), "allocate(residual)", st)) != HELM_OK ||
+         (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "allocate(work)", st)) != HELM_OK))
         return s;
-    if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "cudaMalloc(norms)")) != HELM_OK) return s;
-    if (cudaMallocHost((void **)&f->norms_host, cols * 2 * sizeof(double)) != cudaSuccess) {
-        f->norms_host = nullptr;
-        helm_set_msg("cudaMallocHost(norms)");
-        return HELM_ENOMEM;
-    }
+    if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "allocate(norms)", st)) != HELM_OK) return s;
+    f->norms_host.assign(cols * 2, 0.0);
     f->cap = nrhs;
     return HELM_OK;
 }
@@ -313,12 +323,12 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
             e = cudaMemsetAsync(f->norms, 0, cols * 2 * sizeof(double), op->st);
             if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, f->norms, conj, op->st);
             if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
-            if ((s = max_relres(op, cols, f->norms, f->norms_host, &info->max_relres)) != HELM_OK) return s;
+            if ((s = max_relres(op, cols, f->norms, f->norms_host.data(), &info->max_relres)) != HELM_OK) return s;
         }
         return HELM_OK;
     }
     if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
-    const MixedWork w{f->bd, f->xa, f->xb, f->r32, f->y, f->norms, f->norms_host};
+    const MixedWork w{f->bd, f->xa, f->xb, f->r32, f->y, f->norms, f->norms_host.data()};
     int it = 0;
     double rel = INFINITY;
     if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;
@@ -372,18 +382,19 @@ helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d) {
         const double x = acq->rec_xz[2 * r], z = acq->rec_xz[2 * r + 1];
         if (!(x >= 0 && x <= op->lx && z >= 0 && z <= op->lz)) { helm_set_msg("receiver outside the grid"); return HELM_EINVAL; }
     }
+    d->st = op->st;
     d->n_src = acq->n_src;
     d->n_rec = acq->n_rec;
     const int ns = std::max(1, acq->n_src), nr = std::max(1, acq->n_rec);
     helm_status s;
-    if ((s = dev_alloc((void **)&d->src_xz, ns * 2 * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->src_amp, ns * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->rec_xz, nr * 2 * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->rec_w, nr * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->tap_idx, nr * 16 * sizeof(int), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->tap_w, nr * 16 * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->tap_wx, nr * 16 * sizeof(double), "acq")) != HELM_OK ||
-        (s = dev_alloc((void **)&d->tap_wz, nr * 16 * sizeof(double), "acq")) != HELM_OK) {
+    if ((s = dev_alloc((void **)&d->src_xz, ns * 2 * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->src_amp, ns * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->rec_xz, nr * 2 * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->rec_w, nr * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_idx, nr * 16 * sizeof(int), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_w, nr * 16 * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_wx, nr * 16 * sizeof(double), "acq", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&d->tap_wz, nr * 16 * sizeof(double), "acq", op->st)) != HELM_OK) {
         acq_free(d);
         return s;
     }
@@ -407,14 +418,14 @@ helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d) {
 }
 
 void acq_free(DevAcq *d) {
-    dev_free(d->src_xz);
-    dev_free(d->src_amp);
-    dev_free(d->rec_xz);
-    dev_free(d->rec_w);
-    dev_free(d->tap_idx);
-    dev_free(d->tap_w);
-    dev_free(d->tap_wx);
-    dev_free(d->tap_wz);
+    dev_free(d->src_xz, d->st);
+    dev_free(d->src_amp, d->st);
+    dev_free(d->rec_xz, d->st);
+    dev_free(d->rec_w, d->st);
+    dev_free(d->tap_idx, d->st);
+    dev_free(d->tap_w, d->st);
+    dev_free(d->tap_wx, d->st);
+    dev_free(d->tap_wz, d->st);
     *d = DevAcq();
 }
 

@@ -30,7 +30,7 @@ struct helm_factor {
     float4 *bd = nullptr, *xa = nullptr, *xb = nullptr;   // mixed: b and the iterate (ping-pong), FP32 pairs
     float2 *r32 = nullptr, *y = nullptr;                  // mixed: correction right-hand side and result
     double *norms = nullptr;
-    double *norms_host = nullptr;
+    std::vector<double> norms_host;   // host copy of the norms (pageable: no pinned allocation)
 };
 
 // working memory of one mixed-precision solve of n_omega x nrhs columns
@@ -43,6 +43,7 @@ struct MixedWork {
 
 // acquisition on the device
 struct DevAcq {
+    cudaStream_t st = nullptr;   // stream the arrays were allocated on (and are freed on)
     int n_src = 0, n_rec = 0;
     double *src_xz = nullptr, *src_amp = nullptr, *rec_xz = nullptr, *rec_w = nullptr;
     int *tap_idx = nullptr;
@@ -51,8 +52,12 @@ struct DevAcq {
 
 void helm_set_error(const char *what, cudaError_t e);
 void helm_set_msg(const char *what);
-helm_status dev_alloc(void **p, size_t bytes, const char *what);
-void dev_free(void *p);
+// Device memory of the library comes from the stream-ordered allocator (cudaMallocAsync on the
+// handle's stream, the pool keeping its memory): unlike cudaMalloc / cudaFree it never waits for
+// work on other streams, so handles can be created and destroyed while other threads' kernels run.
+helm_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+void keep_pool_memory();
 helm_status factor_reserve(helm_factor_t *f, int nrhs);
 helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
                        helm_solve_info *info, int conj);

@@ -390,18 +390,6 @@ struct Ws {
     }
 };
 
-void keep_pool_memory() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-}
 
 inline int nblk(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
 
@@ -436,21 +424,15 @@ helm_status reduce_sum(const double *vals, int n, double *out, cudaStream_t st) 
 
 // device dot product -> host value (synchronises)
 struct Dotter {
-    double *partial = nullptr, *res = nullptr, *host = nullptr;
+    double *partial = nullptr, *res = nullptr;
+    double host[4] = {};
     int nb = 0;
     helm_status init(Ws &ws, int n) {
         helm_status s = HELM_OK;
         nb = std::min(nblk(n), 304);
         partial = ws.get<double>(nb, &s);
         res = ws.get<double>(4, &s);
-        if (s == HELM_OK && cudaMallocHost((void **)&host, 4 * sizeof(double)) != cudaSuccess) {
-            host = nullptr;
-            return HELM_ENOMEM;
-        }
         return s;
-    }
-    ~Dotter() {
-        if (host) cudaFreeHost(host);
     }
     helm_status dot(int n, const double *a, const double *b, int slot, cudaStream_t st) {
         HELM_TRACED(K_DOT, st, (dot_partial_kernel<<<nb, 256, 0, st>>>(n, a, b, partial)));
@@ -726,12 +708,13 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
                             helm_prec prec, const helm_pcg_opts *po, cudaStream_t st, double inv_models,
                             double *acc_dev /*[2]: psi, dalpha*/, double *dp_dev, double *dw_dev,
                             helm_hyper_info *info) {
-    ModelState ms;
     // the data branch (A(m') assembled, factored, u' = A(m')^{-1} e_s, d = R u') runs on
-    // its own stream from a second host thread, concurrently with A(m_fwi) and u
+    // its own stream from a second host thread, concurrently with A(m_fwi) and u; the stream
+    // outlives the handles allocated on it (declared first, destroyed last)
     cudaStream_t st2 = nullptr;
     HK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     struct StreamGuard { cudaStream_t s; ~StreamGuard() { if (s) cudaStreamDestroy(s); } } sg{st2};
+    ModelState ms;
     helm_status s = HELM_OK;
     Ws ws(st);
     Ws ws2(st2);

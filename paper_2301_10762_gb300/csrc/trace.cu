@@ -20,6 +20,7 @@ namespace {
 struct Rec {
     int id;
     cudaEvent_t a, b;
+    cudaStream_t st;
 };
 std::mutex g_mu;
 bool g_on = false;
@@ -56,7 +57,7 @@ TraceScope::~TraceScope() {
     cudaEvent_t b = get_event();
     if (!b) return;
     cudaEventRecord(b, st_);
-    g_recs.push_back(Rec{id_, a_, b});
+    g_recs.push_back(Rec{id_, a_, b, st_});
 }
 
 }  // namespace helm
@@ -113,6 +114,27 @@ extern "C" int32_t helm_trace_read(helm_trace_entry *out, int32_t max) {
     }
     return n;
 }
+
+extern "C" int32_t helm_trace_timeline(helm_trace_event *out, int32_t max) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    std::vector<cudaStream_t> streams;
+    int n = 0;
+    for (size_t i = 0; i < g_recs.size() && n < max; ++i) {
+        const Rec &r = g_recs[i];
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&t0, g_recs[0].a, r.a) != cudaSuccess ||
+            cudaEventElapsedTime(&t1, g_recs[0].a, r.b) != cudaSuccess)
+            return -1;
+        int sid = 0;
+        while (sid < (int)streams.size() && streams[sid] != r.st) ++sid;
+        if (sid == (int)streams.size()) streams.push_back(r.st);
+        out[n++] = helm_trace_event{r.id, sid, (double)t0, (double)t1};
+    }
+    return n;
+}
+
+extern "C" const char *helm_trace_kernel_name(int32_t id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : nullptr; }
 
 extern "C" int64_t helm_launch_count(void) {
     std::lock_guard<std::mutex> lk(g_mu);

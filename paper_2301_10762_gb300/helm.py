@@ -56,6 +56,10 @@ class helm_hyper_info(C.Structure):
                 ("data_solves", C.c_int64), ("max_refine_iters", C.c_int32)]
 
 
+class helm_trace_event(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("stream", C.c_int32), ("start_ms", C.c_double), ("end_ms", C.c_double)]
+
+
 class helm_trace_entry(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("timed", C.c_int64)]
 
@@ -65,7 +69,8 @@ EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_d
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
-            "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count"]
+            "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count",
+            "helm_trace_timeline", "helm_trace_kernel_name"]
 
 _lib = None
 
@@ -120,6 +125,10 @@ def load(path: str = LIB_PATH):
     lib.helm_trace_reset.argtypes = []
     lib.helm_trace_read.restype = C.c_int32
     lib.helm_trace_read.argtypes = [P(helm_trace_entry), i32]
+    lib.helm_trace_timeline.restype = C.c_int32
+    lib.helm_trace_timeline.argtypes = [P(helm_trace_event), i32]
+    lib.helm_trace_kernel_name.restype = C.c_char_p
+    lib.helm_trace_kernel_name.argtypes = [i32]
     lib.helm_launch_count.restype = C.c_int64
     lib.helm_launch_count.argtypes = []
     _lib = lib
@@ -380,6 +389,18 @@ def helm_trace_read():
         raise HelmError(3, "helm_trace_read")
     return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
                                    "timed": buf[i].timed} for i in range(n)}
+
+
+def helm_trace_timeline(max_events=200000):
+    """[(kernel name, stream index, start_ms, end_ms)] of the timed launches since the last
+    reset or read, in launch order (synchronises; the records stay for helm_trace_read)."""
+    lib = load()
+    buf = (helm_trace_event * max_events)()
+    n = lib.helm_trace_timeline(buf, max_events)
+    if n < 0:
+        raise HelmError(3, "helm_trace_timeline")
+    return [(lib.helm_trace_kernel_name(buf[i].kernel).decode(), buf[i].stream, buf[i].start_ms, buf[i].end_ms)
+            for i in range(n)]
 
 
 def helm_launch_count():
