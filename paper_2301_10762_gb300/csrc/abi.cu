@@ -96,7 +96,9 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "allocate(m)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->omega_dev, n_omega * sizeof(double), "allocate(omega)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->diag, (size_t)n_omega * N * sizeof(double2), "allocate(diag)", op->st)) != HELM_OK ||
-        (s = dev_alloc((void **)&op->status, sizeof(int), "allocate(status)", op->st)) != HELM_OK) {
+        (s = dev_alloc((void **)&op->status, sizeof(int), "allocate(status)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->gk, (size_t)n_omega * N * sizeof(double2), "allocate(g)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->gpk, (size_t)n_omega * N * sizeof(double2), "allocate(g')", op->st)) != HELM_OK) {
         helm_op_destroy(op);
         return s;
     }
@@ -106,6 +108,7 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
             cudaSuccess ||
         (e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess ||
         (e = launch_assemble(op->g, op->m, op->omega_dev, n_omega, op->diag, op->st)) != cudaSuccess ||
+        (e = launch_gcoef(op->g, op->m, op->omega_dev, n_omega, op->gk, op->gpk, op->st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(op->st)) != cudaSuccess) {
         helm_set_error("helm_assemble", e);
         helm_op_destroy(op);
@@ -121,6 +124,8 @@ extern "C" void helm_op_destroy(helm_op_t *op) {
     dev_free(op->omega_dev, op->st);
     dev_free(op->diag, op->st);
     dev_free(op->status, op->st);
+    dev_free(op->gk, op->st);
+    dev_free(op->gpk, op->st);
     delete op;
 }
 

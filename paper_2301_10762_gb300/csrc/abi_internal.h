@@ -13,6 +13,8 @@ struct helm_op {
     double *m = nullptr;          // [N] squared slowness (device copy)
     double *omega_dev = nullptr;  // [n_omega]
     double2 *diag = nullptr;      // [n_omega][N] diagonal of A(m, w)
+    double2 *gk = nullptr;        // [n_omega][N] g_k(w) = w^2 d_k + i w b_k / (2 sqrt(m_k))
+    double2 *gpk = nullptr;       // [n_omega][N] g'_k(w) = -i w b_k / (4 m_k^{3/2})
     int *status = nullptr;        // device status word
     cudaStream_t st = nullptr;
 };

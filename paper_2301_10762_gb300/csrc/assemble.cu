@@ -38,6 +38,35 @@ cudaError_t launch_assemble(const GridGeom &g, const double *m, const double *om
     return cudaGetLastError();
 }
 
+// g_k(w) = w^2 d_k + i w b_k / (2 sqrt(m_k)) and g'_k(w) = dg_k/dm_k = -i w b_k / (4 m_k^{3/2})
+// per frequency and node (-dA/dm_k = g_k e_k e_k^T), once per operator: the FWI kernels use them
+// for every right-hand side
+__global__ void gcoef_kernel(GridGeom g, const double *m, const double *omega, int n_omega, double2 *gk,
+                             double2 *gpk) {
+    const int N = g.nx * g.nz;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int i = k / g.nz, j = k % g.nz;
+    const double qx = edge_w(i, g.nx), qz = edge_w(j, g.nz);
+    const double d = g.hx * g.hz * qx * qz;
+    double b = 0.0;
+    if (j == 0 || j == g.nz - 1) b += g.hx * qx;
+    if (i == 0 || i == g.nx - 1) b += g.hz * qz;
+    const double mk = m[k], sq = sqrt(mk);
+    for (int w = 0; w < n_omega; ++w) {
+        const double om = omega[w];
+        gk[(size_t)w * N + k] = make_double2(om * om * d, om * b / (2.0 * sq));
+        gpk[(size_t)w * N + k] = make_double2(0.0, -om * b / (4.0 * mk * sq));
+    }
+}
+
+cudaError_t launch_gcoef(const GridGeom &g, const double *m, const double *omega_dev, int n_omega, double2 *gk,
+                         double2 *gpk, cudaStream_t st) {
+    const int N = g.nx * g.nz;
+    HELM_TRACED(K_GCOEF, st, (gcoef_kernel<<<(N + 255) / 256, 256, 0, st>>>(g, m, omega_dev, n_omega, gk, gpk)));
+    return cudaGetLastError();
+}
+
 // e_s: value src_amp at a source on a node; off a node, bilinear weights of the four
 // nodes of the containing cell.  B [n_omega][n_src][N] must be zeroed beforehand.
 __global__ void sources_kernel(GridGeom g, int n_omega, int n_src, const double *src_xz, const double *amp,

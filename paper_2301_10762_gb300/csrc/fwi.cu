@@ -32,10 +32,6 @@ __device__ __forceinline__ void node_db(const GridGeom &g, int k, double &d, dou
 __device__ __forceinline__ double2 g_of(double om, double d, double b, double mk) {
     return make_double2(om * om * d, om * b / (2.0 * sqrt(mk)));
 }
-// g'_k = dg_k/dm_k = -i w b_k / (4 m_k^{3/2})
-__device__ __forceinline__ double2 gp_of(double om, double b, double mk) {
-    return make_double2(0.0, -om * b / (4.0 * mk * sqrt(mk)));
-}
 
 // (R m)_k of R = D_x^T D_x + D_z^T D_z, D_n = (n-1) bidiag(1, -1) (Eq. (ThisGamma))
 __device__ __forceinline__ double regR(const GridGeom &g, const double *v, int k) {
@@ -177,62 +173,64 @@ __global__ void field_grad_kernel(GridGeom g, int n_omega, int nrhs, const doubl
 }
 
 // out[w][s][k] = g_k(w) u_k p_k   (right-hand side of v, Eq. (defv), and of tau, Eq. (tau_def))
-__global__ void g_u_p_kernel(GridGeom g, int n_omega, int n_src, const double *omega, const double *m,
-                             const double2 *U, const double *p, double2 *out) {
-    const int N = g.nx * g.nz;
+__global__ void g_u_p_kernel(int N, int n_omega, int n_src, const double2 *gk, const double2 *U, const double *p,
+                             double2 *out) {
     const size_t tot = (size_t)n_omega * n_src * N;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % N);
         const int w = (int)(e / ((size_t)n_src * N));
-        double d, b;
-        node_db(g, k, d, b);
-        const double2 gk = g_of(omega[w], d, b, m[k]);
-        out[e] = cscale(cmul(gk, U[e]), p[k]);
+        out[e] = cscale(cmul(gk[(size_t)w * N + k], U[e]), p[k]);
     }
 }
 
 // out[w][s][k] = -p_k conj(g_k) lambda_k  (the G^* lambda term of z, Discussion disc:Hess)
-__global__ void z_base_kernel(GridGeom g, int n_omega, int n_src, const double *omega, const double *m,
-                              const double2 *Lam, const double *p, double2 *out) {
-    const int N = g.nx * g.nz;
+__global__ void z_base_kernel(int N, int n_omega, int n_src, const double2 *gk, const double2 *Lam, const double *p,
+                              double2 *out) {
     const size_t tot = (size_t)n_omega * n_src * N;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % N);
         const int w = (int)(e / ((size_t)n_src * N));
-        double d, b;
-        node_db(g, k, d, b);
-        const double2 gk = g_of(omega[w], d, b, m[k]);
-        out[e] = cscale(cmul(cconj(gk), Lam[e]), -p[k]);
+        out[e] = cscale(cmul(cconj(gk[(size_t)w * N + k]), Lam[e]), -p[k]);
     }
 }
 
-// (H p)_k = sum_{w,s} { Re[g u conj(z)] - Re[g v conj(lambda)] - Re[g' u conj(lambda)] p_k } + (Gamma p)_k
-__global__ void hess_acc_kernel(GridGeom g, int n_omega, int n_src, const double *omega, const double *m,
-                                const double2 *U, const double2 *V, const double2 *Z, const double2 *Lam,
-                                const double *p, double alpha, double mu, int gauss_newton, double *Hp) {
+// (H p)_k = sum_{w,s} { Re[g u conj(z)] - Re[g v conj(lambda)] - Re[g' u conj(lambda)] p_k } + (Gamma p)_k,
+// in two passes: part[c][k] sums the columns of chunk c (HESS_CHUNK columns, grid.y = chunk),
+// hess_finish adds the chunks in order and the regulariser (fixed order: bitwise reproducible)
+constexpr int HESS_CHUNK = 8;
+__global__ void hess_acc_kernel(int N, int n_src, int cols, const double2 *gk, const double2 *gpk, const double2 *U,
+                                const double2 *V, const double2 *Z, const double2 *Lam, const double *p,
+                                int gauss_newton, double *part) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int c0 = blockIdx.y * HESS_CHUNK, c1 = min(cols, c0 + HESS_CHUNK);
+    const double pk = p[k];
+    double acc = 0.0;
+    for (int c = c0; c < c1; ++c) {
+        const int w = c / n_src;
+        const size_t o = (size_t)c * N + k;
+        const double2 g = gk[(size_t)w * N + k];
+        const double2 u = U[o], z = Z[o];
+        const double2 gu = cmul(g, u);
+        acc += gu.x * z.x + gu.y * z.y;
+        if (!gauss_newton) {
+            const double2 l = Lam[o];
+            const double2 gv = cmul(g, V[o]), gpu = cmul(gpk[(size_t)w * N + k], u);
+            acc -= gv.x * l.x + gv.y * l.y;
+            acc -= (gpu.x * l.x + gpu.y * l.y) * pk;
+        }
+    }
+    part[(size_t)blockIdx.y * N + k] = acc;
+}
+
+__global__ void hess_finish_kernel(GridGeom g, int n_chunks, const double *part, const double *p, double alpha,
+                                   double mu, double *Hp) {
     const int N = g.nx * g.nz;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    double d, b;
-    node_db(g, k, d, b);
-    const double mk = m[k], pk = p[k];
     double acc = 0.0;
-    for (int w = 0; w < n_omega; ++w) {
-        const double2 gk = g_of(omega[w], d, b, mk);
-        const double2 gpk = gp_of(omega[w], b, mk);
-        for (int s = 0; s < n_src; ++s) {
-            const size_t o = ((size_t)w * n_src + s) * N + k;
-            const double2 u = U[o], l = Lam[o];
-            const double2 gu = cmul(gk, u), gv = cmul(gk, V[o]), gpu = cmul(gpk, u);
-            const double2 z = Z[o];
-            acc += gu.x * z.x + gu.y * z.y;
-            if (!gauss_newton) {
-                acc -= gv.x * l.x + gv.y * l.y;
-                acc -= (gpu.x * l.x + gpu.y * l.y) * pk;
-            }
-        }
-    }
-    Hp[k] = acc + alpha * regR(g, p, k) + mu * pk;
+    for (int c = 0; c < n_chunks; ++c) acc += part[(size_t)c * N + k];
+    Hp[k] = acc + alpha * regR(g, p, k) + mu * p[k];
 }
 
 // Hypergradient receiver terms for one model, accumulated into dp[r][2], dw[r]:
@@ -517,21 +515,28 @@ static helm_status hess_apply(helm_factor_t *f, const DevAcq &da, const double2 
     const int N = g.nx * g.nz, ns = da.n_src, nr = da.n_rec, nw = op->n_omega;
     const size_t cols = (size_t)nw * ns;
     cudaStream_t st = op->st;
-    HELM_TRACED(K_GUP, st, (g_u_p_kernel<<<nblk(cols * N), 256, 0, st>>>(g, nw, ns, op->omega_dev, op->m, U, pv, E)));
+    HELM_TRACED(K_GUP, st, (g_u_p_kernel<<<nblk(cols * N), 256, 0, st>>>(N, nw, ns, op->gk, U, pv, E)));
     HL();
     HS(run_solve(f, ns, E, V, rtol, 0, count, max_it));
     if (gauss_newton) {
         HK(cudaMemsetAsync(E, 0, cols * N * sizeof(double2), st));
     } else {
-        HELM_TRACED(K_ZBASE, st, (z_base_kernel<<<nblk(cols * N), 256, 0, st>>>(g, nw, ns, op->omega_dev, op->m, Lam, pv, E)));
+        HELM_TRACED(K_ZBASE, st, (z_base_kernel<<<nblk(cols * N), 256, 0, st>>>(N, nw, ns, op->gk, Lam, pv, E)));
         HL();
     }
     HK(launch_restrict(g, (int)cols, nr, da.tap_idx, da.tap_w, V, dtmp, st));
     HELM_TRACED(K_SCATTER, st, (scatter_kernel<<<(unsigned)cols, 32, 0, st>>>(N, nr, da.tap_idx, da.tap_w, da.rec_w, 1, dtmp, E)));
     HL();
     HS(run_solve(f, ns, E, Z, rtol, 1, count, max_it));
-    HELM_TRACED(K_HESS, st, (hess_acc_kernel<<<nblk(N), 256, 0, st>>>(g, nw, ns, op->omega_dev, op->m, U, V, Z, Lam, pv, alpha, mu, gauss_newton, out)));
-    HL();
+    {   // E is free after the second solve: it holds the per-chunk partial sums
+        const int n_chunks = (int)((cols + HESS_CHUNK - 1) / HESS_CHUNK);
+        double *part = reinterpret_cast<double *>(E);
+        HELM_TRACED(K_HESS, st, (hess_acc_kernel<<<dim3(nblk(N), n_chunks), 256, 0, st>>>(
+                                     N, ns, (int)cols, op->gk, op->gpk, U, V, Z, Lam, pv, gauss_newton, part)));
+        HL();
+        HELM_TRACED(K_HESSFIN, st, (hess_finish_kernel<<<nblk(N), 256, 0, st>>>(g, n_chunks, part, pv, alpha, mu, out)));
+        HL();
+    }
     return HELM_OK;
 }
 
@@ -827,7 +832,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     }
     const double relres = r0 > 0 ? rn / r0 : 0.0;
     // tau = A^{-1}(g u rho) and the receiver terms
-    HELM_TRACED(K_GUP, st, (g_u_p_kernel<<<nblk(cols * N), 256, 0, st>>>(g, n_omega, ns, op->omega_dev, op->m, U, x, E)));
+    HELM_TRACED(K_GUP, st, (g_u_p_kernel<<<nblk(cols * N), 256, 0, st>>>(N, n_omega, ns, op->gk, U, x, E)));
     HL();
     HS(run_solve(ms.fac_f, ns, E, V, rtol, 0, &count, &max_it));
     HELM_TRACED(K_HYPER, st, (hyper_terms_kernel<<<nr, 256, 0, st>>>(N, (int)cols, nr, da.tap_idx, da.tap_w, da.tap_wx, da.tap_wz, da.rec_w,

@@ -10,6 +10,9 @@ constexpr int NB = 16;   // diagonal-block size of the line inversions
 // ---- assemble.cu
 cudaError_t launch_assemble(const GridGeom &g, const double *m, const double *omega_dev, int n_omega,
                             double2 *diag, cudaStream_t st);
+// gk, gpk [n_omega][N]: g_k(w) and g'_k(w) of the model derivative of A
+cudaError_t launch_gcoef(const GridGeom &g, const double *m, const double *omega_dev, int n_omega, double2 *gk,
+                         double2 *gpk, cudaStream_t st);
 cudaError_t launch_sources(const GridGeom &g, int n_omega, int n_src, const double *src_xz_dev,
                            const double *src_amp_dev, double2 *B, cudaStream_t st);
 // taps: [n_rec][16] node index, weight, d/dx weight, d/dz weight
