@@ -27,6 +27,9 @@ typedef struct {
  * events up front (16384), so that timed launches create none.  Host only; not thread safe
  * with concurrent library calls. */
 void helm_trace_enable(int on);
+/* Time only the launches of the kernel with this name (NULL or "": every kernel).  Returns 0,
+ * or -1 if no kernel has that name.  Counting is unaffected. */
+int32_t helm_trace_select(const char *kernel_name);
 /* Forget all counts and timings. */
 void helm_trace_reset(void);
 /* Synchronise the device, fold the recorded events into per-kernel totals and copy up

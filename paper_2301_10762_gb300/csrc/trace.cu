@@ -24,6 +24,7 @@ struct Rec {
 };
 std::mutex g_mu;
 bool g_on = false;
+int g_only = -1;   // kernel index timed alone (-1: all)
 int64_t g_launch[K_COUNT] = {};
 int64_t g_timed[K_COUNT] = {};
 double g_ms[K_COUNT] = {};
@@ -45,7 +46,7 @@ cudaEvent_t get_event() {
 TraceScope::TraceScope(int id, cudaStream_t st) : id_(id), st_(st), a_(nullptr) {
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_launch[id];
-    if (g_on) {
+    if (g_on && (g_only < 0 || g_only == id)) {
         a_ = get_event();
         if (a_) cudaEventRecord(a_, st_);
     }
@@ -75,6 +76,14 @@ extern "C" void helm_trace_enable(int on) {
         if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); break; }
         g_pool.push_back(e);
     }
+}
+
+extern "C" int32_t helm_trace_select(const char *kernel_name) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!kernel_name || !kernel_name[0]) { g_only = -1; return 0; }
+    for (int i = 0; i < K_COUNT; ++i)
+        if (strcmp(kNames[i], kernel_name) == 0) { g_only = i; return 0; }
+    return -1;
 }
 
 extern "C" void helm_trace_reset(void) {

@@ -70,7 +70,7 @@ EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_d
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
             "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count",
-            "helm_trace_timeline", "helm_trace_kernel_name"]
+            "helm_trace_timeline", "helm_trace_kernel_name", "helm_trace_select"]
 
 _lib = None
 
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
     lib.helm_trace_timeline.argtypes = [P(helm_trace_event), i32]
     lib.helm_trace_kernel_name.restype = C.c_char_p
     lib.helm_trace_kernel_name.argtypes = [i32]
+    lib.helm_trace_select.restype = C.c_int32
+    lib.helm_trace_select.argtypes = [C.c_char_p]
     lib.helm_launch_count.restype = C.c_int64
     lib.helm_launch_count.argtypes = []
     _lib = lib
@@ -375,6 +377,12 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu,
 
 def helm_trace_enable(on=True):
     load().helm_trace_enable(1 if on else 0)
+
+
+def helm_trace_select(kernel_name=None):
+    """Time only the launches of this kernel (None: every kernel)."""
+    if load().helm_trace_select((kernel_name or "").encode()) != 0:
+        raise ValueError(f"no kernel named {kernel_name!r}")
 
 
 def helm_trace_reset():
