@@ -322,7 +322,7 @@ __device__ __forceinline__ void st_cluster_c(uint32_t addr, double2 v) { st_clus
 // The two teams only meet at the middle line (G_{m+1} is read back from global memory);
 // the panel exchange of each block step stays inside a team.
 template <typename T>
-__global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArgs<T> a) {
+__global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(FactorArgs<T> a) {
     using V = cx_t<T>;
     const GridGeom g = a.g;
     const int nx = g.nx, nz = g.nz, cs = a.cs;
@@ -458,31 +458,40 @@ __global__ void __launch_bounds__(FAC_THREADS) line_factor_smem_kernel(FactorArg
                     }
                 }
                 __syncthreads();
+                // rank-kb update of the own columns: W_Ik <- -W_Ik P and W_kk <- P in block column
+                // k, W_Ij <- W_Ij - W_Ik Rk elsewhere, rows of block k <- Rk.  A thread keeps its
+                // column's kb coefficients in registers; the 16 threads of a row read the old
+                // panel row U[r][:] as broadcast 16-byte loads.
                 for (int cb = 0; cb < ncb; ++cb) {
                     const int cc = cb * NB + cl, c = c0 + cc;
                     if (c >= c1) continue;
                     const bool inblk = (c >= k0 && c < k0 + kb);
+                    V coef[NB];
+#pragma unroll
+                    for (int u = 0; u < NB; ++u)
+                        coef[u] = (u < kb) ? (inblk ? recvP[u * NB + (c - k0)] : sR[u * ldr + cc]) : mkc<T>(T(0), T(0));
                     for (int r = rw; r < nz; r += FAC_THREADS / NB) {
-                        const bool inrow = (r >= k0 && r < k0 + kb);
                         V *w = sW + (size_t)r * ldw + cc;
-                        if (inblk) {
-                            // W_Ik <- -W_Ik P ; W_kk <- P
-                            if (inrow) {
-                                *w = recvP[(r - k0) * NB + (c - k0)];
-                            } else {
-                                V acc = mkc<T>(T(0), T(0));
-#pragma unroll 4
-                                for (int u = 0; u < kb; ++u) cfma(acc, recvU[(size_t)r * NB + u], recvP[u * NB + (c - k0)]);
-                                *w = mkc<T>(-acc.x, -acc.y);
-                            }
-                        } else if (inrow) {
-                            *w = sR[(r - k0) * ldr + cc];
-                        } else {
-                            V acc = *w;
-#pragma unroll 4
-                            for (int u = 0; u < kb; ++u) cfms(acc, recvU[(size_t)r * NB + u], sR[u * ldr + cc]);
-                            *w = acc;
+                        if (r >= k0 && r < k0 + kb) {
+                            *w = inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc];
+                            continue;
                         }
+                        V acc = inblk ? mkc<T>(T(0), T(0)) : *w;
+                        const V *ur = recvU + (size_t)r * NB;
+                        if constexpr (sizeof(T) == 4) {
+                            const float4 *u4 = reinterpret_cast<const float4 *>(ur);
+#pragma unroll
+                            for (int h = 0; h < NB / 2; ++h) {
+                                const float4 q = u4[h];
+                                if (2 * h < kb) cfms(acc, make_float2(q.x, q.y), coef[2 * h]);
+                                if (2 * h + 1 < kb) cfms(acc, make_float2(q.z, q.w), coef[2 * h + 1]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < NB; ++u)
+                                if (u < kb) cfms(acc, ur[u], coef[u]);
+                        }
+                        *w = acc;
                     }
                 }
             }
