@@ -309,6 +309,55 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
     return ok;
 }
 
+// Inverse of the 16 x 16 block M (shared, row stride ld) by Newton-Schulz iteration from the
+// seed X0 (row stride NB), one element per thread of a 256-thread CTA (thread (r, c) =
+// (tid / 16, tid % 16)):  E = I - M X,  X <- X + X E  (quadratic convergence while |E| < 1).
+// Consecutive lines have nearly equal Schur complements, so the inverse of the same pivot block
+// on the previous line is a seed with |E| around 1e-3 (1e-2 at worst away from the first lines),
+// and two or three iterations reach the FP32 floor: about ten times fewer dependent steps than
+// the pivoted Gauss-Jordan of warp_invert16.  Returns false (P untouched) when the seed is too
+// far (|E| > 1/4 at the start) or the iteration stalls above 1e-4; the caller then uses
+// Gauss-Jordan.  |E| is the largest entry modulus; all threads take the same decisions.
+template <typename T>
+__device__ bool ns_invert16(const cx_t<T> *M, int ld, const cx_t<T> *X0, cx_t<T> *P, cx_t<T> (*sM)[NB + 1],
+                            cx_t<T> (*sX)[NB + 1], cx_t<T> (*sE)[NB + 1], float *sred) {
+    using V = cx_t<T>;
+    const int tid = threadIdx.x, r = tid >> 4, c = tid & 15, lane = tid & 31, wid = tid >> 5;
+    sM[r][c] = M[r * ld + c];
+    sX[r][c] = X0[r * NB + c];
+    __syncthreads();
+    float eprev = 0.f;
+    bool ok = false;
+    for (int it = 0; it < 6; ++it) {
+        V e = mkc<T>(r == c ? T(1) : T(0), T(0));
+#pragma unroll
+        for (int u = 0; u < NB; ++u) cfms(e, sM[r][u], sX[u][c]);
+        sE[r][c] = e;
+        float a = (float)(e.x * e.x + e.y * e.y);
+        a = isfinite(a) ? a : 3.0e38f;
+        for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        if (lane == 0) sred[wid] = a;
+        __syncthreads();   // sE and sred complete
+        float en2 = 0.f;
+#pragma unroll
+        for (int w = 0; w < FAC_THREADS / 32; ++w) en2 = fmaxf(en2, sred[w]);
+        const float en = sqrtf(en2);
+        if (it == 0 && !(en <= 0.25f)) break;                       // seed too far: Gauss-Jordan
+        if (en < 1e-7f) { ok = true; break; }                        // converged
+        if (it > 0 && en > 0.5f * eprev) { ok = eprev < 1e-4f; break; }   // FP32 floor (X of the last step)
+        eprev = en;
+        V x = sX[r][c];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) cfma(x, sX[r][u], sE[u][c]);
+        __syncthreads();   // every read of the old X and of sred done
+        sX[r][c] = x;
+        __syncthreads();
+    }
+    if (ok) P[r * NB + c] = sX[r][c];
+    __syncthreads();
+    return ok;
+}
+
 __device__ __forceinline__ void st_cluster_c(uint32_t addr, float2 v) { st_cluster(addr, v); }
 __device__ __forceinline__ void st_cluster_c(uint32_t addr, double2 v) { st_cluster(addr, v); }
 
@@ -349,6 +398,13 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
     __shared__ int s_bad;
     __shared__ __align__(8) uint64_t bars[2];                 // panel arrival, one per receive buffer
+    // Newton-Schulz pivot inversion (complex FP32): work blocks and the previous line's inverse of
+    // each pivot block this CTA owns (the seed)
+    constexpr bool kNS = sizeof(T) == 4;
+    constexpr int kSeedBlocks = 4;
+    __shared__ __align__(16) V s_nsM[kNS ? NB : 1][NB + 1], s_nsX[kNS ? NB : 1][NB + 1], s_nsE[kNS ? NB : 1][NB + 1];
+    __shared__ __align__(16) V s_seed[kNS ? kSeedBlocks : 1][kNS ? NB * NB : 1];
+    __shared__ float s_nsred[FAC_THREADS / 32];
 
     V *Gs = a.G + (size_t)sys * nx * nz * nz;
     const double2 *dg = a.diag + (size_t)sys * nx * nz;
@@ -424,10 +480,23 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                     // bulk-copy engine deliver them to the other CTAs of the team
                     for (int r = rw; r < nz; r += FAC_THREADS / NB)
                         if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
-                    if (tid < 32) {
-                        if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP) && tid == 0) s_bad = 1;
+                    bool done = false;
+                    if constexpr (kNS) {
+                        // seeded by this block's inverse on the team's previous line
+                        const int kl = k - kb_lo;
+                        if (slot > 0 && kb == NB && bpc <= kSeedBlocks)
+                            done = ns_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, s_seed[kl], recvP, s_nsM, s_nsX,
+                                                  s_nsE, s_nsred);
                     }
-                    __syncthreads();
+                    if (!done) {
+                        if (tid < 32) {
+                            if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP) && tid == 0) s_bad = 1;
+                        }
+                        __syncthreads();
+                    }
+                    if constexpr (kNS) {
+                        if (kb == NB && bpc <= kSeedBlocks) s_seed[k - kb_lo][tid] = recvP[tid];   // next line's seed
+                    }
                     if (tid == 0) {
                         fence_proxy_async_smem();
                         const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
