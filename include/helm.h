@@ -148,7 +148,7 @@ helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *
  * take the device-wide synchronisation of cudaMalloc / cudaFree).  The paper has no
  * counterpart: this is a property of the library, not of the method.
  * The working memory of the refinement (right-hand side and iterates as FP32 pairs, FP32
- * line vectors, per-column norms) lives in one fixed 32 MiB array in device global memory
+ * line vectors, per-column norms, the refinement's stopping state) lives in one fixed 32 MiB array in device global memory
  * that every GPU loading the library holds until exit; the caller still passes B_dev and
  * X_dev.  Limits: n_omega * nrhs * N * 64 bytes (mixed; norms only for FP64) within 32 MiB and at most
  * 16384 columns, else HELM_EINVAL.  The first call on a device resolves the array's

@@ -203,6 +203,7 @@ extern "C" void helm_factor_destroy(helm_factor_t *f) {
     dev_free(f->r32, st);
     dev_free(f->y, st);
     dev_free(f->norms, st);
+    dev_free(f->state, st);
     delete f;
 }
 
@@ -218,9 +219,11 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
     dev_free(f->r32, st);
     dev_free(f->y, st);
     dev_free(f->norms, st);
+    dev_free(f->state, st);
     f->bd = f->xa = f->xb = nullptr;
     f->r32 = f->y = nullptr;
     f->norms = nullptr;
+    f->state = nullptr;
     f->cap = 0;
     helm_status s;
     if (f->prec == HELM_MIXED &&
@@ -228,7 +231,8 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
          (s = dev_alloc((void **)&f->xa, cols * N * sizeof(float4), "allocate(iterate)", st)) != HELM_OK ||
          (s = dev_alloc((void **)&f->xb, cols * N * sizeof(float4), "allocate(iterate)", st)) != HELM_OK ||
          (s = dev_alloc((void **)&f->r32, cols * N * sizeof(float2), "allocate(residual)", st)) != HELM_OK ||
-         (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "allocate(work)", st)) != HELM_OK))
+         (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "allocate(work)", st)) != HELM_OK ||
+         (s = dev_alloc((void **)&f->state, sizeof(RefineState), "allocate(refinement state)", st)) != HELM_OK))
         return s;
     if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "allocate(norms)", st)) != HELM_OK) return s;
     f->norms_host.assign(cols * 2, 0.0);
@@ -255,9 +259,14 @@ helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, 
 // correction solves.  The iterate and the residual are FP32 pairs (refine.cu) down to
 // kPairFloor or until the pair residual stops falling; a tighter rtol continues with FP64
 // residuals on the FP64 iterate.
+// The stopping test of the pair phase runs on the device (refine_check after every update), so
+// the host enqueues several sweeps at a time and reads the state once per batch; sweeps and
+// updates enqueued after the test has stopped the loop return at once.  The first batch is as
+// long as the previous solve with this factor took.
 helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, double2 *X, int conj, double rtol,
                          int max_iter, const MixedWork &w, int *iters, double *relres) {
     constexpr double kPairFloor = 1e-12;   // well above the pair residual's floor (about 1e-13)
+    constexpr int kLaterBatch = 2;
     const helm_op *op = f->op;
     const GridGeom &g = op->g;
     const int n_sys = op->n_omega;
@@ -265,29 +274,37 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     const size_t n = (size_t)cols * g.nx * g.nz;
     const int rchunk = 16;
     if (max_iter < 1) max_iter = 1;
-    cudaError_t e = launch_refine_start(g, cols, B, conj, w.bd, w.r32, w.norms, op->st);
+    cudaError_t e = cudaMemsetAsync(w.state, 0, sizeof(RefineState), op->st);
+    if (e == cudaSuccess) e = launch_refine_start(g, cols, B, conj, w.bd, w.r32, w.norms, op->st);
     if (e != cudaSuccess) { helm_set_error("refinement start", e); return HELM_ECUDA; }
-    auto sweep = [&]() {
+    const int *skip = &w.state->done;
+    auto sweep = [&](const int *skip_flag) {
         return launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, w.r32, nullptr, w.y, 0, rchunk,
-                                        op->status, op->st, f->mid);
+                                        op->status, op->st, f->mid, skip_flag);
     };
-    const float4 *x_in = nullptr;
-    float4 *x_out = w.xa;
-    int it = 0;
-    double rel = INFINITY, prev = INFINITY;
+    RefineState hs{};
+    int enq = 0, batch = std::max(1, std::min(f->last_iters.load(std::memory_order_relaxed), max_iter));
     helm_status s;
-    for (;;) {   // FP32-pair phase
-        if ((e = sweep()) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
-        ++it;
-        e = launch_refine_update(g, n_sys, nrhs, f->diag2, w.bd, x_in, w.y, x_out, w.r32, w.norms, op->st);
-        if (e != cudaSuccess) { helm_set_error("refinement update", e); return HELM_ECUDA; }
-        if ((s = max_relres(op, (size_t)cols, w.norms, w.norms_host, &rel)) != HELM_OK) return s;
-        x_in = x_out;
-        x_out = (x_out == w.xa) ? w.xb : w.xa;
-        if (rel <= rtol || it >= max_iter || !isfinite(rel) || rel <= kPairFloor || rel > 0.25 * prev) break;
-        prev = rel;
+    while (enq < max_iter) {   // FP32-pair phase
+        for (const int end = std::min(enq + batch, max_iter); enq < end; ++enq) {
+            // sweep k (from 0) writes xa for even k, xb for odd k and reads the other
+            const float4 *x_in = enq == 0 ? nullptr : ((enq & 1) ? w.xa : w.xb);
+            float4 *x_out = (enq & 1) ? w.xb : w.xa;
+            if ((e = sweep(skip)) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+            e = launch_refine_update(g, n_sys, nrhs, f->diag2, w.bd, x_in, w.y, x_out, w.r32, w.norms, op->st, skip);
+            if (e == cudaSuccess) e = launch_refine_check(cols, w.norms, rtol, kPairFloor, max_iter, w.state, op->st);
+            if (e != cudaSuccess) { helm_set_error("refinement update", e); return HELM_ECUDA; }
+        }
+        e = cudaMemcpyAsync(&hs, w.state, sizeof(RefineState), cudaMemcpyDeviceToHost, op->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+        if (e != cudaSuccess) { helm_set_error("read refinement state", e); return HELM_ECUDA; }
+        if (hs.done) break;
+        batch = kLaterBatch;
     }
-    e = launch_refine_finish(n, x_in, conj, X, op->st);
+    int it = hs.iters;
+    double rel = hs.rel;
+    f->last_iters.store(std::max(1, it), std::memory_order_relaxed);
+    e = launch_refine_finish(n, w.xa, w.xb, w.state, conj, X, op->st);
     if (e != cudaSuccess) { helm_set_error("refinement finish", e); return HELM_ECUDA; }
     if (!(rel <= rtol) && it < max_iter && isfinite(rel)) {
         // FP64 phase: r = b - A x in FP64 on the FP64 iterate, correction conj?(A~^{-1} conj?(r))
@@ -297,7 +314,7 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
             if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
             if ((s = max_relres(op, (size_t)cols, w.norms, w.norms_host, &rel)) != HELM_OK) return s;
             if (rel <= rtol || it >= max_iter || !isfinite(rel)) break;
-            if ((e = sweep()) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
+            if ((e = sweep(nullptr)) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
             e = launch_refine_accumulate(n, w.y, conj, X, op->st);
             if (e != cudaSuccess) { helm_set_error("refinement accumulate", e); return HELM_ECUDA; }
             ++it;
@@ -333,7 +350,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
         return HELM_OK;
     }
     if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
-    const MixedWork w{f->bd, f->xa, f->xb, f->r32, f->y, f->norms, f->norms_host.data()};
+    const MixedWork w{f->bd, f->xa, f->xb, f->r32, f->y, f->norms, f->norms_host.data(), f->state};
     int it = 0;
     double rel = INFINITY;
     if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;

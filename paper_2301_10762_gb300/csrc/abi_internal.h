@@ -1,5 +1,6 @@
 // Internal definitions of the opaque handles of include/helm.h (C++ only).
 #pragma once
+#include <atomic>
 #include <vector>
 #include <cuda_runtime.h>
 #include "helm.h"
@@ -19,6 +20,10 @@ struct helm_op {
     cudaStream_t st = nullptr;
 };
 
+namespace helm {
+struct RefineState;   // device-side refinement control (kernels.h)
+}
+
 struct helm_factor {
     helm_op *op = nullptr;
     helm_prec prec = HELM_FP64;
@@ -33,6 +38,8 @@ struct helm_factor {
     float2 *r32 = nullptr, *y = nullptr;                  // mixed: correction right-hand side and result
     double *norms = nullptr;
     std::vector<double> norms_host;   // host copy of the norms (pageable: no pinned allocation)
+    helm::RefineState *state = nullptr;       // mixed: device-side refinement control
+    mutable std::atomic<int> last_iters{3};   // correction sweeps the previous mixed solve took
 };
 
 // working memory of one mixed-precision solve of n_omega x nrhs columns
@@ -41,6 +48,7 @@ struct MixedWork {
     float2 *r32, *y;
     double *norms;        // device [cols][2]
     double *norms_host;   // host [cols][2]
+    helm::RefineState *state;   // device
 };
 
 // acquisition on the device

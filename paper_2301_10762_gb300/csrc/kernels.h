@@ -28,10 +28,12 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
                                int *status, int cs, cudaStream_t st, int *mid_out);
 
 // ---- sweep.cu
-// B in the working precision; TG = double writes X (conjugated if conj), TG = float writes Y
+// B in the working precision; TG = double writes X (conjugated if conj), TG = float writes Y.
+// skip (optional, device): nonzero when the launch runs makes it do nothing.
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid);
+                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid,
+                              const int *skip = nullptr);
 // FP64 residual B - A X (A^H X for conj), norms[col] += (||R||^2, ||B||^2); R32 = conj?(R) in FP32 if given
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
                             const double2 *X, float2 *R32, double *norms, int conj, cudaStream_t st);
@@ -53,11 +55,24 @@ cudaError_t launch_split_diag(size_t n, const double2 *diag, float4 *diag2, cuda
 cudaError_t launch_refine_start(const GridGeom &g, int cols, const double2 *B, int conj, float4 *bd, float2 *r32,
                                 double *norms, cudaStream_t st);
 // x_out = x_in (none: 0) + delta; r32 = leading part of bd - A x_out; norms[col][0] += ||r||^2
+// (zero on entry: refine_start and refine_check leave it so).  skip (optional, device): nonzero when the launch runs makes it do nothing.
 cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const float4 *diag2, const float4 *bd,
                                  const float4 *x_in, const float2 *delta, float4 *x_out, float2 *r32, double *norms,
-                                 cudaStream_t st);
-// X = conj?(hi + lo) in FP64
-cudaError_t launch_refine_finish(size_t n, const float4 *x, int conj, double2 *X, cudaStream_t st);
+                                 cudaStream_t st, const int *skip = nullptr);
+// Device-side control of the refinement loop: after each update, one block computes
+// rel = max_col ||r|| / ||b|| from norms, decides whether the pair iteration is done and
+// zeroes norms[col][0] for the next update.
+struct RefineState {
+    int done;      // 1: converged (rel <= rtol), 2: stopped (floor, stagnation, max_iter, not finite)
+    int iters;     // correction sweeps applied
+    double rel;    // latest max relative residual
+    double prev;   // the one before
+};
+cudaError_t launch_refine_check(int cols, double *norms, double rtol, double floor_rel, int max_iter,
+                                RefineState *state, cudaStream_t st);
+// X = conj?(hi + lo) in FP64 of the newest iterate: xa after an odd number of sweeps, else xb
+cudaError_t launch_refine_finish(size_t n, const float4 *xa, const float4 *xb, const RefineState *state, int conj,
+                                 double2 *X, cudaStream_t st);
 // X += conj?(delta) in FP64 (refinement tail with FP64 residuals)
 cudaError_t launch_refine_accumulate(size_t n, const float2 *delta, int conj, double2 *X, cudaStream_t st);
 

@@ -40,6 +40,7 @@ template <typename TG> struct SweepArgs {
     cx_t<TG> *Y;         // forward vectors y_i, [n_sys][nrhs][N] (== X for TG = double)
     int conj;            // FP64 path: B and X conjugated (adjoint solve)
     int *status;
+    const int *skip;     // optional: nonzero -> the launch does nothing (refinement finished)
 };
 
 // Padded row stride (in complex elements) of the shared-memory operands of the sweep product.
@@ -140,8 +141,10 @@ constexpr int PP_KC = 32;      // K chunk
 // tr + 32, whose padded stride keeps the G reads free of bank conflicts.
 template <typename TG>
 __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nrhs, const cx_t<TG> *G,
-                                                             const cx_t<TG> *B, cx_t<TG> *Y, int conj) {
+                                                             const cx_t<TG> *B, cx_t<TG> *Y, int conj,
+                                                             const int *skip) {
     using V = cx_t<TG>;
+    if (skip && *skip) return;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     const int n_rt = (nz + PP_ROWS - 1) / PP_ROWS;
     const int n_ch = (nrhs + PP_RHS - 1) / PP_RHS;
@@ -313,6 +316,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     };
     auto bwd_index = [&](int s) { return team == 0 ? s - len - 1 : s - len; };   // 0 for the first backward step
 
+    // a refinement that has already finished leaves the rest of its enqueued sweeps empty; every
+    // CTA reads the same flag (written by an earlier launch) and leaves before any cluster sync
+    if (a.skip && *a.skip) return;
     if (tid == 0) {
         for (int b = 0; b < 4; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init_cluster();
@@ -709,7 +715,8 @@ template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP) {
 
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
-                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid) {
+                              double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid,
+                              const int *skip) {
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
     const int teams = (mid < g.nx - 1) ? 2 : 1;
@@ -797,12 +804,12 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         }
         if (!mma) {   // CUDA-core sweep: Y_i = G_i b_i for all lines first
             const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + PP_RHS - 1) / PP_RHS);
-            HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj)));
+            HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj, skip)));
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status};
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status, skip};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);
@@ -822,9 +829,10 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
 }
 
 template cudaError_t launch_line_sweep<double>(const GridGeom &, int, int, const double2 *, const double2 *,
-                                               double2 *, double2 *, int, int, int *, cudaStream_t, int);
+                                               double2 *, double2 *, int, int, int *, cudaStream_t, int,
+                                               const int *);
 template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const float2 *,
-                                              double2 *, float2 *, int, int, int *, cudaStream_t, int);
+                                              double2 *, float2 *, int, int, int *, cudaStream_t, int, const int *);
 
 
 // ------------------------------------------------------------------ FP64 residual
