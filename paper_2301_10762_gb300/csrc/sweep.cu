@@ -29,6 +29,7 @@ constexpr int SW_KC = 64;      // K chunk of the streamed (non-prefetched) G pat
 constexpr int SW_MAXOPT = 2;   // outputs per thread (rows_per_cta * R <= 2 * 256)
 constexpr size_t SW_SMEM_MAX = 200 * 1024;
 constexpr uint32_t SW_WAIT_TRIES = 1u << 22;   // bounded mbarrier wait (seconds at worst)
+constexpr int FM_MAX_RHS = 4;   // right-hand sides per cluster up to which the FMA product is taken
 
 template <typename TG> struct SweepArgs {
     GridGeom g;
@@ -240,6 +241,39 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// FMA product of one lane: facc[q] += sum_p G(row, c_p) t_q(c_p) over its 4*KP complex columns
+// c_p = c0 .. c0 + 4*KP - 1 (held in g, two per float4), for the first NQ right-hand sides of
+// the line buffer tv ([rhs][nzp], complex FP32); rhs >= nq and columns >= nz read as zero.  The
+// loads of one column pair for every right-hand side are issued together, then 2*NQ
+// independent FMA chains.
+template <int NQ, int KP>
+__device__ __forceinline__ void fma_product(const float2 *tv, int nzp, int c0, int nz, int nq,
+                                            const float4 (&g)[2 * KP], float2 (&facc)[MMA_RHS]) {
+#pragma unroll
+    for (int p = 0; p < 2 * KP; ++p) {
+        const int c = c0 + 2 * p;
+        float4 t2[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            t2[q] = (c < nz && q < nq) ? *reinterpret_cast<const float4 *>(tv + (size_t)q * nzp + c)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 g2 = g[p];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float2 f = facc[q];
+            f.x = fmaf(g2.x, t2[q].x, f.x);
+            f.y = fmaf(g2.x, t2[q].y, f.y);
+            f.x = fmaf(-g2.y, t2[q].y, f.x);
+            f.y = fmaf(g2.y, t2[q].x, f.y);
+            f.x = fmaf(g2.z, t2[q].z, f.x);
+            f.y = fmaf(g2.z, t2[q].w, f.y);
+            f.x = fmaf(-g2.w, t2[q].w, f.x);
+            f.y = fmaf(g2.w, t2[q].z, f.y);
+            facc[q] = f;
+        }
+    }
+}
+
 // Persistent twisted sweep, after the pre-pass has stored G_i b_i in Y.  The cluster holds
 // `teams` teams of `cs` CTAs; CTA rank%cs of a team owns a slab of rows of every line.
 //   left team:   y_i = G_i b_i - G_i C y_{i-1},  i = 0 .. m-1            (forward)
@@ -262,7 +296,14 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // KP 8-column blocks of K per warp (the eight warps split K and meet in shared memory), the
 // G_i slab read from L2 straight into fragment registers one step ahead.  MT = 0 is the
 // CUDA-core product (FP64, or shapes the tensor tiles do not cover).
-template <typename TG, int MT, int KP>
+// FM (with MT = 1) keeps the register-held G_i slab of the tensor path but forms the product
+// with FP32 FMAs: lane (row, half) of a warp holds 4*KP complex entries of one row and reads
+// the matching entries of every right-hand side from shared memory as a broadcast over the
+// sixteen lanes of its half.  The 16 x 8 x 8 tile of the legacy mma.sync needs three TF32
+// passes for FP32 accuracy and always eight right-hand sides; the FMA product does R of them
+// at full FP32 precision.  The producer folds the right-hand side into its push,
+// C y - b_{i+1}, so that the consumer's product is G_i t with no per-lane b.
+template <typename TG, int MT, int KP, bool FM>
 __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a) {
     using V = cx_t<TG>;
     const GridGeom g = a.g;
@@ -356,8 +397,21 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     float4 gfr[MT > 0 ? MT : 1][2][KP > 0 ? KP : 1];
     float4 bfr[KP > 0 ? KP : 1];   // b_i (forward and middle lines): rhs fg, columns 8j + 2t, 8j + 2t + 1
     const V *Bs = a.B + ((size_t)sys * a.nrhs + q0) * N;
+    // FMA product: lane (frow, fh) holds row frow, complex columns fc0 .. fc0 + 4*KP - 1
+    const int frow = lane & 15, fh = lane >> 4;
+    const int fc0 = KP == 2 ? 8 * (wid + 8 * fh) : 8 * wid + 4 * fh;
+    float4 gq[FM ? 2 * KP : 1], gcur[FM ? 2 * KP : 1];
     auto load_g = [&](int s1) {
-        if constexpr (MT > 0) {
+        if constexpr (FM) {
+            if (s1 >= nsteps) return;
+            const float2 *Gl = reinterpret_cast<const float2 *>(Gs) + ((size_t)line_of(s1) * nz + r0) * nz;
+#pragma unroll
+            for (int p = 0; p < 2 * KP; ++p) {
+                const int c = fc0 + 2 * p;
+                gq[p] = (frow < nrows && c < nz) ? __ldg(reinterpret_cast<const float4 *>(Gl + (size_t)frow * nz + c))
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else if constexpr (MT > 0) {
             if (s1 >= nsteps) return;
             const int i1 = line_of(s1);
             const bool fwd1 = kind_of(s1) != 2;
@@ -409,9 +463,18 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     // tensor path with few fragments: the TF32 splits of this step's G_i fragments and the
     // loads of the next step's are made at the top of the step, while the team's pushes are
     // still in flight; larger tiles split inside the product (register budget)
-    constexpr bool kPreSplit = MT > 0 && MT * KP <= 2;
+    constexpr bool kPreSplit = !FM && MT > 0 && MT * KP <= 2;
     uint32_t ahs[kPreSplit ? MT : 1][kPreSplit ? KP : 1][2][4], als[kPreSplit ? MT : 1][kPreSplit ? KP : 1][2][4];
     float4 bcur[KP > 0 ? KP : 1];
+    if constexpr (FM) {   // input of the first forward line: -b (no predecessor pushes to it)
+        const int i0 = line_of(0);
+        for (int e = tid; e < Rc * nz; e += SW_THREADS) {
+            const int q = e / nz, k = e % nz;
+            const V b = Bs[(size_t)q * N + (size_t)i0 * nz + k];
+            sY[(size_t)q * nzp + k] = mkc<TG>(-b.x, -b.y);
+        }
+    }
+    V bpush = mkc<TG>(TG(0), TG(0));   // FM: b of the line the push of this step feeds
     prefetch(0);
     cp_async_commit();
     load_g(0);
@@ -436,6 +499,14 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             }
             load_g(s + 1);
         }
+        if constexpr (FM) {   // a forward or middle consumer takes C y - b of its line
+#pragma unroll
+            for (int p = 0; p < 2 * KP; ++p) gcur[p] = gq[p];
+            load_g(s + 1);   // next line's slab: in flight for a whole step
+            bpush = mkc<TG>(TG(0), TG(0));
+            if (ov[0] && s + 1 < nsteps && kind_of(s + 1) != 2)
+                bpush = Bs[(size_t)oq[0] * N + (size_t)line_of(s + 1) * nz + r0 + orow[0]];
+        }
         // input vector of the product: none (first forward line), the middle buffers, the
         // x_m buffer (first backward line) or the team ping-pong buffer
         const V *tin = nullptr;
@@ -457,7 +528,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
         if (kind == 1) { tin = sMid; tin2 = (teams == 2) ? sMid + (size_t)R * nzp : nullptr; }
         else if (kind == 2 && bi == 0) tin = sX;
-        else if (!(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
+        else if (FM || !(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
         const bool final_line = (kind != 0);
         cp_async_wait<0>();
         __syncthreads();   // step s operands landed; every thread is done with step s - 1
@@ -486,7 +557,32 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                                      : mkc<TG>(TG(0), TG(0));
             acc[u] = mkc<TG>(TG(0), TG(0));
         }
-        if constexpr (MT > 0) {
+        if constexpr (FM) {
+            float2 facc[MMA_RHS];
+#pragma unroll
+            for (int q = 0; q < MMA_RHS; ++q) facc[q] = make_float2(0.f, 0.f);
+            const float2 *tv = reinterpret_cast<const float2 *>(tin);
+            if (Rc > 4) fma_product<8, KP>(tv, nzp, fc0, nz, Rc, gcur, facc);
+            else if (Rc > 2) fma_product<4, KP>(tv, nzp, fc0, nz, Rc, gcur, facc);
+            else if (Rc > 1) fma_product<2, KP>(tv, nzp, fc0, nz, Rc, gcur, facc);
+            else fma_product<1, KP>(tv, nzp, fc0, nz, Rc, gcur, facc);
+            // partial products of this lane's K part -> red[2 * wid + fh][rhs][row]
+#pragma unroll
+            for (int q = 0; q < MMA_RHS; ++q)
+                if (q < Rc) red[((size_t)(2 * wid + fh) * MMA_RHS + q) * RP + frow] = facc[q];
+            __syncthreads();
+            if (ov[0]) {
+                const int q = oq[0], r = orow[0], wpp = 16 / tpo;
+                float2 sum = make_float2(0.f, 0.f);
+                for (int w = part * wpp; w < (part + 1) * wpp; ++w) {
+                    const float2 v = red[((size_t)w * MMA_RHS + q) * RP + r];
+                    sum.x += v.x;
+                    sum.y += v.y;
+                }
+                acc[0].x = sum.x;
+                acc[0].y = sum.y;
+            }
+        } else if constexpr (MT > 0) {
             {
                 const bool fwd = kind != 2;
                 float accB[MT][2][4], accS[MT][2][4];   // hi*hi and the two cross terms
@@ -619,7 +715,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
                 const V v = mkc<TG>(yown[u].x - acc[u].x, yown[u].y - acc[u].y);
                 vlast[u] = v;
                 if (dstbuf) {
-                    const V cv = mkc<TG>(ocoef[u] * v.x, ocoef[u] * v.y);
+                    const V cv = FM ? mkc<TG>(ocoef[u] * v.x - bpush.x, ocoef[u] * v.y - bpush.y)
+                                    : mkc<TG>(ocoef[u] * v.x, ocoef[u] * v.y);
                     const uint32_t la = lbuf + obyte[u];
                     for (int t = t_lo + part; t < t_hi; t += tpo)
                         st_async(mapa_u32(la, (uint32_t)t), cv, mapa_u32(lbar, (uint32_t)t));
@@ -704,11 +801,13 @@ cudaError_t ensure_dyn_smem(const void *fn, size_t bytes) {
 template <typename TG> using SweepFn = void (*)(SweepArgs<TG>);
 
 // kernel of the tensor-pipe product with MT m tiles and KP K blocks per warp (null if none)
-template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP) {
+template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP, bool fm) {
     if constexpr (sizeof(TG) == 4) {
-        if (MT == 1 && KP == 1) return line_sweep_kernel<TG, 1, 1>;
-        if (MT == 1 && KP == 2) return line_sweep_kernel<TG, 1, 2>;
-        if (MT == 2 && KP == 4) return line_sweep_kernel<TG, 2, 4>;
+        if (fm && MT == 1 && KP == 1) return line_sweep_kernel<TG, 1, 1, true>;
+        if (fm && MT == 1 && KP == 2) return line_sweep_kernel<TG, 1, 2, true>;
+        if (MT == 1 && KP == 1) return line_sweep_kernel<TG, 1, 1, false>;
+        if (MT == 1 && KP == 2) return line_sweep_kernel<TG, 1, 2, false>;
+        if (MT == 2 && KP == 4) return line_sweep_kernel<TG, 2, 4, false>;
     }
     return nullptr;
 }
@@ -728,6 +827,9 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
     // HELM_SWEEP_CUDA_CORES=1 keeps complex-FP32 sweeps on the CUDA-core product
     const char *env_cc = getenv("HELM_SWEEP_CUDA_CORES");
     const bool allow_mma = !(env_cc && atoi(env_cc) > 0);
+    // HELM_SWEEP_MMA=1 / =0 forces the tensor-pipe / FMA product where both cover the shape
+    const char *env_mma = getenv("HELM_SWEEP_MMA");
+    const int force_mma = (env_mma && *env_mma) ? (atoi(env_mma) > 0 ? 1 : 0) : -1;
     cudaError_t e;
     for (;;) {
         const int rpc = (nz + cs - 1) / cs;
@@ -760,7 +862,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         }
         size_t smem = smem_of(R, pf);
         int tpo = tpo_of(R);
-        SweepFn<TG> kfn = line_sweep_kernel<TG, 0, 0>;
+        SweepFn<TG> kfn = line_sweep_kernel<TG, 0, 0, false>;
         bool mma = false;
         // tensor-pipe product: complex FP32, even n_z (16-byte fragment loads), at most two m
         // tiles of rows per CTA and K blocks that the kernels below cover; one n tile of eight
@@ -773,14 +875,17 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
                 else if (rpc <= 16 && np <= 16) { MT = 1; KP = 2; }
                 else if (rpc <= 32 && np <= 32) { MT = 2; KP = 4; }
             }
-            SweepFn<TG> mfn = MT > 0 ? sweep_mma_fn<TG>(MT, KP) : nullptr;
+            int Rm = std::min(nrhs, MMA_RHS);
+            if (rchunk > 0 && Rm > rchunk) Rm = rchunk;
+            if (env_r && atoi(env_r) > 0) Rm = std::min(atoi(env_r), MMA_RHS);
+            // one m tile of rows and few right-hand sides: the FMA product on the same
+            // register-held slab (its cost grows with R; the tensor tile always pays for eight)
+            const bool fm = MT == 1 && (force_mma < 0 ? Rm <= FM_MAX_RHS : force_mma == 0);
+            SweepFn<TG> mfn = MT > 0 ? sweep_mma_fn<TG>(MT, KP, fm) : nullptr;
             if (mfn) {
-                int Rm = std::min(nrhs, MMA_RHS);
-                if (rchunk > 0 && Rm > rchunk) Rm = rchunk;
-                if (env_r && atoi(env_r) > 0) Rm = std::min(atoi(env_r), MMA_RHS);
                 const size_t nzp = (size_t)padded_mma(nz);
                 const size_t sm = (size_t)32 + vsz * 5 * (size_t)Rm * nzp + vsz * 2 * (size_t)Rm * rpc +
-                                  sizeof(float2) * 8 * MMA_RHS * (size_t)(16 * MT + 2);
+                                  sizeof(float2) * (fm ? 16 : 8) * MMA_RHS * (size_t)(16 * MT + 2);
                 if (sm <= SW_SMEM_MAX) {
                     kfn = mfn;
                     mma = true;

@@ -69,6 +69,25 @@ def test_solve_and_adjoint_match_oracle(nx, nz, lx, lz, n_om, nrhs, prec):
         assert info["max_relres"] <= 1e-12 and info["iters"] >= 2
 
 
+@pytest.mark.parametrize("product", ["fma", "mma"])
+@pytest.mark.parametrize("nx,nz,nrhs", [(24, 128, 11), (30, 64, 3), (24, 128, 1)])
+def test_sweep_products_match_oracle(monkeypatch, product, nx, nz, nrhs):
+    # 16 rows per CTA (n_z = 64: one K block per warp, n_z = 128: two): the FP32-FMA and the
+    # tensor-pipe product of the complex-FP32 sweep, forced either way, with a ragged last
+    # chunk of right-hand sides (11 = 8 + 3)
+    monkeypatch.setenv("HELM_SWEEP_MMA", "0" if product == "fma" else "1")
+    m, om, B = _setup(nx, nz, 1.0, 1.0, 2, nrhs, seed=3)
+    g = H.Grid(nx, nz, 1.0, 1.0)
+    op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
+    f = hm.helm_factor(op, 1)
+    Bd = torch.tensor(B, device="cuda")
+    X, info = hm.helm_solve(f, Bd, rtol=1e-12, max_iter=10)
+    assert colerr(X.cpu().numpy(), oracle_solve(g, m, om, B)) <= TOL_MIXED
+    assert info["max_relres"] <= 1e-12
+    Y, _ = hm.helm_adjoint_solve(f, Bd, rtol=1e-12, max_iter=10)
+    assert colerr(Y.cpu().numpy(), oracle_solve(g, m, om, B, adjoint=True)) <= TOL_MIXED
+
+
 def test_plain_forward_config_64():
     """The plain forward workload: 64 x 64, omega = 10, Gaussian inclusion, 8 top-row
     sources; both precisions against the oracle."""
