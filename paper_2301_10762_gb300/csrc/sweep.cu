@@ -291,7 +291,11 @@ __device__ __forceinline__ void fma_product(const float2 *tv, int nzp, int c0, i
 // the left team's middle buffers, and the left team pushes C x_m to every CTA.  Exchange
 // buffers alternate; no CTA overwrites a buffer before every consumer is done with it,
 // because producing the data of step s+2 needs the data of step s+1 from every CTA of the
-// team, which each CTA sends only after it has finished step s.
+// team, which each CTA sends only after it has finished step s (its pushes follow the CTA
+// barrier of the reduction, which follows every thread's reads of the step's input).
+// MT > 0: every thread waits on the mbarrier itself and there is no CTA barrier between the
+// arrival of the inputs and the product; the own rows of a backward step come from a register
+// loaded one step ahead, and the partial sums alternate between two buffers.
 // MT > 0 selects the tensor-pipe product (complex FP32 only): MT m16 tiles of rows per CTA,
 // KP 8-column blocks of K per warp (the eight warps split K and meet in shared memory), the
 // G_i slab read from L2 straight into fragment registers one step ahead.  MT = 0 is the
@@ -335,7 +339,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     V *sG = sX + (size_t)R * nzp;                                       // pf: [2][rpc][nzp]; else [rpc][kcp]
     V *sOwn = sG + (MT > 0 ? 0 : (pf ? 2 * (size_t)rpc * nzp : (size_t)rpc * kcp));   // [2][R][rpc]: own rows
     constexpr int RP = 16 * (MT > 0 ? MT : 1) + 2;   // tensor path: padded row count of the partials
-    float2 *red = reinterpret_cast<float2 *>(sOwn + 2 * (size_t)R * rpc);   // [8 warps][MMA_RHS][RP]
+    // tensor / FMA partial sums: [step parity][8 warps (FM: 16 lane halves)][MMA_RHS][RP]
+    float2 *red = reinterpret_cast<float2 *>(sOwn + 2 * (size_t)R * rpc);
     __shared__ int s_abort;
 
     const V *Gs = a.G + (size_t)sys * nx * nz * nz;
@@ -473,8 +478,12 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             const V b = Bs[(size_t)q * N + (size_t)i0 * nz + k];
             sY[(size_t)q * nzp + k] = mkc<TG>(-b.x, -b.y);
         }
+        __syncthreads();
     }
     V bpush = mkc<TG>(TG(0), TG(0));   // FM: b of the line the push of this step feeds
+    // MT > 0: own rows y_i of this and of the next backward step, loaded a step ahead by the
+    // K part 0 of each output (the thread that stored them on the forward pass)
+    V ycur = mkc<TG>(TG(0), TG(0)), ypre = ycur;
     prefetch(0);
     cp_async_commit();
     load_g(0);
@@ -507,20 +516,31 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             if (ov[0] && s + 1 < nsteps && kind_of(s + 1) != 2)
                 bpush = Bs[(size_t)oq[0] * N + (size_t)line_of(s + 1) * nz + r0 + orow[0]];
         }
+        if constexpr (MT > 0) {
+            ycur = ypre;
+            ypre = mkc<TG>(TG(0), TG(0));
+            if (part == 0 && ov[0] && s + 1 < nsteps && kind_of(s + 1) == 2 && !(team == 1 && bwd_index(s + 1) == 0))
+                ypre = Ys[ogl[0] + (size_t)line_of(s + 1) * nz];
+        }
         // input vector of the product: none (first forward line), the middle buffers, the
         // x_m buffer (first backward line) or the team ping-pong buffer
         const V *tin = nullptr;
         const V *tin2 = nullptr;
-        if (tid == 0 && !(kind == 0 && s == 0)) {
+        if (!(kind == 0 && s == 0)) {
             uint64_t *bar;
             uint32_t bytes = vec_bytes, par;
             if (kind == 1) { bar = &bars[2]; bytes = vec_bytes * (uint32_t)teams; par = 0; }
             else if (kind == 2 && bi == 0) { bar = &bars[3]; par = 0; }
             else { bar = &bars[s & 1]; par = (s & 1) ? ph1 : ph0; }
-            mbar_arrive_expect_tx(bar, bytes);
-            if (!mbar_wait_bounded(bar, par, SW_WAIT_TRIES)) {
-                atomicOr(a.status, ST_TIMEOUT);
-                s_abort = 1;
+            if (tid == 0) mbar_arrive_expect_tx(bar, bytes);
+            // tensor and FMA products: every thread waits for the inputs itself, with no CTA
+            // barrier at the top of the step (the own rows come from registers); the CUDA-core
+            // product also needs the slab its threads prefetched, behind the barrier below
+            if (MT > 0 || tid == 0) {
+                if (!mbar_wait_bounded(bar, par, SW_WAIT_TRIES)) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    s_abort = 1;
+                }
             }
         }
         if (!(kind == 0 && s == 0) && kind != 1 && !(kind == 2 && bi == 0)) {
@@ -530,11 +550,13 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         else if (kind == 2 && bi == 0) tin = sX;
         else if (FM || !(kind == 0 && s == 0)) tin = sY + (size_t)(s & 1) * R * nzp;
         const bool final_line = (kind != 0);
-        cp_async_wait<0>();
-        __syncthreads();   // step s operands landed; every thread is done with step s - 1
-        if (s_abort) return;
-        prefetch(s + 1);   // into the staging buffers that step s - 1 used
-        cp_async_commit();
+        if constexpr (MT == 0) {
+            cp_async_wait<0>();
+            __syncthreads();   // step s operands landed; every thread is done with step s - 1
+            if (s_abort) return;
+            prefetch(s + 1);   // into the staging buffers that step s - 1 used
+            cp_async_commit();
+        }
         if (tin2) {
             // middle line: t = C y_{m-1} + C y_{m+1}
             V *tsum = const_cast<V *>(tin);
@@ -552,11 +574,20 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
 #pragma unroll
         for (int u = 0; u < NOPT; ++u) {
             // the tensor path folds b_i into its forward product: v = 0 - G_i (t - b_i)
-            const bool own = MT == 0 || kind == 2;
-            yown[u] = (ov[u] && own) ? (same_line ? vlast[u] : sOwn[(size_t)(s & 1) * R * rpc + oq[u] * rpc + orow[u]])
-                                     : mkc<TG>(TG(0), TG(0));
+            if constexpr (MT > 0) {
+                V yb = ycur;   // from the output's K part 0 (adjacent lanes)
+                yb.x = __shfl_sync(0xffffffffu, yb.x, lane & ~(tpo - 1));
+                yb.y = __shfl_sync(0xffffffffu, yb.y, lane & ~(tpo - 1));
+                yown[u] = (ov[u] && kind == 2) ? (same_line ? vlast[u] : yb) : mkc<TG>(TG(0), TG(0));
+            } else {
+                yown[u] = ov[u] ? (same_line ? vlast[u] : sOwn[(size_t)(s & 1) * R * rpc + oq[u] * rpc + orow[u]])
+                                : mkc<TG>(TG(0), TG(0));
+            }
             acc[u] = mkc<TG>(TG(0), TG(0));
         }
+        // partial sums of this step: alternate buffers, so that a warp that starts step s + 1
+        // early cannot overwrite partials another warp is still summing
+        float2 *redb = red + (size_t)(s & 1) * (FM ? 16 : 8) * MMA_RHS * RP;
         if constexpr (FM) {
             float2 facc[MMA_RHS];
 #pragma unroll
@@ -569,13 +600,14 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             // partial products of this lane's K part -> red[2 * wid + fh][rhs][row]
 #pragma unroll
             for (int q = 0; q < MMA_RHS; ++q)
-                if (q < Rc) red[((size_t)(2 * wid + fh) * MMA_RHS + q) * RP + frow] = facc[q];
+                if (q < Rc) redb[((size_t)(2 * wid + fh) * MMA_RHS + q) * RP + frow] = facc[q];
             __syncthreads();
+            if (s_abort) return;   // a wait gave up (every thread sees the flag after the barrier)
             if (ov[0]) {
                 const int q = oq[0], r = orow[0], wpp = 16 / tpo;
                 float2 sum = make_float2(0.f, 0.f);
                 for (int w = part * wpp; w < (part + 1) * wpp; ++w) {
-                    const float2 v = red[((size_t)w * MMA_RHS + q) * RP + r];
+                    const float2 v = redb[((size_t)w * MMA_RHS + q) * RP + r];
                     sum.x += v.x;
                     sum.y += v.y;
                 }
@@ -640,18 +672,19 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int row = 16 * mt + fg + 8 * (e >> 1), q = 2 * ft + (e & 1);
-                        red[((size_t)wid * MMA_RHS + q) * RP + row] =
+                        redb[((size_t)wid * MMA_RHS + q) * RP + row] =
                             make_float2(accB[mt][0][e] + accS[mt][0][e], accB[mt][1][e] + accS[mt][1][e]);
                     }
             }
             if constexpr (!kPreSplit) load_g(s + 1);   // next line's fragments, in flight during the exchange
             {
                 __syncthreads();
+                if (s_abort) return;   // a wait gave up (every thread sees the flag after the barrier)
                 if (ov[0]) {
                     const int q = oq[0], r = orow[0], wpp = 8 / tpo;
                     float2 sum = make_float2(0.f, 0.f);
                     for (int w = part * wpp; w < (part + 1) * wpp; ++w) {
-                        const float2 v = red[((size_t)w * MMA_RHS + q) * RP + r];
+                        const float2 v = redb[((size_t)w * MMA_RHS + q) * RP + r];
                         sum.x += v.x;
                         sum.y += v.y;
                     }
@@ -885,7 +918,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             if (mfn) {
                 const size_t nzp = (size_t)padded_mma(nz);
                 const size_t sm = (size_t)32 + vsz * 5 * (size_t)Rm * nzp + vsz * 2 * (size_t)Rm * rpc +
-                                  sizeof(float2) * (fm ? 16 : 8) * MMA_RHS * (size_t)(16 * MT + 2);
+                                  2 * sizeof(float2) * (fm ? 16 : 8) * MMA_RHS * (size_t)(16 * MT + 2);
                 if (sm <= SW_SMEM_MAX) {
                     kfn = mfn;
                     mma = true;
