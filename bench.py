@@ -202,6 +202,101 @@ def roofline(name, trace, breakdown, w, peaks, prec):
 
 # ------------------------------------------------------------------------ main
 
+def server_session(args):
+    """Solve-server load (include/helm_server.h): a capacity run (all requests queued at
+    once), then Poisson arrivals at 50 / 80 / 95 % of that capacity.  Requests: grids of the
+    given sizes, 1..128 right-hand sides, 16 fixed frequencies per model in [5, 60], FP64 or
+    mixed (workloads.server_requests).  Latency = submission -> X on the host, from the
+    library.  Prints one JSON line."""
+    import queue
+    import threading
+    import time
+
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2301_10762_gb300 import helm as hm
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (the library has no CPU path)")
+    sizes = [int(x) for x in args.server_sizes.split(",")]
+    cfg = W.config_server(seed=5, sizes=sizes)
+    srv = hm.Server()   # 180 GiB budget, batches of up to 128 right-hand sides, 8 workers
+    ids = {}
+    for si, n in enumerate(sizes):
+        for k, m in enumerate(cfg["m"][si]):
+            ids[(si, k)] = srv.add_model(n, n, 1.0, 1.0, m)
+    gen = torch.Generator().manual_seed(55)
+    bpool = [torch.complex(torch.randn(128, n * n, dtype=torch.float64, generator=gen),
+                           torch.randn(128, n * n, dtype=torch.float64, generator=gen)).pin_memory() for n in sizes]
+    slots = [queue.Queue() for _ in sizes]   # pinned result blocks, reused
+    for si, n in enumerate(sizes):
+        for _ in range(12):
+            slots[si].put(torch.empty(128, n * n, dtype=torch.complex128).pin_memory())
+
+    def run(reqs, arrivals):
+        done, lock, q = [], threading.Lock(), queue.Queue()
+
+        def waiter():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                t, si, X, nrhs = item
+                out = srv.wait(t)
+                slots[si].put(X)
+                out["nrhs"] = nrhs
+                with lock:
+                    done.append(out)
+
+        ws = [threading.Thread(target=waiter) for _ in range(8)]
+        for th in ws:
+            th.start()
+        t0 = time.perf_counter()
+        for (si, k, om, prec, nrhs), ta in zip(reqs, arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            X = slots[si].get()
+            t = srv.submit(ids[(si, k)], om, bpool[si][:nrhs], X[:nrhs], prec=prec, rtol=1e-10)
+            q.put((t, si, X, nrhs))
+        for _ in ws:
+            q.put(None)
+        for th in ws:
+            th.join()
+        wall = time.perf_counter() - t0
+        lat = np.array([d["total_ms"] for d in done])
+        rhs = sum(d["nrhs"] for d in done)
+        return {"requests": len(done), "rhs": rhs, "seconds": round(wall, 3),
+                "rhs_solves_per_s": rhs / wall, "requests_per_s": len(done) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "cache_hit_rate": float(np.mean([d["cache_hit"] for d in done])),
+                "errors": sum(1 for d in done if "error" in d),
+                "max_relres": float(max(d["max_relres"] for d in done))}
+
+    cap_reqs = W.server_requests(cfg, args.server_requests, seed=50)
+    cap = run(cap_reqs, np.zeros(len(cap_reqs)))
+    sessions = []
+    for j, load in enumerate((0.5, 0.8, 0.95)):
+        rate = load * cap["requests_per_s"]
+        count = max(1, int(rate * args.server_seconds))
+        r = run(W.server_requests(cfg, count, seed=51 + j), W.poisson_arrivals(count, rate, seed=61 + j))
+        r.update({"load": load, "rate_rps": rate})
+        sessions.append(r)
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({
+        "metric": "solve server: RHS-solves/s and p50/p99 request latency (arrival -> X on host) under Poisson "
+                  "arrivals",
+        "unit": "RHS-solves/s", "n_gpus": 1, "data": "synthetic (seeded Gaussian-random-field models)",
+        "config": {"workload": "solve_server", "sizes": sizes, "models_per_size": 16, "frequencies_per_model": 16,
+                   "rhs": "log-uniform 1..128", "precision": "FP64 or mixed (1/2 each), mixed refined to 1e-10",
+                   "hbm_budget_GiB": 180, "max_batch_rhs": 128, "workers": 8},
+        "capacity": cap, "sessions": sessions,
+        "server": {k: st[k] for k in ("batches", "factor_builds", "cache_hits", "evictions", "entries",
+                                      "bytes_peak", "refused")}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +309,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--server", action="store_true",
+                    help="solve-server session (Poisson arrivals) instead of the hypergradient step")
+    ap.add_argument("--server-sizes", default="64,128,256")
+    ap.add_argument("--server-seconds", type=float, default=10.0)
+    ap.add_argument("--server-requests", type=int, default=200, help="requests of the capacity run")
     ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-reps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -229,6 +329,10 @@ def main():
 
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        return
+    if args.server:
+        if rank == 0:
+            server_session(args)
         return
 
     import numpy as np

@@ -60,6 +60,28 @@ class helm_trace_event(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("stream", C.c_int32), ("start_ms", C.c_double), ("end_ms", C.c_double)]
 
 
+class helm_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch_rhs", C.c_int32), ("workers", C.c_int32),
+                ("max_iter", C.c_int32)]
+
+
+class helm_request(C.Structure):
+    _fields_ = [("model", C.c_int32), ("omega", C.c_double), ("prec", C.c_int32), ("adjoint", C.c_int32),
+                ("nrhs", C.c_int32), ("B", C.c_void_p), ("X", C.c_void_p), ("rtol", C.c_double)]
+
+
+class helm_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cache_hit", C.c_int32), ("batch_rhs", C.c_int32), ("iters", C.c_int32),
+                ("max_relres", C.c_double), ("queue_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class helm_server_counters(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("refused", C.c_int64),
+                ("rhs_solved", C.c_int64), ("batches", C.c_int64), ("factor_builds", C.c_int64),
+                ("cache_hits", C.c_int64), ("evictions", C.c_int64), ("entries", C.c_int64),
+                ("bytes_used", C.c_uint64), ("bytes_peak", C.c_uint64), ("bytes_budget", C.c_uint64)]
+
+
 class helm_trace_entry(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("timed", C.c_int64)]
 
@@ -70,7 +92,10 @@ EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_d
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
             "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count",
-            "helm_trace_timeline", "helm_trace_kernel_name", "helm_trace_select"]
+            "helm_trace_timeline", "helm_trace_kernel_name", "helm_trace_select",
+            # include/helm_server.h
+            "helm_server_create", "helm_server_add_model", "helm_server_footprint", "helm_server_submit",
+            "helm_server_wait", "helm_server_stats", "helm_server_destroy"]
 
 _lib = None
 
@@ -133,6 +158,20 @@ def load(path: str = LIB_PATH):
     lib.helm_trace_select.argtypes = [C.c_char_p]
     lib.helm_launch_count.restype = C.c_int64
     lib.helm_launch_count.argtypes = []
+    lib.helm_server_create.restype = C.c_int
+    lib.helm_server_create.argtypes = [P(helm_server_opts), P(vp)]
+    lib.helm_server_add_model.restype = C.c_int
+    lib.helm_server_add_model.argtypes = [vp, P(helm_grid), P(dbl), P(i32)]
+    lib.helm_server_footprint.restype = C.c_uint64
+    lib.helm_server_footprint.argtypes = [vp, i32, i32, i32]
+    lib.helm_server_submit.restype = C.c_int
+    lib.helm_server_submit.argtypes = [vp, P(helm_request), P(C.c_int64)]
+    lib.helm_server_wait.restype = C.c_int
+    lib.helm_server_wait.argtypes = [vp, C.c_int64, P(helm_request_info)]
+    lib.helm_server_stats.restype = C.c_int
+    lib.helm_server_stats.argtypes = [vp, P(helm_server_counters)]
+    lib.helm_server_destroy.restype = None
+    lib.helm_server_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -413,3 +452,76 @@ def helm_trace_timeline(max_events=200000):
 
 def helm_launch_count():
     return int(load().helm_launch_count())
+
+
+class Server:
+    """Solve server of include/helm_server.h: factor cache, HBM admission, batching, workers.
+
+    submit() takes host complex128 tensors B [nrhs][N] (pinned memory makes the copies
+    asynchronous) and returns a ticket; the server writes X, and the tensors are kept alive
+    here until wait() returns for the ticket."""
+
+    def __init__(self, hbm_budget_bytes=0, max_batch_rhs=0, workers=0, max_iter=0):
+        lib = load()
+        o = helm_server_opts(int(hbm_budget_bytes), int(max_batch_rhs), int(workers), int(max_iter))
+        h = C.c_void_p()
+        _check(lib.helm_server_create(C.byref(o), C.byref(h)), "helm_server_create")
+        self._lib, self.handle = lib, h
+        self._keep = {}
+        self._grids = {}
+
+    def add_model(self, nx, nz, lx, lz, m) -> int:
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(-1))
+        if m.size != nx * nz:
+            raise ValueError("m must have nx*nz entries")
+        g = helm_grid(nx, nz, lx, lz)
+        mid = C.c_int32()
+        _check(self._lib.helm_server_add_model(self.handle, C.byref(g), m.ctypes.data_as(C.POINTER(C.c_double)),
+                                               C.byref(mid)), "helm_server_add_model")
+        self._grids[mid.value] = (nx, nz)
+        return mid.value
+
+    def footprint(self, model, prec, nrhs) -> int:
+        return int(self._lib.helm_server_footprint(self.handle, model, prec, nrhs))
+
+    def submit(self, model, omega, B: torch.Tensor, X: torch.Tensor | None = None, prec=HELM_MIXED, rtol=1e-10,
+               adjoint=False):
+        grid = self._grids.get(model)   # an unknown id is left to the library (HELM_EINVAL)
+        if B.device.type != "cpu" or B.dtype != torch.complex128 or not B.is_contiguous() or B.dim() != 2 \
+                or (grid is not None and B.shape[1] != grid[0] * grid[1]):
+            raise ValueError("B must be a contiguous host complex128 tensor [nrhs][N]")
+        if X is None:
+            X = torch.empty_like(B, pin_memory=B.is_pinned())
+        req = helm_request(model, float(omega), int(prec), 1 if adjoint else 0, B.shape[0], C.c_void_p(B.data_ptr()),
+                           C.c_void_p(X.data_ptr()), float(rtol))
+        t = C.c_int64()
+        _check(self._lib.helm_server_submit(self.handle, C.byref(req), C.byref(t)), "helm_server_submit")
+        self._keep[t.value] = (B, X)
+        return t.value
+
+    def wait(self, ticket):
+        info = helm_request_info()
+        st = self._lib.helm_server_wait(self.handle, ticket, C.byref(info))
+        B, X = self._keep.pop(ticket, (None, None))
+        out = {k: getattr(info, k) for k, _ in helm_request_info._fields_}
+        out["X"] = X
+        if st != 0:
+            out["error"] = HelmError(st, "helm_server_wait")
+        return out
+
+    def stats(self):
+        c = helm_server_counters()
+        _check(self._lib.helm_server_stats(self.handle, C.byref(c)), "helm_server_stats")
+        return {k: getattr(c, k) for k, _ in helm_server_counters._fields_}
+
+    def close(self):
+        if self.handle:
+            self._lib.helm_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,7 +7,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("helm.h", "helm_trace.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("helm.h", "helm_trace.h", "helm_server.h")]
 LIB = os.path.join(ROOT, "paper_2301_10762_gb300", "libhelm.so")
 
 

@@ -244,6 +244,49 @@ def config_hypergrad(seed=4, n_models=32):
     return models
 
 
+def config_server(seed=5, sizes=(64, 128, 256), n_models=16, n_freq=16):
+    """Solve-server load: per grid size n, n_models velocity models (Gaussian random fields,
+    correlation length 0.1, mapped to c in [1.5, 4.5]) on the unit square, each with n_freq
+    fixed angular frequencies drawn from U[5, 60] (so that requests can hit cached factors).
+    Returns {"sizes", "m": [size][model] -> m, "omegas": [size][model][n_freq]}."""
+    rng = np.random.default_rng(seed)
+    out = {"sizes": list(sizes), "m": [], "omegas": []}
+    for si, n in enumerate(sizes):
+        ms, oms = [], []
+        for k in range(n_models):
+            g = gaussian_random_field(n, n, 0.1, seed * 100000 + si * 1000 + k)
+            c = 1.5 + 3.0 * (g - g.min()) / (g.max() - g.min())
+            ms.append(_flat(1.0 / c ** 2))
+            oms.append(np.sort(rng.uniform(5.0, 60.0, n_freq)))
+        out["m"].append(ms)
+        out["omegas"].append(oms)
+    return out
+
+
+def server_requests(cfg, count, seed, max_rhs=128):
+    """count requests of the solve-server load: grid size uniform over cfg["sizes"] (log-uniform
+    n), model uniform, frequency uniform over the model's fixed values, right-hand sides
+    log-uniform integer in [1, max_rhs], FP64 or mixed with probability 1/2 each.
+    Each request is (size index, model index, omega, prec (0 FP64, 1 mixed), nrhs)."""
+    rng = np.random.default_rng(seed)
+    n_models = len(cfg["m"][0])
+    n_freq = len(cfg["omegas"][0][0])
+    reqs = []
+    for _ in range(count):
+        si = int(rng.integers(len(cfg["sizes"])))
+        k = int(rng.integers(n_models))
+        om = float(cfg["omegas"][si][k][int(rng.integers(n_freq))])
+        nrhs = int(min(max_rhs, max(1, round(float(np.exp(rng.uniform(0.0, np.log(max_rhs))))))))
+        reqs.append((si, k, om, int(rng.integers(2)), nrhs))
+    return reqs
+
+
+def poisson_arrivals(count, rate, seed):
+    """Arrival times (seconds from the start) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, count))
+
+
 def tiny_case(nx=8, nz=7, n_omega=2, n_src=2, n_rec=3, seed=0, lx=1.0, lz=0.9):
     """Small random case for pins and parity: random smooth-ish m in [1/4, 1], on-grid
     sources on the top row, off-grid receivers in the interior."""
