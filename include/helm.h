@@ -119,8 +119,10 @@ void helm_op_destroy(helm_op_t *op);
  * diagonal couplings C_i; the factor stores G_i = S_i^{-1} with
  * S_0 = D_0, S_i = D_i - C_i S_{i-1}^{-1} C_i.  This replaces the sparse direct
  * (backslash) factorisation of the Appendix ("Computing the wavefield").
- * Each S_i is inverted by block Gauss-Jordan with partial pivoting inside 16 x 16
- * diagonal blocks.  Errors: ESINGULAR (zero / non-finite pivot), ENOMEM, ECUDA.
+ * Each S_i is inverted by block Gauss-Jordan over 16-column blocks; a 16 x 16 pivot block
+ * is inverted by Newton-Schulz iteration seeded with the same block's inverse on the
+ * previous line, or by Gauss-Jordan with partial pivoting where that seed is not close
+ * enough.  Errors: ESINGULAR (zero / non-finite pivot), ENOMEM, ECUDA.
  * The factor keeps a reference to op: destroy the factor before the op. */
 helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out);
 void helm_factor_destroy(helm_factor_t *f);
