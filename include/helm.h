@@ -127,6 +127,14 @@ void helm_op_destroy(helm_op_t *op);
 helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out);
 void helm_factor_destroy(helm_factor_t *f);
 
+/* helm_factor_fp64_blocks -- HELM_MIXED: number of 16 x 16 pivot blocks of the factor that
+ * were flagged and inverted in FP64.  A block is flagged when its FP32 Gauss-Jordan inverse X
+ * leaves max |I - M X| above 1e-4 (an ill-conditioned pivot of a line); it is then inverted
+ * again from the same FP32 entries by Gauss-Jordan with partial pivoting in FP64 and rounded
+ * to FP32.  0 for HELM_FP64; -1 for NULL.  (The paper's solver has no counterpart: it factors
+ * in FP64 throughout.) */
+int32_t helm_factor_fp64_blocks(const helm_factor_t *f);
+
 /* helm_solve -- X = A(m, w_q)^{-1} B for every frequency q and column (Eq. (defu)
  * discretised: u = A^{-1} e_s).  B_dev, X_dev: [n_omega][nrhs][N] complex (device);
  * they may not alias.  rtol / max_iter drive the refinement of HELM_MIXED (ignored by

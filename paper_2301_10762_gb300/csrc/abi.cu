@@ -96,7 +96,7 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "allocate(m)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->omega_dev, n_omega * sizeof(double), "allocate(omega)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->diag, (size_t)n_omega * N * sizeof(double2), "allocate(diag)", op->st)) != HELM_OK ||
-        (s = dev_alloc((void **)&op->status, sizeof(int), "allocate(status)", op->st)) != HELM_OK ||
+        (s = dev_alloc((void **)&op->status, 2 * sizeof(int), "allocate(status)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->gk, (size_t)n_omega * N * sizeof(double2), "allocate(g)", op->st)) != HELM_OK ||
         (s = dev_alloc((void **)&op->gpk, (size_t)n_omega * N * sizeof(double2), "allocate(g')", op->st)) != HELM_OK) {
         helm_op_destroy(op);
@@ -106,7 +106,7 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     if ((e = cudaMemcpyAsync(op->m, m_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, op->st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(op->omega_dev, omega, n_omega * sizeof(double), cudaMemcpyHostToDevice, op->st)) !=
             cudaSuccess ||
-        (e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(op->status, 0, 2 * sizeof(int), op->st)) != cudaSuccess ||
         (e = launch_assemble(op->g, op->m, op->omega_dev, n_omega, op->diag, op->st)) != cudaSuccess ||
         (e = launch_gcoef(op->g, op->m, op->omega_dev, n_omega, op->gk, op->gpk, op->st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(op->st)) != cudaSuccess) {
@@ -151,7 +151,7 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
         return s;
     }
     cudaError_t e;
-    if ((e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess) {
+    if ((e = cudaMemsetAsync(op->status, 0, 2 * sizeof(int), op->st)) != cudaSuccess) {
         helm_set_error("helm_factor", e);
         helm_factor_destroy(f);
         return HELM_ECUDA;
@@ -162,15 +162,16 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
     else
         e = launch_line_factor<float>(g, op->n_omega, op->diag, (float2 *)f->G, (float2 *)f->xch, op->status,
                                       f->cs, op->st, &f->mid);
-    int st_host = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
+    int st_host[2] = {0, 0};   // status bits, pivot blocks inverted in FP64
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st_host, op->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    f->fp64_blocks = st_host[1];
     if (e != cudaSuccess) {
         helm_set_error("helm_factor: launch", e);
         helm_factor_destroy(f);
         return HELM_ECUDA;
     }
-    if (st_host & ST_SINGULAR) {
+    if (st_host[0] & ST_SINGULAR) {
         helm_set_msg("helm_factor: zero or non-finite pivot");
         helm_factor_destroy(f);
         return HELM_ESINGULAR;
@@ -190,6 +191,8 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
     *out = f;
     return HELM_OK;
 }
+
+extern "C" int32_t helm_factor_fp64_blocks(const helm_factor_t *f) { return f ? f->fp64_blocks : -1; }
 
 extern "C" void helm_factor_destroy(helm_factor_t *f) {
     if (!f) return;

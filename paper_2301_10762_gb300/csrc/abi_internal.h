@@ -32,6 +32,7 @@ struct helm_factor {
     void *G = nullptr;     // [n_omega][nx][nz][nz] complex (FP64 or FP32)
     void *xch = nullptr;   // factor exchange slots
     float4 *diag2 = nullptr;   // mixed: [n_omega][N] diagonal of A as FP32 pairs
+    int fp64_blocks = 0;       // mixed: pivot blocks inverted in FP64 (flagged)
     // solve scratch, sized for `cap` right-hand sides per frequency
     int cap = 0;
     float4 *bd = nullptr, *xa = nullptr, *xb = nullptr;   // mixed: b and the iterate (ping-pong), FP32 pairs

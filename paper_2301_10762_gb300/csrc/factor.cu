@@ -41,6 +41,8 @@ template <typename T> struct FactorArgs {
     int *status;
     int cs;               // CTAs per team (cluster = teams * cs)
     int mid;              // middle line of the twisted factorisation (nx - 1: one-sided)
+    float flag_tol;       // complex FP32: a Gauss-Jordan pivot inverse with max |I - M X| above
+                          // this is redone in FP64 (status[1] counts those blocks)
 };
 
 // In-place Gauss-Jordan inversion of the kb x kb block M (row stride NB, shared memory)
@@ -309,6 +311,50 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
     return ok;
 }
 
+// Flagged pivot block, one warp: the FP32 kb x kb block M (row stride ld) promoted to FP64
+// (identity outside kb), inverted by warp_invert16<double>, the inverse rounded into P (row
+// stride NB, rows and columns < kb).  d64 is a 2 x 16 x 16 FP64 scratch.  Kept out of line so
+// that the FP64 registers do not weigh on the factor's main loop.
+__device__ __noinline__ bool fp64_pivot_inverse(const float2 *M, int ld, int kb, double2 *d64, float2 *P) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < NB * NB; e += 32) {
+        const int r = e >> 4, c = e & 15;
+        const float2 v = M[(size_t)(r < kb ? r : 0) * ld + (c < kb ? c : 0)];
+        d64[e] = (r < kb && c < kb) ? make_double2((double)v.x, (double)v.y) : make_double2(r == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
+    const bool ok = warp_invert16<double>(d64, NB, kb, d64 + NB * NB);
+    __syncwarp();
+    for (int e = lane; e < NB * NB; e += 32) {
+        const int r = e >> 4, c = e & 15;
+        if (r < kb && c < kb) P[e] = to_c64(d64[NB * NB + e]);
+    }
+    return ok;
+}
+
+// max |I - M X| over the kb x kb block (M shared with row stride ld, X row stride NB), the rest
+// of the 16 x 16 tile taken as the identity; every thread of the 256-thread CTA returns it.
+template <typename T>
+__device__ float block_residual(const cx_t<T> *M, int ld, const cx_t<T> *X, int kb, float *sred) {
+    using V = cx_t<T>;
+    const int tid = threadIdx.x, r = tid >> 4, c = tid & 15, lane = tid & 31, wid = tid >> 5;
+    float a = 0.f;
+    if (r < kb && c < kb) {
+        V e = mkc<T>(r == c ? T(1) : T(0), T(0));
+        for (int u = 0; u < kb; ++u) cfms(e, M[r * ld + u], X[u * NB + c]);
+        a = (float)(e.x * e.x + e.y * e.y);
+        a = isfinite(a) ? a : 3.0e38f;
+    }
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if (lane == 0) sred[wid] = a;
+    __syncthreads();
+    float en2 = 0.f;
+#pragma unroll
+    for (int w = 0; w < FAC_THREADS / 32; ++w) en2 = fmaxf(en2, sred[w]);
+    __syncthreads();   // sred reusable
+    return sqrtf(en2);
+}
+
 // Inverse of the 16 x 16 block M (shared, row stride ld) by Newton-Schulz iteration from the
 // seed X0 (row stride NB), one element per thread of a 256-thread CTA (thread (r, c) =
 // (tid / 16, tid % 16)):  E = I - M X,  X <- X + X E  (quadratic convergence while |E| < 1).
@@ -405,6 +451,8 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     __shared__ __align__(16) V s_nsM[kNS ? NB : 1][NB + 1], s_nsX[kNS ? NB : 1][NB + 1], s_nsE[kNS ? NB : 1][NB + 1];
     __shared__ __align__(16) V s_seed[kNS ? kSeedBlocks : 1][kNS ? NB * NB : 1];
     __shared__ float s_nsred[FAC_THREADS / 32];
+    // flagged pivot blocks: the FP32 entries and the FP64 inverse
+    __shared__ __align__(16) double2 s_d64[kNS ? 2 : 1][kNS ? NB * NB : 1];
 
     V *Gs = a.G + (size_t)sys * nx * nz * nz;
     const double2 *dg = a.diag + (size_t)sys * nx * nz;
@@ -493,6 +541,18 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                             if (!warp_invert16<T>(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP) && tid == 0) s_bad = 1;
                         }
                         __syncthreads();
+                        if constexpr (kNS) {
+                            // a flagged block (ill-conditioned pivot: the FP32 inverse leaves a large
+                            // residual) is inverted again by Gauss-Jordan in FP64 on the same entries
+                            const V *Mk = sW + (size_t)k0 * ldw + kc;
+                            if (block_residual<T>(Mk, ldw, recvP, kb, s_nsred) > a.flag_tol) {
+                                if (tid < 32) {
+                                    if (!fp64_pivot_inverse(Mk, ldw, kb, &s_d64[0][0], recvP) && tid == 0) s_bad = 1;
+                                    if (tid == 0) atomicAdd(a.status + 1, 1);
+                                }
+                                __syncthreads();
+                            }
+                        }
                     }
                     if constexpr (kNS) {
                         if (kb == NB && bpc <= kSeedBlocks) s_seed[k - kb_lo][tid] = recvP[tid];   // next line's seed
@@ -625,7 +685,10 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     }
     const int mid = (teams == 2) ? g.nx / 2 : g.nx - 1;
     if (mid_out) *mid_out = mid;
-    FactorArgs<T> a{g, diag, G, xch, status, cs, mid};
+    // HELM_FACTOR_FLAG_TOL overrides the residual above which a pivot inverse is redone in FP64
+    const char *env_tol = getenv("HELM_FACTOR_FLAG_TOL");
+    const float flag_tol = (env_tol && *env_tol) ? (float)atof(env_tol) : 1e-4f;
+    FactorArgs<T> a{g, diag, G, xch, status, cs, mid, flag_tol};
     const size_t smem = resident ? smem_res : factor_smem_bytes<T>(g.nz, cs);
     auto kern = resident ? line_factor_smem_kernel<T> : line_factor_kernel<T>;
     if (!resident) {

@@ -87,7 +87,7 @@ class helm_trace_entry(C.Structure):
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
-            "helm_factor_destroy", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
+            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
             # include/helm_trace.h
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.helm_op_destroy.argtypes = [vp]
     lib.helm_factor.restype = C.c_int
     lib.helm_factor.argtypes = [vp, C.c_int, P(vp)]
+    lib.helm_factor_fp64_blocks.restype = i32
+    lib.helm_factor_fp64_blocks.argtypes = [vp]
     lib.helm_factor_destroy.restype = None
     lib.helm_factor_destroy.argtypes = [vp]
     for name in ("helm_solve", "helm_adjoint_solve"):
@@ -247,6 +249,11 @@ class Op:
 class Factor:
     def __init__(self, handle, op, prec):
         self.handle, self.op, self.prec = handle, op, prec
+
+    @property
+    def fp64_blocks(self) -> int:
+        """Pivot blocks of a mixed factor that were flagged and inverted in FP64."""
+        return int(load().helm_factor_fp64_blocks(self.handle))
 
     def close(self):
         if self.handle:

@@ -39,7 +39,9 @@ def _err(X, ref):
 
 
 def test_server_results_batching_and_cache():
-    srv = hm.Server(workers=2)
+    # one worker: while it builds the first factor the other requests queue up, so requests
+    # with the same key are batched
+    srv = hm.Server(workers=1)
     ms = [_m(*g[:2], seed=k) for k, g in enumerate(GRIDS)]
     ids = [srv.add_model(*g, m) for g, m in zip(GRIDS, ms)]
     # (model, omega, prec, adjoint, nrhs): four factor keys, two batches of more than one request
@@ -47,12 +49,9 @@ def test_server_results_batching_and_cache():
             (0, 5.0, hm.HELM_MIXED, True, 1), (1, 9.0, hm.HELM_FP64, False, 1), (0, 7.0, hm.HELM_FP64, True, 2),
             (1, 12.0, hm.HELM_MIXED, False, 5), (0, 5.0, hm.HELM_MIXED, False, 1)]
     for wave in range(2):
-        tickets, inputs = [], []
-        for k, (mi, om, prec, adj, nrhs) in enumerate(reqs):
-            N = GRIDS[mi][0] * GRIDS[mi][1]
-            B = _rhs(nrhs, N, seed=100 * wave + k)
-            inputs.append(B)
-            tickets.append(srv.submit(ids[mi], om, B, prec=prec, rtol=1e-12, adjoint=adj))
+        inputs = [_rhs(r[4], GRIDS[r[0]][0] * GRIDS[r[0]][1], seed=100 * wave + k) for k, r in enumerate(reqs)]
+        tickets = [srv.submit(ids[mi], om, B, prec=prec, rtol=1e-12, adjoint=adj)
+                   for (mi, om, prec, adj, nrhs), B in zip(reqs, inputs)]
         for k, t in enumerate(tickets):
             out = srv.wait(t)
             assert "error" not in out, out["error"]
@@ -67,6 +66,27 @@ def test_server_results_batching_and_cache():
         assert st["rhs_solved"] == sum(r[4] for r in reqs) * (wave + 1)
         assert st["factor_builds"] == 4 and st["entries"] == 4 and st["evictions"] == 0
     assert st["batches"] < st["completed"] and st["refused"] == 0
+    srv.close()
+
+
+def test_server_workers_run_concurrently():
+    # eight workers (the default), requests of eight keys at once: all correct
+    srv = hm.Server()
+    grid = GRIDS[1]
+    m = _m(*grid[:2], seed=9)
+    mid = srv.add_model(*grid, m)
+    N = grid[0] * grid[1]
+    oms = [4.0 + k for k in range(8)]
+    inputs = [_rhs(3, N, seed=200 + k) for k in range(8)]
+    tickets = [srv.submit(mid, om, B, prec=hm.HELM_MIXED if k % 2 else hm.HELM_FP64, rtol=1e-12)
+               for k, (om, B) in enumerate(zip(oms, inputs))]
+    for k, t in enumerate(tickets):
+        out = srv.wait(t)
+        assert "error" not in out
+        prec = hm.HELM_MIXED if k % 2 else hm.HELM_FP64
+        assert _err(out["X"].numpy(), _oracle(grid, m, oms[k], inputs[k].numpy(), False)) <= TOL[prec]
+    st = srv.stats()
+    assert st["factor_builds"] == 8 and st["completed"] == 8
     srv.close()
 
 

@@ -88,6 +88,27 @@ def test_sweep_products_match_oracle(monkeypatch, product, nx, nz, nrhs):
     assert colerr(Y.cpu().numpy(), oracle_solve(g, m, om, B, adjoint=True)) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("tol", ["0", None])
+def test_flagged_pivot_blocks_inverted_in_fp64(monkeypatch, tol):
+    # tolerance 0 flags every pivot block that the complex-FP32 factor inverts by Gauss-Jordan
+    # (first line of each team, ragged last block): those are redone in FP64 and the solve still
+    # matches the oracle; the default tolerance flags none on this smooth medium
+    if tol is not None:
+        monkeypatch.setenv("HELM_FACTOR_FLAG_TOL", tol)
+    nx, nz, lx, lz, n_om, nrhs = 40, 37, 1.3, 1.0, 3, 6
+    m, om, B = _setup(nx, nz, lx, lz, n_om, nrhs, seed=4)
+    g = H.Grid(nx, nz, lx, lz)
+    op = hm.helm_assemble(nx, nz, lx, lz, torch.tensor(m, device="cuda"), om)
+    f = hm.helm_factor(op, hm.HELM_MIXED)
+    if tol is not None:
+        assert f.fp64_blocks > 0
+    else:
+        assert f.fp64_blocks == 0
+    X, info = hm.helm_solve(f, torch.tensor(B, device="cuda"), rtol=1e-12, max_iter=10)
+    assert colerr(X.cpu().numpy(), oracle_solve(g, m, om, B)) <= TOL_MIXED
+    assert hm.helm_factor(op, hm.HELM_FP64).fp64_blocks == 0
+
+
 def test_plain_forward_config_64():
     """The plain forward workload: 64 x 64, omega = 10, Gaussian inclusion, 8 top-row
     sources; both precisions against the oracle."""
