@@ -444,6 +444,10 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
     __shared__ int s_bad;
     __shared__ __align__(8) uint64_t bars[2];                 // panel arrival, one per receive buffer
+    // buffer release: the other CTAs of the team arrive on the empty barrier of the CTA that
+    // next writes into a receive buffer (the owner of the step two later) once they are done
+    // with it; that owner waits before it stages and sends the panel
+    __shared__ __align__(8) uint64_t empty_bars[2];
     // Newton-Schulz pivot inversion (complex FP32): work blocks and the previous line's inverse of
     // each pivot block this CTA owns (the seed)
     constexpr bool kNS = sizeof(T) == 4;
@@ -463,11 +467,17 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
         s_bad = 0;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        mbar_init(&empty_bars[0], (uint32_t)max(cs - 1, 1));
+        mbar_init(&empty_bars[1], (uint32_t)max(cs - 1, 1));
         fence_mbar_init_cluster();
     }
     __syncthreads();
     const uint32_t panel_bytes = (uint32_t)(recv_elems * sizeof(V));
     uint32_t ph0 = 0, ph1 = 0;   // completed panel phases per receive buffer (consumer side)
+    uint32_t eph0 = 0, eph1 = 0;   // completed release phases of this CTA's empty barriers (thread 0)
+    bool tmo = false;              // thread 0: a wait gave up; later waits are skipped
+    // whether this team works on a line at the given slot
+    auto active_slot = [&](int sl) { return team == 0 ? sl <= m : sl < lenR; };
     int t = 0;
 
     for (int slot = 0; slot <= m; ++slot) {
@@ -519,10 +529,21 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
             const int buf = t & 1;
             V *recvU = sRecv + (size_t)buf * recv_elems;        // nz x NB: old column panel W_:k
             V *recvP = recvU + (size_t)nz * NB;                 // NB x NB: inverse of W_kk
-            // every CTA of the cluster is done with step t - 1 (and so with this buffer's last use)
-            cluster_sync_all();
             if (active) {
                 if (rank == owner) {
+                    // the other CTAs of the team are done with this buffer (its use two steps ago,
+                    // including a bulk copy this CTA sent from it)
+                    if (t >= 2 && cs > 1) {
+                        if (tid == 0) {
+                            const uint32_t par = buf ? eph1 : eph0;
+                            if (!tmo && !mbar_wait_bounded(&empty_bars[buf], par, 1u << 22)) {
+                                atomicOr(a.status, ST_TIMEOUT);
+                                tmo = true;
+                            }
+                            if (buf) eph1 ^= 1u; else eph0 ^= 1u;
+                        }
+                        __syncthreads();
+                    }
                     const int kc = k0 - c0;
                     // stage the old column panel and the block inverse contiguously, then let the
                     // bulk-copy engine deliver them to the other CTAs of the team
@@ -570,7 +591,10 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                     if (tid == 0) {
                         mbar_arrive_expect_tx(&bars[buf], panel_bytes);
                         const uint32_t par = buf ? ph1 : ph0;
-                        if (!mbar_wait_bounded(&bars[buf], par, 1u << 22)) atomicOr(a.status, ST_TIMEOUT);
+                        if (!tmo && !mbar_wait_bounded(&bars[buf], par, 1u << 22)) {
+                            atomicOr(a.status, ST_TIMEOUT);
+                            tmo = true;
+                        }
                     }
                     if (buf) ph1 ^= 1u; else ph0 ^= 1u;
                     __syncthreads();
@@ -625,6 +649,12 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                 }
             }
             __syncthreads();
+            // done with this step's buffer: release it to the owner of step t + 2, its next writer
+            if (active && tid == 0 && cs > 1) {
+                const int t2 = t + 2, owner2 = (t2 % p) / bpc;
+                if (active_slot(t2 / p) && owner2 != rank)
+                    mbar_arrive_remote(mapa_u32(smem_u32(&empty_bars[buf]), (uint32_t)(team * cs + owner2)));
+            }
         }
         if (active) {
             // G_i (own columns) to the factor storage
