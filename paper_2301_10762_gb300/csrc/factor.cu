@@ -398,6 +398,9 @@ __device__ bool ns_invert16(const cx_t<T> *M, int ld, const cx_t<T> *X0, cx_t<T>
         __syncthreads();   // every read of the old X and of sred done
         sX[r][c] = x;
         __syncthreads();
+        // quadratic convergence: the new X leaves about |E|^2, below the FP32 floor when
+        // |E| < 3e-4, so it is final without another residual
+        if (en < 3e-4f) { ok = true; break; }
     }
     if (ok) P[r * NB + c] = sX[r][c];
     __syncthreads();
@@ -472,7 +475,9 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
         fence_mbar_init_cluster();
     }
     __syncthreads();
-    const uint32_t panel_bytes = (uint32_t)(recv_elems * sizeof(V));
+    const uint32_t panel_bytes = (uint32_t)(recv_elems * sizeof(V));     // what a consumer receives per step
+    const uint32_t panel_u_bytes = (uint32_t)((size_t)nz * NB * sizeof(V));   // old column panel
+    const uint32_t panel_p_bytes = panel_bytes - panel_u_bytes;               // block inverse
     uint32_t ph0 = 0, ph1 = 0;   // completed panel phases per receive buffer (consumer side)
     uint32_t eph0 = 0, eph1 = 0;   // completed release phases of this CTA's empty barriers (thread 0)
     bool tmo = false;              // thread 0: a wait gave up; later waits are skipped
@@ -545,10 +550,21 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                         __syncthreads();
                     }
                     const int kc = k0 - c0;
-                    // stage the old column panel and the block inverse contiguously, then let the
-                    // bulk-copy engine deliver them to the other CTAs of the team
+                    // stage the old column panel and send it to the other CTAs of the team at once
+                    // (the bulk-copy engine delivers it while the pivot block is inverted); the
+                    // block inverse, staged right after it, follows on the same barrier
                     for (int r = rw; r < nz; r += FAC_THREADS / NB)
                         if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
+                    __syncthreads();
+                    if (tid == 0) {
+                        fence_proxy_async_smem();
+                        const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
+                        for (int d = 0; d < cs; ++d)
+                            if (d != rank) {
+                                const uint32_t dst = (uint32_t)(team * cs + d);
+                                bulk_copy_s2s(mapa_u32(src, dst), src, panel_u_bytes, mapa_u32(lbar, dst));
+                            }
+                    }
                     bool done = false;
                     if constexpr (kNS) {
                         // seeded by this block's inverse on the team's previous line
@@ -580,11 +596,11 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                     }
                     if (tid == 0) {
                         fence_proxy_async_smem();
-                        const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
+                        const uint32_t src = smem_u32(recvP), lbar = smem_u32(&bars[buf]);
                         for (int d = 0; d < cs; ++d)
                             if (d != rank) {
                                 const uint32_t dst = (uint32_t)(team * cs + d);
-                                bulk_copy_s2s(mapa_u32(src, dst), src, panel_bytes, mapa_u32(lbar, dst));
+                                bulk_copy_s2s(mapa_u32(src, dst), src, panel_p_bytes, mapa_u32(lbar, dst));
                             }
                     }
                 } else {
