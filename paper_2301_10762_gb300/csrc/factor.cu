@@ -639,28 +639,59 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
 #pragma unroll
                     for (int u = 0; u < NB; ++u)
                         coef[u] = (u < kb) ? (inblk ? recvP[u * NB + (c - k0)] : sR[u * ldr + cc]) : mkc<T>(T(0), T(0));
-                    for (int r = rw; r < nz; r += FAC_THREADS / NB) {
-                        V *w = sW + (size_t)r * ldw + cc;
-                        if (r >= k0 && r < k0 + kb) {
-                            *w = inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc];
-                            continue;
-                        }
-                        V acc = inblk ? mkc<T>(T(0), T(0)) : *w;
-                        const V *ur = recvU + (size_t)r * NB;
-                        if constexpr (sizeof(T) == 4) {
-                            const float4 *u4 = reinterpret_cast<const float4 *>(ur);
+                    const int rstep = FAC_THREADS / NB;
+                    if constexpr (sizeof(T) == 4) {
+                        // two rows per pass; the 16 products of a row go into four partial sums
+                        // that are combined pairwise and then subtracted from the old value once
+                        // (the summation error of the update is what limits the factor's accuracy,
+                        // and so the refinement sweeps a solve needs)
+                        for (int r = rw; r < nz; r += 2 * rstep) {
+                            const int r2 = r + rstep;
+                            const bool has2 = r2 < nz;
+                            const bool blk1 = r >= k0 && r < k0 + kb, blk2 = has2 && r2 >= k0 && r2 < k0 + kb;
+                            V *w1 = sW + (size_t)r * ldw + cc, *w2 = sW + (size_t)(has2 ? r2 : r) * ldw + cc;
+                            const V zero = mkc<T>(T(0), T(0));
+                            V p1[4] = {zero, zero, zero, zero}, p2[4] = {zero, zero, zero, zero};
+                            const float4 *u1 = reinterpret_cast<const float4 *>(recvU + (size_t)r * NB);
+                            const float4 *u2 = reinterpret_cast<const float4 *>(recvU + (size_t)(has2 ? r2 : r) * NB);
 #pragma unroll
                             for (int h = 0; h < NB / 2; ++h) {
-                                const float4 q = u4[h];
-                                if (2 * h < kb) cfms(acc, make_float2(q.x, q.y), coef[2 * h]);
-                                if (2 * h + 1 < kb) cfms(acc, make_float2(q.z, q.w), coef[2 * h + 1]);
+                                const float4 q1 = u1[h], q2 = u2[h];
+                                const int e = (2 * h) & 3, o = (2 * h + 1) & 3;
+                                if (2 * h < kb) {
+                                    cfma(p1[e], make_float2(q1.x, q1.y), coef[2 * h]);
+                                    cfma(p2[e], make_float2(q2.x, q2.y), coef[2 * h]);
+                                }
+                                if (2 * h + 1 < kb) {
+                                    cfma(p1[o], make_float2(q1.z, q1.w), coef[2 * h + 1]);
+                                    cfma(p2[o], make_float2(q2.z, q2.w), coef[2 * h + 1]);
+                                }
                             }
-                        } else {
+                            const V w1o = (inblk || blk1) ? zero : *w1, w2o = (!has2 || inblk || blk2) ? zero : *w2;
+                            const V s1 = mkc<T>((p1[0].x + p1[1].x) + (p1[2].x + p1[3].x),
+                                                (p1[0].y + p1[1].y) + (p1[2].y + p1[3].y));
+                            const V s2 = mkc<T>((p2[0].x + p2[1].x) + (p2[2].x + p2[3].x),
+                                                (p2[0].y + p2[1].y) + (p2[2].y + p2[3].y));
+                            *w1 = blk1 ? (inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc])
+                                       : mkc<T>(w1o.x - s1.x, w1o.y - s1.y);
+                            if (has2)
+                                *w2 = blk2 ? (inblk ? recvP[(r2 - k0) * NB + (c - k0)] : sR[(r2 - k0) * ldr + cc])
+                                           : mkc<T>(w2o.x - s2.x, w2o.y - s2.y);
+                        }
+                    } else {
+                        for (int r = rw; r < nz; r += rstep) {
+                            V *w = sW + (size_t)r * ldw + cc;
+                            if (r >= k0 && r < k0 + kb) {
+                                *w = inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc];
+                                continue;
+                            }
+                            V acc = inblk ? mkc<T>(T(0), T(0)) : *w;
+                            const V *ur = recvU + (size_t)r * NB;
 #pragma unroll
                             for (int u = 0; u < NB; ++u)
                                 if (u < kb) cfms(acc, ur[u], coef[u]);
+                            *w = acc;
                         }
-                        *w = acc;
                     }
                 }
             }
