@@ -332,6 +332,48 @@ __device__ __noinline__ bool fp64_pivot_inverse(const float2 *M, int ld, int kb,
     return ok;
 }
 
+// Accurate residual correction of a complex-FP32 16 x 16 inverse, 256 threads (thread (r, c)):
+// E = I - M X with every product exact (the FMA gives its rounding error) and the sums kept as
+// FP32 pairs (Knuth's two-sum), then X <- X + X E in FP32.  E is about the inverse's rounding
+// error, so one step brings X to the inverse of M rounded to FP32, whatever route (Newton-Schulz,
+// Gauss-Jordan) produced it.  M shared with row stride ld, P (in and out) row stride NB; the
+// kb x kb block is extended by the identity.
+// hi + lo += a b exactly up to the final rounding of lo (intrinsics: no contraction into FMAs)
+__device__ __forceinline__ void pair_add_prod(float &hi, float &lo, float a, float b) {
+    const float p = __fmul_rn(a, b), pe = fmaf(a, b, -p);
+    const float s = __fadd_rn(hi, p), bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    hi = s;
+}
+__device__ void polish_inverse16(const float2 *M, int ld, int kb, float2 *P, float2 (*sM)[NB + 1],
+                                 float2 (*sX)[NB + 1], float2 (*sE)[NB + 1]) {
+    const int tid = threadIdx.x, r = tid >> 4, c = tid & 15;
+    const bool in = r < kb && c < kb;
+    sM[r][c] = in ? M[r * ld + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+    sX[r][c] = in ? P[r * NB + c] : make_float2(r == c ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    float erh = r == c ? 1.f : 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const float2 a = sM[r][u], b = sX[u][c];
+        pair_add_prod(erh, erl, -a.x, b.x);   // Re(I - M X): - Re M Re X + Im M Im X
+        pair_add_prod(erh, erl, a.y, b.y);
+        pair_add_prod(eih, eil, -a.x, b.y);   // Im: - Re M Im X - Im M Re X
+        pair_add_prod(eih, eil, -a.y, b.x);
+    }
+    sE[r][c] = make_float2(erh + erl, eih + eil);
+    __syncthreads();
+    float2 xe[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int u = 0; u < NB; ++u) cfma(xe[u & 3], sX[r][u], sE[u][c]);
+    const float2 x0 = sX[r][c];
+    const float2 x = make_float2(x0.x + ((xe[0].x + xe[1].x) + (xe[2].x + xe[3].x)),
+                                 x0.y + ((xe[0].y + xe[1].y) + (xe[2].y + xe[3].y)));
+    if (in) P[r * NB + c] = x;
+    __syncthreads();
+}
+
 // max |I - M X| over the kb x kb block (M shared with row stride ld, X row stride NB), the rest
 // of the 16 x 16 tile taken as the identity; every thread of the 256-thread CTA returns it.
 template <typename T>
@@ -592,6 +634,9 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                         }
                     }
                     if constexpr (kNS) {
+                        // FP32 inverse to the FP32 rounding of the exact one: the pivot inverses set
+                        // the factor's accuracy, and so the refinement sweeps of every solve
+                        polish_inverse16(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP, s_nsM, s_nsX, s_nsE);
                         if (kb == NB && bpc <= kSeedBlocks) s_seed[k - kb_lo][tid] = recvP[tid];   // next line's seed
                     }
                     if (tid == 0) {
