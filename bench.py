@@ -43,7 +43,7 @@ FP64_ALU_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch from an ncu capture of the same kernel build, on this
 # workload (profiles/line_sweep_fp32_hypergrad_step_128.md); absent: not captured for the
 # current kernel.
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float] = {"line_sweep_fp32": 56.73e6 + 0.60e6}
+NCU_TRAFFIC_PER_LAUNCH: dict[str, float] = {"line_sweep_fp32": 56.67e6 + 0.75e6}
 
 
 def workload(rank=0, n=N_GRID):
