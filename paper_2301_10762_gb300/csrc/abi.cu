@@ -262,7 +262,7 @@ helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, 
 // correction solves.  The iterate and the residual are FP32 pairs (refine.cu) down to
 // kPairFloor or until the pair residual stops falling; a tighter rtol continues with FP64
 // residuals on the FP64 iterate.
-// The stopping test of the pair phase runs on the device (refine_check after every update), so
+// The stopping test of the pair phase runs on the device (the last block of every update), so
 // the host enqueues several sweeps at a time and reads the state once per batch; sweeps and
 // updates enqueued after the test has stopped the loop return at once.  The first batch is as
 // long as the previous solve with this factor took.
@@ -294,8 +294,8 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
             const float4 *x_in = enq == 0 ? nullptr : ((enq & 1) ? w.xa : w.xb);
             float4 *x_out = (enq & 1) ? w.xb : w.xa;
             if ((e = sweep(skip)) != cudaSuccess) { helm_set_error("sweep mixed", e); return HELM_ECUDA; }
-            e = launch_refine_update(g, n_sys, nrhs, f->diag2, w.bd, x_in, w.y, x_out, w.r32, w.norms, op->st, skip);
-            if (e == cudaSuccess) e = launch_refine_check(cols, w.norms, rtol, kPairFloor, max_iter, w.state, op->st);
+            e = launch_refine_update(g, n_sys, nrhs, f->diag2, w.bd, x_in, w.y, x_out, w.r32, w.norms, op->st, w.state,
+                                     RefineStop{rtol, kPairFloor, max_iter});
             if (e != cudaSuccess) { helm_set_error("refinement update", e); return HELM_ECUDA; }
         }
         e = cudaMemcpyAsync(&hs, w.state, sizeof(RefineState), cudaMemcpyDeviceToHost, op->st);

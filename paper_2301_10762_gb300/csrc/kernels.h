@@ -54,22 +54,28 @@ cudaError_t launch_split_diag(size_t n, const double2 *diag, float4 *diag2, cuda
 // bd = pair form of conj?(B), r32 = its leading part; norms[col][1] = ||B||^2, norms[col][0] = 0
 cudaError_t launch_refine_start(const GridGeom &g, int cols, const double2 *B, int conj, float4 *bd, float2 *r32,
                                 double *norms, cudaStream_t st);
+// Device-side control of the refinement loop: after each update pass, the stopping test computes
+// rel = max_col ||r|| / ||b|| from the norms, decides whether the pair iteration is done and
+// zeroes norms[col][0] for the next pass.
+struct RefineState {
+    int done;        // 1: converged (rel <= rtol), 2: stopped (floor, stagnation, max_iter, not finite)
+    int iters;       // correction sweeps applied
+    double rel;      // latest max relative residual
+    double prev;     // the one before
+    unsigned blocks; // update blocks finished in the current pass (the last one runs the test)
+};
+struct RefineStop {  // stopping rule of the pair phase, applied on the device
+    double rtol, floor_rel;
+    int max_iter;
+};
 // x_out = x_in (none: 0) + delta; r32 = leading part of bd - A x_out; norms[col][0] += ||r||^2
-// (zero on entry: refine_start and refine_check leave it so).  skip (optional, device): nonzero when the launch runs makes it do nothing.
+// (zero on entry: refine_start and the stopping test leave it so).  With state, the last block to
+// finish applies the stopping test, and state->done makes later launches do
+// nothing.
 cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const float4 *diag2, const float4 *bd,
                                  const float4 *x_in, const float2 *delta, float4 *x_out, float2 *r32, double *norms,
-                                 cudaStream_t st, const int *skip = nullptr);
-// Device-side control of the refinement loop: after each update, one block computes
-// rel = max_col ||r|| / ||b|| from norms, decides whether the pair iteration is done and
-// zeroes norms[col][0] for the next update.
-struct RefineState {
-    int done;      // 1: converged (rel <= rtol), 2: stopped (floor, stagnation, max_iter, not finite)
-    int iters;     // correction sweeps applied
-    double rel;    // latest max relative residual
-    double prev;   // the one before
-};
-cudaError_t launch_refine_check(int cols, double *norms, double rtol, double floor_rel, int max_iter,
-                                RefineState *state, cudaStream_t st);
+                                 cudaStream_t st, RefineState *state = nullptr, RefineStop stop = {});
+
 // X = conj?(hi + lo) in FP64 of the newest iterate: xa after an odd number of sweeps, else xb
 cudaError_t launch_refine_finish(size_t n, const float4 *xa, const float4 *xb, const RefineState *state, int conj,
                                  double2 *X, cudaStream_t st);

@@ -154,15 +154,49 @@ __device__ __forceinline__ cff iterate_at(const float4 *x, const float2 *d, size
     return {ff_add1(xv.re, dv.x), ff_add1(xv.im, dv.y)};
 }
 
+// Stopping test of the pair phase, one block: rel = max over columns of sqrt(rr / bb) (bb = 0: 0 if
+// rr = 0 else inf); record it and decide; rr = 0 again for the next update.  The norms were
+// accumulated by atomics of other blocks, so they are read from L2.
+__device__ void refine_stop_test(int cols, double *norms, RefineStop stop, RefineState *st, double *sh) {
+    double mx = 0.0;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        const double rr = __ldcg(norms + 2 * (size_t)c), bb = __ldcg(norms + 2 * (size_t)c + 1);
+        const double rel = bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0);
+        if (!(rel <= mx)) mx = rel;   // propagates NaN
+        norms[2 * (size_t)c] = 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, mx, o);
+        if (!(v <= mx)) mx = v;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rel = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
+            if (!(sh[w] <= rel)) rel = sh[w];
+        const int it = st->iters + 1;
+        const double prev = it > 1 ? st->rel : INFINITY;
+        st->iters = it;
+        st->prev = prev;
+        st->rel = rel;
+        if (rel <= stop.rtol) st->done = 1;
+        else if (!(rel < INFINITY) || it >= stop.max_iter || rel <= stop.floor_rel || rel > 0.25 * prev) st->done = 2;
+    }
+}
+
 // grid: (node blocks, columns); norms[col][0] pre-zeroed, norms[col][1] = ||b||^2
 __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, int nrhs, int cols, const float4 *diag2,
                                                                    const float4 *bd, const float4 *x_in,
                                                                    const float2 *delta, float4 *x_out, float2 *r32,
                                                                    double *norms, StencilPairs cp,
-                                                                   const int *skip) {
+                                                                   RefineState *state, RefineStop stop) {
     __shared__ float shf[RF_THREADS / 32];
     __shared__ float s_scale;
-    if (skip && *skip) return;
+    __shared__ int s_last;
+    __shared__ double shd[32];
+    if (state && state->done) return;   // the refinement has stopped: later passes do nothing
     const int nx = g.nx, nz = g.nz, N = nx * nz;
     for (int c = blockIdx.y; c < cols; c += gridDim.y) {
         const int sys = c / nrhs;
@@ -198,6 +232,18 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
         if (threadIdx.x == 0) atomicAdd(norms + 2 * (size_t)c, (double)rr * bb);
         __syncthreads();   // shf and s_scale reused by the next column
     }
+    if (state) {   // the last block to finish applies the stopping test
+        if (threadIdx.x == 0) {
+            __threadfence();   // this block's norm contributions before its count
+            s_last = atomicAdd(&state->blocks, 1u) == gridDim.x * gridDim.y - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            refine_stop_test(cols, norms, stop, state, shd);
+            if (threadIdx.x == 0) state->blocks = 0;
+        }
+    }
 }
 
 __global__ void refine_accumulate_kernel(size_t n, const float2 *d, int conj, double2 *X) {
@@ -207,40 +253,6 @@ __global__ void refine_accumulate_kernel(size_t n, const float2 *d, int conj, do
         x.x += (double)v.x;
         x.y += conj ? -(double)v.y : (double)v.y;
         X[e] = x;
-    }
-}
-
-// one block: rel = max over columns of sqrt(rr / bb) (bb = 0: 0 if rr = 0 else inf); decide;
-// rr = 0 again for the next update
-__global__ void refine_check_kernel(int cols, double *norms, double rtol, double floor_rel, int max_iter,
-                                    RefineState *st) {
-    __shared__ double sh[32];
-    if (st->done) return;
-    double mx = 0.0;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        const double rr = norms[2 * (size_t)c], bb = norms[2 * (size_t)c + 1];
-        const double rel = bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0);
-        if (!(rel <= mx)) mx = rel;   // propagates NaN
-        norms[2 * (size_t)c] = 0.0;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, mx, o);
-        if (!(v <= mx)) mx = v;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double rel = 0.0;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
-            if (!(sh[w] <= rel)) rel = sh[w];
-        const int it = st->iters + 1;
-        const double prev = it > 1 ? st->rel : INFINITY;
-        st->iters = it;
-        st->prev = prev;
-        st->rel = rel;
-        if (rel <= rtol) st->done = 1;
-        else if (!(rel < INFINITY) || it >= max_iter || rel <= floor_rel || rel > 0.25 * prev) st->done = 2;
     }
 }
 
@@ -281,18 +293,12 @@ cudaError_t launch_refine_start(const GridGeom &g, int cols, const double2 *B, i
 
 cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const float4 *diag2, const float4 *bd,
                                  const float4 *x_in, const float2 *delta, float4 *x_out, float2 *r32, double *norms,
-                                 cudaStream_t st, const int *skip) {
+                                 cudaStream_t st, RefineState *state, RefineStop stop) {
     const int N = g.nx * g.nz, cols = n_sys * nrhs;
     StencilPairs cp{pair_of(coup_x(g, 1)), pair_of(coup_x(g, 0)), pair_of(coup_z(g, 1)), pair_of(coup_z(g, 0))};
     dim3 grid((N + RF_THREADS - 1) / RF_THREADS, std::min(cols, 65535));
     HELM_TRACED(K_REFUPDATE, st, (refine_update_kernel<<<grid, RF_THREADS, 0, st>>>(g, nrhs, cols, diag2, bd, x_in, delta,
-                                                                                    x_out, r32, norms, cp, skip)));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refine_check(int cols, double *norms, double rtol, double floor_rel, int max_iter,
-                                RefineState *state, cudaStream_t st) {
-    HELM_TRACED(K_REFCHECK, st, (refine_check_kernel<<<1, 256, 0, st>>>(cols, norms, rtol, floor_rel, max_iter, state)));
+                                                                                    x_out, r32, norms, cp, state, stop)));
     return cudaGetLastError();
 }
 

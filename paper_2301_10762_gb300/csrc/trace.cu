@@ -13,7 +13,7 @@ static const char *kNames[K_COUNT] = {
     "line_sweep_fp64", "line_sweep_fp32", "residual_fp64", "misfit", "scatter_adjoint_rhs", "grad_accumulate",
     "g_u_p_rhs", "z_rhs_base", "hess_accumulate", "hyper_terms", "dot_partial", "sum_partials", "axpby",
     "fill", "sub", "regR", "dct_matrix", "p2_scale", "dgemm_dct", "line_gb_prepass", "split_diag", "refine_start", "refine_update",
-    "refine_finish", "refine_accumulate", "field_grad", "g_coefficients", "hess_finish", "refine_check",
+    "refine_finish", "refine_accumulate", "field_grad", "g_coefficients", "hess_finish",
 };
 
 namespace {
