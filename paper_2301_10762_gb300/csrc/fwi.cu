@@ -297,6 +297,24 @@ __global__ void axpby_kernel(int n, double a, const double *x, double b, double 
     if (k < n) y[k] = a * x[k] + b * y[k];
 }
 
+// PCG step with the scalars on the device: a = rz / pHp (0 if pHp = 0), x += a p, r -= a Hp
+__global__ void cg_step_kernel(int n, const double *rz, const double *php, const double *p, const double *hp,
+                               double *x, double *r) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double den = *php, a = den != 0.0 ? *rz / den : 0.0;
+    x[k] = a * p[k] + 1.0 * x[k];
+    r[k] = -a * hp[k] + 1.0 * r[k];
+}
+
+// PCG direction with the scalars on the device: p = z + (rz_new / rz) p (beta 0 if rz = 0)
+__global__ void cg_dir_kernel(int n, const double *z, const double *rz_new, const double *rz, double *p) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double den = *rz, beta = den != 0.0 ? *rz_new / den : 0.0;
+    p[k] = 1.0 * z[k] + beta * p[k];
+}
+
 __global__ void fill_kernel(int n, double v, double *y) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) y[k] = v;
@@ -810,8 +828,28 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     const double r0 = sqrt(dot.host[1]);
     double rn = r0;
     const int iters = po->fixed_iters > 0 ? po->fixed_iters : po->max_iter;
-    for (int it = 0; it < iters; ++it) {
-        if (r0 == 0.0 || (po->fixed_iters <= 0 && rn <= po->rtol * r0)) break;
+    if (po->fixed_iters > 0 && r0 != 0.0) {
+        // a fixed iteration count needs no stopping test: the scalars stay on the device (r.z in
+        // res[0] / res[1] by iteration parity, p.Hp in res[2]) and the host does not wait on the
+        // GPU inside the loop; ||r|| is read once at the end
+        for (int it = 0; it < iters; ++it) {
+            double *rz_cur = dot.res + (it & 1), *rz_next = dot.res + ((it + 1) & 1);
+            HS(hess(p, Hp));
+            ++nmv;
+            HS(dot.dot(N, p, Hp, 2, st));
+            HELM_TRACED(K_AXPBY, st, (cg_step_kernel<<<nblk(N), 256, 0, st>>>(N, rz_cur, dot.res + 2, p, Hp, x, r)));
+            HL();
+            HS(p2.apply(r, zz, st));
+            HS(dot.dot(N, r, zz, (it + 1) & 1, st));
+            HELM_TRACED(K_AXPBY, st, (cg_dir_kernel<<<nblk(N), 256, 0, st>>>(N, zz, rz_next, rz_cur, p)));
+            HL();
+        }
+        HS(dot.dot(N, r, r, 3, st));
+        HS(dot.fetch(4, st));
+        rn = sqrt(dot.host[3]);
+    }
+    for (int it = 0; po->fixed_iters <= 0 && it < iters; ++it) {
+        if (r0 == 0.0 || rn <= po->rtol * r0) break;
         HS(hess(p, Hp));
         ++nmv;
         HS(dot.dot(N, p, Hp, 0, st));
