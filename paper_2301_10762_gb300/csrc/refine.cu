@@ -193,7 +193,6 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
                                                                    double *norms, StencilPairs cp,
                                                                    RefineState *state, RefineStop stop) {
     __shared__ float shf[RF_THREADS / 32];
-    __shared__ float s_scale;
     __shared__ int s_last;
     __shared__ double shd[32];
     if (state && state->done) return;   // the refinement has stopped: later passes do nothing
@@ -201,9 +200,12 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
     for (int c = blockIdx.y; c < cols; c += gridDim.y) {
         const int sys = c / nrhs;
         const double bb = norms[2 * (size_t)c + 1];
-        if (threadIdx.x == 0) s_scale = bb > 0.0 ? (float)(1.0 / sqrt(bb)) : 1.f;   // ||r|| / ||b|| in range
-        __syncthreads();
-        const float scale = s_scale;
+        // power-of-two scale 2^-ks, ks about half the binary exponent of ||b||^2: keeps the FP32
+        // squares of r 2^-ks in range; the sum is scaled back exactly by 2^(2 ks) (no FP64
+        // arithmetic in the block's way)
+        const int eb = (int)(((unsigned long long)__double_as_longlong(bb) >> 52) & 0x7FF);
+        const int ks = bb > 0.0 ? max(-62, min(62, (eb - 1023) / 2)) : 0;
+        const float scale = __uint_as_float((unsigned)(127 - ks) << 23);
         const int k = blockIdx.x * RF_THREADS + threadIdx.x;
         float rr = 0.f;
         if (k < N) {
@@ -229,8 +231,8 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
             rr = sr * sr + si * si;
         }
         rr = block_sum(rr, shf);
-        if (threadIdx.x == 0) atomicAdd(norms + 2 * (size_t)c, (double)rr * bb);
-        __syncthreads();   // shf and s_scale reused by the next column
+        if (threadIdx.x == 0) atomicAdd(norms + 2 * (size_t)c, ldexp((double)rr, 2 * ks));
+        __syncthreads();   // shf reused by the next column
     }
     if (state) {   // the last block to finish applies the stopping test
         if (threadIdx.x == 0) {
