@@ -358,20 +358,23 @@ __global__ void p2_scale_kernel(int nx, int nz, const double *lx, const double *
 }
 
 // C[i][j] = sum_k A(i, k) B(k, j), A(i,k) = A[i*as0 + k*as1], B(k,j) = B[k*bs0 + j*bs1],
-// C row-major M x N.  16 x 16 tiles in shared memory, FP64.
+// C row-major M x N.  DT x DT tiles in shared memory, FP64, k summed in ascending order.  The
+// small tiles give a 128 x 128 product 256 blocks, enough to occupy the FP64 units of every SM
+// (GB300's FP64 rate per SM is low).
+constexpr int DT = 8;
 __global__ void dgemm_strided_kernel(int M, int Nn, int K, const double *A, int as0, int as1, const double *B,
                                      int bs0, int bs1, double *Cout) {
-    __shared__ double sA[16][17], sB[16][17];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+    __shared__ double sA[DT][DT + 1], sB[DT][DT + 1];
+    const int tx = threadIdx.x % DT, ty = threadIdx.x / DT;
+    const int i = blockIdx.y * DT + ty, j = blockIdx.x * DT + tx;
     double acc = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = 0; k0 < K; k0 += DT) {
         const int ka = k0 + tx, kb = k0 + ty;
         sA[ty][tx] = (i < M && ka < K) ? A[(size_t)i * as0 + (size_t)ka * as1] : 0.0;
         sB[ty][tx] = (kb < K && j < Nn) ? B[(size_t)kb * bs0 + (size_t)j * bs1] : 0.0;
         __syncthreads();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) acc = fma(sA[ty][t], sB[t][tx], acc);
+        for (int t = 0; t < DT; ++t) acc = fma(sA[ty][t], sB[t][tx], acc);
         __syncthreads();
     }
     if (i < M && j < Nn) Cout[(size_t)i * Nn + j] = acc;
@@ -490,8 +493,8 @@ struct P2Solver {
     }
     static void gemm(int M, int Nn, int K, const double *A, int as0, int as1, const double *B, int bs0, int bs1,
                      double *C, cudaStream_t st) {
-        dim3 grid((Nn + 15) / 16, (M + 15) / 16);
-        HELM_TRACED(K_DGEMM, st, (dgemm_strided_kernel<<<grid, 256, 0, st>>>(M, Nn, K, A, as0, as1, B, bs0, bs1, C)));
+        dim3 grid((Nn + DT - 1) / DT, (M + DT - 1) / DT);
+        HELM_TRACED(K_DGEMM, st, (dgemm_strided_kernel<<<grid, DT * DT, 0, st>>>(M, Nn, K, A, as0, as1, B, bs0, bs1, C)));
     }
     helm_status apply(const double *r, double *out, cudaStream_t st) {
         // T1 = Cx r          (nx x nx)(nx x nz)
