@@ -427,7 +427,7 @@ def main():
         mf_d = torch.empty_like(mf)
         mt_d = torch.empty_like(mt)
         et, es = [], 0
-        for _ in range(max(1, args.steps)):
+        for it in range(args.warmup + max(1, args.steps)):   # the first W untimed, as in the main loop
             flush.fill_(2.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -437,8 +437,9 @@ def main():
             o = step(mf_d, mt_d)           # results come back to host inside the call
             e1.record()
             e1.synchronize()
-            et.append(e0.elapsed_time(e1) / 1e3)
-            es += o["solves"] + o["data_solves"]
+            if it >= args.warmup:
+                et.append(e0.elapsed_time(e1) / 1e3)
+                es += o["solves"] + o["data_solves"]
         e2e = {"value": es / sum(et), "unit": UNIT, "h2d_bytes_per_step": 2 * w.n_nodes * 8,
                "d2h_bytes_per_step": (2 + 3 * w.acq.n_rec) * 8}
 
