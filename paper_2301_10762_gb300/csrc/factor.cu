@@ -594,10 +594,14 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                     const int kc = k0 - c0;
                     // stage the old column panel and send it to the other CTAs of the team at once
                     // (the bulk-copy engine delivers it while the pivot block is inverted); the
-                    // block inverse, staged right after it, follows on the same barrier
-                    for (int r = rw; r < nz; r += FAC_THREADS / NB)
-                        if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
-                    __syncthreads();
+                    // block inverse, staged right after it, follows on the same barrier.  Within a
+                    // line (complex FP32, at most two blocks per CTA) the previous step's update
+                    // has already written the panel here.
+                    if (!(kNS && k > 0 && bpc <= 2)) {
+                        for (int r = rw; r < nz; r += FAC_THREADS / NB)
+                            if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
+                        __syncthreads();
+                    }
                     if (tid == 0) {
                         fence_proxy_async_smem();
                         const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
@@ -686,6 +690,15 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                         coef[u] = (u < kb) ? (inblk ? recvP[u * NB + (c - k0)] : sR[u * ldr + cc]) : mkc<T>(T(0), T(0));
                     const int rstep = FAC_THREADS / NB;
                     if constexpr (sizeof(T) == 4) {
+                        // owner of the next block step of this line: its old column panel is the
+                        // block column k + 1 written here; stage it for the send as well.  With at
+                        // most two blocks per CTA this CTA did not send from that buffer at the
+                        // previous step, and other CTAs only copy into their own buffers.
+                        const int kn = k + 1;
+                        const bool stage_next = kn < p && bpc <= 2 && kn / bpc == rank && c >= kn * NB &&
+                                                c < kn * NB + min(NB, nz - kn * NB);
+                        V *recvUn = sRecv + (size_t)((t + 1) & 1) * recv_elems;
+                        const int cn = c - kn * NB;
                         // two rows per pass; the 16 products of a row go into four partial sums
                         // that are combined pairwise and then subtracted from the old value once
                         // (the summation error of the update is what limits the factor's accuracy,
@@ -717,11 +730,16 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                                                 (p1[0].y + p1[1].y) + (p1[2].y + p1[3].y));
                             const V s2 = mkc<T>((p2[0].x + p2[1].x) + (p2[2].x + p2[3].x),
                                                 (p2[0].y + p2[1].y) + (p2[2].y + p2[3].y));
-                            *w1 = blk1 ? (inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc])
-                                       : mkc<T>(w1o.x - s1.x, w1o.y - s1.y);
-                            if (has2)
-                                *w2 = blk2 ? (inblk ? recvP[(r2 - k0) * NB + (c - k0)] : sR[(r2 - k0) * ldr + cc])
-                                           : mkc<T>(w2o.x - s2.x, w2o.y - s2.y);
+                            const V n1 = blk1 ? (inblk ? recvP[(r - k0) * NB + (c - k0)] : sR[(r - k0) * ldr + cc])
+                                              : mkc<T>(w1o.x - s1.x, w1o.y - s1.y);
+                            *w1 = n1;
+                            if (stage_next) recvUn[(size_t)r * NB + cn] = n1;
+                            if (has2) {
+                                const V n2 = blk2 ? (inblk ? recvP[(r2 - k0) * NB + (c - k0)] : sR[(r2 - k0) * ldr + cc])
+                                                  : mkc<T>(w2o.x - s2.x, w2o.y - s2.y);
+                                *w2 = n2;
+                                if (stage_next) recvUn[(size_t)r2 * NB + cn] = n2;
+                            }
                         }
                     } else {
                         for (int r = rw; r < nz; r += rstep) {
