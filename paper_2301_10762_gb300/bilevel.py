@@ -23,6 +23,36 @@ from __future__ import annotations
 import numpy as np
 
 
+def mre(recon, truth):
+    """Mean relative percentage error (Eq. relerr): the mean over the parameters j of
+    |recon_j - truth_j| / |truth_j| * 100."""
+    recon = np.asarray(recon, dtype=np.float64)
+    truth = np.asarray(truth, dtype=np.float64)
+    return float(np.mean(np.abs((recon - truth) / truth)) * 100.0)
+
+
+def improvement_factor(psi_initial, psi_optimised):
+    """IF = psi(alpha_0, P_0) / psi(alpha_opt, P_opt)."""
+    return float(psi_initial) / float(psi_optimised)
+
+
+def add_noise(data, draws, level=0.01):
+    """Data with white noise at the given relative level (1 % is 40 dB SNR, the setting of the
+    paper's tests).  draws: standard complex Gaussian samples of data's shape [n_omega, ...],
+    drawn by the caller from a seeded generator; each frequency's noise is scaled to
+    ||eta_w||_2 = level * ||d_w||_2.  Works on numpy arrays and torch tensors alike."""
+    if tuple(draws.shape) != tuple(data.shape):
+        raise ValueError(f"draws {tuple(draws.shape)} must have the data's shape {tuple(data.shape)}")
+    out = data.clone() if hasattr(data, "clone") else np.array(data, copy=True)
+    for q in range(data.shape[0]):
+        dn = float((abs(data[q]) ** 2).sum()) ** 0.5
+        en = float((abs(draws[q]) ** 2).sum()) ** 0.5
+        if en == 0.0:
+            raise ValueError("noise draws of a frequency are all zero")
+        out[q] = data[q] + draws[q] * (level * dn / en)
+    return out
+
+
 def frequency_continuation(evaluate, z0, alpha0, groups, z_bounds, alpha_bounds=(1e-10, None), free_alpha="last",
                            max_iter=50, pgtol=1e-10, ftol=1e-15, callback=None):
     """Algorithm allg:fcb1 with L-BFGS-B on each frequency group.
@@ -102,6 +132,35 @@ class GpuBilevelProblem:
         f = hm.helm_factor(op, self.prec)
         U, _ = hm.helm_solve(f, hm.helm_sources(op, acq), rtol=self.refine_rtol, max_iter=40)
         return hm.helm_restrict(op, acq, U)
+
+    def reconstruct(self, omegas, z, alpha, m_true, m0, noise_draws=None, level=0.01):
+        """m_FWI for one model from data at receiver depths z (with noise at the given level if
+        noise_draws, [n_omega, n_src, n_rec] complex, are given), by the lower level from m0."""
+        from .autograd import HelmholtzProblem
+        from .lbfgs import fwi_lower_level
+        torch = self.torch
+        omegas = np.atleast_1d(np.asarray(omegas, dtype=np.float64))
+        acq = self.acquisition(z)
+        mt = torch.as_tensor(np.asarray(m_true, dtype=np.float64), device="cuda")
+        d = self.data(omegas, acq, mt)
+        if noise_draws is not None:
+            d = add_noise(d, torch.as_tensor(np.asarray(noise_draws), dtype=torch.complex128, device="cuda"), level)
+        prob = HelmholtzProblem(*self.grid, omegas, acq=acq, prec=self.prec, rtol=self.refine_rtol)
+        res = fwi_lower_level(prob, d, alpha, self.mu, np.asarray(m0, dtype=np.float64), gtol=self.lower_gtol,
+                              max_iter=self.lower_max_iter)
+        return res["x"], res
+
+    def test_metrics(self, omegas, z, alpha, m_tests, m0, noise_draws=None, level=0.01):
+        """psi (Eq. SOobj averaged over the test models) and the MRE of the reconstructed
+        wavespeed c = m^(-1/2) against the ground truth, per test model."""
+        psi, mres = 0.0, []
+        for k, mt in enumerate(m_tests):
+            draws = None if noise_draws is None else noise_draws[k]
+            m_fwi, _ = self.reconstruct(omegas, z, alpha, mt, m0, draws, level)
+            mt = np.asarray(mt, dtype=np.float64)
+            psi += 0.5 * float(np.sum((mt - m_fwi) ** 2)) / len(m_tests)
+            mres.append(mre(1.0 / np.sqrt(m_fwi), 1.0 / np.sqrt(mt)))
+        return psi, mres
 
     def evaluate(self, omegas, z, alpha):
         """(psi, dpsi/dz, dpsi/dalpha) at receiver depths z and Tikhonov weight alpha."""

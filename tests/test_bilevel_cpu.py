@@ -6,8 +6,10 @@ the closed-form box-constrained minimiser (the unconstrained one clipped to the 
 stays at its initial value until the final group ("last"), moves in every group ("all") or never
 ("none"), and every evaluation stays inside the bounds.  On a tiny bilevel problem evaluated by
 the oracle (dense Newton lower level, Algorithm alg:box hypergradient averaged over two training
-models), the loop lowers psi in every group, keeps the receivers in the borehole, and starts each
-group from the previous group's design."""
+models), the loop lowers psi in every group, keeps the receivers in the borehole, starts each
+group from the previous group's design and ends with an improvement factor above 1.  The metrics
+of the experiments: MRE (Eq. relerr) and IF on closed-form cases, and the 1 % test-time noise is
+40 dB SNR per frequency."""
 import numpy as np
 import pytest
 
@@ -124,3 +126,37 @@ def test_oracle_bilevel_continuation_lowers_psi():
     # the second group's frequencies gives that group's starting psi
     psi_g2, _, _ = evaluate(np.array(groups[1]), seen[0][1], seen[0][2])
     assert np.isclose(psi_g2, out["history"][1]["psi_start"], rtol=1e-9)
+    # improvement factor on the final group's frequencies: the learned design beats the initial one
+    psi_init, _, _ = evaluate(np.array(groups[-1]), z0, 1e-4)
+    assert B.improvement_factor(psi_init, out["history"][-1]["psi"]) > 1.0
+
+
+def test_mre_and_improvement_factor_closed_forms():
+    # errors of 10 %, 5 % and 0 %: mean 5 %
+    assert np.isclose(B.mre([1.1, 1.9, 3.0], [1.0, 2.0, 3.0]), 5.0, rtol=1e-12)
+    assert B.mre([-2.0], [-1.0]) == 100.0          # relative to |truth|
+    assert B.improvement_factor(3.0, 1.5) == 2.0
+
+
+@pytest.mark.parametrize("backend", ["numpy", "torch"])
+def test_noise_is_40db_per_frequency(backend):
+    rng = np.random.default_rng(3)
+    scale = np.array([1.0, 1e-3, 1e4])[:, None, None]        # very different amplitudes per frequency
+    d = (rng.standard_normal((3, 4, 5)) + 1j * rng.standard_normal((3, 4, 5))) * scale
+    eta = rng.standard_normal((3, 4, 5)) + 1j * rng.standard_normal((3, 4, 5))
+    if backend == "torch":
+        torch = pytest.importorskip("torch")
+        dn = B.add_noise(torch.tensor(d), torch.tensor(eta)).numpy()
+    else:
+        dn = B.add_noise(d, eta)
+    for q in range(3):
+        snr = 10 * np.log10(np.sum(np.abs(d[q]) ** 2) / np.sum(np.abs(dn[q] - d[q]) ** 2))
+        assert abs(snr - 40.0) <= 1e-9
+        # the noise is the draws, rescaled: same direction
+        r = (dn[q] - d[q]) / eta[q]
+        assert np.allclose(r, r.flat[0], rtol=1e-12)
+    assert np.array_equal(B.add_noise(d, eta, level=0.0), d)
+    with pytest.raises(ValueError):
+        B.add_noise(d, eta[:2])
+    with pytest.raises(ValueError):
+        B.add_noise(d, np.zeros_like(eta))
