@@ -37,3 +37,34 @@ def test_library_exports_every_declared_symbol():
 def test_binding_covers_the_header():
     from paper_2301_10762_gb300 import helm as hm
     assert sorted(hm.EXPORTED) == declared_functions()
+
+
+def test_binding_struct_layouts_match_the_headers(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that a C compiler
+    gives the struct of the same name in include/*.h (a drift would pass garbage across the
+    boundary without any error)."""
+    import shutil
+    import subprocess
+    from paper_2301_10762_gb300 import helm as hm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [v for v in vars(hm).values()
+               if isinstance(v, type) and issubclass(v, ctypes.Structure) and v.__name__.startswith("helm_")]
+    assert len(structs) >= 11
+    lines = ["#include <stdio.h>", "#include <stddef.h>"] + [f'#include "{h}"' for h in HEADERS]
+    lines.append("int main(void) {")
+    expect = []
+    for s in structs:
+        lines.append(f'printf("%zu\\n", sizeof({s.__name__}));')
+        expect.append(ctypes.sizeof(s))
+        for name, *_ in s._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({s.__name__}, {name}));')
+            expect.append(getattr(s, name).offset)
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
