@@ -207,6 +207,17 @@ helm_status fwi_misfit_grad(helm_factor_t *f, const helm_acq *acq, const helm_c1
                             double alpha, double mu, double rtol, double *phi, double *grad_dev,
                             helm_c128 *u_out, helm_c128 *lam_out);
 
+/* helm_gamma_solve -- Z = Gamma(alpha0, mu)^{-1} R for ncol real vectors: the preconditioner
+ * P2 = Gamma(alpha0, mu) = alpha0 R + mu I of Eq. (P2) (R the regulariser of Eq. (Gamma), with
+ * the literal (n - 1) difference scaling, so Gamma depends on nx and nz only, not on lx, lz).
+ * The same solver as the PCG of bilevel_hypergrad: the 2D DCT-II diagonalises R, so the
+ * inverse is exact (FP64 rounding), not iterative.
+ *   R_dev, Z_dev: [ncol][N] FP64 (device, canonical node order); Z_dev may alias R_dev.
+ *   stream: cudaStream_t (as void *); the call synchronises it.
+ * Errors: EINVAL (nx or nz < 2, ncol < 0, alpha0 < 0, mu <= 0, NULL arrays), ENOMEM, ECUDA. */
+helm_status helm_gamma_solve(const helm_grid *grid, double alpha0, double mu, int32_t ncol, const double *R_dev,
+                             double *Z_dev, void *stream);
+
 /* fwi_hessian_vec -- Hessian-vector product of phi for a real direction m~ (Lemmas
  * thm:H1 and thm:H2, Discussion disc:Hess): per (s, w) two new solves
  *   v = A^{-1}(g u m~),  z = (A^H)^{-1}(R^T W^2 R v - m~ conj(g) lambda),

@@ -631,6 +631,35 @@ extern "C" helm_status fwi_hessian_vec(helm_factor_t *f, const helm_acq *acq, co
     return s;
 }
 
+// --------------------------------------------------------------- helm_gamma_solve
+
+// Z = Gamma(alpha0, mu)^{-1} R column by column with the DCT solver of the PCG (P2 of Eq. (P2))
+extern "C" helm_status helm_gamma_solve(const helm_grid *grid, double alpha0, double mu, int32_t ncol,
+                                        const double *R_dev, double *Z_dev, void *stream) {
+    if (!grid || grid->nx < 2 || grid->nz < 2 || ncol < 0 || !(alpha0 >= 0.0) || !(mu > 0.0) ||
+        (ncol > 0 && (!R_dev || !Z_dev))) {
+        helm_set_msg("helm_gamma_solve: bad arguments");
+        return HELM_EINVAL;
+    }
+    if (ncol == 0) return HELM_OK;
+    keep_pool_memory();
+    cudaStream_t st = (cudaStream_t)stream;
+    const GridGeom g{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1)};
+    const size_t N = (size_t)g.nx * g.nz;
+    helm_status s = HELM_OK;
+    {
+        Ws ws(st);
+        P2Solver p2;
+        s = p2.init(ws, g, alpha0, mu, st);
+        for (int32_t c = 0; s == HELM_OK && c < ncol; ++c) s = p2.apply(R_dev + c * N, Z_dev + c * N, st);
+        if (s == HELM_OK) {
+            const cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { helm_set_error("helm_gamma_solve", e); s = HELM_ECUDA; }
+        }
+    }
+    return s;
+}
+
 // --------------------------------------------------------------- fwi_misfit_grad
 
 // forward part: u = A^{-1} E (E = point sources, scratch supplied by the caller)

@@ -89,7 +89,7 @@ class helm_trace_entry(C.Structure):
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
             "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
-            "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad",
+            "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad", "helm_gamma_solve",
             # include/helm_trace.h
             "helm_trace_enable", "helm_trace_reset", "helm_trace_read", "helm_launch_count",
             "helm_trace_timeline", "helm_trace_kernel_name", "helm_trace_select",
@@ -142,6 +142,8 @@ def load(path: str = LIB_PATH):
     lib.fwi_misfit_grad.argtypes = [vp, P(helm_acq), vp, dbl, dbl, dbl, P(dbl), vp, vp, vp]
     lib.fwi_hessian_vec.restype = C.c_int
     lib.fwi_hessian_vec.argtypes = [vp, P(helm_acq), vp, vp, vp, dbl, dbl, dbl, i32, vp]
+    lib.helm_gamma_solve.restype = C.c_int
+    lib.helm_gamma_solve.argtypes = [P(helm_grid), dbl, dbl, i32, vp, vp, vp]
     lib.bilevel_hypergrad.restype = C.c_int
     lib.bilevel_hypergrad.argtypes = [i32, P(helm_grid), P(vp), P(vp), P(helm_acq), P(dbl), i32, dbl, dbl,
                                       dbl, C.c_int, P(helm_pcg_opts), vp, P(dbl), P(dbl), P(dbl), P(dbl),
@@ -392,6 +394,24 @@ def fwi_hessian_vec(f: Factor, acq: Acq, U: torch.Tensor, Lam: torch.Tensor | No
     _check(lib.fwi_hessian_vec(f.handle, C.byref(acq.struct), pu, pl, pm, float(alpha), float(mu), float(rtol),
                                1 if gauss_newton else 0, C.c_void_p(hv.data_ptr())), "fwi_hessian_vec")
     return hv
+
+
+def helm_gamma_solve(nx, nz, alpha0, mu, R: torch.Tensor, Z: torch.Tensor | None = None, lx=1.0, lz=1.0,
+                     stream=None) -> torch.Tensor:
+    """Z = Gamma(alpha0, mu)^{-1} R; R [N] or [ncol, N] FP64 CUDA tensor."""
+    lib = load()
+    N = int(nx) * int(nz)
+    if R.dim() not in (1, 2) or R.shape[-1] != N:
+        raise ValueError(f"R must be [N={N}] or [ncol, N]")
+    pr = _dev(R, torch.float64, "R")
+    if Z is None:
+        Z = torch.empty_like(R)
+    pz = _dev(Z, torch.float64, "Z", tuple(R.shape))
+    ncol = 1 if R.dim() == 1 else R.shape[0]
+    g = helm_grid(int(nx), int(nz), float(lx), float(lz))
+    _check(lib.helm_gamma_solve(C.byref(g), float(alpha0), float(mu), ncol, pr, pz, _stream_ptr(stream)),
+           "helm_gamma_solve")
+    return Z
 
 
 def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
