@@ -101,10 +101,12 @@ class GpuBilevelProblem:
 
     m_true: list of squared-slowness models m' (host arrays, N values); m0: the lower-level initial
     guess shared by all models; src_xz: [n_src][2]; alpha0, mu: P2 = Gamma(alpha0, mu) and the
-    Tikhonov mu; prec: factor precision of every solve."""
+    Tikhonov mu; prec: factor precision of every solve.  cg_rtol: the PCG tolerance for rho; the
+    paper's 1e-15 lies below what FP64 PCG reaches on an ill-conditioned Hessian (the library then
+    reports non-convergence), so the default is 1e-13."""
 
     def __init__(self, nx, nz, lx, lz, m_true, m0, src_xz, rec_x, alpha0, mu, prec=None, refine_rtol=1e-10,
-                 lower_gtol=1e-10, lower_max_iter=500, cg_rtol=1e-15, cg_max_iter=500):
+                 lower_gtol=1e-10, lower_max_iter=500, cg_rtol=1e-13, cg_max_iter=500):
         import torch
 
         from . import helm as hm

@@ -81,3 +81,36 @@ def test_preconditioner_study_on_gpu_hessian_matches_oracle():
     for k in ref:
         assert got[k]["converged"]
         assert abs(got[k]["iters"] - ref[k]["iters"]) <= 1, (k, got[k], ref[k])
+
+
+def test_bilevel_evaluate_matches_oracle_evaluator():
+    """GpuBilevelProblem.evaluate (data at the receivers, GPU L-BFGS lower level to
+    ||grad phi|| <= 1e-10, bilevel_hypergrad) against the same composition on the oracle (dense
+    Newton lower level, Algorithm alg:box hypergradient), averaged over two training models.
+    The lower-level solutions differ by up to ||grad phi|| / mu, hence the 1e-4 tolerance."""
+    from paper_2301_10762_gb300.bilevel import GpuBilevelProblem
+    w0 = W.tiny_case(7, 6, seed=11, n_omega=3, n_src=4, n_rec=6)
+    w1 = W.tiny_case(7, 6, seed=12, n_omega=3, n_src=4, n_rec=6)
+    g = H.Grid(w0.nx, w0.nz, w0.lx, w0.lz)
+    alpha, alpha0, mu = 1e-4, 1e-4, 1e-4
+    rec_x = 0.55 * w0.lx
+    z = np.linspace(0.15, 0.75, 6) * w0.lz
+    omegas = np.array([2.0, 3.0])
+    src = w0.acq.src_xz
+    rec = np.stack([np.full(6, rec_x), z], axis=1)
+    psi_o, dz_o, da_o = 0.0, np.zeros(6), 0.0
+    for mt in (w0.m_true, w1.m_true):
+        data, _ = H.synthetic_data(g, mt, omegas, src, rec)
+        m_fwi, gn = D.lower_level_newton(g, w0.m, omegas, src, rec, data, alpha, mu)
+        assert gn < 1e-10
+        hg = H.hypergradient(g, m_fwi, mt, omegas, src, rec, alpha, alpha0, mu, cg_rtol=1e-14)
+        psi_o += hg["psi"] / 2
+        dz_o += hg["dpsi_dp"][:, 1] / 2
+        da_o += hg["dpsi_dalpha"] / 2
+    prob = GpuBilevelProblem(w0.nx, w0.nz, w0.lx, w0.lz, [w0.m_true, w1.m_true], w0.m, src, rec_x, alpha0, mu,
+                             prec=hm.HELM_FP64, lower_max_iter=2000)
+    psi, dz, da = prob.evaluate(omegas, z, alpha)
+    assert abs(psi - psi_o) <= 1e-4 * abs(psi_o)
+    assert np.abs(dz - dz_o).max() <= 1e-4 * np.abs(dz_o).max()
+    assert abs(da - da_o) <= 1e-4 * abs(da_o)
+    assert prob.evaluations == 1
