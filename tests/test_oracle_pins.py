@@ -243,6 +243,37 @@ def test_source_vector_on_node_is_unit_vector():
     assert E[1, 2 * 7 + 4] == 1 and np.count_nonzero(E[1]) == 1
 
 
+def test_off_grid_source_weights_reproduce_bilinear_functions():
+    """Reading for off-grid sources: the bilinear (hat-function) weights of the containing cell.
+    They reproduce every bilinear function f = a + b x + c z + d x z exactly (E f = f(p)), are
+    non-negative with 4 nonzeros, sum to the amplitude, and put weight 1 on the node at the
+    far corner (x = lx, z = lz).  Swapping the weights of a cell (a plausible slip) fails."""
+    g = H.Grid(9, 7, 1.3, 0.8)
+    X = np.repeat(np.arange(g.nx) * g.hx, g.nz)
+    Z = np.tile(np.arange(g.nz) * g.hz, g.nx)
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.uniform(0, g.lx, 20), rng.uniform(0, g.lz, 20)], axis=1)
+    E = H.source_vectors(g, pts, np.full(20, 2.5))
+    for a, b, c, d in ((1.0, 0, 0, 0), (0, 1.0, 0, 0), (0, 0, 1.0, 0), (0.3, -1.2, 0.7, 2.0)):
+        f = a + b * X + c * Z + d * X * Z
+        assert np.allclose(np.real(E @ f), 2.5 * (a + b * pts[:, 0] + c * pts[:, 1] + d * pts[:, 0] * pts[:, 1]),
+                           rtol=1e-13, atol=1e-13)
+    assert np.all(np.real(E) >= 0) and np.all(np.count_nonzero(E, axis=1) <= 4)
+    assert np.allclose(E.sum(axis=1), 2.5, rtol=1e-14)
+    corner = H.source_vectors(g, [[g.lx, g.lz]])
+    assert corner[0, g.N - 1] == 1 and np.count_nonzero(corner) == 1
+    # planted slip: swapping the two x-weights of every cell breaks the linear reproduction
+    Es = np.zeros_like(E)
+    for q, (x, z) in enumerate(pts):
+        i0 = min(int(x / g.hx), g.nx - 2)
+        j0 = min(int(z / g.hz), g.nz - 2)
+        fx, fz = x / g.hx - i0, z / g.hz - j0
+        for di, wx in ((0, fx), (1, 1 - fx)):
+            for dj, wz in ((0, 1 - fz), (1, fz)):
+                Es[q, (i0 + di) * g.nz + j0 + dj] += wx * wz
+    assert not np.allclose(np.real(Es @ X), pts[:, 0], atol=1e-6)
+
+
 # ------------------------------------------------------------------ derivative pins
 
 def _tiny_fwi(seed=0, nx=8, nz=7):
