@@ -127,24 +127,33 @@ class GpuBilevelProblem:
         rec = np.stack([np.full(z.size, self.rec_x), z], axis=1)
         return self.hm.Acq(self.src_xz, rec)
 
-    def data(self, omegas, acq, m_true):
-        """d = R(P) u(m') at the current receivers (the training data of model m')."""
+    def data(self, omegas, acq, m_true, grid=None):
+        """d = R(P) u(m') at the current receivers (the training data of model m'), on the
+        inversion grid or on another grid (nx, nz) of the same domain, on which m_true is then
+        given (data from a finer grid avoid the inverse crime)."""
         hm = self.hm
-        op = hm.helm_assemble(*self.grid, m_true, omegas)
+        g = self.grid if grid is None else (int(grid[0]), int(grid[1]), self.grid[2], self.grid[3])
+        op = hm.helm_assemble(*g, m_true, omegas)
         f = hm.helm_factor(op, self.prec)
         U, _ = hm.helm_solve(f, hm.helm_sources(op, acq), rtol=self.refine_rtol, max_iter=40)
         return hm.helm_restrict(op, acq, U)
 
-    def reconstruct(self, omegas, z, alpha, m_true, m0, noise_draws=None, level=0.01):
+    def reconstruct(self, omegas, z, alpha, m_true, m0, noise_draws=None, level=0.01, data_model=None):
         """m_FWI for one model from data at receiver depths z (with noise at the given level if
-        noise_draws, [n_omega, n_src, n_rec] complex, are given), by the lower level from m0."""
+        noise_draws, [n_omega, n_src, n_rec] complex, are given), by the lower level from m0.
+        data_model: None (data from m_true on the inversion grid) or (nx, nz, m) to generate the
+        data from m on another nx x nz grid of the same domain."""
         from .autograd import HelmholtzProblem
         from .lbfgs import fwi_lower_level
         torch = self.torch
         omegas = np.atleast_1d(np.asarray(omegas, dtype=np.float64))
         acq = self.acquisition(z)
-        mt = torch.as_tensor(np.asarray(m_true, dtype=np.float64), device="cuda")
-        d = self.data(omegas, acq, mt)
+        if data_model is None:
+            mt = torch.as_tensor(np.asarray(m_true, dtype=np.float64), device="cuda")
+            d = self.data(omegas, acq, mt)
+        else:
+            md = torch.as_tensor(np.asarray(data_model[2], dtype=np.float64), device="cuda")
+            d = self.data(omegas, acq, md, grid=data_model[:2])
         if noise_draws is not None:
             d = add_noise(d, torch.as_tensor(np.asarray(noise_draws), dtype=torch.complex128, device="cuda"), level)
         prob = HelmholtzProblem(*self.grid, omegas, acq=acq, prec=self.prec, rtol=self.refine_rtol)
@@ -152,13 +161,15 @@ class GpuBilevelProblem:
                               max_iter=self.lower_max_iter)
         return res["x"], res
 
-    def test_metrics(self, omegas, z, alpha, m_tests, m0, noise_draws=None, level=0.01):
+    def test_metrics(self, omegas, z, alpha, m_tests, m0, noise_draws=None, level=0.01, data_models=None):
         """psi (Eq. SOobj averaged over the test models) and the MRE of the reconstructed
-        wavespeed c = m^(-1/2) against the ground truth, per test model."""
+        wavespeed c = m^(-1/2) against the ground truth, per test model.  data_models: None or
+        one (nx, nz, m) per test model (data from another grid, see reconstruct)."""
         psi, mres = 0.0, []
         for k, mt in enumerate(m_tests):
             draws = None if noise_draws is None else noise_draws[k]
-            m_fwi, _ = self.reconstruct(omegas, z, alpha, mt, m0, draws, level)
+            dm = None if data_models is None else data_models[k]
+            m_fwi, _ = self.reconstruct(omegas, z, alpha, mt, m0, draws, level, data_model=dm)
             mt = np.asarray(mt, dtype=np.float64)
             psi += 0.5 * float(np.sum((mt - m_fwi) ** 2)) / len(m_tests)
             mres.append(mre(1.0 / np.sqrt(m_fwi), 1.0 / np.sqrt(mt)))

@@ -124,3 +124,18 @@ def test_tiny_case_geometry():
     assert np.all((w.acq.rec_xz[:, 0] > 0) & (w.acq.rec_xz[:, 0] < w.lx))
     assert np.all((w.acq.rec_xz[:, 1] > 0) & (w.acq.rec_xz[:, 1] < w.lz))
     assert np.all(w.m > 0.25 - 1e-12) and np.all(w.m <= 1.0)
+
+
+def test_resample_bilinear_exact_on_bilinear_fields_and_shared_nodes():
+    fn = lambda X, Z: 1.0 + 2.0 * X - 3.0 * Z + 0.5 * X * Z   # noqa: E731
+    f = W.sample_on_grid(fn, 7, 5, 1.4, 0.8)
+    g = W.resample_bilinear(f, 7, 5, 13, 9)
+    assert np.allclose(g, W.sample_on_grid(fn, 13, 9, 1.4, 0.8), rtol=0, atol=1e-14)
+    # the 13 x 9 grid contains every node of the 7 x 5 grid: going back copies them
+    assert np.array_equal(W.resample_bilinear(g, 13, 9, 7, 5), f)
+    assert np.array_equal(W.resample_bilinear(f, 7, 5, 7, 5), f)
+    # a non-bilinear field is reproduced at shared nodes and bounded by its neighbours elsewhere
+    h = W.sample_on_grid(lambda X, Z: np.sin(3 * X) * np.cos(2 * Z), 7, 5)
+    hr = W.resample_bilinear(h, 7, 5, 13, 9).reshape(13, 9)
+    assert np.array_equal(hr[::2, ::2].reshape(-1), h)
+    assert hr.min() >= h.min() - 1e-15 and hr.max() <= h.max() + 1e-15

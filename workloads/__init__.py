@@ -24,7 +24,7 @@ __all__ = [
     "Acquisition", "Workload", "gaussian_inclusion_velocity", "gaussian_random_field",
     "layered_velocity", "gaussian_smooth", "top_row_sources", "surface_receivers",
     "config_plain", "config_fwi_step", "config_mixed", "config_hypergrad", "tiny_case",
-    "random_rhs",
+    "random_rhs", "resample_bilinear", "sample_on_grid",
 ]
 
 
@@ -82,6 +82,29 @@ def _coords(nx: int, nz: int, lx: float, lz: float):
 def _flat(field2d: np.ndarray) -> np.ndarray:
     """[nx, nz] -> canonical vector with k = i*nz + j."""
     return np.ascontiguousarray(field2d, dtype=np.float64).reshape(-1)
+
+
+def sample_on_grid(fn, nx, nz, lx=1.0, lz=1.0) -> np.ndarray:
+    """fn(X, Z) evaluated at the nodes of an nx x nz grid (flat, canonical order)."""
+    X, Z = _coords(nx, nz, lx, lz)
+    return _flat(fn(X, Z))
+
+
+def resample_bilinear(field: np.ndarray, nx: int, nz: int, nx2: int, nz2: int) -> np.ndarray:
+    """A nodal field on an nx x nz grid, interpolated bilinearly to the nodes of an nx2 x nz2
+    grid of the same domain (flat, canonical order).  Used to carry a model between the grid
+    the data are generated on and the grid it is reconstructed on."""
+    f = np.asarray(field, dtype=np.float64).reshape(nx, nz)
+    tx = np.linspace(0.0, nx - 1, nx2)
+    tz = np.linspace(0.0, nz - 1, nz2)
+    i0 = np.minimum(np.floor(tx).astype(np.int64), nx - 2)
+    j0 = np.minimum(np.floor(tz).astype(np.int64), nz - 2)
+    fx = (tx - i0)[:, None]
+    fz = (tz - j0)[None, :]
+    I, J = i0[:, None], j0[None, :]
+    out = ((1 - fx) * (1 - fz) * f[I, J] + fx * (1 - fz) * f[I + 1, J]
+           + (1 - fx) * fz * f[I, J + 1] + fx * fz * f[I + 1, J + 1])
+    return _flat(out)
 
 
 # ------------------------------------------------------------------- velocity models
