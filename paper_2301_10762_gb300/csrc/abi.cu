@@ -74,7 +74,7 @@ void dev_free(void *p, cudaStream_t st) {
 
 extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev, const double *omega,
                                      int32_t n_omega, void *stream, helm_op_t **out) {
-    if (!out) return HELM_EINVAL;
+    if (!out) { helm_set_msg("helm_assemble: NULL out"); return HELM_EINVAL; }
     *out = nullptr;
     if (!grid || !m_dev || !omega || n_omega < 1) { helm_set_msg("helm_assemble: NULL argument or n_omega < 1"); return HELM_EINVAL; }
     if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0)) {
@@ -132,7 +132,7 @@ extern "C" void helm_op_destroy(helm_op_t *op) {
 // ------------------------------------------------------------------------ factor
 
 extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out) {
-    if (!out) return HELM_EINVAL;
+    if (!out) { helm_set_msg("helm_factor: NULL out"); return HELM_EINVAL; }
     *out = nullptr;
     if (!op || (prec != HELM_FP64 && prec != HELM_MIXED)) { helm_set_msg("helm_factor: bad op or precision"); return HELM_EINVAL; }
     helm_factor_t *f = new (std::nothrow) struct helm_factor();
@@ -455,7 +455,7 @@ void acq_free(DevAcq *d) {
 }
 
 extern "C" helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, helm_c128 *B_dev) {
-    if (!op || !acq || !B_dev) return HELM_EINVAL;
+    if (!op || !acq || !B_dev) { helm_set_msg("helm_sources: bad arguments"); return HELM_EINVAL; }
     DevAcq d;
     helm_status s = acq_upload(op, acq, &d);
     if (s != HELM_OK) return s;
@@ -468,7 +468,10 @@ extern "C" helm_status helm_sources(const helm_op_t *op, const helm_acq *acq, he
 
 extern "C" helm_status helm_restrict(const helm_op_t *op, const helm_acq *acq, int32_t ncol,
                                      const helm_c128 *X_dev, helm_c128 *Y_dev) {
-    if (!op || !acq || ncol < 0 || (ncol > 0 && (!X_dev || !Y_dev))) return HELM_EINVAL;
+    if (!op || !acq || ncol < 0 || (ncol > 0 && (!X_dev || !Y_dev))) {
+        helm_set_msg("helm_restrict: bad arguments");
+        return HELM_EINVAL;
+    }
     DevAcq d;
     helm_status s = acq_upload(op, acq, &d);
     if (s != HELM_OK) return s;

@@ -389,7 +389,7 @@ extern "C" helm_status helm_server_submit(helm_server_t *s, const helm_request *
 }
 
 extern "C" helm_status helm_server_wait(helm_server_t *s, int64_t ticket, helm_request_info *info) {
-    if (!s) return HELM_EINVAL;
+    if (!s) { helm_set_msg("helm_server_wait: NULL server"); return HELM_EINVAL; }
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->states.find(ticket);
     if (it == s->states.end()) {
@@ -412,7 +412,7 @@ extern "C" helm_status helm_server_wait(helm_server_t *s, int64_t ticket, helm_r
 }
 
 extern "C" helm_status helm_server_stats(const helm_server_t *s, helm_server_counters *out) {
-    if (!s || !out) return HELM_EINVAL;
+    if (!s || !out) { helm_set_msg("helm_server_stats: NULL argument"); return HELM_EINVAL; }
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
     out->cache_hits = (int64_t)s->cache.hits();

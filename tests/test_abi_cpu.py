@@ -68,3 +68,38 @@ def test_binding_struct_layouts_match_the_headers(tmp_path):
     subprocess.run([cc, "-std=c11", "-Wall", "-Werror", str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == expect
+
+
+@pytest.mark.skipif(not os.path.exists(LIB), reason="libhelm.so not built (run __graft_entry__.build())")
+def test_invalid_arguments_return_einval_with_a_message():
+    """Every entry point validates its arguments before any CUDA call: NULL or out-of-range
+    arguments give HELM_EINVAL (no abort, no GPU needed) and a helm_last_error message naming
+    the call."""
+    lib = ctypes.CDLL(LIB)
+    lib.helm_last_error.restype = ctypes.c_char_p
+    d = ctypes.c_double
+    calls = {
+        "helm_assemble": lambda: lib.helm_assemble(None, None, None, 0, None, None),
+        "helm_factor": lambda: lib.helm_factor(None, 0, None),
+        "helm_solve": lambda: lib.helm_solve(None, 1, None, None, d(1e-10), 8, None),
+        "helm_solve_noalloc": lambda: lib.helm_solve_noalloc(None, 1, None, None, d(1e-10), 8, 0, None),
+        "helm_sources": lambda: lib.helm_sources(None, None, None),
+        "helm_restrict": lambda: lib.helm_restrict(None, None, 1, None, None),
+        "helm_restrict_adjoint": lambda: lib.helm_restrict_adjoint(None, None, 1, None, None),
+        "helm_field_grad": lambda: lib.helm_field_grad(None, 1, None, None, None),
+        "fwi_misfit_grad": lambda: lib.fwi_misfit_grad(None, None, None, d(0), d(0), d(1e-10), None, None, None,
+                                                       None),
+        "fwi_hessian_vec": lambda: lib.fwi_hessian_vec(None, None, None, None, None, d(0), d(0), d(1e-10), 0, None),
+        "helm_gamma_solve": lambda: lib.helm_gamma_solve(None, d(1e-3), d(1e-6), 1, None, None, None),
+        "bilevel_hypergrad": lambda: lib.bilevel_hypergrad(0, None, None, None, None, None, 0, d(0), d(0), d(0), 0,
+                                                           None, None, None, None, None, None, None),
+        "helm_server_create": lambda: lib.helm_server_create(None, None),
+        "helm_server_add_model": lambda: lib.helm_server_add_model(None, None, None, None),
+        "helm_server_submit": lambda: lib.helm_server_submit(None, None, None),
+        "helm_server_wait": lambda: lib.helm_server_wait(None, ctypes.c_int64(0), None),
+        "helm_server_stats": lambda: lib.helm_server_stats(None, None),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name                        # HELM_EINVAL
+        assert lib.helm_last_error().decode().startswith(name), (name, lib.helm_last_error())
+    assert lib.helm_adjoint_solve(None, 1, None, None, d(1e-10), 8, None) == 1
