@@ -71,3 +71,16 @@ def test_two_rank_gloo_hypergradient_equals_single_process(tmp_path):
     assert np.isclose(float(got["dalpha"]), ref["dpsi_dalpha"], rtol=1e-12)
     assert np.allclose(got["dp"], ref["dpsi_dp"], rtol=1e-12, atol=1e-14)
     assert np.allclose(got["dw"], ref["dpsi_dw"], rtol=1e-12, atol=1e-14)
+
+
+def test_four_ranks_three_models_one_rank_idle(tmp_path):
+    """More ranks than models: the rank without a model contributes zeros to the all-reduce and
+    the average is still the single-process one."""
+    out = str(tmp_path / "res4.npz")
+    mp.start_processes(_worker, args=(4, _free_port(), out), nprocs=4, start_method="spawn")
+    got = np.load(out)
+    ref = _oracle_compute(_models())
+    assert np.isclose(float(got["psi"]), ref["psi"], rtol=1e-13)
+    assert np.isclose(float(got["dalpha"]), ref["dpsi_dalpha"], rtol=1e-12)
+    assert np.allclose(got["dp"], ref["dpsi_dp"], rtol=1e-12, atol=1e-14)
+    assert np.allclose(got["dw"], ref["dpsi_dw"], rtol=1e-12, atol=1e-14)
