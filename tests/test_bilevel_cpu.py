@@ -160,3 +160,68 @@ def test_noise_is_40db_per_frequency(backend):
         B.add_noise(d, eta[:2])
     with pytest.raises(ValueError):
         B.add_noise(d, np.zeros_like(eta))
+
+
+def test_oracle_miniature_of_the_experiment_protocol():
+    """The paper's protocol in miniature, with the oracle as evaluator.
+    - Setup: 8 x 8 grid, two layered training models, crosswell (3 sources at x = 0.05,
+      4 receivers in a borehole at x = 0.9, depths bounded to [0.05, 0.95]).
+    - Lower level: from a vertically varying start model.
+    - Frequency groups: overlapping, [(2), (2, 4), (4, 8)]; alpha freed in the last group only.
+    - Test: a held-out layered model, data with 1 % noise (40 dB).
+    The learned design beats the initial one on the training set and on the held-out model, in
+    psi (IF > 1) and in the wavespeed MRE."""
+    from oracle import dense as D
+    from oracle import helmholtz as H
+    import workloads as W
+    n = 8
+    g = H.Grid(n, n, 1.0, 1.0)
+    train = [W.layered_velocity(n, n, 100 + k) for k in range(2)]
+    test = W.layered_velocity(n, n, 200)
+    m0 = W.sample_on_grid(lambda X, Z: 1.0 / (1.5 + 3.0 * Z) ** 2, n, n)
+    h = 1.0 / (n - 1)
+    src = np.stack([np.full(3, round(0.05 / h) * h), np.round(np.array([0.2, 0.5, 0.8]) / h) * h], axis=1)
+    rec_x, z0, alpha0, mu = 0.9, np.linspace(0.3, 0.7, 4), 1e-2, 1e-4
+    groups = [[2.0], [2.0, 4.0], [4.0, 8.0]]
+    warm = [m0.copy() for _ in train]
+    seen_alpha = []
+
+    def evaluate(om, z, alpha):
+        seen_alpha.append((len(om), float(om[-1]), alpha))
+        rec = np.stack([np.full(len(z), rec_x), z], axis=1)
+        psi, dz, da = 0.0, np.zeros(len(z)), 0.0
+        for k, mt in enumerate(train):
+            data, _ = H.synthetic_data(g, mt, om, src, rec)
+            m_fwi, gn = D.lower_level_newton(g, warm[k], om, src, rec, data, alpha, mu)
+            assert gn < 1e-10
+            warm[k] = m_fwi
+            hg = H.hypergradient(g, m_fwi, mt, om, src, rec, alpha, alpha0, mu, cg_rtol=1e-13)
+            psi += hg["psi"] / len(train)
+            dz += hg["dpsi_dp"][:, 1] / len(train)
+            da += hg["dpsi_dalpha"] / len(train)
+        return psi, dz, da
+
+    def test_metrics(z, alpha):
+        rec = np.stack([np.full(len(z), rec_x), z], axis=1)
+        om = np.array(groups[-1])
+        data, _ = H.synthetic_data(g, test, om, src, rec)
+        rng = np.random.default_rng(7)
+        data = B.add_noise(data, rng.standard_normal(data.shape) + 1j * rng.standard_normal(data.shape))
+        m_fwi, _ = D.lower_level_newton(g, m0, om, src, rec, data, alpha, mu)
+        return 0.5 * np.sum((test - m_fwi) ** 2), B.mre(1 / np.sqrt(m_fwi), 1 / np.sqrt(test))
+
+    psi_train0 = evaluate(np.array(groups[-1]), z0, alpha0)[0]
+    warm = [m0.copy() for _ in train]
+    # alpha >= 1e-5 keeps every lower-level problem well posed for the Newton solve (at 1e-6 a
+    # trial point's Newton iteration stalled); the optimum lies inside, at about 2.7e-5
+    out = B.frequency_continuation(evaluate, z0, alpha0, groups, (0.05, 0.95), alpha_bounds=(1e-5, 1.0),
+                                   max_iter=15)
+    assert all(a == alpha0 for k, top, a in seen_alpha if top < 8.0)     # alpha fixed before the last group
+    assert out["alpha"] != alpha0
+    assert np.all((out["z"] >= 0.05) & (out["z"] <= 0.95))
+    psi_train = evaluate(np.array(groups[-1]), out["z"], out["alpha"])[0]
+    assert B.improvement_factor(psi_train0, psi_train) > 5.0
+    psi_test0, mre0 = test_metrics(z0, alpha0)
+    psi_test, mre1 = test_metrics(out["z"], out["alpha"])
+    assert B.improvement_factor(psi_test0, psi_test) > 2.0
+    assert mre1 < 0.5 * mre0
