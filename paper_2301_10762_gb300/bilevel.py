@@ -96,6 +96,32 @@ def frequency_continuation(evaluate, z0, alpha0, groups, z_bounds, alpha_bounds=
     return {"z": z, "alpha": alpha, "history": history}
 
 
+def run_protocol(problem, z0, alpha0, groups, z_bounds, m_tests, m0, alpha_bounds=(1e-10, None),
+                 free_alpha="last", max_iter=50, noise_draws=None, level=0.01, data_models=None):
+    """The experiments' protocol: learn the design by bilevel frequency continuation on the
+    training models, then report IF and MRE (Eq. relerr) on the training set and on test models.
+
+    problem: an object with evaluate(omegas, z, alpha) -> (psi, dpsi/dz, dpsi/dalpha) over the
+    training models, and test_metrics(omegas, z, alpha, m_tests, m0, noise_draws, level,
+    data_models) -> (psi, [MRE per test model]) (e.g. GpuBilevelProblem).  Both IFs are taken
+    on the final group's frequencies; the training psi at the initial design is evaluated last,
+    so that the lower-level warm starts of the continuation are those of the algorithm.
+    Returns a dict: z, alpha, history, train_psi (initial, learned), train_if, test_psi
+    (initial, learned), test_if, test_mre (initial, learned; lists per test model)."""
+    out = frequency_continuation(problem.evaluate, z0, alpha0, groups, z_bounds, alpha_bounds=alpha_bounds,
+                                 free_alpha=free_alpha, max_iter=max_iter)
+    last = np.atleast_1d(np.asarray(groups[-1], dtype=np.float64))
+    psi_opt = problem.evaluate(last, out["z"], out["alpha"])[0]
+    psi_init = problem.evaluate(last, np.asarray(z0, dtype=np.float64), alpha0)[0]
+    kw = {"noise_draws": noise_draws, "level": level, "data_models": data_models}
+    t_init, mre_init = problem.test_metrics(last, np.asarray(z0, dtype=np.float64), alpha0, m_tests, m0, **kw)
+    t_opt, mre_opt = problem.test_metrics(last, out["z"], out["alpha"], m_tests, m0, **kw)
+    return {"z": out["z"], "alpha": out["alpha"], "history": out["history"],
+            "train_psi": (float(psi_init), float(psi_opt)), "train_if": improvement_factor(psi_init, psi_opt),
+            "test_psi": (float(t_init), float(t_opt)), "test_if": improvement_factor(t_init, t_opt),
+            "test_mre": (list(mre_init), list(mre_opt))}
+
+
 class GpuBilevelProblem:
     """Training models on one grid, fixed sources, receivers in a vertical borehole x = rec_x.
 

@@ -162,8 +162,55 @@ def test_noise_is_40db_per_frequency(backend):
         B.add_noise(d, np.zeros_like(eta))
 
 
+class _OracleProblem:
+    """The interface of GpuBilevelProblem (evaluate, test_metrics) on the oracle: data from the
+    training models at the current receivers, the lower level by Newton with the dense Hessian
+    (warm-started per model), the hypergradient of Algorithm alg:box averaged over the models."""
+
+    def __init__(self, g, train, m0, src, rec_x, alpha0, mu):
+        self.g, self.train, self.m0, self.src, self.rec_x = g, train, m0, src, rec_x
+        self.alpha0, self.mu = alpha0, mu
+        self.warm = [m0.copy() for _ in train]
+        self.calls = []
+
+    def _rec(self, z):
+        return np.stack([np.full(len(z), self.rec_x), z], axis=1)
+
+    def evaluate(self, om, z, alpha):
+        from oracle import dense as D
+        from oracle import helmholtz as H
+        self.calls.append((float(om[-1]), float(alpha)))
+        rec = self._rec(z)
+        psi, dz, da = 0.0, np.zeros(len(z)), 0.0
+        for k, mt in enumerate(self.train):
+            data, _ = H.synthetic_data(self.g, mt, om, self.src, rec)
+            m_fwi, gn = D.lower_level_newton(self.g, self.warm[k], om, self.src, rec, data, alpha, self.mu)
+            assert gn < 1e-10
+            self.warm[k] = m_fwi
+            hg = H.hypergradient(self.g, m_fwi, mt, om, self.src, rec, alpha, self.alpha0, self.mu, cg_rtol=1e-13)
+            psi += hg["psi"] / len(self.train)
+            dz += hg["dpsi_dp"][:, 1] / len(self.train)
+            da += hg["dpsi_dalpha"] / len(self.train)
+        return psi, dz, da
+
+    def test_metrics(self, om, z, alpha, m_tests, m0, noise_draws=None, level=0.01, data_models=None):
+        from oracle import dense as D
+        from oracle import helmholtz as H
+        rec = self._rec(z)
+        psi, mres = 0.0, []
+        for k, mt in enumerate(m_tests):
+            data, _ = H.synthetic_data(self.g, mt, om, self.src, rec)
+            if noise_draws is not None:
+                data = B.add_noise(data, noise_draws[k], level)
+            m_fwi, _ = D.lower_level_newton(self.g, m0, om, self.src, rec, data, alpha, self.mu)
+            psi += 0.5 * np.sum((mt - m_fwi) ** 2) / len(m_tests)
+            mres.append(B.mre(1 / np.sqrt(m_fwi), 1 / np.sqrt(mt)))
+        return psi, mres
+
+
 def test_oracle_miniature_of_the_experiment_protocol():
-    """The paper's protocol in miniature, with the oracle as evaluator.
+    """The paper's protocol in miniature, through bilevel.run_protocol with the oracle as the
+    problem (the GPU run passes a GpuBilevelProblem instead).
     - Setup: 8 x 8 grid, two layered training models, crosswell (3 sources at x = 0.05,
       4 receivers in a borehole at x = 0.9, depths bounded to [0.05, 0.95]).
     - Lower level: from a vertically varying start model.
@@ -171,7 +218,6 @@ def test_oracle_miniature_of_the_experiment_protocol():
     - Test: a held-out layered model, data with 1 % noise (40 dB).
     The learned design beats the initial one on the training set and on the held-out model, in
     psi (IF > 1) and in the wavespeed MRE."""
-    from oracle import dense as D
     from oracle import helmholtz as H
     import workloads as W
     n = 8
@@ -181,47 +227,17 @@ def test_oracle_miniature_of_the_experiment_protocol():
     m0 = W.sample_on_grid(lambda X, Z: 1.0 / (1.5 + 3.0 * Z) ** 2, n, n)
     h = 1.0 / (n - 1)
     src = np.stack([np.full(3, round(0.05 / h) * h), np.round(np.array([0.2, 0.5, 0.8]) / h) * h], axis=1)
-    rec_x, z0, alpha0, mu = 0.9, np.linspace(0.3, 0.7, 4), 1e-2, 1e-4
-    groups = [[2.0], [2.0, 4.0], [4.0, 8.0]]
-    warm = [m0.copy() for _ in train]
-    seen_alpha = []
-
-    def evaluate(om, z, alpha):
-        seen_alpha.append((len(om), float(om[-1]), alpha))
-        rec = np.stack([np.full(len(z), rec_x), z], axis=1)
-        psi, dz, da = 0.0, np.zeros(len(z)), 0.0
-        for k, mt in enumerate(train):
-            data, _ = H.synthetic_data(g, mt, om, src, rec)
-            m_fwi, gn = D.lower_level_newton(g, warm[k], om, src, rec, data, alpha, mu)
-            assert gn < 1e-10
-            warm[k] = m_fwi
-            hg = H.hypergradient(g, m_fwi, mt, om, src, rec, alpha, alpha0, mu, cg_rtol=1e-13)
-            psi += hg["psi"] / len(train)
-            dz += hg["dpsi_dp"][:, 1] / len(train)
-            da += hg["dpsi_dalpha"] / len(train)
-        return psi, dz, da
-
-    def test_metrics(z, alpha):
-        rec = np.stack([np.full(len(z), rec_x), z], axis=1)
-        om = np.array(groups[-1])
-        data, _ = H.synthetic_data(g, test, om, src, rec)
-        rng = np.random.default_rng(7)
-        data = B.add_noise(data, rng.standard_normal(data.shape) + 1j * rng.standard_normal(data.shape))
-        m_fwi, _ = D.lower_level_newton(g, m0, om, src, rec, data, alpha, mu)
-        return 0.5 * np.sum((test - m_fwi) ** 2), B.mre(1 / np.sqrt(m_fwi), 1 / np.sqrt(test))
-
-    psi_train0 = evaluate(np.array(groups[-1]), z0, alpha0)[0]
-    warm = [m0.copy() for _ in train]
+    z0, alpha0 = np.linspace(0.3, 0.7, 4), 1e-2
+    prob = _OracleProblem(g, train, m0, src, 0.9, alpha0, 1e-4)
+    rng = np.random.default_rng(7)
+    draws = [rng.standard_normal((2, 3, 4)) + 1j * rng.standard_normal((2, 3, 4))]
     # alpha >= 1e-5 keeps every lower-level problem well posed for the Newton solve (at 1e-6 a
     # trial point's Newton iteration stalled); the optimum lies inside, at about 2.7e-5
-    out = B.frequency_continuation(evaluate, z0, alpha0, groups, (0.05, 0.95), alpha_bounds=(1e-5, 1.0),
-                                   max_iter=15)
-    assert all(a == alpha0 for k, top, a in seen_alpha if top < 8.0)     # alpha fixed before the last group
-    assert out["alpha"] != alpha0
-    assert np.all((out["z"] >= 0.05) & (out["z"] <= 0.95))
-    psi_train = evaluate(np.array(groups[-1]), out["z"], out["alpha"])[0]
-    assert B.improvement_factor(psi_train0, psi_train) > 5.0
-    psi_test0, mre0 = test_metrics(z0, alpha0)
-    psi_test, mre1 = test_metrics(out["z"], out["alpha"])
-    assert B.improvement_factor(psi_test0, psi_test) > 2.0
-    assert mre1 < 0.5 * mre0
+    res = B.run_protocol(prob, z0, alpha0, [[2.0], [2.0, 4.0], [4.0, 8.0]], (0.05, 0.95), [test], m0,
+                         alpha_bounds=(1e-5, 1.0), max_iter=15, noise_draws=draws)
+    assert all(a == alpha0 for top, a in prob.calls if top < 8.0)     # alpha fixed before the last group
+    assert res["alpha"] != alpha0
+    assert np.all((res["z"] >= 0.05) & (res["z"] <= 0.95))
+    assert res["train_if"] > 5.0
+    assert res["test_if"] > 2.0
+    assert res["test_mre"][1][0] < 0.5 * res["test_mre"][0][0]
