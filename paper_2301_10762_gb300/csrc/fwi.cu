@@ -62,7 +62,6 @@ template <int NT> __device__ double block_sum(double v, double *sh) {
 // Block per column, warp per receiver (16 taps), fixed-order reduction.
 __global__ void misfit_kernel(int N, int n_rec, const int *idx, const double *tw, const double *rec_w,
                               const double2 *U, const double2 *data, double2 *eps, double *phi_col) {
-    __shared__ double sh[32];
     __shared__ double s_acc[32];
     const int col = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
