@@ -93,7 +93,6 @@ __global__ void misfit_kernel(int N, int n_rec, const int *idx, const double *tw
         for (int w = 0; w < nw; ++w) t += s_acc[w];
         phi_col[col] = t;
     }
-    (void)sh;
 }
 
 // out[col][idx_t] += tw_t * s_r * z[col][r] for every receiver r, sequentially over r
