@@ -103,3 +103,14 @@ def test_invalid_arguments_return_einval_with_a_message():
         assert call() == 1, name                        # HELM_EINVAL
         assert lib.helm_last_error().decode().startswith(name), (name, lib.helm_last_error())
     assert lib.helm_adjoint_solve(None, 1, None, None, d(1e-10), 8, None) == 1
+
+
+@pytest.mark.skipif(not os.path.exists(LIB), reason="libhelm.so not built (run __graft_entry__.build())")
+def test_library_is_not_older_than_its_sources():
+    """A build that failed after a source change leaves the previous libhelm.so behind; the ABI
+    checks above would then test stale code.  The library must be newer than every CUDA source
+    and header."""
+    import glob
+    srcs = glob.glob(os.path.join(ROOT, "paper_2301_10762_gb300", "csrc", "*")) + HEADERS
+    newest = max(os.path.getmtime(p) for p in srcs)
+    assert os.path.getmtime(LIB) >= newest, "libhelm.so is older than its sources: rebuild"
