@@ -31,7 +31,26 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+DIGEST = LIB + ".sources"   # sha256 of the sources the library was built from
+
+
+def source_digest() -> str:
+    """sha256 over every file of csrc/ and include/ (names and contents, in name order)."""
+    import hashlib
+    h = hashlib.sha256()
+    inc = os.path.join(ROOT, "include")
+    for d in (CSRC, inc):
+        for f in sorted(os.listdir(d)):
+            path = os.path.join(d, f)
+            if os.path.isfile(path):
+                h.update(f.encode())
+                with open(path, "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()
+
+
 def build_library(verbose: bool = False, extra_flags=()) -> str:
+    digest = source_digest()
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
     procs = []
@@ -59,6 +78,8 @@ def build_library(verbose: bool = False, extra_flags=()) -> str:
         sys.stdout.write(r.stdout.decode(errors="replace"))
         raise RuntimeError("link of libhelm.so failed")
     os.replace(tmp, LIB)
+    with open(DIGEST, "w") as fh:
+        fh.write(digest + "\n")
     return LIB
 
 

@@ -106,11 +106,12 @@ def test_invalid_arguments_return_einval_with_a_message():
 
 
 @pytest.mark.skipif(not os.path.exists(LIB), reason="libhelm.so not built (run __graft_entry__.build())")
-def test_library_is_not_older_than_its_sources():
-    """A build that failed after a source change leaves the previous libhelm.so behind; the ABI
-    checks above would then test stale code.  The library must be newer than every CUDA source
-    and header."""
-    import glob
-    srcs = glob.glob(os.path.join(ROOT, "paper_2301_10762_gb300", "csrc", "*")) + HEADERS
-    newest = max(os.path.getmtime(p) for p in srcs)
-    assert os.path.getmtime(LIB) >= newest, "libhelm.so is older than its sources: rebuild"
+def test_library_was_built_from_the_current_sources():
+    """A build that failed after a source change leaves the previous libhelm.so behind, and the
+    ABI checks above would then test stale code.  The build records a digest of the sources it
+    compiled; it must match the sources as they are now."""
+    from paper_2301_10762_gb300 import build as b
+    if not os.path.exists(b.DIGEST):
+        pytest.skip("library built without a source digest")
+    with open(b.DIGEST) as fh:
+        assert fh.read().strip() == b.source_digest(), "libhelm.so was built from other sources: rebuild"
