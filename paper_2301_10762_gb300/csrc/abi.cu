@@ -367,9 +367,10 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     return HELM_OK;
 }
 
-static helm_status check_solve_args(helm_factor_t *f, int32_t nrhs, const helm_c128 *B, helm_c128 *X) {
+static helm_status check_solve_args(const char *who, helm_factor_t *f, int32_t nrhs, const helm_c128 *B,
+                                    helm_c128 *X) {
     if (!f || nrhs < 0 || (nrhs > 0 && (!B || !X)) || (const void *)B == (const void *)X) {
-        helm_set_msg("helm_solve: bad arguments (NULL, nrhs < 0 or B aliases X)");
+        helm_set_msg((std::string(who) + ": bad arguments (NULL, nrhs < 0 or B aliases X)").c_str());
         return HELM_EINVAL;
     }
     return HELM_OK;
@@ -377,7 +378,7 @@ static helm_status check_solve_args(helm_factor_t *f, int32_t nrhs, const helm_c
 
 extern "C" helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
                                   double rtol, int32_t max_iter, helm_solve_info *info) {
-    helm_status s = check_solve_args(f, nrhs, B_dev, X_dev);
+    helm_status s = check_solve_args("helm_solve", f, nrhs, B_dev, X_dev);
     if (s != HELM_OK || nrhs == 0) return s;
     return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 0);
 }
@@ -385,7 +386,7 @@ extern "C" helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c12
 extern "C" helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
                                           helm_c128 *X_dev, double rtol, int32_t max_iter,
                                           helm_solve_info *info) {
-    helm_status s = check_solve_args(f, nrhs, B_dev, X_dev);
+    helm_status s = check_solve_args("helm_adjoint_solve", f, nrhs, B_dev, X_dev);
     if (s != HELM_OK || nrhs == 0) return s;
     return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 1);
 }
