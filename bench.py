@@ -1,19 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark of the hot path: one bilevel-hypergradient pass per step.
+"""Benchmark of the hot path: batched Helmholtz right-hand-side solves, mixed precision
+against FP64 on the GPU.
 
-Workload (the FWI-step geometry): 128 x 128 unit square, omega in {5, 10, 15}, 16
-top-row sources, 32 surface receivers, alpha = alpha0 = 1e-3, mu = 1e-6; training model
-m' = 1/c'^2 with c' = 1 + 0.3 g (Gaussian random field, correlation length 0.1, seed 2 +
-rank), lower-level reconstruction stood in for by m' smoothed with sigma = 4h.  One
-step runs every row of the path: assemble, line factors of A(m_fwi) and A(m'),
-point sources, data solves, forward solves, misfit, adjoint solves, gradient, PCG
-with 10 iterations (11 Hessian products, 2 solve batches each) preconditioned by P2,
-the tau solve and the hypergradient reductions.  Metric: Helmholtz right-hand-side
-solves per second, every solve delivered at relative residual <= 1e-10 (mixed) or
-by the FP64 factor (fp64).
+Default step (the mixed-precision workload): 256 x 256 nodes on the unit square, omega in
+{5, 10, ..., 40} (8 values), 64 point sources on top-row nodes as right-hand sides, smooth
+random velocity c = 1 + 2 (g - min) / (max - min) in [1, 3] (Gaussian random field,
+correlation length 0.1, seed 3 + rank).  One step runs the solve path end to end on data
+already in HBM: assemble A(m, w) for the 8 frequencies, factor them (line factors in complex
+FP32), form the 64 point-source right-hand sides and solve all 512 columns, each refined
+with FP64-accurate residuals to ||b - A x|| / ||b|| <= 1e-10.  Metric: right-hand-side
+solves per second with the factor time included (512 per step).  The same step with FP64
+factors is the comparison the metric names; the per-frequency error of sampled columns
+against the CPU oracle is reported for both.
 
-Multi-GPU (torchrun): every rank owns its own training model (weak scaling); no
-collective touches the data path, only the timing max over ranks.
+Also reported: per-solve latency (p50 / p99 of helm_solve calls on a resident factor, one
+right-hand side per frequency and the full 64), the bilevel-hypergradient step of the
+FWI-step geometry (128 x 128, omega in {5, 10, 15}, 16 sources, 32 receivers, ten PCG
+iterations) and a short solve-server session (Poisson arrivals, 64^2 .. 256^2, FP64 and
+mixed).
+
+Multi-GPU (torchrun): every rank solves its own velocity model (weak scaling); no collective
+touches the data path, only the timing max over ranks and the solve count.
 """
 from __future__ import annotations
 
@@ -30,50 +37,79 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-N_GRID = 128
-N_CG = 10
 METRIC = "Helmholtz RHS-solves/sec at 1e-8 rel. error (mixed vs FP64 GPU); p50/p99 solve latency"
 UNIT = "RHS-solves/s"
-WORKLOAD = "hypergrad_step_128: 128x128, omega {5,10,15}, 16 sources, 32 receivers, N_CG=10"
+N_GRID = 256
+REFINE_RTOL = 1e-10
+SAMPLE_COLS = (0, 21, 42, 63)   # right-hand sides compared with the oracle, every frequency
 
-# FP32 SIMT peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
+# FP32 SIMT peak of GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x
+# 2.07 GHz (the peak of the CUDA-core line factor, which issues no tensor instructions)
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 nominal of GB300 (vendor figure; the measured cuBLAS DGEMM reached 1.05)
-FP64_ALU_TFLOPS = 1.25
-# DRAM bytes (read + write) per launch from an ncu capture of the same kernel build, on this
-# workload (profiles/line_sweep_fp32_hypergrad_step_128.md); absent: not captured for the
-# current kernel.
-NCU_TRAFFIC_PER_LAUNCH: dict[str, float] = {"line_sweep_fp32": 56.67e6 + 0.75e6}
 
 
 def workload(rank=0, n=N_GRID):
     import workloads as W
-    return W.config_hyper_step(n, seed=2 + rank)
+    return W.config_mixed(n, seed=3 + rank)
+
+
+def workload_desc(w):
+    return (f"mixed_{w.nx}: {w.nx}x{w.nz}, omega {{{', '.join(f'{o:g}' for o in w.omegas)}}}, "
+            f"{w.acq.n_src} top-row point sources as right-hand sides, c in [1, 3] (GRF, l = 0.1), "
+            f"refined to 1e-10")
 
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_sample(n_cg, n=N_GRID):
-    """Time the CPU oracle on one hypergradient pass of the workload (one core)."""
+def _oracle_unit(args):
+    """One frequency of the workload on one host core: the oracle's sparse LU of A(m, w) and
+    its solve of every right-hand side.  Returns the time and the sampled columns."""
+    n, seed, q, cols = args
+    import numpy as np
+    import workloads as W
     from oracle import helmholtz as H
-    w = workload(0, n)
+    w = W.config_mixed(n, seed=seed)
     g = H.Grid(w.nx, w.nz, w.lx, w.lz)
-    H.reset_solve_counter()
+    E = H.source_vectors(g, w.acq.src_xz)
     t0 = time.perf_counter()
-    H.hypergradient(g, w.m, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz, w.alpha, w.alpha, w.mu,
-                    cg_fixed_iters=n_cg)
+    X = H.Factor(H.helmholtz_matrix(g, w.m, w.omegas[q])).solve(E)
     dt = time.perf_counter() - t0
-    return {"solves": H.SOLVE_COUNTER["solves"], "seconds": dt}
+    return q, dt, int(E.shape[0]), np.ascontiguousarray(X[list(cols)])
 
 
-def run_oracle_subprocess(n_cg, reps=1, n=N_GRID):
+def oracle_pool_run(n, seed, reps, out_npy=None):
+    """`reps` runs of the whole workload by the oracle: the frequencies are independent units,
+    spread over a process pool of the allowed host cores (one thread each)."""
+    import multiprocessing as mp
+    import numpy as np
+    import workloads as W
+    n_om = len(W.config_mixed(n, seed=seed).omegas)
+    cores = len(os.sched_getaffinity(0))
+    procs = max(1, min(n_om, cores))
+    recs = []
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for r in range(reps):
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_unit, [(n, seed, q, SAMPLE_COLS) for q in range(n_om)])
+            wall = time.perf_counter() - t0
+            solves = sum(x[2] for x in res)
+            recs.append({"seconds": wall, "solves": solves, "cpu_seconds": sum(x[1] for x in res),
+                         "procs": procs, "cores_allowed": cores})
+            if out_npy and r == reps - 1:
+                cols = np.stack([x[3] for x in sorted(res, key=lambda x: x[0])])   # [n_omega][len(SAMPLE_COLS)][N]
+                np.save(out_npy, cols)
+    return recs
+
+
+def run_oracle_subprocess(n, seed, reps, out_npy=None):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_cg), "--oracle-reps", str(reps),
-           "--n", str(n)]
-    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=900)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-run", str(reps), "--n", str(n), "--seed", str(seed)]
+    if out_npy:
+        cmd += ["--oracle-out", out_npy]
+    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1800)
     if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return [json.loads(l) for l in r.stdout.strip().splitlines() if l.startswith("{")]
 
 
@@ -132,12 +168,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- roofline
 
-def kernel_cost(name, w, n_cols_per_solve):
-    """Algorithmic (flops, bytes) of one launch of `name` in this workload.
-    n_cols_per_solve = n_omega * n_src right-hand sides per solve batch."""
-    nx, nz = w.nx, w.nz
-    n_sys = len(w.omegas)
-    nrhs = n_cols_per_solve // n_sys
+def kernel_cost(name, nx, nz, n_sys, nrhs):
+    """Algorithmic (flops, bytes) of one launch of `name` that covers n_sys systems of nrhs
+    right-hand sides each (one factor launch covers every frequency of an operator)."""
     N = nx * nz
     if name.startswith("line_sweep"):
         esz = 8 if name.endswith("fp32") else 16
@@ -157,69 +190,54 @@ def kernel_cost(name, w, n_cols_per_solve):
     return None, None
 
 
-def roofline(name, trace, breakdown, w, peaks, prec):
+def roofline(name, trace, breakdown, dims, peaks):
     """name: the dominant kernel; trace: the timed region's trace (that kernel timed on every
     launch); breakdown: one fully traced step outside the timed region (for the share)."""
-    cols = len(w.omegas) * w.acq.n_src
     st = trace.get(name)
     if not st or st["timed"] == 0:
         return None
     avg_s = st["total_ms"] / st["timed"] / 1e3
-    flops, byts = kernel_cost(name, w, cols)
+    flops, byts = kernel_cost(name, *dims)
     total_ms = sum(v["total_ms"] for v in breakdown.values())
-    st = dict(st, total_ms=breakdown[name]["total_ms"])
-    out = {"kernel": name, "share": st["total_ms"] / total_ms if total_ms else None,
-           "avg_launch_us": avg_s * 1e6, "launches": st["timed"]}
-    traffic = NCU_TRAFFIC_PER_LAUNCH.get(name)
-    if name.startswith("line_sweep") and byts is not None:
-        # the solve phase streams the factor: HBM-bound at these right-hand-side counts (its
-        # intensity, about nrhs/2 flop per byte, is far below the tensor ridge)
-        ach = byts / avg_s / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": traffic,
-                    "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else
-                                    "fallback 6800 GB/s"),
-                    "algorithmic_bytes_per_launch": byts, "algorithmic_flops_per_launch": flops,
-                    "useful_tflops": flops / avg_s / 1e12})
-    elif flops is not None and name.startswith("line_factor"):
-        fp32 = name.endswith("fp32")
-        peak = FP32_ALU_TFLOPS if fp32 else FP64_ALU_TFLOPS
+    out = {"kernel": name, "share": breakdown[name]["total_ms"] / total_ms if total_ms else None,
+           "avg_launch_us": avg_s * 1e6, "launches": st["timed"],
+           # DRAM bytes of this kernel come from ncu captures committed beside the code; the bench
+           # does not run under a profiler, so the live line carries none
+           "traffic": None}
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6800 GB/s (of fallback)"
+    if name.startswith("line_factor") and flops is not None:
         ach = flops / avg_s / 1e12
-        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": traffic,
-                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if fp32 else
-                                    "nominal GB300 FP64 1.25 TFLOP/s"),
+        out.update({"bound": "alu", "achieved": ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_ALU_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                     "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": byts})
     elif byts is not None:
         ach = byts / avg_s / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
+        peak = hbm or 6800.0
         out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                    "algorithmic_bytes_per_launch": byts})
+                    "peak_source": hbm_src, "algorithmic_bytes_per_launch": byts})
+        if flops is not None:
+            out.update({"algorithmic_flops_per_launch": flops, "useful_tflops": flops / avg_s / 1e12})
     return out
 
 
-# ------------------------------------------------------------------------ main
+# --------------------------------------------------------------- solve server
 
-def server_session(args):
-    """Solve-server load (include/helm_server.h): a capacity run (all requests queued at
-    once), then Poisson arrivals at 50 / 80 / 95 % of that capacity.  Requests: grids of the
-    given sizes, 1..128 right-hand sides, 16 fixed frequencies per model in [5, 60], FP64 or
-    mixed (workloads.server_requests).  Latency = submission -> X on the host, from the
-    library.  Prints one JSON line."""
+def server_run(sizes, n_cap, seconds, loads):
+    """Solve-server load (include/helm_server.h): a capacity run (n_cap requests queued at
+    once), then Poisson arrivals at the given fractions of that capacity.  Requests: grids of
+    the given sizes, 1..128 right-hand sides, 16 fixed frequencies per model in [5, 60], FP64
+    or mixed (workloads.server_requests).  Latency = submission -> X on the host, from the
+    library."""
     import queue
     import threading
-    import time
 
     import numpy as np
     import torch
     import workloads as W
     from paper_2301_10762_gb300 import helm as hm
 
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a GPU (the library has no CPU path)")
-    sizes = [int(x) for x in args.server_sizes.split(",")]
     cfg = W.config_server(seed=5, sizes=sizes)
     srv = hm.Server()   # 180 GiB budget, batches of up to 128 right-hand sides, 8 workers
     ids = {}
@@ -274,53 +292,101 @@ def server_session(args):
                 "errors": sum(1 for d in done if "error" in d),
                 "max_relres": float(max(d["max_relres"] for d in done))}
 
-    cap_reqs = W.server_requests(cfg, args.server_requests, seed=50)
+    cap_reqs = W.server_requests(cfg, n_cap, seed=50)
     cap = run(cap_reqs, np.zeros(len(cap_reqs)))
     sessions = []
-    for j, load in enumerate((0.5, 0.8, 0.95)):
+    for j, load in enumerate(loads):
         rate = load * cap["requests_per_s"]
-        count = max(1, int(rate * args.server_seconds))
+        count = max(1, int(rate * seconds))
         r = run(W.server_requests(cfg, count, seed=51 + j), W.poisson_arrivals(count, rate, seed=61 + j))
         r.update({"load": load, "rate_rps": rate})
         sessions.append(r)
     st = srv.stats()
     srv.close()
-    print(json.dumps({
-        "metric": "solve server: RHS-solves/s and p50/p99 request latency (arrival -> X on host) under Poisson "
-                  "arrivals",
-        "unit": "RHS-solves/s", "n_gpus": 1, "data": "synthetic (seeded Gaussian-random-field models)",
-        "config": {"workload": "solve_server", "sizes": sizes, "models_per_size": 16, "frequencies_per_model": 16,
-                   "rhs": "log-uniform 1..128", "precision": "FP64 or mixed (1/2 each), mixed refined to 1e-10",
-                   "hbm_budget_GiB": 180, "max_batch_rhs": 128, "workers": 8},
-        "capacity": cap, "sessions": sessions,
-        "server": {k: st[k] for k in ("batches", "factor_builds", "cache_hits", "evictions", "entries",
-                                      "bytes_peak", "refused")}}), flush=True)
+    return {"config": {"workload": "solve_server", "sizes": sizes, "models_per_size": 16, "frequencies_per_model": 16,
+                       "rhs": "log-uniform 1..128", "precision": "FP64 or mixed (1/2 each), mixed refined to 1e-10",
+                       "hbm_budget_GiB": 180, "max_batch_rhs": 128, "workers": 8},
+            "capacity": cap, "sessions": sessions,
+            "server": {k: st[k] for k in ("batches", "factor_builds", "cache_hits", "evictions", "entries",
+                                          "bytes_peak", "refused")}}
 
+
+def server_session(args):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (the library has no CPU path)")
+    sizes = [int(x) for x in args.server_sizes.split(",")]
+    out = server_run(sizes, args.server_requests, args.server_seconds, (0.5, 0.8, 0.95))
+    print(json.dumps(dict({"metric": "solve server: RHS-solves/s and p50/p99 request latency (arrival -> X on host) "
+                                     "under Poisson arrivals", "unit": UNIT, "n_gpus": 1,
+                           "data": "synthetic (seeded Gaussian-random-field models)"}, **out)), flush=True)
+
+
+# -------------------------------------------------------- hypergradient step
+
+def hypergrad_step(hm, torch, steps, warmup, rank):
+    """The bilevel-hypergradient pass of the FWI-step geometry (every row of the path): time
+    per step and RHS-solves per second, mixed refined to 1e-10, ten PCG iterations."""
+    import numpy as np
+    import workloads as W
+    w = W.config_hyper_step(128, seed=2 + rank)
+    grid = (w.nx, w.nz, w.lx, w.lz)
+    acq = hm.Acq(w.acq.src_xz, w.acq.rec_xz, rec_w=np.ones(w.acq.n_rec))
+    mf = torch.tensor(w.m, device="cuda")
+    mt = torch.tensor(w.m_true, device="cuda")
+
+    def step(p):
+        return hm.bilevel_hypergrad([grid], [mf], [mt], acq, w.omegas, w.alpha, w.alpha, w.mu, prec=p,
+                                    cg_fixed_iters=10, refine_rtol=REFINE_RTOL)
+
+    out = {}
+    for name, p, k in (("mixed", hm.HELM_MIXED, steps), ("fp64", hm.HELM_FP64, 1)):
+        for _ in range(warmup if p == hm.HELM_MIXED else 1):
+            step(p)
+        torch.cuda.synchronize()
+        ts, sol = [], 0
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = step(p)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            sol += o["solves"] + o["data_solves"]
+        out[name] = {"value": sol / sum(ts), "unit": UNIT, "ms_per_step": 1e3 * sum(ts) / len(ts), "steps": k,
+                     "solves_per_step": sol // k, "dpsi_dalpha": o["dpsi_dalpha"]}
+    out["workload"] = "hypergrad_step_128: 128x128, omega {5,10,15}, 16 sources, 32 receivers, N_CG=10"
+    out["dpsi_dalpha_rel_diff_fp64_vs_mixed"] = abs(out["fp64"]["dpsi_dalpha"] - out["mixed"]["dpsi_dalpha"]) / abs(
+        out["fp64"]["dpsi_dalpha"])
+    return out
+
+
+# ------------------------------------------------------------------------ main
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--n", type=int, default=N_GRID)
-    ap.add_argument("--ncg", type=int, default=N_CG)
+    ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--server", action="store_true",
-                    help="solve-server session (Poisson arrivals) instead of the hypergradient step")
+    ap.add_argument("--no-extras", action="store_true", help="skip the hypergradient step and the server session")
+    ap.add_argument("--server", action="store_true", help="long solve-server session instead of the solve step")
     ap.add_argument("--server-sizes", default="64,128,256")
     ap.add_argument("--server-seconds", type=float, default=10.0)
     ap.add_argument("--server-requests", type=int, default=200, help="requests of the capacity run")
-    ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--oracle-reps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-run", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
-    if args.oracle_sample is not None:
-        for _ in range(args.oracle_reps):
-            print(json.dumps(oracle_sample(args.oracle_sample, args.n)), flush=True)
+    if args.oracle_run is not None:
+        for r in oracle_pool_run(args.n, args.seed, args.oracle_run, args.oracle_out):
+            print(json.dumps(r), flush=True)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -352,29 +418,38 @@ def main():
     if os.path.exists(pp):
         peaks = json.load(open(pp))
 
-    w = workload(rank, args.n)
-    grid = (w.nx, w.nz, w.lx, w.lz)
-    acq = hm.Acq(w.acq.src_xz, w.acq.rec_xz, rec_w=np.ones(w.acq.n_rec))
-    mf = torch.tensor(w.m, device="cuda")
-    mt = torch.tensor(w.m_true, device="cuda")
+    seed = args.seed + rank
+    w = workload(rank, args.n) if args.seed == 3 else __import__("workloads").config_mixed(args.n, seed=seed)
+    n_om, ns, N = len(w.omegas), w.acq.n_src, w.n_nodes
+    acq = hm.Acq.from_workload(w.acq)
+    m_dev = torch.tensor(w.m, device="cuda")
     prec = hm.HELM_MIXED if args.prec == "mixed" else hm.HELM_FP64
+    B = torch.empty((n_om, ns, N), dtype=torch.complex128, device="cuda")
+    X = torch.empty_like(B)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(m_f, m_t, p=prec):
-        return hm.bilevel_hypergrad([grid], [m_f], [m_t], acq, w.omegas, w.alpha, w.alpha, w.mu, prec=p,
-                                    cg_fixed_iters=args.ncg, refine_rtol=1e-10)
+    def step(p, ev=None, m=m_dev):
+        """assemble + factor + sources + refined solve of all columns; ev: events after the factor"""
+        op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, m, w.omegas)
+        f = hm.helm_factor(op, p)
+        if ev is not None:
+            ev.record()
+        hm.helm_sources(op, acq, B)
+        _, info = hm.helm_solve(f, B, X, rtol=REFINE_RTOL, max_iter=40)
+        f.close()
+        op.close()
+        return info
 
     for _ in range(args.warmup):
-        out = step(mf, mt)
+        step(prec)
     torch.cuda.synchronize()
 
     # ---- one fully traced step (outside the timed region): per-kernel device times, and the
-    # dominant kernel, which alone is timed launch by launch inside the timed region (timing
-    # every launch adds two event records per launch to the host's critical path)
+    # dominant kernel, which alone is timed launch by launch inside the timed region
     hm.helm_trace_reset()
     hm.helm_trace_select(None)
     hm.helm_trace_enable(True)
-    step(mf, mt)
+    step(prec)
     hm.helm_trace_enable(False)
     breakdown = hm.helm_trace_read()
     dominant = max(breakdown.items(), key=lambda kv: kv[1]["total_ms"])[0]
@@ -389,17 +464,17 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     launches0 = hm.helm_launch_count()
-    times, solves = [], 0
+    times, fac_times, iters = [], [], []
     for _ in range(args.steps):
         flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, ef, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
-        out = step(mf, mt)
+        info = step(prec, ef)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-        solves += out["solves"] + out["data_solves"]
+        fac_times.append(e0.elapsed_time(ef) / 1e3)
+        iters.append(info["iters"])
     torch.cuda.synchronize()
     launches = hm.helm_launch_count() - launches0
     clocks = sampler.stop()
@@ -407,6 +482,7 @@ def main():
     trace = hm.helm_trace_read()
     hm.helm_trace_select(None)
     total = sum(times)
+    solves = args.steps * n_om * ns
     if dist:
         t = torch.tensor([total, float(solves)], device="cuda", dtype=torch.float64)
         tmax = t.clone()
@@ -416,77 +492,132 @@ def main():
     else:
         all_solves = float(solves)
     value = all_solves / total
-    per_step_solves = solves / args.steps
-    lat = sorted(times)
+    X_mixed_sample = X[:, list(SAMPLE_COLS)].cpu().numpy()
 
-    # ---- end to end through the public call with host buffers (H2D + D2H in the region)
+    # ---- end to end through the public calls with host buffers: the model from pinned host
+    # memory to the device, the point sources formed from host positions, every solution
+    # column back to pinned host memory, all inside the timed region
     e2e = None
     if not args.no_e2e:
-        mf_h = torch.tensor(w.m).pin_memory()
-        mt_h = torch.tensor(w.m_true).pin_memory()
-        mf_d = torch.empty_like(mf)
-        mt_d = torch.empty_like(mt)
-        et, es = [], 0
+        m_h = torch.tensor(w.m).pin_memory()
+        X_h = torch.empty(X.shape, dtype=X.dtype).pin_memory()
+        m_d = torch.empty_like(m_dev)
+        et = []
         for it in range(args.warmup + max(1, args.steps)):   # the first W untimed, as in the main loop
             flush.fill_(2.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            mf_d.copy_(mf_h, non_blocking=True)
-            mt_d.copy_(mt_h, non_blocking=True)
-            o = step(mf_d, mt_d)           # results come back to host inside the call
+            m_d.copy_(m_h, non_blocking=True)
+            step(prec, m=m_d)
+            X_h.copy_(X, non_blocking=True)
             e1.record()
             e1.synchronize()
             if it >= args.warmup:
                 et.append(e0.elapsed_time(e1) / 1e3)
-                es += o["solves"] + o["data_solves"]
-        e2e = {"value": es / sum(et), "unit": UNIT, "h2d_bytes_per_step": 2 * w.n_nodes * 8,
-               "d2h_bytes_per_step": (2 + 3 * w.acq.n_rec) * 8}
+        e2e = {"value": len(et) * n_om * ns / sum(et), "unit": UNIT, "ms_per_step": 1e3 * sum(et) / len(et),
+               "h2d_bytes_per_step": N * 8 + ns * 2 * 8 + w.acq.n_rec * 3 * 8,
+               "d2h_bytes_per_step": X.numel() * 16}
 
-    # ---- FP64 GPU path on the same workload (the comparison the metric names)
+    # ---- FP64 GPU path on the same step (the comparison the metric names)
     fp64 = None
+    X_fp64_sample = None
     if not args.no_fp64_compare and prec == hm.HELM_MIXED:
-        step(mf, mt, hm.HELM_FP64)
+        step(hm.HELM_FP64)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        e0, ef, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
-        o = step(mf, mt, hm.HELM_FP64)
+        step(hm.HELM_FP64, ef)
         e1.record()
         e1.synchronize()
         dt = e0.elapsed_time(e1) / 1e3
-        fp64 = {"value": (o["solves"] + o["data_solves"]) / dt, "ms_per_step": dt * 1e3,
-                "dpsi_dalpha_rel_diff_vs_mixed": abs(o["dpsi_dalpha"] - out["dpsi_dalpha"]) / abs(o["dpsi_dalpha"])}
+        X_fp64_sample = X[:, list(SAMPLE_COLS)].cpu().numpy()
+        fp64 = {"value": n_om * ns / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+                "factor_ms": e0.elapsed_time(ef), "solve_ms": ef.elapsed_time(e1),
+                "mixed_speedup": value / world / (n_om * ns / dt)}
 
-    rl = roofline(dominant, trace, breakdown, w, peaks, args.prec)
+    # ---- per-solve latency on a resident factor: one right-hand side per frequency, and all
+    latency = {}
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, m_dev, w.omegas)
+    hm.helm_sources(op, acq, B)
+    for name, p in (("mixed", hm.HELM_MIXED), ("fp64", hm.HELM_FP64)):
+        f = hm.helm_factor(op, p)
+        for nr, reps in ((1, 30), (ns, 10)):
+            Bs = B[:, :nr].contiguous()
+            Xs = torch.empty_like(Bs)
+            hm.helm_solve(f, Bs, Xs, rtol=REFINE_RTOL, max_iter=40)
+            lat = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                hm.helm_solve(f, Bs, Xs, rtol=REFINE_RTOL, max_iter=40)
+                e1.record()
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+            latency[f"{name}_{nr}rhs"] = {"p50_ms": float(np.percentile(lat, 50)),
+                                          "p99_ms": float(np.percentile(lat, 99)), "calls": reps,
+                                          "columns_per_call": nr * n_om}
+        f.close()
+    op.close()
+
+    rl = roofline(dominant, trace, breakdown, (w.nx, w.nz, n_om, ns), peaks)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["hypergrad_step_128"] = hypergrad_step(hm, torch, 10, args.warmup, rank)
+        try:
+            extras["server"] = server_run([64, 128, 256], 40, 3.0, (0.8,))
+        except Exception as e:  # keep the main line if the session fails
+            extras["server"] = {"failed": str(e)[:300]}
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            r = run_oracle_subprocess(args.ncg, 1, args.n)[0]
-            cpu = {"value": r["solves"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"one full step of the workload ({r['solves']} solves, {r['seconds']:.1f} s) by the "
-                             f"FP64 CPU oracle (SuperLU sparse LU), one thread"}
+            fd, npy = tempfile.mkstemp(suffix=".npy")
+            os.close(fd)
+            r = run_oracle_subprocess(args.n, seed, 1, npy)[0]
+            ref = np.load(npy)
+            os.unlink(npy)
+            cpu = {"value": r["solves"] / r["seconds"], "unit": UNIT, "cores": r["procs"], "kind": "oracle",
+                   "cores_allowed": r["cores_allowed"],
+                   "sample": f"the whole workload ({r['solves']} right-hand sides, {n_om} factors) by the FP64 CPU "
+                             f"oracle (SciPy SuperLU), one frequency per process on {r['procs']} processes, "
+                             f"{r['seconds']:.1f} s wall, {r['cpu_seconds']:.1f} s CPU"}
+
+            def per_omega(Xs):
+                e = np.linalg.norm(Xs - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+                return [float(v) for v in e.max(axis=1)]
+            errors = {"columns": list(SAMPLE_COLS), "metric": "max over the sampled columns of ||x - x_oracle|| / "
+                                                              "||x_oracle||, per frequency",
+                      "mixed": per_omega(X_mixed_sample)}
+            if X_fp64_sample is not None:
+                errors["fp64"] = per_omega(X_fp64_sample)
         except Exception as e:  # keep the GPU line even if the host leg fails
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:200]}
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"[:300]}
 
     if rank == 0:
+        lat_steps = sorted(times)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if args.prec == "mixed" else "f64",
-            "data": "synthetic (seeded Gaussian-random-field training model; Marmousi not available)",
-            "config": {"workload": WORKLOAD, "precision": args.prec, "solves_per_step": per_step_solves,
-                       "cg_iterations": args.ncg, "refine_rtol": 1e-10, "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"one training model per GPU x{world}"},
-            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "per": "hypergradient step"},
-            "solve_latency_us": {"mean_per_rhs": 1e6 * total / max(1.0, all_solves / world)},
+            "data": "synthetic (seeded Gaussian-random-field velocity; Marmousi not available)",
+            "config": {"workload": workload_desc(w), "precision": args.prec, "solves_per_step": n_om * ns,
+                       "refine_rtol": REFINE_RTOL, "factor_included": True,
+                       "l2": "flushed between steps (256 MB write); the factors (1.1 GB) exceed L2",
+                       "parallelism": f"one velocity model per GPU x{world}"},
+            "phase_ms": {"factor": 1e3 * statistics.median(fac_times),
+                         "solve": 1e3 * statistics.median([t - f for t, f in zip(times, fac_times)]),
+                         "refinement_sweeps": max(iters)},
+            "latency_ms": {"per": "helm_solve call on a resident factor (columns_per_call columns)", **latency,
+                           "step_p50": 1e3 * lat_steps[len(lat_steps) // 2],
+                           "step_p99": 1e3 * lat_steps[min(len(lat_steps) - 1, int(0.99 * len(lat_steps)))]},
+            "error_vs_oracle": errors,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": rl, "cpu_baseline": cpu,
             "fp64_gpu": fp64,
-            # one fully traced step outside the timed region (every launch bracketed by events)
             "kernels_one_step": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}
                                  for k, v in breakdown.items()},
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -495,25 +626,28 @@ def main():
 
 
 def reference_arm(args, world, rank):
-    """The CPU oracle timed as the reference arm: every step is a bounded sample of the
-    workload (one hypergradient pass with 2 PCG iterations, one core)."""
+    """The CPU oracle timed as the reference arm on the same workload: every step is the whole
+    workload (every frequency factored, every right-hand side solved), one frequency per
+    process of a pool over the allowed host cores."""
     if rank != 0:
         return
-    n_cg = 2
-    recs = run_oracle_subprocess(n_cg, args.warmup + args.steps, args.n)
+    recs = run_oracle_subprocess(args.n, args.seed, args.warmup + args.steps)
     timed = recs[args.warmup:]
     tot = sum(r["seconds"] for r in timed)
     sol = sum(r["solves"] for r in timed)
     value = sol / tot
+    import workloads as W
+    w = W.config_mixed(args.n, seed=args.seed)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Gaussian-random-field training model; Marmousi not available)",
-        "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "sample": f"N_CG={n_cg} per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed steps, each one hypergradient pass with {n_cg} PCG "
-                                   f"iterations ({timed[0]['solves']} solves), one thread"},
+        "data": "synthetic (seeded Gaussian-random-field velocity; Marmousi not available)",
+        "config": {"workload": workload_desc(w), "precision": "fp64 oracle (SciPy SuperLU)",
+                   "solves_per_step": timed[0]["solves"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": timed[0]["procs"], "kind": "oracle",
+                         "sample": f"{args.steps} timed steps, each the whole workload, one frequency per process on "
+                                   f"{timed[0]['procs']} processes ({timed[0]['cores_allowed']} cores allowed)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

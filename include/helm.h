@@ -22,8 +22,11 @@
  *     host memory owned by the caller.  Opaque handles (helm_op_t, helm_factor_t) and
  *     the HBM behind them are owned by the library and released by helm_*_destroy.
  *   - every call is asynchronous on the stream given to helm_assemble, except where a
- *     result is returned through a host pointer (that call synchronises the stream).
+ *     result is returned through a host pointer (that call synchronises the stream) and
+ *     helm_solve / helm_adjoint_solve, which synchronise it to report the device status.
  *     A handle must not be used from two host threads or two streams at once.
+ *   - a handle belongs to the device that was current at helm_assemble; make that device
+ *     current for every later call on it (helm_solve_noalloc selects it itself).
  *   - no entry point aborts, exits or throws; each returns a helm_status.
  */
 #ifndef HELM_H
@@ -122,10 +125,20 @@ void helm_op_destroy(helm_op_t *op);
  * Each S_i is inverted by block Gauss-Jordan over 16-column blocks; a 16 x 16 pivot block
  * is inverted by Newton-Schulz iteration seeded with the same block's inverse on the
  * previous line, or by Gauss-Jordan with partial pivoting where that seed is not close
- * enough.  Errors: ESINGULAR (zero / non-finite pivot), ENOMEM, ECUDA.
+ * enough.  Errors: ESINGULAR (zero / non-finite pivot), ETIMEOUT (a bounded device-side
+ * wait gave up), ENOMEM, ECUDA.
  * The factor keeps a reference to op: destroy the factor before the op. */
 helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out);
 void helm_factor_destroy(helm_factor_t *f);
+
+/* helm_set_wait_tries -- diagnostic setting (no counterpart in the paper): the number of
+ * times a bounded device-side wait of the line factor and sweep kernels polls its barrier
+ * before it gives up, for launches made after the call.  tries < 0 restores the default
+ * (2^22 polls, each suspended for a hardware time limit: seconds at worst); 0 gives up at
+ * the first wait that is not already complete.  A kernel that gives up stops all CTAs of its
+ * cluster, leaves its outputs incomplete and the call returns HELM_ETIMEOUT; the context stays
+ * usable and the next call starts clean.  Process-wide; meant for tests of that error path. */
+void helm_set_wait_tries(int64_t tries);
 
 /* helm_factor_fp64_blocks -- HELM_MIXED: number of 16 x 16 pivot blocks of the factor that
  * were flagged and inverted in FP64.  A block is flagged when its FP32 Gauss-Jordan inverse X
@@ -138,9 +151,11 @@ int32_t helm_factor_fp64_blocks(const helm_factor_t *f);
 /* helm_solve -- X = A(m, w_q)^{-1} B for every frequency q and column (Eq. (defu)
  * discretised: u = A^{-1} e_s).  B_dev, X_dev: [n_omega][nrhs][N] complex (device);
  * they may not alias.  rtol / max_iter drive the refinement of HELM_MIXED (ignored by
- * HELM_FP64 except that info->max_relres is computed when info != NULL).
+ * HELM_FP64 except that info->max_relres is computed when info != NULL).  The call
+ * synchronises the op's stream.
  * Errors: EINVAL, ENOCONV (mixed: max_iter reached above rtol; X holds the last
- * iterate), ECUDA. */
+ * iterate), ETIMEOUT (a bounded device-side wait of a sweep gave up; X is incomplete),
+ * ECUDA. */
 helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
                        double rtol, int32_t max_iter, helm_solve_info *info);
 
@@ -161,8 +176,10 @@ helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *
  * line vectors, per-column norms, the refinement's stopping state) lives in one fixed 32 MiB array in device global memory
  * that every GPU loading the library holds until exit; the caller still passes B_dev and
  * X_dev.  Limits: n_omega * nrhs * N * 64 bytes (mixed; norms only for FP64) within 32 MiB and at most
- * 16384 columns, else HELM_EINVAL.  The first call on a device resolves the array's
- * device address with that device current: make it before any stream capture.  Calls
+ * 16384 columns, else HELM_EINVAL.  The call makes the op's device (the one current at
+ * helm_assemble) current while it runs and restores the caller's device before returning.
+ * The first call on a device resolves the array's device address with that device
+ * current: make it before any stream capture.  Calls
  * share the array (each clears what must start at zero); calls that overlap on the GPU
  * race and must be serialised by the caller.  Other arguments and errors as helm_solve. */
 helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
@@ -243,11 +260,13 @@ helm_status fwi_hessian_vec(helm_factor_t *f, const helm_acq *acq, const helm_c1
  *   dpsi/dp_{j,l} = 1/N_m' sum_{m',s,w} w_j^2 Re[conj((dR_l tau)_j)(R(u-u'))_j
  *                                              + conj((R tau)_j)(dR_l(u-u'))_j],
  *   dpsi/dw_j = -1/N_m' sum 2 w_j Re[conj((R tau)_j)(R(u'-u))_j].
- *   grids[n_models], m_fwi[n_models], m_true[n_models]: per model (device vectors of
- *   length nx*nz of that model's grid); acq and omega are shared by all models.
+ *   grids[n_models], m_fwi[n_models], m_true[n_models], acq[n_models]: per model (device
+ *   vectors of length nx*nz of that model's grid; each model's own sources, and receivers in
+ *   the same number for all models, since dpsi_dp and dpsi_dw are per receiver); omega is
+ *   shared by all models.
  *   Outputs are host scalars / arrays (the call synchronises).  dpsi_dw may be NULL. */
 helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grids, const double *const *m_fwi,
-                              const double *const *m_true, const helm_acq *acq,
+                              const double *const *m_true, const helm_acq *acq /* [n_models] */,
                               const double *omega, int32_t n_omega, double alpha, double alpha0,
                               double mu, helm_prec prec, const helm_pcg_opts *pcg, void *stream,
                               double *psi, double *dpsi_dalpha, double *dpsi_dp, double *dpsi_dw,

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
 #include <mutex>
 #include "helm.h"
 #include "kernels.h"
@@ -38,6 +39,15 @@ extern "C" const char *helm_status_string(helm_status s) {
 }
 
 extern "C" const char *helm_last_error(void) { return g_last_error.c_str(); }
+
+static std::atomic<int64_t> g_wait_tries{-1};
+
+uint32_t helm::wait_tries() {
+    const int64_t v = g_wait_tries.load(std::memory_order_relaxed);
+    return v < 0 ? kDefaultWaitTries : (uint32_t)std::min<int64_t>(v, 0xffffffffLL);
+}
+
+extern "C" void helm_set_wait_tries(int64_t tries) { g_wait_tries.store(tries < 0 ? -1 : tries); }
 
 void keep_pool_memory() {
     static std::once_flag once;
@@ -91,6 +101,12 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     op->n_omega = n_omega;
     op->omega.assign(omega, omega + n_omega);
     op->st = (cudaStream_t)stream;
+    if (cudaGetDevice(&op->dev) != cudaSuccess) {
+        cudaGetLastError();
+        helm_set_msg("helm_assemble: cudaGetDevice failed");
+        delete op;
+        return HELM_ECUDA;
+    }
     const size_t N = (size_t)grid->nx * grid->nz;
     helm_status s;
     if ((s = dev_alloc((void **)&op->m, N * sizeof(double), "allocate(m)", op->st)) != HELM_OK ||
@@ -170,6 +186,11 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t 
         helm_set_error("helm_factor: launch", e);
         helm_factor_destroy(f);
         return HELM_ECUDA;
+    }
+    if (st_host[0] & ST_TIMEOUT) {
+        helm_set_msg("helm_factor: a factor kernel gave up waiting for its cluster");
+        helm_factor_destroy(f);
+        return HELM_ETIMEOUT;
     }
     if (st_host[0] & ST_SINGULAR) {
         helm_set_msg("helm_factor: zero or non-finite pivot");
@@ -328,6 +349,15 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     return HELM_OK;
 }
 
+helm_status read_sweep_status(const helm_op *op) {
+    int st_host = 0;
+    cudaError_t e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) { helm_set_error("solve status", e); return HELM_ECUDA; }
+    if (st_host & ST_TIMEOUT) { helm_set_msg("a sweep kernel gave up waiting for its cluster"); return HELM_ETIMEOUT; }
+    return HELM_OK;
+}
+
 helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
                        helm_solve_info *info, int conj) {
     const helm_op *op = f->op;
@@ -338,10 +368,16 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     cudaError_t e;
     helm_status s;
     if (info) { info->iters = 0; info->max_relres = -1.0; }
+    // the status bits report this solve only (a give-up of an earlier call does not stick)
+    if ((e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess) {
+        helm_set_error("solve: clear status", e);
+        return HELM_ECUDA;
+    }
     if (f->prec == HELM_FP64) {
         e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, rchunk, op->status, op->st,
                                       f->mid);
         if (e != cudaSuccess) { helm_set_error("sweep fp64", e); return HELM_ECUDA; }
+        if ((s = read_sweep_status(op)) != HELM_OK) return s;
         if (info) {
             info->iters = 1;
             if ((s = factor_reserve(f, nrhs)) != HELM_OK) return s;
@@ -358,11 +394,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
     double rel = INFINITY;
     if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;
     if (info) { info->iters = it; info->max_relres = rel; }
-    int st_host = 0;
-    e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
-    if (e != cudaSuccess) { helm_set_error("solve status", e); return HELM_ECUDA; }
-    if (st_host & ST_TIMEOUT) { helm_set_msg("a sweep kernel gave up waiting for its cluster"); return HELM_ETIMEOUT; }
+    if ((s = read_sweep_status(op)) != HELM_OK) return s;
     if (!(rel <= rtol)) { helm_set_msg("refinement did not reach rtol"); return HELM_ENOCONV; }
     return HELM_OK;
 }

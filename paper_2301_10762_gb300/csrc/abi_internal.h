@@ -18,6 +18,7 @@ struct helm_op {
     double2 *gpk = nullptr;       // [n_omega][N] g'_k(w) = -i w b_k / (4 m_k^{3/2})
     int *status = nullptr;        // device status word
     cudaStream_t st = nullptr;
+    int dev = 0;                  // device that was current at helm_assemble (owns every buffer)
 };
 
 namespace helm {
@@ -70,6 +71,9 @@ helm_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st)
 void dev_free(void *p, cudaStream_t st);
 void keep_pool_memory();
 helm_status factor_reserve(helm_factor_t *f, int nrhs);
+// status bits of the op after its sweeps (synchronises the op's stream): HELM_ETIMEOUT if a
+// bounded wait of a sweep gave up
+helm_status read_sweep_status(const helm_op *op);
 helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
                        helm_solve_info *info, int conj);
 // mixed-precision refinement (refine.cu kernels) to ||b - A x|| / ||b|| <= rtol per column

@@ -141,6 +141,42 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// bounded wait that also gives up as soon as the CTA's abort word is set (by this CTA or,
+// remotely, by another CTA of the cluster that gave up first)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, uint32_t max_tries,
+                                                   const int *abort_word) {
+    for (uint32_t t = 0; t < max_tries; ++t) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(const volatile int *)abort_word) return false;
+    }
+    return false;
+}
+// Abort protocol of the cluster kernels.  A CTA whose bounded wait gives up sets the abort word
+// (a __shared__ int at the same offset in every CTA) in every CTA of its cluster, so that the
+// others stop waiting and stop producing.  No CTA leaves before the final cluster barrier,
+// which every CTA reaches in bounded time since every wait is bounded; after it a CTA whose
+// abort word is set waits a fixed drain time, so that asynchronous stores and bulk copies that
+// peers issued before they saw the word land in (or finish reading) shared memory that is still
+// alive.
+__device__ __forceinline__ void cluster_abort_broadcast(int *abort_word, unsigned cluster_ctas) {
+    const uint32_t a = smem_u32(abort_word);
+    for (unsigned r = 0; r < cluster_ctas; ++r)
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(mapa_u32(a, r)), "r"(1) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr uint64_t kAbortDrainNs = 50000;   // 50 us: far beyond the latency of an in-flight copy
+__device__ __forceinline__ void abort_drain() {
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < kAbortDrainNs) __nanosleep(1000);
+}
+// default try count of the bounded mbarrier waits (each try suspends for a hardware time
+// limit, so this is seconds at worst); helm_set_wait_tries overrides it for later launches
+constexpr uint32_t kDefaultWaitTries = 1u << 22;
+uint32_t wait_tries();   // host: the try count the next launches take
 // asynchronous store into another CTA's shared memory that completes `bytes` of the
 // transaction count of the mbarrier at remote shared address `rbar`
 __device__ __forceinline__ void st_async(uint32_t raddr, float2 v, uint32_t rbar) {

@@ -43,6 +43,7 @@ template <typename T> struct FactorArgs {
     int mid;              // middle line of the twisted factorisation (nx - 1: one-sided)
     float flag_tol;       // complex FP32: a Gauss-Jordan pivot inverse with max |I - M X| above
                           // this is redone in FP64 (status[1] counts those blocks)
+    uint32_t tries;       // polls of a bounded mbarrier wait before it gives up
 };
 
 // In-place Gauss-Jordan inversion of the kb x kb block M (row stride NB, shared memory)
@@ -276,8 +277,11 @@ __device__ bool warp_invert16(const cx_t<T> *M, int ld, int kb, cx_t<T> *P) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const float mag = fminf((float)(a[q].x * a[q].x + a[q].y * a[q].y), 3.0e38f);
-        const unsigned key =
-            (h == 0 && !((used >> r) & 1u)) ? ((__float_as_uint(mag) & ~0xFu) | (unsigned)(15 - r)) : 0u;
+        const bool cand = h == 0 && !((used >> r) & 1u);
+        // a non-finite entry among the pivot candidates (a NaN or infinite input, or a blow-up
+        // of the line recurrence) fails the inversion like a zero pivot
+        if (__any_sync(0xffffffffu, cand && !(isfinite(a[q].x) && isfinite(a[q].y)))) ok = false;
+        const unsigned key = cand ? ((__float_as_uint(mag) & ~0xFu) | (unsigned)(15 - r)) : 0u;
         const unsigned best = __reduce_max_sync(0xffffffffu, key);
         const int p = 15 - (int)(best & 0xFu);
         if ((best >> 4) == 0u || (best >> 23) >= 255u) ok = false;
@@ -480,6 +484,8 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     const int ldr = bpc * NB + 1;
     const int m = a.mid;                      // middle line (nx - 1 without a right team)
     const int lenR = nx - 1 - m;              // lines of the right team
+    unsigned cluster_ctas;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(cluster_ctas));
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sW = reinterpret_cast<V *>(smem_raw);                  // nz x ldw   own columns of S_i / G_i
@@ -488,6 +494,7 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     const size_t recv_elems = (size_t)nz * NB + NB * NB;
     V *sR = sRecv + 2 * recv_elems;                           // NB x ldr
     __shared__ int s_bad;
+    __shared__ int s_abort;                                   // a wait of the cluster gave up
     __shared__ __align__(8) uint64_t bars[2];                 // panel arrival, one per receive buffer
     // buffer release: the other CTAs of the team arrive on the empty barrier of the CTA that
     // next writes into a receive buffer (the owner of the step two later) once they are done
@@ -510,6 +517,7 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     const int cl = tid & (NB - 1), rw = tid >> 4;   // (row group, column) of the 2D loops
     if (tid == 0) {
         s_bad = 0;
+        s_abort = 0;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init(&empty_bars[0], (uint32_t)max(cs - 1, 1));
@@ -523,6 +531,9 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
     uint32_t ph0 = 0, ph1 = 0;   // completed panel phases per receive buffer (consumer side)
     uint32_t eph0 = 0, eph1 = 0;   // completed release phases of this CTA's empty barriers (thread 0)
     bool tmo = false;              // thread 0: a wait gave up; later waits are skipped
+    // thread 0: after a give-up anywhere in the cluster it sends, expects and releases nothing
+    // more, so that no barrier sees arrivals or bytes that nobody accounts for
+    auto quiet = [&]() { return tmo || *(volatile int *)&s_abort != 0; };
     // whether this team works on a line at the given slot
     auto active_slot = [&](int sl) { return team == 0 ? sl <= m : sl < lenR; };
     int t = 0;
@@ -583,9 +594,10 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                     if (t >= 2 && cs > 1) {
                         if (tid == 0) {
                             const uint32_t par = buf ? eph1 : eph0;
-                            if (!tmo && !mbar_wait_bounded(&empty_bars[buf], par, 1u << 22)) {
+                            if (!quiet() && !mbar_wait_or_abort(&empty_bars[buf], par, a.tries, &s_abort)) {
                                 atomicOr(a.status, ST_TIMEOUT);
                                 tmo = true;
+                                if (atomicExch(&s_abort, 1) == 0) cluster_abort_broadcast(&s_abort, (unsigned)cluster_ctas);
                             }
                             if (buf) eph1 ^= 1u; else eph0 ^= 1u;
                         }
@@ -602,7 +614,7 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                             if (cl < kb) recvU[(size_t)r * NB + cl] = sW[(size_t)r * ldw + kc + cl];
                         __syncthreads();
                     }
-                    if (tid == 0) {
+                    if (tid == 0 && !quiet()) {
                         fence_proxy_async_smem();
                         const uint32_t src = smem_u32(recvU), lbar = smem_u32(&bars[buf]);
                         for (int d = 0; d < cs; ++d)
@@ -643,7 +655,7 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                         polish_inverse16(sW + (size_t)k0 * ldw + kc, ldw, kb, recvP, s_nsM, s_nsX, s_nsE);
                         if (kb == NB && bpc <= kSeedBlocks) s_seed[k - kb_lo][tid] = recvP[tid];   // next line's seed
                     }
-                    if (tid == 0) {
+                    if (tid == 0 && !quiet()) {
                         fence_proxy_async_smem();
                         const uint32_t src = smem_u32(recvP), lbar = smem_u32(&bars[buf]);
                         for (int d = 0; d < cs; ++d)
@@ -653,12 +665,13 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
                             }
                     }
                 } else {
-                    if (tid == 0) {
+                    if (tid == 0 && !quiet()) {
                         mbar_arrive_expect_tx(&bars[buf], panel_bytes);
                         const uint32_t par = buf ? ph1 : ph0;
-                        if (!tmo && !mbar_wait_bounded(&bars[buf], par, 1u << 22)) {
+                        if (!mbar_wait_or_abort(&bars[buf], par, a.tries, &s_abort)) {
                             atomicOr(a.status, ST_TIMEOUT);
                             tmo = true;
+                            if (atomicExch(&s_abort, 1) == 0) cluster_abort_broadcast(&s_abort, (unsigned)cluster_ctas);
                         }
                     }
                     if (buf) ph1 ^= 1u; else ph0 ^= 1u;
@@ -760,7 +773,7 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
             }
             __syncthreads();
             // done with this step's buffer: release it to the owner of step t + 2, its next writer
-            if (active && tid == 0 && cs > 1) {
+            if (active && tid == 0 && cs > 1 && !quiet()) {
                 const int t2 = t + 2, owner2 = (t2 % p) / bpc;
                 if (active_slot(t2 / p) && owner2 != rank)
                     mbar_arrive_remote(mapa_u32(smem_u32(&empty_bars[buf]), (uint32_t)(team * cs + owner2)));
@@ -777,8 +790,11 @@ __global__ void __launch_bounds__(FAC_THREADS, 1) line_factor_smem_kernel(Factor
         }
     }
     // no CTA leaves while the bulk-copy engine may still read its shared memory: every
-    // consumer has waited for the last panel before arriving here
+    // consumer has waited for the last panel before arriving here.  After a give-up (the
+    // waits of the cluster are skipped from then on, so every CTA reaches this barrier in
+    // bounded time) copies may still be in flight: they are drained first.
     cluster_sync_all();
+    if (*(volatile int *)&s_abort) abort_drain();
     if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
 }
 
@@ -828,7 +844,7 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
     // HELM_FACTOR_FLAG_TOL overrides the residual above which a pivot inverse is redone in FP64
     const char *env_tol = getenv("HELM_FACTOR_FLAG_TOL");
     const float flag_tol = (env_tol && *env_tol) ? (float)atof(env_tol) : 1e-4f;
-    FactorArgs<T> a{g, diag, G, xch, status, cs, mid, flag_tol};
+    FactorArgs<T> a{g, diag, G, xch, status, cs, mid, flag_tol, wait_tries()};
     const size_t smem = resident ? smem_res : factor_smem_bytes<T>(g.nz, cs);
     auto kern = resident ? line_factor_smem_kernel<T> : line_factor_kernel<T>;
     if (!resident) {

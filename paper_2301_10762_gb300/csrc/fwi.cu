@@ -941,15 +941,21 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
                                          const helm_pcg_opts *pcg, void *stream, double *psi, double *dpsi_dalpha,
                                          double *dpsi_dp, double *dpsi_dw, helm_hyper_info *info) {
     if (n_models < 1 || !grids || !m_fwi || !m_true || !acq || !omega || n_omega < 1 || !psi || !dpsi_dalpha ||
-        !dpsi_dp || acq->n_src < 1 || acq->n_rec < 1) {
+        !dpsi_dp || acq[0].n_rec < 1) {
         helm_set_msg("bilevel_hypergrad: bad arguments");
         return HELM_EINVAL;
     }
+    // one acquisition per model: its own sources, the same receivers (the design P)
+    for (int k = 0; k < n_models; ++k)
+        if (acq[k].n_src < 1 || acq[k].n_rec != acq[0].n_rec) {
+            helm_set_msg("bilevel_hypergrad: every model needs sources and the same number of receivers");
+            return HELM_EINVAL;
+        }
     keep_pool_memory();
     helm_pcg_opts po = pcg ? *pcg : helm_pcg_opts{500, 0, 1e-13, 1.0, 1e-10, 0};
     cudaStream_t st = (cudaStream_t)stream;
     if (info) *info = helm_hyper_info{0, 0.0, 0, 0, 0};
-    const int nr = acq->n_rec;
+    const int nr = acq[0].n_rec;
     // Independent training models run concurrently, each on its own streams from its own host
     // thread (the chain of one model is latency bound and leaves most of the GPU idle); every
     // model writes its own partial results, which are summed here in model order.
@@ -996,7 +1002,7 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
                 if (s == HELM_OK && e == cudaSuccess) e = cudaMemsetAsync(dw, 0, nr * sizeof(double), sw);
                 if (e != cudaSuccess) { helm_set_error("bilevel_hypergrad", e); s = HELM_ECUDA; }
                 if (s == HELM_OK)
-                    s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], acq, omega, n_omega, alpha, alpha0, mu, prec,
+                    s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], &acq[k], omega, n_omega, alpha, alpha0, mu, prec,
                                         &po, sw, 1.0 / n_models, acc, dp, dw, &infos[k]);
                 if (s == HELM_OK || s == HELM_ENOCONV) {
                     e = cudaMemcpyAsync(&acc_h[2 * (size_t)k], acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, sw);

@@ -12,6 +12,9 @@
 // below, which every GPU that loads the library holds until the process exits.
 //
 // Consequences for the caller:
+//   * the call runs with the op's device current (the device that was current at
+//     helm_assemble), whichever device the caller has made current, and restores the
+//     caller's device before it returns;
 //   * the first call on a device resolves the device address of the array
 //     (cudaGetSymbolAddress, with that device current); make that first call before
 //     any stream capture;
@@ -43,17 +46,15 @@ double g_norms_host[2 * kMaxCols];
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// device address of the array on the current device (resolved once per device)
-helm_status scratch_address(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        helm_set_error("helm_solve_noalloc: cudaGetDevice", e);
-        return HELM_ECUDA;
+// device address of the array on device `dev`, which must be current (resolved once per device)
+helm_status scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        helm_set_msg("helm_solve_noalloc: device index beyond the library's table");
+        return HELM_EINVAL;
     }
     if (!g_dev_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             helm_set_error("helm_solve_noalloc: cudaGetSymbolAddress", e);
             return HELM_ECUDA;
@@ -63,6 +64,24 @@ helm_status scratch_address(void **out) {
     *out = g_dev_addr[dev];
     return HELM_OK;
 }
+
+// makes `dev` the current device for the lifetime of the guard and restores the caller's
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    cudaError_t enter(int dev) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return e;
+        if (prev != dev) {
+            if ((e = cudaSetDevice(dev)) != cudaSuccess) return e;
+            switched = true;
+        }
+        return cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -91,17 +110,26 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
         return HELM_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_mu);
+    // every buffer of the op, its stream and the array's address belong to the device that was
+    // current at helm_assemble: the call runs with that device current, whichever is current now
+    DeviceGuard dg;
+    cudaError_t e = dg.enter(op->dev);
+    if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: select the op's device", e); return HELM_ECUDA; }
     void *base = nullptr;
-    helm_status s = scratch_address(&base);
+    helm_status s = scratch_address(op->dev, &base);
     if (s != HELM_OK) return s;
     unsigned char *p = (unsigned char *)base;
     const double2 *B = (const double2 *)B_dev;
     double2 *X = (double2 *)X_dev;
     const int conj = adjoint ? 1 : 0;
     const int rchunk = 16;
-    cudaError_t e;
     double rel = -1.0;
     int it = 1;
+    // the status bits report this call only
+    if ((e = cudaMemsetAsync(op->status, 0, sizeof(int), op->st)) != cudaSuccess) {
+        helm_set_error("helm_solve_noalloc: clear status", e);
+        return HELM_ECUDA;
+    }
     if (!mixed) {
         double *norms = (double *)p;
         e = launch_line_sweep<double>(g, n_sys, nrhs, (const double2 *)f->G, B, X, X, conj, rchunk, op->status, op->st,
@@ -125,12 +153,8 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
         w.state = (RefineState *)(p + 3 * p_bytes + 2 * v_bytes + n_bytes);
         if ((s = mixed_refine(f, nrhs, B, X, conj, rtol, max_iter, w, &it, &rel)) != HELM_OK) return s;
     }
-    int st_host = 0;
-    e = cudaMemcpyAsync(&st_host, op->status, sizeof(int), cudaMemcpyDeviceToHost, op->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
-    if (e != cudaSuccess) { helm_set_error("helm_solve_noalloc: status", e); return HELM_ECUDA; }
     if (info) { info->iters = it; info->max_relres = rel; }
-    if (st_host & ST_TIMEOUT) { helm_set_msg("a sweep kernel gave up waiting for its cluster"); return HELM_ETIMEOUT; }
+    if ((s = read_sweep_status(op)) != HELM_OK) return s;
     if (mixed && !(rel <= rtol)) { helm_set_msg("refinement did not reach rtol"); return HELM_ENOCONV; }
     return HELM_OK;
 }

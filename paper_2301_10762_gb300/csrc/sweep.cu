@@ -28,7 +28,6 @@ constexpr int SW_THREADS = 256;
 constexpr int SW_KC = 64;      // K chunk of the streamed (non-prefetched) G path
 constexpr int SW_MAXOPT = 2;   // outputs per thread (rows_per_cta * R <= 2 * 256)
 constexpr size_t SW_SMEM_MAX = 200 * 1024;
-constexpr uint32_t SW_WAIT_TRIES = 1u << 22;   // bounded mbarrier wait (seconds at worst)
 constexpr int FM_MAX_RHS = 4;   // right-hand sides per cluster up to which the FMA product is taken
 
 template <typename TG> struct SweepArgs {
@@ -42,6 +41,7 @@ template <typename TG> struct SweepArgs {
     int conj;            // FP64 path: B and X conjugated (adjoint solve)
     int *status;
     const int *skip;     // optional: nonzero -> the launch does nothing (refinement finished)
+    uint32_t tries;      // polls of a bounded mbarrier wait before it gives up
 };
 
 // Padded row stride (in complex elements) of the shared-memory operands of the sweep product.
@@ -537,9 +537,10 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             // barrier at the top of the step (the own rows come from registers); the CUDA-core
             // product also needs the slab its threads prefetched, behind the barrier below
             if (MT > 0 || tid == 0) {
-                if (!mbar_wait_bounded(bar, par, SW_WAIT_TRIES)) {
+                if (!mbar_wait_or_abort(bar, par, a.tries, &s_abort)) {
                     atomicOr(a.status, ST_TIMEOUT);
-                    s_abort = 1;
+                    // the first thread of the CTA to give up stops the whole cluster
+                    if (atomicExch(&s_abort, 1) == 0) cluster_abort_broadcast(&s_abort, (unsigned)(teams * cs));
                 }
             }
         }
@@ -552,8 +553,9 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         const bool final_line = (kind != 0);
         if constexpr (MT == 0) {
             cp_async_wait<0>();
-            __syncthreads();   // step s operands landed; every thread is done with step s - 1
-            if (s_abort) return;
+            // step s operands landed; every thread is done with step s - 1; the abort word
+            // (which another CTA may set at any time) is read once for the whole CTA
+            if (__syncthreads_or(*(volatile int *)&s_abort)) break;
             prefetch(s + 1);   // into the staging buffers that step s - 1 used
             cp_async_commit();
         }
@@ -601,8 +603,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
 #pragma unroll
             for (int q = 0; q < MMA_RHS; ++q)
                 if (q < Rc) redb[((size_t)(2 * wid + fh) * MMA_RHS + q) * RP + frow] = facc[q];
-            __syncthreads();
-            if (s_abort) return;   // a wait gave up (every thread sees the flag after the barrier)
+            if (__syncthreads_or(*(volatile int *)&s_abort)) break;   // a wait of the cluster gave up
             if (ov[0]) {
                 const int q = oq[0], r = orow[0], wpp = 16 / tpo;
                 float2 sum = make_float2(0.f, 0.f);
@@ -678,8 +679,7 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
             }
             if constexpr (!kPreSplit) load_g(s + 1);   // next line's fragments, in flight during the exchange
             {
-                __syncthreads();
-                if (s_abort) return;   // a wait gave up (every thread sees the flag after the barrier)
+                if (__syncthreads_or(*(volatile int *)&s_abort)) break;   // a wait of the cluster gave up
                 if (ov[0]) {
                     const int q = oq[0], r = orow[0], wpp = 8 / tpo;
                     float2 sum = make_float2(0.f, 0.f);
@@ -768,6 +768,12 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
         }
     }
     cp_async_wait<0>();
+    // no CTA leaves while another can still push into it; after a give-up, pushes issued
+    // before the abort word was seen are drained first
+    __syncthreads();
+    cluster_arrive();
+    cluster_wait();
+    if (*(volatile int *)&s_abort) abort_drain();
 }
 
 // Number of co-resident clusters of `cs` CTAs (0 if the size cannot be scheduled).
@@ -947,7 +953,7 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
             if (e != cudaSuccess) return e;
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status, skip};
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status, skip, wait_tries()};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);

@@ -87,7 +87,7 @@ class helm_trace_entry(C.Structure):
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
-            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
+            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_set_wait_tries", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad", "helm_gamma_solve",
             # include/helm_trace.h
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.helm_op_destroy.argtypes = [vp]
     lib.helm_factor.restype = C.c_int
     lib.helm_factor.argtypes = [vp, C.c_int, P(vp)]
+    lib.helm_set_wait_tries.restype = None
+    lib.helm_set_wait_tries.argtypes = [C.c_int64]
     lib.helm_factor_fp64_blocks.restype = i32
     lib.helm_factor_fp64_blocks.argtypes = [vp]
     lib.helm_factor_destroy.restype = None
@@ -279,6 +281,12 @@ def helm_assemble(nx, nz, lx, lz, m: torch.Tensor, omegas, stream=None) -> Op:
     return Op(h, nx, nz, lx, lz, om, stream)
 
 
+def helm_set_wait_tries(tries=-1):
+    """Polls of a bounded device-side wait before it gives up, for later launches (< 0: the
+    library default; 0: give up at the first wait that is not already complete)."""
+    load().helm_set_wait_tries(int(tries))
+
+
 def helm_factor(op: Op, prec=HELM_FP64) -> Factor:
     lib = load()
     h = C.c_void_p()
@@ -325,10 +333,12 @@ def helm_solve_noalloc(f: Factor, B: torch.Tensor, X: torch.Tensor, rtol=1e-10, 
     return X, {"iters": info.iters, "max_relres": info.max_relres}
 
 
-def helm_sources(op: Op, acq: Acq) -> torch.Tensor:
+def helm_sources(op: Op, acq: Acq, B: torch.Tensor | None = None) -> torch.Tensor:
     lib = load()
-    B = torch.empty((op.n_omega, acq.n_src, op.N), dtype=torch.complex128, device="cuda")
-    _check(lib.helm_sources(op.handle, C.byref(acq.struct), _dev(B, torch.complex128, "B")), "helm_sources")
+    if B is None:
+        B = torch.empty((op.n_omega, acq.n_src, op.N), dtype=torch.complex128, device="cuda")
+    _check(lib.helm_sources(op.handle, C.byref(acq.struct), _dev(B, torch.complex128, "B", (op.n_omega, acq.n_src, op.N))),
+           "helm_sources")
     return B
 
 
@@ -414,12 +424,18 @@ def helm_gamma_solve(nx, nz, alpha0, mu, R: torch.Tensor, Z: torch.Tensor | None
     return Z
 
 
-def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
+def bilevel_hypergrad(grids, m_fwi, m_true, acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
                       cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
                       stream=None, concurrent_models=0):
-    """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors."""
+    """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors; acq: one
+    Acq for every model, or a list with one per model (the same number of receivers)."""
     lib = load()
     n = len(grids)
+    acqs = list(acq) if isinstance(acq, (list, tuple)) else [acq] * n
+    if len(acqs) != n:
+        raise ValueError("one acquisition per model")
+    A = (helm_acq * n)(*[a.struct for a in acqs])
+    acq = acqs[0]
     G = (helm_grid * n)(*[helm_grid(*g) for g in grids])
     pf = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_fwi", (g[0] * g[1],)).value for t, g in zip(m_fwi, grids)])
     pt = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_true", (g[0] * g[1],)).value for t, g in zip(m_true, grids)])
@@ -430,7 +446,7 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq: Acq, omegas, alpha, alpha0, mu,
     dp = np.zeros((acq.n_rec, 2))
     dw = np.zeros(acq.n_rec)
     info = helm_hyper_info()
-    _check(lib.bilevel_hypergrad(n, G, pf, pt, C.byref(acq.struct), p_om, len(om), float(alpha), float(alpha0),
+    _check(lib.bilevel_hypergrad(n, G, pf, pt, A, p_om, len(om), float(alpha), float(alpha0),
                                  float(mu), int(prec), C.byref(opts), _stream_ptr(stream), C.byref(psi),
                                  C.byref(dalpha), dp.ctypes.data_as(C.POINTER(C.c_double)),
                                  dw.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bilevel_hypergrad")

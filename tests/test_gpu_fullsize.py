@@ -79,3 +79,34 @@ def test_mixed_factor_accuracy_sets_two_sweep_forward_solves():
         assert info.iters == sweeps
         rel[sweeps] = info.max_relres
     assert rel[2] <= 2e-10 and rel[3] <= 1e-12, rel
+
+
+@pytest.fixture(scope="module")
+def hyper_step_oracle():
+    """The oracle's hypergradient of the benchmark step: 128 x 128, omega in {5, 10, 15}, 16
+    sources, 32 receivers, alpha = alpha0 = 1e-3, mu = 1e-6, ten PCG iterations with P2."""
+    w = W.config_hyper_step(128)
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    o = H.hypergradient(g, w.m, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz, w.alpha, w.alpha, w.mu,
+                        cg_fixed_iters=10)
+    return w, o
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_benchmark_hypergradient_step_matches_oracle(hyper_step_oracle, prec, tol):
+    """The hypergradient of the timed step itself, in the launch configuration bench.py uses
+    (refinement to 1e-10, ten PCG iterations), compared component by component with the
+    oracle.  At mu = 1e-6 PCG with P2 reaches ||r|| / ||r_0|| ~ 2e-12 in these ten iterations,
+    and the result moves by about 1e-11 under a 1e-13 change of m_fwi: the comparison is well
+    posed at these tolerances."""
+    w, o = hyper_step_oracle
+    out = hm.bilevel_hypergrad([(w.nx, w.nz, w.lx, w.lz)], [torch.tensor(w.m, device="cuda")],
+                               [torch.tensor(w.m_true, device="cuda")], hm.Acq.from_workload(w.acq), w.omegas,
+                               w.alpha, w.alpha, w.mu, prec=prec, cg_fixed_iters=10, refine_rtol=BENCH_RTOL)
+    assert out["cg_matvecs"] == o["cg_matvecs"] == 11
+    assert abs(out["psi"] - o["psi"]) <= 1e-12 * abs(o["psi"])
+    assert abs(out["dpsi_dalpha"] - o["dpsi_dalpha"]) <= tol * abs(o["dpsi_dalpha"])
+    for k in ("dpsi_dp", "dpsi_dw"):
+        err = np.linalg.norm(out[k] - o[k]) / np.linalg.norm(o[k])
+        assert err <= tol, (k, err)
+    assert out["cg_relres"] <= 1e-10
