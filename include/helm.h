@@ -87,6 +87,7 @@ typedef struct {
     int32_t concurrent_models;  /* training models processed at once (own streams and host
                                    threads); <= 0: library default (up to 3).  The results are
                                    summed in model order, so they do not depend on it. */
+    int32_t factor_method;      /* helm_factor_method of every factor of the pass */
 } helm_pcg_opts;
 
 typedef struct {
@@ -117,6 +118,19 @@ helm_status helm_assemble(const helm_grid *grid, const double *m_dev, const doub
                           int32_t n_omega, void *stream, helm_op_t **out);
 void helm_op_destroy(helm_op_t *op);
 
+/* Factor methods.  HELM_FACTOR_LINE: the line-by-line Schur recurrence below.
+ * HELM_FACTOR_BCR (HELM_MIXED only, even nz >= 16): block cyclic reduction of the same
+ * block-tridiagonal system -- every other line of the current system is eliminated at once,
+ * level by level (log2(nx) levels), so that each level is a batch of independent dense block
+ * inversions and block products over all lines and frequencies, run on the tensor cores
+ * (complex products as real TF32 products with the 3xTF32 split, FP32 accumulation).  Its
+ * storage is about 3 nx nz^2 complex FP32 entries per frequency.  HELM_FACTOR_AUTO: BCR where
+ * it applies (unless the environment sets HELM_FACTOR=line), else the line recurrence. */
+typedef enum { HELM_FACTOR_AUTO = 0, HELM_FACTOR_LINE = 1, HELM_FACTOR_BCR = 2 } helm_factor_method;
+typedef struct {
+    int32_t method;       /* helm_factor_method */
+} helm_factor_opts;
+
 /* helm_factor -- block-tridiagonal (line-by-line) factorisation of every A(m, w_q):
  * with lines of constant i, A has diagonal blocks D_i (tridiagonal n_z x n_z) and
  * diagonal couplings C_i; the factor stores G_i = S_i^{-1} with
@@ -125,10 +139,11 @@ void helm_op_destroy(helm_op_t *op);
  * Each S_i is inverted by block Gauss-Jordan over 16-column blocks; a 16 x 16 pivot block
  * is inverted by Newton-Schulz iteration seeded with the same block's inverse on the
  * previous line, or by Gauss-Jordan with partial pivoting where that seed is not close
- * enough.  Errors: ESINGULAR (zero / non-finite pivot), ETIMEOUT (a bounded device-side
- * wait gave up), ENOMEM, ECUDA.
+ * enough.  opts may be NULL (HELM_FACTOR_AUTO).
+ * Errors: EINVAL (bad method, or HELM_FACTOR_BCR where it does not apply), ESINGULAR (zero /
+ * non-finite pivot), ETIMEOUT (a bounded device-side wait gave up), ENOMEM, ECUDA.
  * The factor keeps a reference to op: destroy the factor before the op. */
-helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out);
+helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_factor_opts *opts, helm_factor_t **out);
 void helm_factor_destroy(helm_factor_t *f);
 
 /* helm_set_wait_tries -- diagnostic setting (no counterpart in the paper): the number of

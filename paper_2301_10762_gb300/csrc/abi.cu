@@ -2,6 +2,7 @@
 // argument checks and orchestration of the kernels.  No computation of the path runs
 // on the host; the host only sequences launches and reads scalars back.
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 #include <algorithm>
@@ -147,37 +148,68 @@ extern "C" void helm_op_destroy(helm_op_t *op) {
 
 // ------------------------------------------------------------------------ factor
 
-extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, helm_factor_t **out) {
+// Factor method of a mixed factor: the options, else HELM_FACTOR=line|bcr, else BCR where it
+// applies (an even n_z of at least 16) and the line recurrence otherwise.  FP64 factors are line
+// factors (the tensor cores have no FP64 path).
+static bool pick_bcr(const helm_op *op, helm_prec prec, const helm_factor_opts *opts) {
+    if (prec != HELM_MIXED || !bcr_supported(op->g)) return false;
+    int m = opts ? opts->method : HELM_FACTOR_AUTO;
+    if (m == HELM_FACTOR_AUTO) {
+        const char *env = getenv("HELM_FACTOR");
+        if (env && !strcmp(env, "line")) m = HELM_FACTOR_LINE;
+    }
+    return m != HELM_FACTOR_LINE;
+}
+
+extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_factor_opts *opts, helm_factor_t **out) {
     if (!out) { helm_set_msg("helm_factor: NULL out"); return HELM_EINVAL; }
     *out = nullptr;
-    if (!op || (prec != HELM_FP64 && prec != HELM_MIXED)) { helm_set_msg("helm_factor: bad op or precision"); return HELM_EINVAL; }
+    if (!op || (prec != HELM_FP64 && prec != HELM_MIXED) ||
+        (opts && (opts->method < HELM_FACTOR_AUTO || opts->method > HELM_FACTOR_BCR))) {
+        helm_set_msg("helm_factor: bad op, precision or method");
+        return HELM_EINVAL;
+    }
+    if (opts && opts->method == HELM_FACTOR_BCR && (prec != HELM_MIXED || !bcr_supported(op->g))) {
+        helm_set_msg("helm_factor: block cyclic reduction needs HELM_MIXED and an even nz >= 16");
+        return HELM_EINVAL;
+    }
     helm_factor_t *f = new (std::nothrow) struct helm_factor();
     if (!f) return HELM_ENOMEM;
     f->op = op;
     f->prec = prec;
+    f->use_bcr = pick_bcr(op, prec, opts);
     const GridGeom &g = op->g;
     f->cs = pick_cluster_size(g.nz);
     const size_t esz = prec == HELM_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t gelems = (size_t)op->n_omega * g.nx * g.nz * g.nz;
     helm_status s;
-    if ((s = dev_alloc(&f->G, gelems * esz, "allocate(factor)", op->st)) != HELM_OK ||
-        (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "allocate(exchange)", op->st)) !=
-            HELM_OK) {
-        helm_factor_destroy(f);
-        return s;
-    }
     cudaError_t e;
     if ((e = cudaMemsetAsync(op->status, 0, 2 * sizeof(int), op->st)) != cudaSuccess) {
         helm_set_error("helm_factor", e);
         helm_factor_destroy(f);
         return HELM_ECUDA;
     }
-    if (prec == HELM_FP64)
-        e = launch_line_factor<double>(g, op->n_omega, op->diag, (double2 *)f->G, (double2 *)f->xch, op->status,
-                                       f->cs, op->st, &f->mid);
-    else
-        e = launch_line_factor<float>(g, op->n_omega, op->diag, (float2 *)f->G, (float2 *)f->xch, op->status,
-                                      f->cs, op->st, &f->mid);
+    if (f->use_bcr) {
+        if ((s = bcr_factor(f)) != HELM_OK) {
+            cudaStreamSynchronize(op->st);
+            helm_factor_destroy(f);
+            return s;
+        }
+        e = cudaSuccess;
+    } else {
+        if ((s = dev_alloc(&f->G, gelems * esz, "allocate(factor)", op->st)) != HELM_OK ||
+            (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "allocate(exchange)",
+                           op->st)) != HELM_OK) {
+            helm_factor_destroy(f);
+            return s;
+        }
+        if (prec == HELM_FP64)
+            e = launch_line_factor<double>(g, op->n_omega, op->diag, (double2 *)f->G, (double2 *)f->xch, op->status,
+                                           f->cs, op->st, &f->mid);
+        else
+            e = launch_line_factor<float>(g, op->n_omega, op->diag, (float2 *)f->G, (float2 *)f->xch, op->status,
+                                          f->cs, op->st, &f->mid);
+    }
     int st_host[2] = {0, 0};   // status bits, pivot blocks inverted in FP64
     if (e == cudaSuccess) e = cudaMemcpyAsync(st_host, op->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
@@ -228,6 +260,7 @@ extern "C" void helm_factor_destroy(helm_factor_t *f) {
     dev_free(f->y, st);
     dev_free(f->norms, st);
     dev_free(f->state, st);
+    bcr_free(f);
     delete f;
 }
 
@@ -302,7 +335,13 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     if (e == cudaSuccess) e = launch_refine_start(g, cols, B, conj, w.bd, w.r32, w.norms, op->st);
     if (e != cudaSuccess) { helm_set_error("refinement start", e); return HELM_ECUDA; }
     const int *skip = &w.state->done;
-    auto sweep = [&](const int *skip_flag) {
+    // the correction A~^{-1} r: line sweep, or the block-cyclic-reduction solve (which works in
+    // place on r, recomputed before every correction)
+    auto sweep = [&](const int *skip_flag) -> cudaError_t {
+        if (f->use_bcr) {
+            const helm_status bs = bcr_solve(f, nrhs, w.r32, w.y, skip_flag);
+            return bs == HELM_OK ? cudaSuccess : cudaErrorLaunchFailure;
+        }
         return launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, w.r32, nullptr, w.y, 0, rchunk,
                                         op->status, op->st, f->mid, skip_flag);
     };

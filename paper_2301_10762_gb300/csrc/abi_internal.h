@@ -1,6 +1,7 @@
 // Internal definitions of the opaque handles of include/helm.h (C++ only).
 #pragma once
 #include <atomic>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 #include "helm.h"
@@ -25,8 +26,21 @@ namespace helm {
 struct RefineState;   // device-side refinement control (kernels.h)
 }
 
+// Block-cyclic-reduction factor (bcr.cu): the inverse of every line's block at the level it was
+// eliminated, the back-substitution blocks P_j, Q_j and the forward blocks W_j, V_j of the lines
+// eliminated at levels >= 1 (slot j / 2), and the solve's GEMM task lists on the device.
+struct BcrData {
+    int levels = 0, half = 0;
+    float2 *Dinv = nullptr, *P = nullptr, *Q = nullptr, *W = nullptr, *V = nullptr;
+    int *tasks = nullptr;
+    std::vector<std::pair<int, int>> fwd, bwd;   // per level: (first task, task count)
+    std::pair<int, int> last{0, 0};
+};
+
 struct helm_factor {
     helm_op *op = nullptr;
+    bool use_bcr = false;  // mixed: block-cyclic-reduction factor on the tensor cores
+    BcrData bcr;
     helm_prec prec = HELM_FP64;
     int cs = 1;
     int mid = 0;           // middle line of the (twisted) line factorisation
@@ -82,4 +96,16 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
 // max over columns of ||r|| / ||b|| from a device norms buffer (synchronises the op's stream)
 helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, double *norms_host, double *out);
 helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d);
+// block cyclic reduction (bcr.cu)
+namespace helm {
+bool bcr_supported(const GridGeom &g);
+helm_status bcr_factor(helm_factor_t *f);
+void bcr_free(helm_factor_t *f);
+helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip);
+helm_status blas_zgemm(int batch, int M, int N, int K, const float2 *A, long long sa, int lda, const float2 *Bt,
+                       long long sb, int ldb, float sign, const float2 *C0, float2 *C, long long sc, int ldc,
+                       cudaStream_t st, int *status);
+helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, float2 *X, long long sx, int ldx,
+                      cudaStream_t st, int *status);
+}  // namespace helm
 void acq_free(DevAcq *d);

@@ -1,0 +1,759 @@
+// Block cyclic reduction (BCR) of the block-tridiagonal line system, mixed precision.
+//
+// With lines of constant x (n_z nodes each) the discrete operator A(m, w) of the Appendix
+// ("Numerical forward model") is block tridiagonal: diagonal blocks D_i (tridiagonal) and the
+// diagonal horizontal couplings C between neighbouring lines; A is complex symmetric, so the
+// coupling of line k to a line a is the transpose of that of a to k.  Where the line factor
+// (factor.cu) runs the Schur recurrence line after line, BCR eliminates every other line of
+// the current system at once, level by level (spacing s = 2^l):
+//     eliminated j (j = s mod 2s):    Dinv_j = D_j^{-1}
+//     kept k (k = 0 mod 2s), a = k - s, c = k + s:
+//         D_k <- D_k - L_k Dinv_a U_a - U_k Dinv_c L_c
+//         L_k <- -L_k Dinv_a L_a      (coupling to k - 2s)
+//         U_k <- -U_k Dinv_c U_c      (coupling to k + 2s)
+// until one line is left (line 0, whose inverse ends the factor).  Every level is a batch of
+// independent dense block products and inversions over all lines and frequencies, which the
+// tensor-core GEMM (zgemm_tc.cu) and the batched block inversion below run; the depth of the
+// dependent chain is log2(n_x) levels instead of n_x lines.  By symmetry L_k = U_a^T and
+// U_k = L_c^T, so every product is a GEMM of row-major operands:
+//     W_a = L_k Dinv_a (= (Dinv_a U_a)^T),   V_c = U_k Dinv_c (= (Dinv_c L_c)^T),
+//     D_k -= L_k W_a^T + U_k V_c^T,   L_k <- -L_k V_a^T,   U_k <- -U_k W_c^T,
+// and the back substitution takes P_j = V_j^T = Dinv_j L_j, Q_j = W_j^T = Dinv_j U_j.
+// Level 0 has the diagonal couplings C: its products are elementwise scalings.
+//
+// The solve of A x = b (all right-hand sides of a system as the GEMM N dimension):
+//     forward, level 0:  y_j = Dinv_j b_j;  b_k -= C (y_a + y_c)
+//     forward, level l:  b_k -= W_a b_a + V_c b_c
+//     last line:         x_0 = Dinv_0 b_0
+//     backward, level l: x_j = Dinv_j b_j - P_j x_{j-s} - Q_j x_{j+s}
+//     backward, level 0: x_j = y_j - Dinv_j C (x_{j-1} + x_{j+1}).
+// Everything is complex FP32 (3xTF32 tensor products): the factor is the preconditioner of
+// the FP64-residual refinement of the mixed path, exactly as the line factor is.
+//
+// Dense inversion of a batch of n x n blocks: n <= 128 in shared memory, one CTA per block
+// (block Gauss-Jordan over 16-column blocks, partial pivoting inside each pivot block, as in
+// the line factor); larger n by the 2 x 2 block inverse of a symmetric matrix
+//     [[D11, D21^T], [D21, D22]]^{-1}:  X11 = D11^{-1}, T = X11 D21^T, S = D22 - D21 T,
+//     X22 = S^{-1}, X12 = -T X22, X21 = X12^T, X11 <- X11 - T X21,
+// with the products on the tensor cores and the two half-size inverses recursive.
+#include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "abi_internal.h"
+#include "kernels.h"
+#include "pivot16.cuh"
+#include "trace.h"
+
+namespace helm {
+
+namespace {
+
+constexpr int INV_THREADS = 512;
+constexpr int INV_MAX = 128;   // largest block inverted in one CTA's shared memory
+
+// ------------------------------------------------------------------- kernels
+
+// dense D_i of every line and system: the diagonal of A and the vertical couplings next to it
+__global__ void bcr_form_kernel(GridGeom g, const double2 *diag, float2 *D) {
+    const int nz = g.nz, nx = g.nx;
+    const int i = blockIdx.y, s = blockIdx.z;
+    const float cz = (float)coup_z(g, i);
+    float2 *Di = D + ((size_t)s * nx + i) * nz * nz;
+    const double2 *dg = diag + ((size_t)s * nx + i) * nz;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nz * nz; e += gridDim.x * blockDim.x) {
+        const int r = e / nz, c = e % nz;
+        float2 v = make_float2(0.f, 0.f);
+        if (r == c) v = to_c64(dg[r]);
+        else if (r == c + 1 || c == r + 1) v.x = cz;
+        Di[e] = v;
+    }
+}
+
+// level 0 (couplings C = diag(cx)): kept line k (even) with eliminated neighbours k - 1, k + 1:
+//   D_k -= C Dinv_{k-1} C + C Dinv_{k+1} C,  L_k = -C Dinv_{k-1} C,  U_k = -C Dinv_{k+1} C
+__global__ void bcr_level0_kernel(GridGeom g, float2 *D, const float2 *Dinv, float2 *Lnew, float2 *Unew, int half) {
+    const int nz = g.nz, nx = g.nx, nz2 = nz * nz;
+    const int k = 2 * blockIdx.y, s = blockIdx.z;
+    const bool ha = k >= 1, hc = k + 1 < nx;
+    const float2 *Da = Dinv + ((size_t)s * nx + (ha ? k - 1 : 0)) * nz2;
+    const float2 *Dc = Dinv + ((size_t)s * nx + (hc ? k + 1 : 0)) * nz2;
+    float2 *Dk = D + ((size_t)s * nx + k) * nz2;
+    float2 *Lk = Lnew + ((size_t)s * half + k / 2) * nz2;
+    float2 *Uk = Unew + ((size_t)s * half + k / 2) * nz2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nz2; e += gridDim.x * blockDim.x) {
+        const int r = e / nz, c = e % nz;
+        const float sc = (float)(coup_x(g, r) * coup_x(g, c));
+        float2 ta = make_float2(0.f, 0.f), tc = ta;
+        if (ha) { const float2 v = Da[e]; ta = make_float2(sc * v.x, sc * v.y); }
+        if (hc) { const float2 v = Dc[e]; tc = make_float2(sc * v.x, sc * v.y); }
+        float2 d = Dk[e];
+        d.x -= ta.x + tc.x;
+        d.y -= ta.y + tc.y;
+        Dk[e] = d;
+        if (k >= 2) Lk[e] = make_float2(-ta.x, -ta.y);
+        if (k + 2 < nx) Uk[e] = make_float2(-tc.x, -tc.y);
+    }
+}
+
+struct InvArgs {
+    int n;
+    ZOperand in;                 // row-major, ld = in.ld
+    float2 *out;                 // row-major, ld = ldo
+    long long out_stride, out_stride_hi;
+    int out_div, ldo;
+    const int *idx;              // [count][2]: input index, output index
+    int *status;
+};
+
+__device__ __forceinline__ long long op_off(int idx, int div, long long stride, long long stride_hi) {
+    return div > 0 ? (long long)(idx / div) * stride_hi + (long long)(idx % div) * stride : (long long)idx * stride;
+}
+
+// X = M^{-1} of one n x n block (n <= 128) per CTA, in shared memory: block Gauss-Jordan over
+// 16-column blocks; the pivot block is inverted by one warp with partial pivoting, the other
+// rows get the rank-16 update from the staged old column panel U and R = P M[k rows, :].
+__global__ void __launch_bounds__(INV_THREADS, 1) zinv_base_kernel(InvArgs a) {
+    extern __shared__ __align__(16) unsigned char inv_smem[];
+    const int n = a.n, ldw = n + 1, tid = threadIdx.x;
+    float2 *W = reinterpret_cast<float2 *>(inv_smem);          // n x ldw
+    float2 *U = W + (size_t)n * ldw;                             // n x 16: old column panel
+    float2 *R = U + (size_t)n * PIV;                             // 16 x ldw: P times the pivot rows
+    float2 *P = R + (size_t)PIV * ldw;                           // 16 x 16: pivot-block inverse
+    __shared__ int s_bad;
+    const int *ix = a.idx + 2 * (size_t)blockIdx.x;
+    const float2 *M = a.in.base + op_off(ix[0], a.in.div, a.in.stride, a.in.stride_hi);
+    float2 *X = a.out + op_off(ix[1], a.out_div, a.out_stride, a.out_stride_hi);
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < n * n; e += INV_THREADS) {
+        const int r = e / n, c = e % n;
+        W[(size_t)r * ldw + c] = M[(size_t)r * a.in.ld + c];
+    }
+    __syncthreads();
+    // update mapping: thread -> column c, row group rg (rows rg, rg + ng, ...)
+    const int ng = INV_THREADS / n, c = tid % n, rg = tid / n;
+    const int nb = (n + PIV - 1) / PIV;
+    for (int kb_i = 0; kb_i < nb; ++kb_i) {
+        const int k0 = kb_i * PIV, kb = min(PIV, n - k0);
+        for (int e = tid; e < n * PIV; e += INV_THREADS) {
+            const int r = e / PIV, u = e % PIV;
+            U[e] = u < kb ? W[(size_t)r * ldw + k0 + u] : make_float2(0.f, 0.f);
+        }
+        if (tid < 32) {
+            if (!warp_invert16<float>(W + (size_t)k0 * ldw + k0, ldw, kb, P) && tid == 0) s_bad = 1;
+        }
+        __syncthreads();
+        for (int e = tid; e < PIV * n; e += INV_THREADS) {
+            const int q = e / n, cc = e % n;
+            if (q < kb && (cc < k0 || cc >= k0 + kb)) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int u = 0; u < kb; ++u) cfma(acc, P[q * PIV + u], W[(size_t)(k0 + u) * ldw + cc]);
+                R[(size_t)q * ldw + cc] = acc;
+            }
+        }
+        __syncthreads();
+        if (rg < ng) {
+            const bool inblk = c >= k0 && c < k0 + kb;
+            float2 col[PIV];   // the R (or P) column this thread multiplies with
+#pragma unroll
+            for (int u = 0; u < PIV; ++u)
+                col[u] = u < kb ? (inblk ? P[u * PIV + (c - k0)] : R[(size_t)u * ldw + c]) : make_float2(0.f, 0.f);
+            for (int r = rg; r < n; r += ng) {
+                float2 *w = W + (size_t)r * ldw + c;
+                if (r >= k0 && r < k0 + kb) {
+                    *w = inblk ? P[(r - k0) * PIV + (c - k0)] : R[(size_t)(r - k0) * ldw + c];
+                    continue;
+                }
+                const float4 *ur = reinterpret_cast<const float4 *>(U + (size_t)r * PIV);
+                float2 p[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int h = 0; h < PIV / 2; ++h) {
+                    const float4 q = ur[h];
+                    cfma(p[(2 * h) & 3], make_float2(q.x, q.y), col[2 * h]);
+                    cfma(p[(2 * h + 1) & 3], make_float2(q.z, q.w), col[2 * h + 1]);
+                }
+                const float2 sum = make_float2((p[0].x + p[1].x) + (p[2].x + p[3].x), (p[0].y + p[1].y) + (p[2].y + p[3].y));
+                const float2 old = inblk ? make_float2(0.f, 0.f) : *w;
+                *w = make_float2(old.x - sum.x, old.y - sum.y);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += INV_THREADS) {
+        const int r = e / n, cc = e % n;
+        X[(size_t)r * a.ldo + cc] = W[(size_t)r * ldw + cc];
+    }
+    if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
+}
+
+size_t inv_smem_bytes(int n) {
+    return sizeof(float2) * ((size_t)n * (n + 1) + (size_t)n * PIV + (size_t)PIV * (n + 1) + PIV * PIV);
+}
+
+// out[idx_out] = in[idx_in]^T for n x n complex blocks (32 x 32 tiles through shared memory)
+__global__ void ztranspose_kernel(int n, const float2 *in, float2 *out, long long stride_in, long long stride_out,
+                                  const int *idx) {
+    __shared__ float2 t[32][33];
+    const int *ix = idx + 2 * (size_t)blockIdx.z;
+    const float2 *A = in + (long long)ix[0] * stride_in;
+    float2 *B = out + (long long)ix[1] * stride_out;
+    const int nt = (n + 31) / 32;
+    const int bi = blockIdx.x / nt, bj = blockIdx.x % nt;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = bi * 32 + y, c = bj * 32 + threadIdx.x;
+        if (r < n && c < n) t[y][threadIdx.x] = A[(size_t)r * n + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = bj * 32 + y, c = bi * 32 + threadIdx.x;
+        if (r < n && c < n) B[(size_t)r * n + c] = t[threadIdx.x][y];
+    }
+}
+
+// solve, level 0 of the forward pass: b_k -= C (y_{k-1} + y_{k+1}) for even k, y in x
+__global__ void bcr_solve_l0_fwd_kernel(GridGeom g, int nrhs, float2 *b, const float2 *x, const int *skip) {
+    if (skip && *skip) return;
+    const int nz = g.nz, nx = g.nx, N = nx * nz;
+    const int k = 2 * blockIdx.y, col = blockIdx.z;   // col = system * nrhs + rhs
+    const size_t off = (size_t)col * N + (size_t)k * nz;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nz; r += gridDim.x * blockDim.x) {
+        float2 t = make_float2(0.f, 0.f);
+        if (k >= 1) { const float2 v = x[off - nz + r]; t.x += v.x; t.y += v.y; }
+        if (k + 1 < nx) { const float2 v = x[off + nz + r]; t.x += v.x; t.y += v.y; }
+        const float cx = (float)coup_x(g, r);
+        float2 v = b[off + r];
+        v.x -= cx * t.x;
+        v.y -= cx * t.y;
+        b[off + r] = v;
+    }
+}
+
+// solve, level 0 of the backward pass: b_j = C (x_{j-1} + x_{j+1}) for odd j
+__global__ void bcr_solve_l0_bwd_kernel(GridGeom g, int nrhs, float2 *b, const float2 *x, const int *skip) {
+    if (skip && *skip) return;
+    const int nz = g.nz, nx = g.nx, N = nx * nz;
+    const int j = 2 * blockIdx.y + 1, col = blockIdx.z;
+    const size_t off = (size_t)col * N + (size_t)j * nz;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nz; r += gridDim.x * blockDim.x) {
+        float2 t = x[off - nz + r];
+        if (j + 1 < nx) { const float2 v = x[off + nz + r]; t.x += v.x; t.y += v.y; }
+        const float cx = (float)coup_x(g, r);
+        b[off + r] = make_float2(cx * t.x, cx * t.y);
+    }
+}
+
+// ----------------------------------------------------------------- host side
+
+struct TaskBuf {   // device copy of host-built task lists (freed on the stream when done)
+    int *dev = nullptr;
+    cudaStream_t st = nullptr;
+    ~TaskBuf() { dev_free(dev, st); }
+};
+
+helm_status upload_ints(const std::vector<int> &h, TaskBuf &b, cudaStream_t st) {
+    b.st = st;
+    helm_status s = dev_alloc((void **)&b.dev, h.size() * sizeof(int), "bcr: task list", st);
+    if (s != HELM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(b.dev, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { helm_set_error("bcr: task upload", e); return HELM_ECUDA; }
+    return HELM_OK;
+}
+
+ZOperand zop(const float2 *base, long long stride, int ld, int div = 0, long long stride_hi = 0) {
+    ZOperand o;
+    o.base = base;
+    o.stride = stride;
+    o.ld = ld;
+    o.div = div;
+    o.stride_hi = stride_hi;
+    return o;
+}
+
+std::vector<int> task8(int a0, int b0, int c0, int c, int a1 = -1, int b1 = -1, int a2 = -1, int b2 = -1) {
+    return {a0, a1, a2, b0, b1, b2, c0, c};
+}
+
+helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, cudaStream_t st) {
+    if (tasks.empty()) return HELM_OK;
+    TaskBuf tb;
+    helm_status s = upload_ints(tasks, tb, st);
+    if (s != HELM_OK) return s;
+    ZGemmArgs a = a0;
+    a.tasks = tb.dev;
+    a.tries = wait_tries();
+    cudaError_t e = launch_zgemm(a, (int)(tasks.size() / 8), st);
+    if (e != cudaSuccess) { helm_set_error("bcr: tensor-core GEMM", e); return HELM_ECUDA; }
+    return HELM_OK;
+}
+
+// A family of n x n row-major blocks within a family of larger row-major matrices: the block
+// at (row r0, column c0) of matrix idx (the larger matrices have row stride ld).
+struct Fam {
+    float2 *base;
+    long long stride;
+    int ld;
+    Fam sub(int r0, int c0) const { return Fam{base + (long long)r0 * ld + c0, stride, ld}; }
+    ZOperand op() const { return zop(base, stride, ld); }
+};
+
+// out[p.second] = in[p.first]^{-1} for every index pair, n x n blocks (may be the same matrices)
+helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, cudaStream_t st) {
+    const int count = (int)(pairs.size() / 2);
+    if (count == 0) return HELM_OK;
+    helm_status s;
+    if (n <= INV_MAX) {
+        TaskBuf tb;
+        if ((s = upload_ints(pairs, tb, st)) != HELM_OK) return s;
+        InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, tb.dev, status};
+        const size_t smem = inv_smem_bytes(n);
+        cudaError_t e = ensure_dyn_smem((const void *)zinv_base_kernel, smem);
+        if (e == cudaSuccess) {
+            HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) { helm_set_error("bcr: block inversion", e); return HELM_ECUDA; }
+        return HELM_OK;
+    }
+    const int n1 = INV_MAX * ((n / INV_MAX + 1) / 2), n2 = n - n1;
+    // X11 = D11^{-1}
+    if ((s = invert_blocks(n1, in, out, pairs, status, st)) != HELM_OK) return s;
+    // scratch T (n1 x n2) and Tt = T^T (n2 x n1) per block
+    float2 *T = nullptr, *Tt = nullptr;
+    const long long ts = (long long)n1 * n2;
+    if ((s = dev_alloc((void **)&T, (size_t)count * ts * sizeof(float2), "bcr: inversion scratch", st)) != HELM_OK)
+        return s;
+    struct Free { float2 *&p; cudaStream_t st; ~Free() { dev_free(p, st); } } f1{T, st};
+    if ((s = dev_alloc((void **)&Tt, (size_t)count * ts * sizeof(float2), "bcr: inversion scratch", st)) != HELM_OK)
+        return s;
+    struct Free2 { float2 *&p; cudaStream_t st; ~Free2() { dev_free(p, st); } } f2{Tt, st};
+    const Fam X11 = out.sub(0, 0), X12 = out.sub(0, n1), X21 = out.sub(n1, 0), X22 = out.sub(n1, n1);
+    const Fam D21 = in.sub(n1, 0), D22 = in.sub(n1, n1);
+    const Fam FT{T, ts, n2}, FTt{Tt, ts, n1};
+    std::vector<int> tk;
+    auto run = [&](int M, int N, int K, Fam A, Fam B, const Fam *C0, Fam C, float sign, int which_a, int which_b,
+                   int which_c0, int which_c) -> helm_status {
+        // which_*: 0 the input index, 1 the output index, 2 the block's position in the batch
+        tk.clear();
+        for (int t = 0; t < count; ++t) {
+            const int id[3] = {pairs[2 * t], pairs[2 * t + 1], t};
+            auto v = task8(id[which_a], id[which_b], C0 ? id[which_c0] : 0, id[which_c]);
+            tk.insert(tk.end(), v.begin(), v.end());
+        }
+        ZGemmArgs g;
+        g.M = M; g.N = N; g.K = K;
+        g.nterms = 1;
+        g.A[0] = A.op();
+        g.B[0] = B.op();
+        g.sign[0] = sign;
+        if (C0) g.C0 = C0->op();
+        g.C = C.base;
+        g.c_stride = C.stride;
+        g.ldc = C.ld;
+        g.status = status;
+        return gemm(g, tk, st);
+    };
+    // T = X11 D12 = X11 D21^T;  Tt = D21 X11 (= T^T, X11 symmetric)
+    if ((s = run(n1, n2, n1, X11, D21, nullptr, FT, 1.f, 1, 0, 0, 2)) != HELM_OK) return s;
+    if ((s = run(n2, n1, n1, D21, X11, nullptr, FTt, 1.f, 0, 1, 0, 2)) != HELM_OK) return s;
+    // S = D22 - D21 T  -> X22, then X22 = S^{-1} in place
+    if ((s = run(n2, n2, n1, D21, FTt, &D22, X22, -1.f, 0, 2, 0, 1)) != HELM_OK) return s;
+    std::vector<int> self(pairs.size());
+    for (int t = 0; t < count; ++t) self[2 * t] = self[2 * t + 1] = pairs[2 * t + 1];
+    if ((s = invert_blocks(n2, X22, X22, self, status, st)) != HELM_OK) return s;
+    // X12 = -T X22;  X21 = -X22 T^T;  X11 <- X11 - T X21
+    if ((s = run(n1, n2, n2, FT, X22, nullptr, X12, -1.f, 2, 1, 0, 1)) != HELM_OK) return s;
+    if ((s = run(n2, n1, n2, X22, FT, nullptr, X21, -1.f, 1, 2, 0, 1)) != HELM_OK) return s;
+    if ((s = run(n1, n1, n2, FT, X12, &X11, X11, -1.f, 2, 1, 1, 1)) != HELM_OK) return s;
+    return HELM_OK;
+}
+
+helm_status transpose_blocks(int n, const float2 *in, float2 *out, long long stride, const std::vector<int> &pairs,
+                             cudaStream_t st) {
+    const int count = (int)(pairs.size() / 2);
+    if (count == 0) return HELM_OK;
+    TaskBuf tb;
+    helm_status s = upload_ints(pairs, tb, st);
+    if (s != HELM_OK) return s;
+    const int nt = (n + 31) / 32;
+    HELM_TRACED(K_ZTRANS, st, (ztranspose_kernel<<<dim3(nt * nt, 1, count), dim3(32, 8), 0, st>>>(n, in, out, stride,
+                                                                                                  stride, tb.dev)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { helm_set_error("bcr: transpose", e); return HELM_ECUDA; }
+    return HELM_OK;
+}
+
+}  // namespace
+
+bool bcr_supported(const GridGeom &g) { return (g.nz % 2) == 0 && g.nz >= 16 && g.nx >= 4; }
+
+// ------------------------------------------------------------------ factor
+
+helm_status bcr_factor(helm_factor_t *f) {
+    helm_op *op = f->op;
+    const GridGeom &g = op->g;
+    const int nx = g.nx, nz = g.nz, ns = op->n_omega;
+    const long long nz2 = (long long)nz * nz;
+    const int half = nx / 2 + 1;
+    const cudaStream_t st = op->st;
+    BcrData &b = f->bcr;
+    b.half = half;
+    helm_status s;
+    const size_t blk = (size_t)nz2 * sizeof(float2);
+    if ((s = dev_alloc((void **)&b.Dinv, (size_t)ns * nx * blk, "bcr: inverses", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&b.P, (size_t)ns * half * blk, "bcr: P", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&b.Q, (size_t)ns * half * blk, "bcr: Q", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&b.W, (size_t)ns * half * blk, "bcr: W", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&b.V, (size_t)ns * half * blk, "bcr: V", st)) != HELM_OK)
+        return s;
+    // working blocks of the reduction: current diagonal blocks and couplings (ping-pong)
+    float2 *Dc = nullptr, *Lc = nullptr, *Ln = nullptr, *Uc = nullptr, *Un = nullptr;
+    struct Work {
+        float2 **p[5];
+        cudaStream_t st;
+        ~Work() { for (auto q : p) dev_free(*q, st); }
+    } work{{&Dc, &Lc, &Ln, &Uc, &Un}, st};
+    if ((s = dev_alloc((void **)&Dc, (size_t)ns * nx * blk, "bcr: work", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&Lc, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&Ln, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&Uc, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK ||
+        (s = dev_alloc((void **)&Un, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK)
+        return s;
+    cudaError_t e;
+    {
+        const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
+        HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(per, nx, ns), 256, 0, st>>>(g, op->diag, Dc)));
+        if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr: form blocks", e); return HELM_ECUDA; }
+    }
+    const Fam fD{Dc, nz2, nz}, fDinv{b.Dinv, nz2, nz};
+    int levels = 0;
+    for (int sp = 1; sp < nx; sp *= 2, ++levels) {
+        std::vector<int> inv_pairs, tv, tw, tp, tq, td, tl, tu;
+        for (int sy = 0; sy < ns; ++sy)
+            for (int j = sp; j < nx; j += 2 * sp) inv_pairs.insert(inv_pairs.end(), {sy * nx + j, sy * nx + j});
+        if ((s = invert_blocks(nz, fD, fDinv, inv_pairs, op->status, st)) != HELM_OK) return s;
+        if (sp == 1) {
+            const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
+            HELM_TRACED(K_BCR_L0, st, (bcr_level0_kernel<<<dim3(per, (nx + 1) / 2, ns), 256, 0, st>>>(g, Dc, b.Dinv,
+                                                                                                    Ln, Un, half)));
+            if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr: level 0", e); return HELM_ECUDA; }
+        } else {
+            std::vector<int> vpairs, wpairs;
+            for (int sy = 0; sy < ns; ++sy) {
+                const int hb = sy * half, lb = sy * nx;
+                for (int j = sp; j < nx; j += 2 * sp) {
+                    // V_j = U_{j-s} Dinv_j;  W_j = L_{j+s} Dinv_j
+                    auto v = task8(hb + (j - sp) / 2, lb + j, 0, hb + j / 2);
+                    tv.insert(tv.end(), v.begin(), v.end());
+                    vpairs.insert(vpairs.end(), {hb + j / 2, hb + j / 2});
+                    if (j + sp < nx) {
+                        auto w = task8(hb + (j + sp) / 2, lb + j, 0, hb + j / 2);
+                        tw.insert(tw.end(), w.begin(), w.end());
+                        wpairs.insert(wpairs.end(), {hb + j / 2, hb + j / 2});
+                    }
+                }
+                for (int k = 0; k < nx; k += 2 * sp) {
+                    const bool ha = k >= sp, hc = k + sp < nx;
+                    if (!ha && !hc) continue;
+                    // D_k -= L_k W_a^T + U_k V_c^T
+                    auto d = task8(ha ? hb + k / 2 : -1, ha ? hb + (k - sp) / 2 : 0, lb + k, lb + k,
+                                   hc ? hb + k / 2 : -1, hc ? hb + (k + sp) / 2 : 0);
+                    td.insert(td.end(), d.begin(), d.end());
+                    if (k >= 2 * sp) {   // L_k <- -L_k V_a^T
+                        auto l = task8(hb + k / 2, hb + (k - sp) / 2, 0, hb + k / 2);
+                        tl.insert(tl.end(), l.begin(), l.end());
+                    }
+                    if (k + 2 * sp < nx) {   // U_k <- -U_k W_c^T
+                        auto u = task8(hb + k / 2, hb + (k + sp) / 2, 0, hb + k / 2);
+                        tu.insert(tu.end(), u.begin(), u.end());
+                    }
+                }
+            }
+            ZGemmArgs ga;
+            ga.M = ga.N = ga.K = nz;
+            ga.status = op->status;
+            ga.nterms = 1;
+            ga.B[0] = zop(b.Dinv, nz2, nz);
+            ga.C = b.V; ga.c_stride = nz2; ga.ldc = nz;
+            ga.A[0] = zop(Uc, nz2, nz);
+            if ((s = gemm(ga, tv, st)) != HELM_OK) return s;
+            ga.C = b.W;
+            ga.A[0] = zop(Lc, nz2, nz);
+            if ((s = gemm(ga, tw, st)) != HELM_OK) return s;
+            if ((s = transpose_blocks(nz, b.V, b.P, nz2, vpairs, st)) != HELM_OK) return s;
+            if ((s = transpose_blocks(nz, b.W, b.Q, nz2, wpairs, st)) != HELM_OK) return s;
+            ZGemmArgs gd;
+            gd.M = gd.N = gd.K = nz;
+            gd.status = op->status;
+            gd.nterms = 2;
+            gd.A[0] = zop(Lc, nz2, nz); gd.B[0] = zop(b.W, nz2, nz); gd.sign[0] = -1.f;
+            gd.A[1] = zop(Uc, nz2, nz); gd.B[1] = zop(b.V, nz2, nz); gd.sign[1] = -1.f;
+            gd.C0 = zop(Dc, nz2, nz);
+            gd.C = Dc; gd.c_stride = nz2; gd.ldc = nz;
+            if ((s = gemm(gd, td, st)) != HELM_OK) return s;
+            ZGemmArgs gl;
+            gl.M = gl.N = gl.K = nz;
+            gl.status = op->status;
+            gl.nterms = 1;
+            gl.sign[0] = -1.f;
+            gl.A[0] = zop(Lc, nz2, nz); gl.B[0] = zop(b.V, nz2, nz);
+            gl.C = Ln; gl.c_stride = nz2; gl.ldc = nz;
+            if ((s = gemm(gl, tl, st)) != HELM_OK) return s;
+            gl.A[0] = zop(Uc, nz2, nz); gl.B[0] = zop(b.W, nz2, nz);
+            gl.C = Un;
+            if ((s = gemm(gl, tu, st)) != HELM_OK) return s;
+        }
+        std::swap(Lc, Ln);
+        std::swap(Uc, Un);
+    }
+    // the last line left: line 0
+    {
+        std::vector<int> last;
+        for (int sy = 0; sy < ns; ++sy) last.insert(last.end(), {sy * nx, sy * nx});
+        if ((s = invert_blocks(nz, fD, fDinv, last, op->status, st)) != HELM_OK) return s;
+    }
+    b.levels = levels;
+    // the solve's task lists, built once: forward levels 1 .. L-1, last line, backward L-1 .. 1,
+    // level 0 both ways (vector operands indexed system * nx + line)
+    std::vector<int> all;
+    b.fwd.assign(levels, {0, 0});
+    b.bwd.assign(levels, {0, 0});
+    auto add = [&](std::vector<int> &&v) { all.insert(all.end(), v.begin(), v.end()); };
+    for (int l = 0, sp = 1; l < levels; ++l, sp *= 2) {
+        const int off = (int)all.size() / 8;
+        for (int sy = 0; sy < ns; ++sy) {
+            const int hb = sy * half, lb = sy * nx;
+            if (l == 0) {
+                for (int j = 1; j < nx; j += 2) add(task8(lb + j, lb + j, 0, lb + j));   // y_j = Dinv_j b_j
+            } else {
+                for (int k = 0; k < nx; k += 2 * sp) {
+                    const bool ha = k >= sp, hc = k + sp < nx;
+                    if (!ha && !hc) continue;
+                    add(task8(ha ? hb + (k - sp) / 2 : -1, ha ? lb + k - sp : 0, lb + k, lb + k,
+                              hc ? hb + (k + sp) / 2 : -1, hc ? lb + k + sp : 0));
+                }
+            }
+        }
+        b.fwd[l] = {off, (int)all.size() / 8 - off};
+    }
+    b.last = {(int)all.size() / 8, ns};
+    for (int sy = 0; sy < ns; ++sy) add(task8(sy * nx, sy * nx, 0, sy * nx));
+    for (int l = 0, sp = 1; l < levels; ++l, sp *= 2) {
+        const int off = (int)all.size() / 8;
+        for (int sy = 0; sy < ns; ++sy) {
+            const int hb = sy * half, lb = sy * nx;
+            for (int j = sp; j < nx; j += 2 * sp) {
+                if (l == 0) {
+                    add(task8(lb + j, lb + j, lb + j, lb + j));   // x_j = y_j - Dinv_j t_j
+                } else {
+                    const bool hc = j + sp < nx;
+                    add(task8(lb + j, lb + j, 0, lb + j, hb + j / 2, lb + j - sp, hc ? hb + j / 2 : -1,
+                              hc ? lb + j + sp : 0));
+                }
+            }
+        }
+        b.bwd[l] = {off, (int)all.size() / 8 - off};
+    }
+    if ((s = dev_alloc((void **)&b.tasks, all.size() * sizeof(int), "bcr: solve plan", st)) != HELM_OK) return s;
+    if ((e = cudaMemcpyAsync(b.tasks, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        helm_set_error("bcr: solve plan", e);
+        return HELM_ECUDA;
+    }
+    // the work blocks are released on the stream after the last kernel that reads them
+    return HELM_OK;
+}
+
+void bcr_free(helm_factor_t *f) {
+    const cudaStream_t st = f->op ? f->op->st : nullptr;
+    BcrData &b = f->bcr;
+    dev_free(b.Dinv, st);
+    dev_free(b.P, st);
+    dev_free(b.Q, st);
+    dev_free(b.W, st);
+    dev_free(b.V, st);
+    dev_free(b.tasks, st);
+    b = BcrData();
+}
+
+// ------------------------------------------------------------------- solve
+
+// x = A~^{-1} r for every system and right-hand side, complex FP32: r [n_sys][nrhs][N] is the
+// working vector (overwritten), x [n_sys][nrhs][N] the result.  skip: launches do nothing
+// while it is set (refinement finished).
+helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip) {
+    const helm_op *op = f->op;
+    const GridGeom &g = op->g;
+    const int nx = g.nx, nz = g.nz, ns = op->n_omega, N = nx * nz;
+    const long long nz2 = (long long)nz * nz;
+    const BcrData &b = f->bcr;
+    const cudaStream_t st = op->st;
+    const long long vhi = (long long)nrhs * N;   // vectors: index system * nx + line
+    auto vec = [&](const float2 *base) { return zop(base, nz, N, nx, vhi); };
+    ZGemmArgs ga;
+    ga.M = nz; ga.N = nrhs; ga.K = nz;
+    ga.c_col = 1;
+    ga.status = op->status;
+    ga.skip = skip;
+    ga.tries = wait_tries();
+    ga.c_stride = nz; ga.c_div = nx; ga.c_stride_hi = vhi; ga.ldc = N;
+    cudaError_t e;
+    auto launch = [&](ZGemmArgs a, std::pair<int, int> lst) -> helm_status {
+        a.tasks = b.tasks + 8 * (size_t)lst.first;
+        e = launch_zgemm(a, lst.second, st);
+        if (e != cudaSuccess) { helm_set_error("bcr solve: tensor-core GEMM", e); return HELM_ECUDA; }
+        return HELM_OK;
+    };
+    helm_status s;
+    const int nodd = nx / 2, neven = (nx + 1) / 2;
+    const int per = (nz + 127) / 128;
+    // forward, level 0: y_j = Dinv_j b_j into x, then b_k -= C (y_{k-1} + y_{k+1})
+    {
+        ZGemmArgs a = ga;
+        a.nterms = 1;
+        a.A[0] = zop(b.Dinv, nz2, nz);
+        a.B[0] = vec(r);
+        a.C = x;
+        if ((s = launch(a, b.fwd[0])) != HELM_OK) return s;
+        HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_fwd_kernel<<<dim3(per, neven, ns * nrhs), 128, 0, st>>>(
+                                            g, nrhs, r, x, skip)));
+        if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
+    }
+    for (int l = 1; l < b.levels; ++l) {   // b_k -= W_a b_a + V_c b_c
+        ZGemmArgs a = ga;
+        a.nterms = 2;
+        a.A[0] = zop(b.W, nz2, nz); a.B[0] = vec(r); a.sign[0] = -1.f;
+        a.A[1] = zop(b.V, nz2, nz); a.B[1] = vec(r); a.sign[1] = -1.f;
+        a.C0 = vec(r);
+        a.C = r;
+        if ((s = launch(a, b.fwd[l])) != HELM_OK) return s;
+    }
+    {   // x_0 = Dinv_0 b_0
+        ZGemmArgs a = ga;
+        a.nterms = 1;
+        a.A[0] = zop(b.Dinv, nz2, nz);
+        a.B[0] = vec(r);
+        a.C = x;
+        if ((s = launch(a, b.last)) != HELM_OK) return s;
+    }
+    for (int l = b.levels - 1; l >= 1; --l) {   // x_j = Dinv_j b_j - P_j x_{j-s} - Q_j x_{j+s}
+        ZGemmArgs a = ga;
+        a.nterms = 3;
+        a.A[0] = zop(b.Dinv, nz2, nz); a.B[0] = vec(r);
+        a.A[1] = zop(b.P, nz2, nz); a.B[1] = vec(x); a.sign[1] = -1.f;
+        a.A[2] = zop(b.Q, nz2, nz); a.B[2] = vec(x); a.sign[2] = -1.f;
+        a.C = x;
+        if ((s = launch(a, b.bwd[l])) != HELM_OK) return s;
+    }
+    {   // backward, level 0: t_j = C (x_{j-1} + x_{j+1}) into b_j, x_j = y_j - Dinv_j t_j
+        if (nodd > 0) {
+            HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_bwd_kernel<<<dim3(per, nodd, ns * nrhs), 128, 0, st>>>(
+                                                g, nrhs, r, x, skip)));
+            if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
+        }
+        ZGemmArgs a = ga;
+        a.nterms = 1;
+        a.A[0] = zop(b.Dinv, nz2, nz); a.B[0] = vec(r); a.sign[0] = -1.f;
+        a.C0 = vec(x);
+        a.C = x;
+        if ((s = launch(a, b.bwd[0])) != HELM_OK) return s;
+    }
+    return HELM_OK;
+}
+
+// ------------------------------------------------ building blocks at the ABI (helm_blas.h)
+
+helm_status blas_zgemm(int batch, int M, int N, int K, const float2 *A, long long sa, int lda, const float2 *Bt,
+                       long long sb, int ldb, float sign, const float2 *C0, float2 *C, long long sc, int ldc,
+                       cudaStream_t st, int *status) {
+    ZGemmArgs a;
+    a.M = M; a.N = N; a.K = K;
+    a.nterms = 1;
+    a.A[0] = zop(A, sa, lda);
+    a.B[0] = zop(Bt, sb, ldb);
+    a.sign[0] = sign;
+    if (C0) a.C0 = zop(C0, sc, ldc);
+    a.C = C; a.c_stride = sc; a.ldc = ldc;
+    a.status = status;
+    std::vector<int> tasks;
+    for (int t = 0; t < batch; ++t) {
+        auto v = task8(t, t, t, t);
+        tasks.insert(tasks.end(), v.begin(), v.end());
+    }
+    return gemm(a, tasks, st);
+}
+
+helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, float2 *X, long long sx, int ldx,
+                      cudaStream_t st, int *status) {
+    std::vector<int> pairs;
+    for (int t = 0; t < batch; ++t) pairs.insert(pairs.end(), {t, t});
+    if (A != X) {   // copy into X first: the recursion works in place on the output blocks
+        cudaError_t e = cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(float2), A, (size_t)lda * sizeof(float2),
+                                          (size_t)n * sizeof(float2), (size_t)n, cudaMemcpyDeviceToDevice, st);
+        for (int t = 1; t < batch && e == cudaSuccess; ++t)
+            e = cudaMemcpy2DAsync(X + (long long)t * sx, (size_t)ldx * sizeof(float2), A + (long long)t * sa,
+                                  (size_t)lda * sizeof(float2), (size_t)n * sizeof(float2), (size_t)n,
+                                  cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { helm_set_error("helm_zinv_batched: copy", e); return HELM_ECUDA; }
+    }
+    const Fam f{X, sx, ldx};
+    return invert_blocks(n, f, f, pairs, status, st);
+}
+
+}  // namespace helm
+
+// ------------------------------------------------------------------ C ABI (helm_blas.h)
+
+#include "helm_blas.h"
+
+namespace {
+struct DevStatus {   // a device status word for the building-block calls
+    int *p = nullptr;
+    cudaStream_t st;
+    explicit DevStatus(cudaStream_t s) : st(s) {}
+    ~DevStatus() { ::dev_free(p, st); }
+};
+}  // namespace
+
+extern "C" helm_status helm_zgemm_batched(int32_t batch, int32_t M, int32_t N, int32_t K, const helm_c64 *A, int64_t sa,
+                                          int32_t lda, const helm_c64 *Bt, int64_t sb, int32_t ldb, float sign,
+                                          const helm_c64 *C0, helm_c64 *C, int64_t sc, int32_t ldc, void *stream) {
+    if (batch < 0 || batch > 65535 || M < 1 || N < 1 || K < 1 || (K & 1) || !A || !Bt || !C || lda < K || ldb < K ||
+        ldc < N || (lda & 1) || (ldb & 1) || (sa & 1) || (sb & 1) || (sign != 1.f && sign != -1.f) ||
+        ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) {
+        helm_set_msg("helm_zgemm_batched: bad sizes, strides, alignment or sign");
+        return HELM_EINVAL;
+    }
+    if (batch == 0) return HELM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevStatus ds(st);
+    helm_status s = dev_alloc((void **)&ds.p, sizeof(int), "helm_zgemm_batched: status", st);
+    if (s != HELM_OK) return s;
+    cudaError_t e = cudaMemsetAsync(ds.p, 0, sizeof(int), st);
+    if (e != cudaSuccess) { helm_set_error("helm_zgemm_batched", e); return HELM_ECUDA; }
+    return helm::blas_zgemm(batch, M, N, K, (const float2 *)A, sa, lda, (const float2 *)Bt, sb, ldb, sign,
+                            (const float2 *)C0, (float2 *)C, sc, ldc, st, ds.p);
+}
+
+extern "C" helm_status helm_zinv_batched(int32_t batch, int32_t n, const helm_c64 *A, int64_t sa, int32_t lda,
+                                         helm_c64 *X, int64_t sx, int32_t ldx, void *stream) {
+    if (batch < 0 || batch > 65535 || n < 2 || (n & 1) || !A || !X || lda < n || ldx < n || (lda & 1) || (ldx & 1) ||
+        (sa & 1) || (sx & 1) || ((uintptr_t)A & 15) || ((uintptr_t)X & 15)) {
+        helm_set_msg("helm_zinv_batched: bad sizes, strides or alignment");
+        return HELM_EINVAL;
+    }
+    if (batch == 0) return HELM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevStatus ds(st);
+    helm_status s = dev_alloc((void **)&ds.p, sizeof(int), "helm_zinv_batched: status", st);
+    if (s != HELM_OK) return s;
+    cudaError_t e = cudaMemsetAsync(ds.p, 0, sizeof(int), st);
+    if (e != cudaSuccess) { helm_set_error("helm_zinv_batched", e); return HELM_ECUDA; }
+    if ((s = helm::blas_zinv(batch, n, (const float2 *)A, sa, lda, (float2 *)X, sx, ldx, st, ds.p)) != HELM_OK) return s;
+    int h = 0;
+    e = cudaMemcpyAsync(&h, ds.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { helm_set_error("helm_zinv_batched", e); return HELM_ECUDA; }
+    if (h & helm::ST_SINGULAR) { helm_set_msg("helm_zinv_batched: zero or non-finite pivot"); return HELM_ESINGULAR; }
+    return HELM_OK;
+}

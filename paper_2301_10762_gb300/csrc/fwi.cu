@@ -764,6 +764,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     // the data branch (A(m') assembled, factored, u' = A(m')^{-1} e_s, d = R u') runs on
     // its own stream from a second host thread, concurrently with A(m_fwi) and u; the stream
     // outlives the handles allocated on it (declared first, destroyed last)
+    const helm_factor_opts fopts{po->factor_method};
     cudaStream_t st2 = nullptr;
     HK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     struct StreamGuard { cudaStream_t s; ~StreamGuard() { if (s) cudaStreamDestroy(s); } } sg{st2};
@@ -781,7 +782,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     std::thread data_branch([&]() {
         auto run = [&]() {
             s2 = helm_assemble(grid, m_true, omega, n_omega, st2, &ms.op_t);
-            if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &ms.fac_t);
+            if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &fopts, &ms.fac_t);
             if (s2 == HELM_OK) s2 = acq_upload(ms.op_t, acq, &da2);
             if (s2 != HELM_OK) return;
             const GridGeom &gt = ms.op_t->g;
@@ -801,7 +802,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     });
     struct Joiner { std::thread &t; ~Joiner() { if (t.joinable()) t.join(); } } joiner{data_branch};
     s = helm_assemble(grid, m_fwi, omega, n_omega, st, &ms.op_f);
-    if (s == HELM_OK) s = helm_factor(ms.op_f, prec, &ms.fac_f);
+    if (s == HELM_OK) s = helm_factor(ms.op_f, prec, &fopts, &ms.fac_f);
     if (s != HELM_OK) { data_branch.join(); return s; }
     helm_op *op = ms.op_f;
     const GridGeom &g = op->g;
@@ -952,7 +953,7 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
             return HELM_EINVAL;
         }
     keep_pool_memory();
-    helm_pcg_opts po = pcg ? *pcg : helm_pcg_opts{500, 0, 1e-13, 1.0, 1e-10, 0};
+    helm_pcg_opts po = pcg ? *pcg : helm_pcg_opts{500, 0, 1e-13, 1.0, 1e-10, 0, HELM_FACTOR_AUTO};
     cudaStream_t st = (cudaStream_t)stream;
     if (info) *info = helm_hyper_info{0, 0.0, 0, 0, 0};
     const int nr = acq[0].n_rec;

@@ -82,4 +82,33 @@ cudaError_t launch_refine_finish(size_t n, const float4 *xa, const float4 *xb, c
 // X += conj?(delta) in FP64 (refinement tail with FP64 residuals)
 cudaError_t launch_refine_accumulate(size_t n, const float2 *delta, int conj, double2 *X, cudaStream_t st);
 
+// ---- zgemm_tc.cu (batched complex GEMM on tcgen05, 3xTF32)
+// A family of complex FP32 matrices: matrix idx starts at base + (idx / div) * stride_hi +
+// (idx % div) * stride (div <= 0: base + idx * stride); rows are ld elements apart.
+struct ZOperand {
+    const float2 *base = nullptr;
+    long long stride = 0, stride_hi = 0;
+    int div = 0;
+    int ld = 0;
+};
+// C_t = C0_t + sum_u sign_u A_{t,u} Bt_{t,u}^T for every task t of tasks[n_tasks][8]
+// (a_idx[3], b_idx[3], c0_idx, c_idx); a term with a negative A index is absent from its task.  A: M x K, Bt: N x K (row-major); C, C0: M x N, row-major or (c_col) column-major.
+struct ZGemmArgs {
+    int M = 0, N = 0, K = 0;
+    int nterms = 1;
+    ZOperand A[3], B[3];
+    float sign[3] = {1.f, 1.f, 1.f};
+    ZOperand C0;          // base == nullptr: no C0
+    float2 *C = nullptr;
+    long long c_stride = 0, c_stride_hi = 0;
+    int c_div = 0;
+    int ldc = 0;
+    int c_col = 0;
+    const int *tasks = nullptr;
+    int *status = nullptr;
+    const int *skip = nullptr;
+    uint32_t tries = 0;
+};
+cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st);
+
 }  // namespace helm

@@ -266,7 +266,7 @@ void helm_server::run_batch(const Model &md, std::vector<Pending> &batch, Slot *
         if (e != cudaSuccess) { helm_set_error("server: stream", e); status = HELM_ECUDA; goto out; }
         const double om = r0.omega;
         if ((status = helm_assemble(&md.grid, md.m_dev, &om, 1, sl->st, &sl->op)) != HELM_OK) goto out;
-        if ((status = helm_factor(sl->op, (helm_prec)r0.prec, &sl->f)) != HELM_OK) goto out;
+        if ((status = helm_factor(sl->op, (helm_prec)r0.prec, nullptr, &sl->f)) != HELM_OK) goto out;
     }
     if ((status = dev_alloc((void **)&Bd, rhs * N * sizeof(helm_c128), "server: allocate(B)", sl->st)) != HELM_OK ||
         (status = dev_alloc((void **)&Xd, rhs * N * sizeof(helm_c128), "server: allocate(X)", sl->st)) != HELM_OK)

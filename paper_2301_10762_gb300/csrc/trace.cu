@@ -14,6 +14,7 @@ static const char *kNames[K_COUNT] = {
     "g_u_p_rhs", "z_rhs_base", "hess_accumulate", "hyper_terms", "dot_partial", "sum_partials", "axpby",
     "fill", "sub", "regR", "dct_matrix", "p2_scale", "dgemm_dct", "line_gb_prepass", "split_diag", "refine_start", "refine_update",
     "refine_finish", "refine_accumulate", "field_grad", "g_coefficients", "hess_finish",
+    "zgemm_tf32x3", "zinv_block", "ztranspose", "bcr_form_blocks", "bcr_level0_update", "bcr_solve_level0",
 };
 
 namespace {

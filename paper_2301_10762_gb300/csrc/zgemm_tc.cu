@@ -1,0 +1,310 @@
+// Batched complex-FP32 GEMM on the fifth-generation tensor cores (tcgen05, accumulator in
+// tensor memory), with the 3xTF32 split that keeps the products near FP32 accuracy:
+//     C_t = C0_t + sum_u s_u A_{t,u} Bt_{t,u}^T      (t: task, u <= 3 terms, s_u = +-1)
+// A (M x K) and Bt (N x K) are row-major complex matrices (interleaved re, im); C and C0 are
+// row-major or column-major.  This is the dense contraction of the block-cyclic-reduction
+// factor and solve (block products of the line blocks; all right-hand sides of a system as
+// the N dimension of the solve's products).
+//
+// Complex products as real ones: with A taken as the real M x 2K matrix of its interleaved
+// entries, and each complex row b of Bt expanded into the two real rows
+//     (Re b0, -Im b0, Re b1, -Im b1, ...)  and  (Im b0, Re b0, Im b1, Re b1, ...),
+// the real product A_r Bt_r^T is the interleaved complex C (column 2n = Re, 2n + 1 = Im).
+// Each real operand x is split into hi = tf32(x) and lo = x - hi, and the tile accumulates
+// hi*hi + hi*lo + lo*hi in FP32 in tensor memory (the lo*lo term is below FP32 rounding).
+//
+// One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Its 256
+// threads load a K chunk of 16 complex columns (one 128-byte row per matrix row) from global
+// memory a chunk ahead into registers, split it and store it into shared memory in the
+// 128-byte-swizzled K-major layout the tensor core reads; one thread issues the 12 MMAs of the
+// chunk and commits them to the chunk's stage barrier, which the writers of that stage wait for
+// STAGES chunks later.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
+// 32 (w % 4) .. + 31, column half w / 4), adds C0 and writes C.
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace helm {
+
+namespace {
+
+constexpr int ZG_THREADS = 256;
+constexpr int ZG_BM = 128;   // tile rows (tcgen05 M)
+constexpr int ZG_KC = 16;    // complex K per chunk: 32 floats = one 128-byte swizzle row
+
+// byte offset of 16-byte chunk j of row r in a 128-byte-swizzled tile (tile base 1024-aligned)
+__device__ __forceinline__ uint32_t sw128(int r, int j) { return (uint32_t)(r * 128 + (((j ^ r) & 7) << 4)); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu)        // start address
+           | ((uint64_t)1 << 16)                      // leading byte offset (unused for this layout)
+           | ((uint64_t)(1024 >> 4) << 32)            // stride byte offset: next 8-row group
+           | ((uint64_t)1 << 46)                      // descriptor version of this architecture
+           | ((uint64_t)2 << 61);                     // 128-byte swizzle
+}
+
+// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M = 128, N = n_real
+__host__ __device__ constexpr uint32_t idesc_tf32(int n_real) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// hi / lo split of the four floats of v (s: the term's sign, exact)
+__device__ __forceinline__ void split4(float4 v, float s, float4 &hi, float4 &lo) {
+    v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+    hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+    lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// arrive on the mbarrier once every tcgen05 operation issued so far by this thread is complete
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ long long zop_off(int idx, int div, long long stride, long long stride_hi) {
+    return div > 0 ? (long long)(idx / div) * stride_hi + (long long)(idx % div) * stride : (long long)idx * stride;
+}
+
+template <int NT> struct ZCfg {
+    static constexpr int NR = 2 * NT;                        // real columns of the tile (tcgen05 N)
+    static constexpr int A_BYTES = ZG_BM * 128;              // one split of the A chunk
+    static constexpr int B_BYTES = NR * 128;                 // one split of the expanded Bt chunk
+    static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int STAGES = NT <= 64 ? 3 : 2;
+    static constexpr int TMEM_COLS = NR < 32 ? 32 : NR;      // a power of two >= 32
+    static constexpr int A_V4 = ZG_BM * 8 / ZG_THREADS;      // float4 of the A chunk per thread
+    static constexpr int B_V4 = (NT * 8 + ZG_THREADS - 1) / ZG_THREADS;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;   // + alignment slack
+};
+
+template <int NT>
+__global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
+    using Cfg = ZCfg<NT>;
+    extern __shared__ uint8_t zg_smem_raw[];
+    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    if (a.skip && *a.skip) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * ZG_BM, n0 = blockIdx.y * NT;
+    const int* task = a.tasks + (size_t)blockIdx.z * 8;
+    const uint32_t smem0 = (smem_u32(zg_smem_raw) + 1023u) & ~1023u;
+
+    // active terms (a term whose A index is negative is absent)
+    int act[3] = {0, 0, 0}, nterms = 0;
+    for (int u = 0; u < a.nterms; ++u)
+        if (task[u] >= 0) act[nterms++] = u;
+    const int nkc = (a.K + ZG_KC - 1) / ZG_KC;
+    const int nchunks = nterms * nkc;
+
+    if (tid == 0) {
+        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&empty_bar[s], 1);
+        mbar_init(&done_bar, 1);
+        fence_mbar_init_cluster();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // ---- operand fetch of one chunk into registers
+    float4 ra[Cfg::A_V4], rb[Cfg::B_V4];
+    auto fetch = [&](int c) {
+        const int cu = c / nkc, u = cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2]), k0 = (c % nkc) * ZG_KC;
+        const float2 *A = a.A[u].base + zop_off(task[u], a.A[u].div, a.A[u].stride, a.A[u].stride_hi);
+        const float2 *B = a.B[u].base + zop_off(task[3 + u], a.B[u].div, a.B[u].stride, a.B[u].stride_hi);
+#pragma unroll
+        for (int i = 0; i < Cfg::A_V4; ++i) {
+            const int e = tid + i * ZG_THREADS, r = e >> 3, k = k0 + 2 * (e & 7);
+            ra[i] = (m0 + r < a.M && k < a.K)
+                        ? __ldg(reinterpret_cast<const float4 *>(A + (long long)(m0 + r) * a.A[u].ld + k))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < Cfg::B_V4; ++i) {
+            const int e = tid + i * ZG_THREADS, n = e >> 3, k = k0 + 2 * (e & 7);
+            rb[i] = (e < NT * 8 && n0 + n < a.N && k < a.K)
+                        ? __ldg(reinterpret_cast<const float4 *>(B + (long long)(n0 + n) * a.B[u].ld + k))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    // ---- split and store of the fetched chunk into stage s
+    auto store = [&](int c, int s) {
+        const int cu = c / nkc;
+        const float sg = a.sign[cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2])];
+        const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
+        const uint32_t a_hi = base, a_lo = base + Cfg::A_BYTES;
+        const uint32_t b_hi = base + 2 * Cfg::A_BYTES, b_lo = b_hi + Cfg::B_BYTES;
+#pragma unroll
+        for (int i = 0; i < Cfg::A_V4; ++i) {
+            const int e = tid + i * ZG_THREADS, r = e >> 3, j = e & 7;
+            float4 hi, lo;
+            split4(ra[i], sg, hi, lo);
+            st_shared_v4(a_hi + sw128(r, j), hi);
+            st_shared_v4(a_lo + sw128(r, j), lo);
+        }
+#pragma unroll
+        for (int i = 0; i < Cfg::B_V4; ++i) {
+            const int e = tid + i * ZG_THREADS, n = e >> 3, j = e & 7;
+            if (e < NT * 8) {
+                const float4 v = rb[i];
+                float4 hi, lo;
+                // real row 2n: (Re, -Im) pairs; real row 2n + 1: (Im, Re) pairs
+                split4(make_float4(v.x, -v.y, v.z, -v.w), 1.f, hi, lo);
+                st_shared_v4(b_hi + sw128(2 * n, j), hi);
+                st_shared_v4(b_lo + sw128(2 * n, j), lo);
+                split4(make_float4(v.y, v.x, v.w, v.z), 1.f, hi, lo);
+                st_shared_v4(b_hi + sw128(2 * n + 1, j), hi);
+                st_shared_v4(b_lo + sw128(2 * n + 1, j), lo);
+            }
+        }
+    };
+
+    constexpr uint32_t idesc = idesc_tf32(Cfg::NR);
+    if (nchunks > 0) fetch(0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % Cfg::STAGES;
+        if (c >= Cfg::STAGES) {   // the MMAs that read this stage STAGES chunks ago are done
+            if (!mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
+                atomicOr(a.status, ST_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        if (!*(volatile int *)&s_abort) store(c, s);
+        if (c + 1 < nchunks) fetch(c + 1);   // in flight while this chunk is multiplied
+        fence_proxy_async_smem();            // the stores are visible to the tensor core's reads
+        if (__syncthreads_or(*(volatile int *)&s_abort)) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
+            const uint32_t a_hi = base, a_lo = base + Cfg::A_BYTES;
+            const uint32_t b_hi = base + 2 * Cfg::A_BYTES, b_lo = b_hi + Cfg::B_BYTES;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {   // hi*hi, hi*lo, lo*hi
+                const uint32_t aa = p == 2 ? a_lo : a_hi, bb = p == 1 ? b_lo : b_hi;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)   // K = 8 TF32 (32 bytes) per instruction
+                    tc_mma(tmem, desc_sw128(aa + 32 * kk), desc_sw128(bb + 32 * kk), idesc,
+                           (c > 0 || p > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc_commit(&empty_bar[s]);
+        }
+    }
+    // every MMA issued is complete before the accumulator is read or freed
+    if (tid == 0) tc_commit(&done_bar);
+    if (!mbar_wait_bounded(&done_bar, 0, a.tries)) {
+        atomicOr(a.status, ST_TIMEOUT);
+        s_abort = 1;
+    }
+    tc_fence_after();
+    const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
+
+    if (ok) {
+        const int q = warp & 3, h = warp >> 2;
+        const int r = 32 * q + lane, m = m0 + r;
+        const float2 *C0 =
+            a.C0.base ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) : nullptr;
+        float2 *C = a.C + zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi);
+        for (int col = h * NT; col < (h + 1) * NT; col += 16) {   // real columns of this warp's half
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+            if (m >= a.M) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int n = n0 + col / 2 + i;
+                if (n >= a.N) break;
+                float2 out = make_float2(v[2 * i], v[2 * i + 1]);
+                const long long o0 = a.c_col ? (long long)n * a.C0.ld + m : (long long)m * a.C0.ld + n;
+                const long long o = a.c_col ? (long long)n * a.ldc + m : (long long)m * a.ldc + n;
+                if (C0) {
+                    const float2 b = C0[o0];
+                    out.x += b.x;
+                    out.y += b.y;
+                }
+                C[o] = out;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+}
+
+template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
+    using Cfg = ZCfg<NT>;
+    const void *fn = (const void *)zgemm_tc_kernel<NT>;
+    cudaError_t e = ensure_dyn_smem(fn, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.M + ZG_BM - 1) / ZG_BM), (unsigned)((a.N + NT - 1) / NT), (unsigned)n_tasks);
+    HELM_TRACED(K_ZGEMM, st, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(a)));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
+    if (n_tasks <= 0) return cudaSuccess;
+    if (a.M <= 0 || a.N <= 0 || a.K <= 0 || (a.K & 1) || a.nterms < 1 || a.nterms > 3 || n_tasks > 65535)
+        return cudaErrorInvalidValue;
+    for (int u = 0; u < a.nterms; ++u)   // 16-byte operand loads: even leading dimensions and offsets
+        if ((a.A[u].ld & 1) || (a.B[u].ld & 1) || (a.A[u].stride & 1) || (a.B[u].stride & 1) ||
+            (a.A[u].stride_hi & 1) || (a.B[u].stride_hi & 1) || ((uintptr_t)a.A[u].base & 15) ||
+            ((uintptr_t)a.B[u].base & 15))
+            return cudaErrorInvalidValue;
+    if (a.N <= 16) return launch_nt<16>(a, n_tasks, st);
+    if (a.N <= 32) return launch_nt<32>(a, n_tasks, st);
+    if (a.N <= 64) return launch_nt<64>(a, n_tasks, st);
+    return launch_nt<128>(a, n_tasks, st);
+}
+
+}  // namespace helm

@@ -48,7 +48,11 @@ class helm_solve_info(C.Structure):
 
 class helm_pcg_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("fixed_iters", C.c_int32), ("rtol", C.c_double), ("x0", C.c_double),
-                ("refine_rtol", C.c_double), ("concurrent_models", C.c_int32)]
+                ("refine_rtol", C.c_double), ("concurrent_models", C.c_int32), ("factor_method", C.c_int32)]
+
+
+class helm_factor_opts(C.Structure):
+    _fields_ = [("method", C.c_int32)]
 
 
 class helm_hyper_info(C.Structure):
@@ -87,7 +91,9 @@ class helm_trace_entry(C.Structure):
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
-            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_set_wait_tries", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
+            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_set_wait_tries",
+            # include/helm_blas.h
+            "helm_zgemm_batched", "helm_zinv_batched", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
             "fwi_misfit_grad", "fwi_hessian_vec", "bilevel_hypergrad", "helm_gamma_solve",
             # include/helm_trace.h
@@ -119,7 +125,12 @@ def load(path: str = LIB_PATH):
     lib.helm_op_destroy.restype = None
     lib.helm_op_destroy.argtypes = [vp]
     lib.helm_factor.restype = C.c_int
-    lib.helm_factor.argtypes = [vp, C.c_int, P(vp)]
+    lib.helm_factor.argtypes = [vp, C.c_int, P(helm_factor_opts), P(vp)]
+    lib.helm_zgemm_batched.restype = C.c_int
+    lib.helm_zgemm_batched.argtypes = [i32, i32, i32, i32, vp, C.c_int64, i32, vp, C.c_int64, i32, C.c_float, vp, vp,
+                                       C.c_int64, i32, vp]
+    lib.helm_zinv_batched.restype = C.c_int
+    lib.helm_zinv_batched.argtypes = [i32, i32, vp, C.c_int64, i32, vp, C.c_int64, i32, vp]
     lib.helm_set_wait_tries.restype = None
     lib.helm_set_wait_tries.argtypes = [C.c_int64]
     lib.helm_factor_fp64_blocks.restype = i32
@@ -287,11 +298,46 @@ def helm_set_wait_tries(tries=-1):
     load().helm_set_wait_tries(int(tries))
 
 
-def helm_factor(op: Op, prec=HELM_FP64) -> Factor:
+HELM_FACTOR_AUTO, HELM_FACTOR_LINE, HELM_FACTOR_BCR = 0, 1, 2
+
+
+def helm_factor(op: Op, prec=HELM_FP64, method=HELM_FACTOR_AUTO) -> Factor:
     lib = load()
     h = C.c_void_p()
-    _check(lib.helm_factor(op.handle, int(prec), C.byref(h)), "helm_factor")
+    opts = helm_factor_opts(int(method))
+    _check(lib.helm_factor(op.handle, int(prec), C.byref(opts), C.byref(h)), "helm_factor")
     return Factor(h, op, prec)
+
+
+def helm_zgemm_batched(A: torch.Tensor, Bt: torch.Tensor, C0: torch.Tensor | None = None, sign=1.0, C=None,
+                       stream=None):
+    """C[t] = C0[t] + sign * A[t] @ Bt[t].T on the tensor cores (complex64, [batch, rows, cols])."""
+    lib = load()
+    if A.dim() != 3 or Bt.dim() != 3 or A.shape[0] != Bt.shape[0] or A.shape[2] != Bt.shape[2]:
+        raise ValueError("A [batch, M, K], Bt [batch, N, K]")
+    b, M, K = A.shape
+    N = Bt.shape[1]
+    pa = _dev(A, torch.complex64, "A")
+    pb = _dev(Bt, torch.complex64, "Bt")
+    if C is None:
+        C = torch.empty((b, M, N), dtype=torch.complex64, device=A.device)
+    pc = _dev(C, torch.complex64, "C", (b, M, N))
+    p0 = _dev(C0, torch.complex64, "C0", (b, M, N)) if C0 is not None else None
+    _check(lib.helm_zgemm_batched(b, M, N, K, pa, M * K, K, pb, N * K, K, float(sign), p0, pc, M * N, N,
+                                  _stream_ptr(stream)), "helm_zgemm_batched")
+    return C
+
+
+def helm_zinv_batched(A: torch.Tensor, X: torch.Tensor | None = None, stream=None):
+    """X[t] = A[t]^{-1} for complex symmetric complex64 matrices [batch, n, n]."""
+    lib = load()
+    b, n, _ = A.shape
+    pa = _dev(A, torch.complex64, "A", (b, n, n))
+    if X is None:
+        X = torch.empty_like(A)
+    px = _dev(X, torch.complex64, "X", (b, n, n))
+    _check(lib.helm_zinv_batched(b, n, pa, n * n, n, px, n * n, n, _stream_ptr(stream)), "helm_zinv_batched")
+    return X
 
 
 def _solve(name, f: Factor, B, X, rtol, max_iter):
@@ -426,7 +472,7 @@ def helm_gamma_solve(nx, nz, alpha0, mu, R: torch.Tensor, Z: torch.Tensor | None
 
 def bilevel_hypergrad(grids, m_fwi, m_true, acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
                       cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
-                      stream=None, concurrent_models=0):
+                      stream=None, concurrent_models=0, factor_method=0):
     """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors; acq: one
     Acq for every model, or a list with one per model (the same number of receivers)."""
     lib = load()
@@ -441,7 +487,7 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq, omegas, alpha, alpha0, mu, prec
     pt = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_true", (g[0] * g[1],)).value for t, g in zip(m_true, grids)])
     om, p_om = _dbuf(np.atleast_1d(omegas))
     opts = helm_pcg_opts(int(cg_max_iter), int(cg_fixed_iters), float(cg_rtol), float(x0), float(refine_rtol),
-                         int(concurrent_models))
+                         int(concurrent_models), int(factor_method))
     psi, dalpha = C.c_double(), C.c_double()
     dp = np.zeros((acq.n_rec, 2))
     dw = np.zeros(acq.n_rec)

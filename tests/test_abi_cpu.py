@@ -7,7 +7,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("helm.h", "helm_trace.h", "helm_server.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("helm.h", "helm_trace.h", "helm_server.h", "helm_blas.h")]
 LIB = os.path.join(ROOT, "paper_2301_10762_gb300", "libhelm.so")
 
 
@@ -80,7 +80,7 @@ def test_invalid_arguments_return_einval_with_a_message():
     d = ctypes.c_double
     calls = {
         "helm_assemble": lambda: lib.helm_assemble(None, None, None, 0, None, None),
-        "helm_factor": lambda: lib.helm_factor(None, 0, None),
+        "helm_factor": lambda: lib.helm_factor(None, 0, None, None),
         "helm_solve": lambda: lib.helm_solve(None, 1, None, None, d(1e-10), 8, None),
         "helm_solve_noalloc": lambda: lib.helm_solve_noalloc(None, 1, None, None, d(1e-10), 8, 0, None),
         "helm_sources": lambda: lib.helm_sources(None, None, None),
@@ -93,6 +93,11 @@ def test_invalid_arguments_return_einval_with_a_message():
         "helm_gamma_solve": lambda: lib.helm_gamma_solve(None, d(1e-3), d(1e-6), 1, None, None, None),
         "bilevel_hypergrad": lambda: lib.bilevel_hypergrad(0, None, None, None, None, None, 0, d(0), d(0), d(0), 0,
                                                            None, None, None, None, None, None, None),
+        "helm_zgemm_batched": lambda: lib.helm_zgemm_batched(1, 0, 1, 2, None, ctypes.c_int64(0), 2, None,
+                                                             ctypes.c_int64(0), 2, ctypes.c_float(1.0), None, None,
+                                                             ctypes.c_int64(0), 1, None),
+        "helm_zinv_batched": lambda: lib.helm_zinv_batched(1, 0, None, ctypes.c_int64(0), 0, None, ctypes.c_int64(0),
+                                                           0, None),
         "helm_server_create": lambda: lib.helm_server_create(None, None),
         "helm_server_add_model": lambda: lib.helm_server_add_model(None, None, None, None),
         "helm_server_submit": lambda: lib.helm_server_submit(None, None, None),
