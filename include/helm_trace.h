@@ -21,6 +21,9 @@ typedef struct {
     int64_t launches;     /* launches since the last reset */
     double total_ms;      /* summed device time of the traced launches (0 if tracing was off) */
     int64_t timed;        /* launches that were timed */
+    double flops;         /* useful floating-point operations of the timed launches, for kernels
+                             that report them (the tensor-core GEMM: 8 M N K per complex product
+                             term, 0 for the others) */
 } helm_trace_entry;
 
 /* Enable (on != 0) or disable per-launch event timing.  Enabling creates a pool of CUDA

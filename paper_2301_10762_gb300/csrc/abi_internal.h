@@ -33,8 +33,12 @@ struct BcrData {
     int levels = 0, half = 0;
     float2 *Dinv = nullptr, *P = nullptr, *Q = nullptr, *W = nullptr, *V = nullptr;
     int *tasks = nullptr;
-    std::vector<std::pair<int, int>> fwd, bwd;   // per level: (first task, task count)
-    std::pair<int, int> last{0, 0};
+    struct List {
+        int first = 0, count = 0;   // tasks of one GEMM launch of the solve
+        long long terms = 0;        // product terms over those tasks
+    };
+    std::vector<List> fwd, bwd;     // per level
+    List last;
 };
 
 struct helm_factor {

@@ -275,6 +275,14 @@ std::vector<int> task8(int a0, int b0, int c0, int c, int a1 = -1, int b1 = -1, 
     return {a0, a1, a2, b0, b1, b2, c0, c};
 }
 
+// product terms of a task list (a term is present when its A index is not negative)
+long long count_terms(const int *tasks, size_t n_tasks, int nterms) {
+    long long t = 0;
+    for (size_t i = 0; i < n_tasks; ++i)
+        for (int u = 0; u < nterms; ++u) t += tasks[8 * i + u] >= 0;
+    return t;
+}
+
 helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, cudaStream_t st) {
     if (tasks.empty()) return HELM_OK;
     TaskBuf tb;
@@ -283,6 +291,7 @@ helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, cudaStream_
     ZGemmArgs a = a0;
     a.tasks = tb.dev;
     a.tries = wait_tries();
+    a.flops = 8.0 * a.M * a.N * a.K * (double)count_terms(tasks.data(), tasks.size() / 8, a.nterms);
     cudaError_t e = launch_zgemm(a, (int)(tasks.size() / 8), st);
     if (e != cudaSuccess) { helm_set_error("bcr: tensor-core GEMM", e); return HELM_ECUDA; }
     return HELM_OK;
@@ -517,8 +526,15 @@ helm_status bcr_factor(helm_factor_t *f) {
     // the solve's task lists, built once: forward levels 1 .. L-1, last line, backward L-1 .. 1,
     // level 0 both ways (vector operands indexed system * nx + line)
     std::vector<int> all;
-    b.fwd.assign(levels, {0, 0});
-    b.bwd.assign(levels, {0, 0});
+    b.fwd.assign(levels, BcrData::List());
+    b.bwd.assign(levels, BcrData::List());
+    auto list_of = [&](int off, int nt) {
+        BcrData::List L;
+        L.first = off;
+        L.count = (int)all.size() / 8 - off;
+        L.terms = count_terms(all.data() + 8 * (size_t)off, (size_t)L.count, nt);
+        return L;
+    };
     auto add = [&](std::vector<int> &&v) { all.insert(all.end(), v.begin(), v.end()); };
     for (int l = 0, sp = 1; l < levels; ++l, sp *= 2) {
         const int off = (int)all.size() / 8;
@@ -535,10 +551,13 @@ helm_status bcr_factor(helm_factor_t *f) {
                 }
             }
         }
-        b.fwd[l] = {off, (int)all.size() / 8 - off};
+        b.fwd[l] = list_of(off, l == 0 ? 1 : 2);
     }
-    b.last = {(int)all.size() / 8, ns};
-    for (int sy = 0; sy < ns; ++sy) add(task8(sy * nx, sy * nx, 0, sy * nx));
+    {
+        const int off = (int)all.size() / 8;
+        for (int sy = 0; sy < ns; ++sy) add(task8(sy * nx, sy * nx, 0, sy * nx));
+        b.last = list_of(off, 1);
+    }
     for (int l = 0, sp = 1; l < levels; ++l, sp *= 2) {
         const int off = (int)all.size() / 8;
         for (int sy = 0; sy < ns; ++sy) {
@@ -553,7 +572,7 @@ helm_status bcr_factor(helm_factor_t *f) {
                 }
             }
         }
-        b.bwd[l] = {off, (int)all.size() / 8 - off};
+        b.bwd[l] = list_of(off, l == 0 ? 1 : 3);
     }
     if ((s = dev_alloc((void **)&b.tasks, all.size() * sizeof(int), "bcr: solve plan", st)) != HELM_OK) return s;
     if ((e = cudaMemcpyAsync(b.tasks, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
@@ -598,9 +617,10 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     ga.tries = wait_tries();
     ga.c_stride = nz; ga.c_div = nx; ga.c_stride_hi = vhi; ga.ldc = N;
     cudaError_t e;
-    auto launch = [&](ZGemmArgs a, std::pair<int, int> lst) -> helm_status {
+    auto launch = [&](ZGemmArgs a, const BcrData::List &lst) -> helm_status {
         a.tasks = b.tasks + 8 * (size_t)lst.first;
-        e = launch_zgemm(a, lst.second, st);
+        a.flops = 8.0 * a.M * a.N * a.K * (double)lst.terms;
+        e = launch_zgemm(a, lst.count, st);
         if (e != cudaSuccess) { helm_set_error("bcr solve: tensor-core GEMM", e); return HELM_ECUDA; }
         return HELM_OK;
     };

@@ -108,6 +108,7 @@ struct ZGemmArgs {
     int *status = nullptr;
     const int *skip = nullptr;
     uint32_t tries = 0;
+    double flops = 0.0;   // useful flops of the launch (8 M N K per complex term of every task), for tracing
 };
 cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st);
 

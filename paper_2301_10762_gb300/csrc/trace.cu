@@ -22,6 +22,7 @@ struct Rec {
     int id;
     cudaEvent_t a, b;
     cudaStream_t st;
+    double flops;
 };
 std::mutex g_mu;
 bool g_on = false;
@@ -29,6 +30,7 @@ int g_only = -1;   // kernel index timed alone (-1: all)
 int64_t g_launch[K_COUNT] = {};
 int64_t g_timed[K_COUNT] = {};
 double g_ms[K_COUNT] = {};
+double g_flops[K_COUNT] = {};
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 
@@ -44,7 +46,7 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 
-TraceScope::TraceScope(int id, cudaStream_t st) : id_(id), st_(st), a_(nullptr) {
+TraceScope::TraceScope(int id, cudaStream_t st, double flops) : id_(id), st_(st), a_(nullptr), flops_(flops) {
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_launch[id];
     if (g_on && (g_only < 0 || g_only == id)) {
@@ -59,7 +61,7 @@ TraceScope::~TraceScope() {
     cudaEvent_t b = get_event();
     if (!b) return;
     cudaEventRecord(b, st_);
-    g_recs.push_back(Rec{id_, a_, b, st_});
+    g_recs.push_back(Rec{id_, a_, b, st_, flops_});
 }
 
 }  // namespace helm
@@ -97,6 +99,7 @@ extern "C" void helm_trace_reset(void) {
     memset(g_launch, 0, sizeof g_launch);
     memset(g_timed, 0, sizeof g_timed);
     memset(g_ms, 0, sizeof g_ms);
+    memset(g_flops, 0, sizeof g_flops);
 }
 
 extern "C" int32_t helm_trace_read(helm_trace_entry *out, int32_t max) {
@@ -106,6 +109,7 @@ extern "C" int32_t helm_trace_read(helm_trace_entry *out, int32_t max) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             g_ms[r.id] += ms;
+            g_flops[r.id] += r.flops;
             ++g_timed[r.id];
         }
         g_pool.push_back(r.a);
@@ -121,6 +125,7 @@ extern "C" int32_t helm_trace_read(helm_trace_entry *out, int32_t max) {
         e.launches = g_launch[i];
         e.total_ms = g_ms[i];
         e.timed = g_timed[i];
+        e.flops = g_flops[i];
     }
     return n;
 }

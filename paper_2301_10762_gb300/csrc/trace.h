@@ -16,7 +16,7 @@ enum KernelId {
 // construction and destruction (bracketing the launch made inside the scope).
 class TraceScope {
   public:
-    TraceScope(int id, cudaStream_t st);
+    TraceScope(int id, cudaStream_t st, double flops = 0.0);
     ~TraceScope();
     TraceScope(const TraceScope &) = delete;
     TraceScope &operator=(const TraceScope &) = delete;
@@ -25,6 +25,7 @@ class TraceScope {
     int id_;
     cudaStream_t st_;
     cudaEvent_t a_;
+    double flops_;
 };
 
 }  // namespace helm
@@ -33,4 +34,10 @@ class TraceScope {
     do {                                       \
         ::helm::TraceScope ts_((id), (st));    \
         launch;                                \
+    } while (0)
+// the same, for a launch doing `flops` useful floating-point operations
+#define HELM_TRACED_W(id, st, flops, launch)           \
+    do {                                               \
+        ::helm::TraceScope ts_((id), (st), (flops));   \
+        launch;                                        \
     } while (0)

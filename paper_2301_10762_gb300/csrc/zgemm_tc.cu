@@ -286,7 +286,7 @@ template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStr
     cudaError_t e = ensure_dyn_smem(fn, Cfg::SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((a.M + ZG_BM - 1) / ZG_BM), (unsigned)((a.N + NT - 1) / NT), (unsigned)n_tasks);
-    HELM_TRACED(K_ZGEMM, st, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(a)));
+    HELM_TRACED_W(K_ZGEMM, st, a.flops, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(a)));
     return cudaGetLastError();
 }
 

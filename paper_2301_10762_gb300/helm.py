@@ -87,7 +87,8 @@ class helm_server_counters(C.Structure):
 
 
 class helm_trace_entry(C.Structure):
-    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("timed", C.c_int64)]
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("timed", C.c_int64),
+                ("flops", C.c_double)]
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
@@ -524,7 +525,7 @@ def helm_trace_read():
     if n < 0:
         raise HelmError(3, "helm_trace_read")
     return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
-                                   "timed": buf[i].timed} for i in range(n)}
+                                   "timed": buf[i].timed, "flops": buf[i].flops} for i in range(n)}
 
 
 def helm_trace_timeline(max_events=200000):
