@@ -6,9 +6,10 @@ Default step (the mixed-precision workload): 256 x 256 nodes on the unit square,
 {5, 10, ..., 40} (8 values), 64 point sources on top-row nodes as right-hand sides, smooth
 random velocity c = 1 + 2 (g - min) / (max - min) in [1, 3] (Gaussian random field,
 correlation length 0.1, seed 3 + rank).  One step runs the solve path end to end on data
-already in HBM: assemble A(m, w) for the 8 frequencies, factor them (line factors in complex
-FP32), form the 64 point-source right-hand sides and solve all 512 columns, each refined
-with FP64-accurate residuals to ||b - A x|| / ||b|| <= 1e-10.  Metric: right-hand-side
+already in HBM: assemble A(m, w) for the 8 frequencies, factor them (block cyclic reduction,
+its block products and Schur updates on the tensor cores in complex FP32), form the 64
+point-source right-hand sides and solve all 512 columns, each refined with FP64-accurate
+residuals to ||b - A x|| / ||b|| <= 1e-10.  Metric: right-hand-side
 solves per second with the factor time included (512 per step).  The same step with FP64
 factors is the comparison the metric names; the per-frequency error of sampled columns
 against the CPU oracle is reported for both.
@@ -190,6 +191,18 @@ def kernel_cost(name, nx, nz, n_sys, nrhs):
     return None, None
 
 
+# nominal dense TF32 / BF16 tensor rate of GB300 (1.1 / 2.25 PFLOP/s): the TF32 peak is the
+# measured BF16 GEMM peak times this ratio
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tensor_peak(peaks, sustained=True):
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    if key in peaks:
+        return peaks[key] * TF32_PER_BF16, f"MEASURED_PEAKS.json {key} x 1.1/2.25 (TF32/BF16 nominal; of measured)"
+    return (1700.0 if sustained else 1900.0) * TF32_PER_BF16, "fallback BF16 x 1.1/2.25 (of fallback)"
+
+
 def roofline(name, trace, breakdown, dims, peaks):
     """name: the dominant kernel; trace: the timed region's trace (that kernel timed on every
     launch); breakdown: one fully traced step outside the timed region (for the share)."""
@@ -206,7 +219,16 @@ def roofline(name, trace, breakdown, dims, peaks):
            "traffic": None}
     hbm = peaks.get("hbm_gbs")
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else "fallback 6800 GB/s (of fallback)"
-    if name.startswith("line_factor") and flops is not None:
+    if name == "zgemm_tf32x3" and st.get("flops"):
+        # the tensor-core GEMM of the block-cyclic-reduction factor and solve: useful flops are
+        # 8 M N K per complex product term (the library counts them per launch); the tensor pipe
+        # issues three TF32 products per useful one (hi*hi + hi*lo + lo*hi)
+        useful = st["flops"] / (st["total_ms"] / 1e3) / 1e12
+        peak, src = tensor_peak(peaks, sustained=True)
+        out.update({"bound": "tensor", "achieved": useful, "peak": peak, "unit": "TFLOP/s", "frac": useful / peak,
+                    "peak_source": src, "issued_tflops": 3 * useful, "issued_frac": 3 * useful / peak,
+                    "algorithmic_flops_per_launch": st["flops"] / st["timed"]})
+    elif name.startswith("line_factor") and flops is not None:
         ach = flops / avg_s / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP32_ALU_TFLOPS,
@@ -322,6 +344,50 @@ def server_session(args):
                            "data": "synthetic (seeded Gaussian-random-field models)"}, **out)), flush=True)
 
 
+# ------------------------------------------------------ tensor-core GEMM alone
+
+GEMM_SHAPES = {   # (batch, M, N, K): the two shapes of the mixed workload's block products
+    "factor_256x256x256": (256, 256, 256, 256),     # Schur updates of a factor level
+    "solve_256x64x256": (1024, 256, 64, 256),       # one level-0 pass of the solve: 8 freq x 128 lines
+}
+
+
+def gemm_kernel_bench(hm, torch, peaks, reps=10):
+    """helm_zgemm_batched on its own at the workload's two product shapes (operands larger
+    than L2): useful TFLOP/s (8 M N K per complex product), the tensor pipe's issued rate (three
+    TF32 products per useful one) against the measured tensor peak, and the operand bytes'
+    GB/s against the measured HBM bandwidth."""
+    out = {}
+    peak, src = tensor_peak(peaks, sustained=False)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    for name, (b, M, N, K) in GEMM_SHAPES.items():
+        A = torch.randn((b, M, K), dtype=torch.complex64, device="cuda", generator=g)
+        Bt = torch.randn((b, N, K), dtype=torch.complex64, device="cuda", generator=g)
+        C = torch.empty((b, M, N), dtype=torch.complex64, device="cuda")
+        for _ in range(2):
+            hm.helm_zgemm_batched(A, Bt, C=C)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hm.helm_zgemm_batched(A, Bt, C=C)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        flops = 8.0 * M * N * K * b
+        byts = 8.0 * b * (M * K + N * K + M * N)
+        out[name] = {"batch": b, "M": M, "N": N, "K": K, "us": t * 1e6, "useful_tflops": flops / t / 1e12,
+                     "issued_tflops": 3 * flops / t / 1e12, "issued_frac": 3 * flops / t / 1e12 / peak,
+                     "gbs": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / hbm}
+        del A, Bt, C
+    out["peak_tflops"] = peak
+    out["peak_source"] = src
+    return out
+
+
 # -------------------------------------------------------- hypergradient step
 
 def hypergrad_step(hm, torch, steps, warmup, rank):
@@ -377,6 +443,7 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the hypergradient step and the server session")
     ap.add_argument("--server", action="store_true", help="long solve-server session instead of the solve step")
+    ap.add_argument("--gemm-only", action="store_true", help="time the tensor-core GEMM alone and exit")
     ap.add_argument("--server-sizes", default="64,128,256")
     ap.add_argument("--server-seconds", type=float, default=10.0)
     ap.add_argument("--server-requests", type=int, default=200, help="requests of the capacity run")
@@ -417,6 +484,10 @@ def main():
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peaks = json.load(open(pp))
+    if args.gemm_only:
+        if rank == 0:
+            print(json.dumps({"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks)}), flush=True)
+        return
 
     seed = args.seed + rank
     w = workload(rank, args.n) if args.seed == 3 else __import__("workloads").config_mixed(args.n, seed=seed)
@@ -561,7 +632,7 @@ def main():
 
     rl = roofline(dominant, trace, breakdown, (w.nx, w.nz, n_om, ns), peaks)
 
-    extras = {}
+    extras = {"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks)} if rank == 0 else {}
     if not args.no_extras and rank == 0:
         extras["hypergrad_step_128"] = hypergrad_step(hm, torch, 10, args.warmup, rank)
         try:

@@ -40,6 +40,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "abi_internal.h"
@@ -261,6 +262,33 @@ helm_status upload_ints(const std::vector<int> &h, TaskBuf &b, cudaStream_t st) 
     return HELM_OK;
 }
 
+// A recorded sequence of launches: every task list goes into one host array, uploaded with a
+// single copy before the launches are enqueued (a copy from pageable host memory waits for the
+// stream, so one copy per launch would serialise the host with the GPU at every launch).
+struct Plan {
+    cudaStream_t st;
+    std::vector<int> ints;
+    std::vector<std::function<helm_status(const int *)>> ops;
+    std::vector<void *> scratch;   // device scratch of the launches, released after the last one
+    explicit Plan(cudaStream_t s) : st(s) {}
+    ~Plan() {
+        for (void *p : scratch) dev_free(p, st);
+    }
+    int add(const std::vector<int> &v) {
+        const int off = (int)ints.size();
+        ints.insert(ints.end(), v.begin(), v.end());
+        return off;
+    }
+    helm_status run() {
+        TaskBuf tb;
+        helm_status s = HELM_OK;
+        if (!ints.empty() && (s = upload_ints(ints, tb, st)) != HELM_OK) return s;
+        for (auto &op : ops)
+            if ((s = op(tb.dev)) != HELM_OK) return s;
+        return HELM_OK;
+    }
+};
+
 ZOperand zop(const float2 *base, long long stride, int ld, int div = 0, long long stride_hi = 0) {
     ZOperand o;
     o.base = base;
@@ -283,17 +311,19 @@ long long count_terms(const int *tasks, size_t n_tasks, int nterms) {
     return t;
 }
 
-helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, cudaStream_t st) {
+helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, Plan &pl) {
     if (tasks.empty()) return HELM_OK;
-    TaskBuf tb;
-    helm_status s = upload_ints(tasks, tb, st);
-    if (s != HELM_OK) return s;
+    const int off = pl.add(tasks), n = (int)(tasks.size() / 8);
     ZGemmArgs a = a0;
-    a.tasks = tb.dev;
     a.tries = wait_tries();
-    a.flops = 8.0 * a.M * a.N * a.K * (double)count_terms(tasks.data(), tasks.size() / 8, a.nterms);
-    cudaError_t e = launch_zgemm(a, (int)(tasks.size() / 8), st);
-    if (e != cudaSuccess) { helm_set_error("bcr: tensor-core GEMM", e); return HELM_ECUDA; }
+    a.flops = 8.0 * a.M * a.N * a.K * (double)count_terms(tasks.data(), (size_t)n, a.nterms);
+    const cudaStream_t st = pl.st;
+    pl.ops.push_back([a, off, n, st](const int *dev) mutable -> helm_status {
+        a.tasks = dev + off;
+        const cudaError_t e = launch_zgemm(a, n, st);
+        if (e != cudaSuccess) { helm_set_error("bcr: tensor-core GEMM", e); return HELM_ECUDA; }
+        return HELM_OK;
+    });
     return HELM_OK;
 }
 
@@ -308,35 +338,42 @@ struct Fam {
 };
 
 // out[p.second] = in[p.first]^{-1} for every index pair, n x n blocks (may be the same matrices)
-helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, cudaStream_t st) {
+helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl) {
     const int count = (int)(pairs.size() / 2);
     if (count == 0) return HELM_OK;
+    const cudaStream_t st = pl.st;
     helm_status s;
     if (n <= INV_MAX) {
-        TaskBuf tb;
-        if ((s = upload_ints(pairs, tb, st)) != HELM_OK) return s;
-        InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, tb.dev, status};
+        const int off = pl.add(pairs);
         const size_t smem = inv_smem_bytes(n);
         cudaError_t e = ensure_dyn_smem((const void *)zinv_base_kernel, smem);
-        if (e == cudaSuccess) {
-            HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
-            e = cudaGetLastError();
-        }
         if (e != cudaSuccess) { helm_set_error("bcr: block inversion", e); return HELM_ECUDA; }
+        InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, nullptr, status};
+        pl.ops.push_back([a, off, count, smem, st](const int *dev) mutable -> helm_status {
+            a.idx = dev + off;
+            HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
+            const cudaError_t e2 = cudaGetLastError();
+            if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
+            return HELM_OK;
+        });
         return HELM_OK;
     }
     const int n1 = INV_MAX * ((n / INV_MAX + 1) / 2), n2 = n - n1;
     // X11 = D11^{-1}
-    if ((s = invert_blocks(n1, in, out, pairs, status, st)) != HELM_OK) return s;
-    // scratch T (n1 x n2) and Tt = T^T (n2 x n1) per block
+    if ((s = invert_blocks(n1, in, out, pairs, status, pl)) != HELM_OK) return s;
+    // scratch T (n1 x n2) and Tt = T^T (n2 x n1) per block: allocated now (stream-ordered, usable
+    // by the launches enqueued later), released on the stream after the last launch that reads it
     float2 *T = nullptr, *Tt = nullptr;
     const long long ts = (long long)n1 * n2;
     if ((s = dev_alloc((void **)&T, (size_t)count * ts * sizeof(float2), "bcr: inversion scratch", st)) != HELM_OK)
         return s;
-    struct Free { float2 *&p; cudaStream_t st; ~Free() { dev_free(p, st); } } f1{T, st};
-    if ((s = dev_alloc((void **)&Tt, (size_t)count * ts * sizeof(float2), "bcr: inversion scratch", st)) != HELM_OK)
+    if ((s = dev_alloc((void **)&Tt, (size_t)count * ts * sizeof(float2), "bcr: inversion scratch", st)) != HELM_OK) {
+        dev_free(T, st);
         return s;
-    struct Free2 { float2 *&p; cudaStream_t st; ~Free2() { dev_free(p, st); } } f2{Tt, st};
+    }
+    // (released by the plan after its last launch)
+    pl.scratch.push_back(T);
+    pl.scratch.push_back(Tt);
     const Fam X11 = out.sub(0, 0), X12 = out.sub(0, n1), X21 = out.sub(n1, 0), X22 = out.sub(n1, n1);
     const Fam D21 = in.sub(n1, 0), D22 = in.sub(n1, n1);
     const Fam FT{T, ts, n2}, FTt{Tt, ts, n1};
@@ -361,7 +398,7 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
         g.c_stride = C.stride;
         g.ldc = C.ld;
         g.status = status;
-        return gemm(g, tk, st);
+        return gemm(g, tk, pl);
     };
     // T = X11 D12 = X11 D21^T;  Tt = D21 X11 (= T^T, X11 symmetric)
     if ((s = run(n1, n2, n1, X11, D21, nullptr, FT, 1.f, 1, 0, 0, 2)) != HELM_OK) return s;
@@ -370,7 +407,7 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
     if ((s = run(n2, n2, n1, D21, FTt, &D22, X22, -1.f, 0, 2, 0, 1)) != HELM_OK) return s;
     std::vector<int> self(pairs.size());
     for (int t = 0; t < count; ++t) self[2 * t] = self[2 * t + 1] = pairs[2 * t + 1];
-    if ((s = invert_blocks(n2, X22, X22, self, status, st)) != HELM_OK) return s;
+    if ((s = invert_blocks(n2, X22, X22, self, status, pl)) != HELM_OK) return s;
     // X12 = -T X22;  X21 = -X22 T^T;  X11 <- X11 - T X21
     if ((s = run(n1, n2, n2, FT, X22, nullptr, X12, -1.f, 2, 1, 0, 1)) != HELM_OK) return s;
     if ((s = run(n2, n1, n2, X22, FT, nullptr, X21, -1.f, 1, 2, 0, 1)) != HELM_OK) return s;
@@ -379,17 +416,19 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
 }
 
 helm_status transpose_blocks(int n, const float2 *in, float2 *out, long long stride, const std::vector<int> &pairs,
-                             cudaStream_t st) {
+                             Plan &pl) {
     const int count = (int)(pairs.size() / 2);
     if (count == 0) return HELM_OK;
-    TaskBuf tb;
-    helm_status s = upload_ints(pairs, tb, st);
-    if (s != HELM_OK) return s;
-    const int nt = (n + 31) / 32;
-    HELM_TRACED(K_ZTRANS, st, (ztranspose_kernel<<<dim3(nt * nt, 1, count), dim3(32, 8), 0, st>>>(n, in, out, stride,
-                                                                                                  stride, tb.dev)));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { helm_set_error("bcr: transpose", e); return HELM_ECUDA; }
+    const int off = pl.add(pairs);
+    const cudaStream_t st = pl.st;
+    pl.ops.push_back([=](const int *dev) -> helm_status {
+        const int nt = (n + 31) / 32;
+        HELM_TRACED(K_ZTRANS, st, (ztranspose_kernel<<<dim3(nt * nt, 1, count), dim3(32, 8), 0, st>>>(
+                                      n, in, out, stride, stride, dev + off)));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { helm_set_error("bcr: transpose", e); return HELM_ECUDA; }
+        return HELM_OK;
+    });
     return HELM_OK;
 }
 
@@ -430,10 +469,17 @@ helm_status bcr_factor(helm_factor_t *f) {
         (s = dev_alloc((void **)&Un, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK)
         return s;
     cudaError_t e;
+    Plan pl(st);
+    const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
     {
-        const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
-        HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(per, nx, ns), 256, 0, st>>>(g, op->diag, Dc)));
-        if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr: form blocks", e); return HELM_ECUDA; }
+        const double2 *diag = op->diag;
+        float2 *D0 = Dc;
+        pl.ops.push_back([=](const int *) -> helm_status {
+            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(per, nx, ns), 256, 0, st>>>(g, diag, D0)));
+            const cudaError_t e2 = cudaGetLastError();
+            if (e2 != cudaSuccess) { helm_set_error("bcr: form blocks", e2); return HELM_ECUDA; }
+            return HELM_OK;
+        });
     }
     const Fam fD{Dc, nz2, nz}, fDinv{b.Dinv, nz2, nz};
     int levels = 0;
@@ -441,12 +487,16 @@ helm_status bcr_factor(helm_factor_t *f) {
         std::vector<int> inv_pairs, tv, tw, tp, tq, td, tl, tu;
         for (int sy = 0; sy < ns; ++sy)
             for (int j = sp; j < nx; j += 2 * sp) inv_pairs.insert(inv_pairs.end(), {sy * nx + j, sy * nx + j});
-        if ((s = invert_blocks(nz, fD, fDinv, inv_pairs, op->status, st)) != HELM_OK) return s;
+        if ((s = invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl)) != HELM_OK) return s;
         if (sp == 1) {
-            const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
-            HELM_TRACED(K_BCR_L0, st, (bcr_level0_kernel<<<dim3(per, (nx + 1) / 2, ns), 256, 0, st>>>(g, Dc, b.Dinv,
-                                                                                                    Ln, Un, half)));
-            if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr: level 0", e); return HELM_ECUDA; }
+            float2 *D0 = Dc, *Di = b.Dinv, *L1 = Ln, *U1 = Un;
+            pl.ops.push_back([=](const int *) -> helm_status {
+                HELM_TRACED(K_BCR_L0, st, (bcr_level0_kernel<<<dim3(per, (nx + 1) / 2, ns), 256, 0, st>>>(
+                                              g, D0, Di, L1, U1, half)));
+                const cudaError_t e2 = cudaGetLastError();
+                if (e2 != cudaSuccess) { helm_set_error("bcr: level 0", e2); return HELM_ECUDA; }
+                return HELM_OK;
+            });
         } else {
             std::vector<int> vpairs, wpairs;
             for (int sy = 0; sy < ns; ++sy) {
@@ -486,12 +536,12 @@ helm_status bcr_factor(helm_factor_t *f) {
             ga.B[0] = zop(b.Dinv, nz2, nz);
             ga.C = b.V; ga.c_stride = nz2; ga.ldc = nz;
             ga.A[0] = zop(Uc, nz2, nz);
-            if ((s = gemm(ga, tv, st)) != HELM_OK) return s;
+            if ((s = gemm(ga, tv, pl)) != HELM_OK) return s;
             ga.C = b.W;
             ga.A[0] = zop(Lc, nz2, nz);
-            if ((s = gemm(ga, tw, st)) != HELM_OK) return s;
-            if ((s = transpose_blocks(nz, b.V, b.P, nz2, vpairs, st)) != HELM_OK) return s;
-            if ((s = transpose_blocks(nz, b.W, b.Q, nz2, wpairs, st)) != HELM_OK) return s;
+            if ((s = gemm(ga, tw, pl)) != HELM_OK) return s;
+            if ((s = transpose_blocks(nz, b.V, b.P, nz2, vpairs, pl)) != HELM_OK) return s;
+            if ((s = transpose_blocks(nz, b.W, b.Q, nz2, wpairs, pl)) != HELM_OK) return s;
             ZGemmArgs gd;
             gd.M = gd.N = gd.K = nz;
             gd.status = op->status;
@@ -500,7 +550,7 @@ helm_status bcr_factor(helm_factor_t *f) {
             gd.A[1] = zop(Uc, nz2, nz); gd.B[1] = zop(b.V, nz2, nz); gd.sign[1] = -1.f;
             gd.C0 = zop(Dc, nz2, nz);
             gd.C = Dc; gd.c_stride = nz2; gd.ldc = nz;
-            if ((s = gemm(gd, td, st)) != HELM_OK) return s;
+            if ((s = gemm(gd, td, pl)) != HELM_OK) return s;
             ZGemmArgs gl;
             gl.M = gl.N = gl.K = nz;
             gl.status = op->status;
@@ -508,10 +558,10 @@ helm_status bcr_factor(helm_factor_t *f) {
             gl.sign[0] = -1.f;
             gl.A[0] = zop(Lc, nz2, nz); gl.B[0] = zop(b.V, nz2, nz);
             gl.C = Ln; gl.c_stride = nz2; gl.ldc = nz;
-            if ((s = gemm(gl, tl, st)) != HELM_OK) return s;
+            if ((s = gemm(gl, tl, pl)) != HELM_OK) return s;
             gl.A[0] = zop(Uc, nz2, nz); gl.B[0] = zop(b.W, nz2, nz);
             gl.C = Un;
-            if ((s = gemm(gl, tu, st)) != HELM_OK) return s;
+            if ((s = gemm(gl, tu, pl)) != HELM_OK) return s;
         }
         std::swap(Lc, Ln);
         std::swap(Uc, Un);
@@ -520,8 +570,9 @@ helm_status bcr_factor(helm_factor_t *f) {
     {
         std::vector<int> last;
         for (int sy = 0; sy < ns; ++sy) last.insert(last.end(), {sy * nx, sy * nx});
-        if ((s = invert_blocks(nz, fD, fDinv, last, op->status, st)) != HELM_OK) return s;
+        if ((s = invert_blocks(nz, fD, fDinv, last, op->status, pl)) != HELM_OK) return s;
     }
+    if ((s = pl.run()) != HELM_OK) return s;
     b.levels = levels;
     // the solve's task lists, built once: forward levels 1 .. L-1, last line, backward L-1 .. 1,
     // level 0 both ways (vector operands indexed system * nx + line)
@@ -700,7 +751,9 @@ helm_status blas_zgemm(int batch, int M, int N, int K, const float2 *A, long lon
         auto v = task8(t, t, t, t);
         tasks.insert(tasks.end(), v.begin(), v.end());
     }
-    return gemm(a, tasks, st);
+    Plan pl(st);
+    helm_status s = gemm(a, tasks, pl);
+    return s == HELM_OK ? pl.run() : s;
 }
 
 helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, float2 *X, long long sx, int ldx,
@@ -717,7 +770,9 @@ helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, 
         if (e != cudaSuccess) { helm_set_error("helm_zinv_batched: copy", e); return HELM_ECUDA; }
     }
     const Fam f{X, sx, ldx};
-    return invert_blocks(n, f, f, pairs, status, st);
+    Plan pl(st);
+    helm_status s = invert_blocks(n, f, f, pairs, status, pl);
+    return s == HELM_OK ? pl.run() : s;
 }
 
 }  // namespace helm
