@@ -57,25 +57,42 @@ constexpr int INV_MAX = 128;   // largest block inverted in one CTA's shared mem
 
 // ------------------------------------------------------------------- kernels
 
-// dense D_i of every line and system: the diagonal of A and the vertical couplings next to it
-__global__ void bcr_form_kernel(GridGeom g, const double2 *diag, float2 *D) {
+// couplings of the grid in FP32: horizontal (between lines, row j) and vertical (within line
+// i), each halved on a boundary edge; computed once on the host
+struct Coup {
+    float cx_in, cx_edge, cz_in, cz_edge;
+    __device__ __forceinline__ float cx(int j, int nz) const { return (j == 0 || j == nz - 1) ? cx_edge : cx_in; }
+    __device__ __forceinline__ float cz(int i, int nx) const { return (i == 0 || i == nx - 1) ? cz_edge : cz_in; }
+};
+Coup coup_of(const GridGeom &g) {
+    return Coup{(float)coup_x(g, 1), (float)coup_x(g, 0), (float)coup_z(g, 1), (float)coup_z(g, 0)};
+}
+
+// dense D_i of every line and system: the diagonal of A and the vertical couplings next to it;
+// one float4 (two complex entries of a row) per thread and step
+__global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2 *D) {
     const int nz = g.nz, nx = g.nx;
     const int i = blockIdx.y, s = blockIdx.z;
-    const float cz = (float)coup_z(g, i);
-    float2 *Di = D + ((size_t)s * nx + i) * nz * nz;
+    const float cz = cp.cz(i, nx);
+    float4 *Di = reinterpret_cast<float4 *>(D + ((size_t)s * nx + i) * nz * nz);
     const double2 *dg = diag + ((size_t)s * nx + i) * nz;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nz * nz; e += gridDim.x * blockDim.x) {
-        const int r = e / nz, c = e % nz;
-        float2 v = make_float2(0.f, 0.f);
-        if (r == c) v = to_c64(dg[r]);
-        else if (r == c + 1 || c == r + 1) v.x = cz;
-        Di[e] = v;
+    const int nq = nz * nz / 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int r = (2 * q) / nz, c = (2 * q) - r * nz;   // columns c, c + 1 of row r
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int c1 = c + 1;
+        if (c == r) { const float2 d = to_c64(dg[r]); v.x = d.x; v.y = d.y; }
+        else if (c == r + 1 || c + 1 == r) v.x = cz;
+        if (c1 == r) { const float2 d = to_c64(dg[r]); v.z = d.x; v.w = d.y; }
+        else if (c1 == r + 1 || c1 + 1 == r) v.z = cz;
+        Di[q] = v;
     }
 }
 
 // level 0 (couplings C = diag(cx)): kept line k (even) with eliminated neighbours k - 1, k + 1:
 //   D_k -= C Dinv_{k-1} C + C Dinv_{k+1} C,  L_k = -C Dinv_{k-1} C,  U_k = -C Dinv_{k+1} C
-__global__ void bcr_level0_kernel(GridGeom g, float2 *D, const float2 *Dinv, float2 *Lnew, float2 *Unew, int half) {
+__global__ void bcr_level0_kernel(GridGeom g, Coup cp, float2 *D, const float2 *Dinv, float2 *Lnew, float2 *Unew,
+                                  int half) {
     const int nz = g.nz, nx = g.nx, nz2 = nz * nz;
     const int k = 2 * blockIdx.y, s = blockIdx.z;
     const bool ha = k >= 1, hc = k + 1 < nx;
@@ -85,8 +102,8 @@ __global__ void bcr_level0_kernel(GridGeom g, float2 *D, const float2 *Dinv, flo
     float2 *Lk = Lnew + ((size_t)s * half + k / 2) * nz2;
     float2 *Uk = Unew + ((size_t)s * half + k / 2) * nz2;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nz2; e += gridDim.x * blockDim.x) {
-        const int r = e / nz, c = e % nz;
-        const float sc = (float)(coup_x(g, r) * coup_x(g, c));
+        const int r = e / nz, c = e - r * nz;
+        const float sc = cp.cx(r, nz) * cp.cx(c, nz);
         float2 ta = make_float2(0.f, 0.f), tc = ta;
         if (ha) { const float2 v = Da[e]; ta = make_float2(sc * v.x, sc * v.y); }
         if (hc) { const float2 v = Dc[e]; tc = make_float2(sc * v.x, sc * v.y); }
@@ -213,35 +230,39 @@ __global__ void ztranspose_kernel(int n, const float2 *in, float2 *out, long lon
     }
 }
 
-// solve, level 0 of the forward pass: b_k -= C (y_{k-1} + y_{k+1}) for even k, y in x
-__global__ void bcr_solve_l0_fwd_kernel(GridGeom g, int nrhs, float2 *b, const float2 *x, const int *skip) {
+// solve, level 0 of the forward pass: b_k -= C (y_{k-1} + y_{k+1}) for even k, y in x.  Thread:
+// two rows (one float4) of the line, for L0_COLS columns (frequency x right-hand side).
+constexpr int L0_COLS = 8;
+__global__ void bcr_solve_l0_fwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip) {
     if (skip && *skip) return;
     const int nz = g.nz, nx = g.nx, N = nx * nz;
-    const int k = 2 * blockIdx.y, col = blockIdx.z;   // col = system * nrhs + rhs
-    const size_t off = (size_t)col * N + (size_t)k * nz;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nz; r += gridDim.x * blockDim.x) {
-        float2 t = make_float2(0.f, 0.f);
-        if (k >= 1) { const float2 v = x[off - nz + r]; t.x += v.x; t.y += v.y; }
-        if (k + 1 < nx) { const float2 v = x[off + nz + r]; t.x += v.x; t.y += v.y; }
-        const float cx = (float)coup_x(g, r);
-        float2 v = b[off + r];
-        v.x -= cx * t.x;
-        v.y -= cx * t.y;
-        b[off + r] = v;
+    const int k = 2 * blockIdx.y, r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nz) return;
+    const float c0 = cp.cx(r, nz), c1 = cp.cx(r + 1, nz);
+    for (int col = blockIdx.z * L0_COLS; col < min(cols, (int)(blockIdx.z + 1) * L0_COLS); ++col) {
+        const size_t off = (size_t)col * N + (size_t)k * nz + r;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k >= 1) { const float4 v = *reinterpret_cast<const float4 *>(x + off - nz); t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w; }
+        if (k + 1 < nx) { const float4 v = *reinterpret_cast<const float4 *>(x + off + nz); t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w; }
+        float4 *bp = reinterpret_cast<float4 *>(b + off);
+        float4 v = *bp;
+        v.x -= c0 * t.x; v.y -= c0 * t.y; v.z -= c1 * t.z; v.w -= c1 * t.w;
+        *bp = v;
     }
 }
 
 // solve, level 0 of the backward pass: b_j = C (x_{j-1} + x_{j+1}) for odd j
-__global__ void bcr_solve_l0_bwd_kernel(GridGeom g, int nrhs, float2 *b, const float2 *x, const int *skip) {
+__global__ void bcr_solve_l0_bwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip) {
     if (skip && *skip) return;
     const int nz = g.nz, nx = g.nx, N = nx * nz;
-    const int j = 2 * blockIdx.y + 1, col = blockIdx.z;
-    const size_t off = (size_t)col * N + (size_t)j * nz;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nz; r += gridDim.x * blockDim.x) {
-        float2 t = x[off - nz + r];
-        if (j + 1 < nx) { const float2 v = x[off + nz + r]; t.x += v.x; t.y += v.y; }
-        const float cx = (float)coup_x(g, r);
-        b[off + r] = make_float2(cx * t.x, cx * t.y);
+    const int j = 2 * blockIdx.y + 1, r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nz) return;
+    const float c0 = cp.cx(r, nz), c1 = cp.cx(r + 1, nz);
+    for (int col = blockIdx.z * L0_COLS; col < min(cols, (int)(blockIdx.z + 1) * L0_COLS); ++col) {
+        const size_t off = (size_t)col * N + (size_t)j * nz + r;
+        float4 t = *reinterpret_cast<const float4 *>(x + off - nz);
+        if (j + 1 < nx) { const float4 v = *reinterpret_cast<const float4 *>(x + off + nz); t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w; }
+        *reinterpret_cast<float4 *>(b + off) = make_float4(c0 * t.x, c0 * t.y, c1 * t.z, c1 * t.w);
     }
 }
 
@@ -474,8 +495,10 @@ helm_status bcr_factor(helm_factor_t *f) {
     {
         const double2 *diag = op->diag;
         float2 *D0 = Dc;
+        const Coup cp = coup_of(g);
+        const int perq = (int)std::min<long long>(64, (nz2 / 2 + 255) / 256);
         pl.ops.push_back([=](const int *) -> helm_status {
-            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(per, nx, ns), 256, 0, st>>>(g, diag, D0)));
+            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(perq, nx, ns), 256, 0, st>>>(g, cp, diag, D0)));
             const cudaError_t e2 = cudaGetLastError();
             if (e2 != cudaSuccess) { helm_set_error("bcr: form blocks", e2); return HELM_ECUDA; }
             return HELM_OK;
@@ -490,9 +513,10 @@ helm_status bcr_factor(helm_factor_t *f) {
         if ((s = invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl)) != HELM_OK) return s;
         if (sp == 1) {
             float2 *D0 = Dc, *Di = b.Dinv, *L1 = Ln, *U1 = Un;
+            const Coup cp = coup_of(g);
             pl.ops.push_back([=](const int *) -> helm_status {
                 HELM_TRACED(K_BCR_L0, st, (bcr_level0_kernel<<<dim3(per, (nx + 1) / 2, ns), 256, 0, st>>>(
-                                              g, D0, Di, L1, U1, half)));
+                                              g, cp, D0, Di, L1, U1, half)));
                 const cudaError_t e2 = cudaGetLastError();
                 if (e2 != cudaSuccess) { helm_set_error("bcr: level 0", e2); return HELM_ECUDA; }
                 return HELM_OK;
@@ -677,7 +701,9 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     };
     helm_status s;
     const int nodd = nx / 2, neven = (nx + 1) / 2;
-    const int per = (nz + 127) / 128;
+    const Coup cp = coup_of(g);
+    const int cols = ns * nrhs, thr = std::min(128, nz / 2), per = (nz / 2 + thr - 1) / thr;
+    const int colb = (cols + L0_COLS - 1) / L0_COLS;
     // forward, level 0: y_j = Dinv_j b_j into x, then b_k -= C (y_{k-1} + y_{k+1})
     {
         ZGemmArgs a = ga;
@@ -686,8 +712,8 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
         a.B[0] = vec(r);
         a.C = x;
         if ((s = launch(a, b.fwd[0])) != HELM_OK) return s;
-        HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_fwd_kernel<<<dim3(per, neven, ns * nrhs), 128, 0, st>>>(
-                                            g, nrhs, r, x, skip)));
+        HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_fwd_kernel<<<dim3(per, neven, colb), thr, 0, st>>>(
+                                            g, cp, cols, r, x, skip)));
         if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
     }
     for (int l = 1; l < b.levels; ++l) {   // b_k -= W_a b_a + V_c b_c
@@ -718,8 +744,8 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     }
     {   // backward, level 0: t_j = C (x_{j-1} + x_{j+1}) into b_j, x_j = y_j - Dinv_j t_j
         if (nodd > 0) {
-            HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_bwd_kernel<<<dim3(per, nodd, ns * nrhs), 128, 0, st>>>(
-                                                g, nrhs, r, x, skip)));
+            HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_bwd_kernel<<<dim3(per, nodd, colb), thr, 0, st>>>(
+                                                g, cp, cols, r, x, skip)));
             if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
         }
         ZGemmArgs a = ga;

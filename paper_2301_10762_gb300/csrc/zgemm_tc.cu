@@ -15,7 +15,7 @@
 //
 // One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Its 256
 // threads load a K chunk of 16 complex columns (one 128-byte row per matrix row) from global
-// memory a chunk ahead into registers, split it and store it into shared memory in the
+// memory two chunks ahead into registers, split it and store it into shared memory in the
 // 128-byte-swizzled K-major layout the tensor core reads; one thread issues the 12 MMAs of the
 // chunk and commits them to the chunk's stage barrier, which the writers of that stage wait for
 // STAGES chunks later.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
@@ -155,10 +155,13 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // ---- operand fetch of one chunk into registers
-    float4 ra[Cfg::A_V4], rb[Cfg::B_V4];
-    auto fetch = [&](int c) {
-        const int cu = c / nkc, u = cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2]), k0 = (c % nkc) * ZG_KC;
+    // ---- operand fetch of one chunk into registers (two register sets: chunk c + 2 is fetched
+    // while chunk c is stored, so that a load has two chunks of work to arrive in)
+    using RA = float4[Cfg::A_V4];
+    using RB = float4[Cfg::B_V4];
+    auto term_of = [&](int c) { const int cu = c / nkc; return cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2]); };
+    auto fetch = [&](int c, RA &ra, RB &rb) {
+        const int u = term_of(c), k0 = (c % nkc) * ZG_KC;
         const float2 *A = a.A[u].base + zop_off(task[u], a.A[u].div, a.A[u].stride, a.A[u].stride_hi);
         const float2 *B = a.B[u].base + zop_off(task[3 + u], a.B[u].div, a.B[u].stride, a.B[u].stride_hi);
 #pragma unroll
@@ -176,10 +179,9 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    // ---- split and store of the fetched chunk into stage s
-    auto store = [&](int c, int s) {
-        const int cu = c / nkc;
-        const float sg = a.sign[cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2])];
+    // ---- split and store of a fetched chunk into stage s
+    auto store = [&](int c, int s, const RA &ra, const RB &rb) {
+        const float sg = a.sign[term_of(c)];
         const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
         const uint32_t a_hi = base, a_lo = base + Cfg::A_BYTES;
         const uint32_t b_hi = base + 2 * Cfg::A_BYTES, b_lo = b_hi + Cfg::B_BYTES;
@@ -209,8 +211,9 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     };
 
     constexpr uint32_t idesc = idesc_tf32(Cfg::NR);
-    if (nchunks > 0) fetch(0);
-    for (int c = 0; c < nchunks; ++c) {
+    // one chunk: wait for its stage, store it, fetch chunk c + 2 into the freed registers, hand
+    // the stage to the tensor core; false once a wait of the CTA has given up
+    auto step = [&](int c, RA &ra, RB &rb) -> bool {
         const int s = c % Cfg::STAGES;
         if (c >= Cfg::STAGES) {   // the MMAs that read this stage STAGES chunks ago are done
             if (!mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
@@ -218,10 +221,10 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                 s_abort = 1;
             }
         }
-        if (!*(volatile int *)&s_abort) store(c, s);
-        if (c + 1 < nchunks) fetch(c + 1);   // in flight while this chunk is multiplied
-        fence_proxy_async_smem();            // the stores are visible to the tensor core's reads
-        if (__syncthreads_or(*(volatile int *)&s_abort)) break;
+        if (!*(volatile int *)&s_abort) store(c, s, ra, rb);
+        if (c + 2 < nchunks) fetch(c + 2, ra, rb);
+        fence_proxy_async_smem();   // the stores are visible to the tensor core's reads
+        if (__syncthreads_or(*(volatile int *)&s_abort)) return false;
         if (tid == 0) {
             tc_fence_after();
             const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
@@ -237,6 +240,14 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             }
             tc_commit(&empty_bar[s]);
         }
+        return true;
+    };
+    float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
+    if (nchunks > 0) fetch(0, ra0, rb0);
+    if (nchunks > 1) fetch(1, ra1, rb1);
+    for (int c = 0; c < nchunks; c += 2) {
+        if (!step(c, ra0, rb0)) break;
+        if (c + 1 < nchunks && !step(c + 1, ra1, rb1)) break;
     }
     // every MMA issued is complete before the accumulator is read or freed
     if (tid == 0) tc_commit(&done_bar);
