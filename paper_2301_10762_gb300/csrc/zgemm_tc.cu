@@ -13,13 +13,13 @@
 // Each real operand x is split into hi = tf32(x) and lo = x - hi, and the tile accumulates
 // hi*hi + hi*lo + lo*hi in FP32 in tensor memory (the lo*lo term is below FP32 rounding).
 //
-// One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Its 256
+// One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Its 512
 // threads load a K chunk of 16 complex columns (one 128-byte row per matrix row) from global
 // memory two chunks ahead into registers, split it and store it into shared memory in the
 // 128-byte-swizzled K-major layout the tensor core reads; one thread issues the 12 MMAs of the
 // chunk and commits them to the chunk's stage barrier, which the writers of that stage wait for
 // STAGES chunks later.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
-// 32 (w % 4) .. + 31, column half w / 4), adds C0 and writes C.
+// 32 (w % 4) .. + 31, column part w / 4), adds C0 and writes C.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -30,7 +30,7 @@ namespace helm {
 
 namespace {
 
-constexpr int ZG_THREADS = 256;
+constexpr int ZG_THREADS = 512;
 constexpr int ZG_BM = 128;   // tile rows (tcgen05 M)
 constexpr int ZG_KC = 16;    // complex K per chunk: 32 floats = one 128-byte swizzle row
 
@@ -258,13 +258,15 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     tc_fence_after();
     const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
 
-    if (ok) {
+    if (ok && (warp >> 2) < (Cfg::NR >= 64 ? 4 : Cfg::NR / 16)) {
+        // warp w reads lanes 32 (w % 4) .. + 31 (rows), real columns of part w / 4
+        constexpr int parts = Cfg::NR >= 64 ? 4 : Cfg::NR / 16, cpp = Cfg::NR / parts;
         const int q = warp & 3, h = warp >> 2;
         const int r = 32 * q + lane, m = m0 + r;
         const float2 *C0 =
             a.C0.base ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) : nullptr;
         float2 *C = a.C + zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi);
-        for (int col = h * NT; col < (h + 1) * NT; col += 16) {   // real columns of this warp's half
+        for (int col = h * cpp; col < (h + 1) * cpp; col += 16) {   // real columns of this warp's part
             float v[16];
             tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
             if (m >= a.M) continue;
