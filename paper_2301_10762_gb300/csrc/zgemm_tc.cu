@@ -13,12 +13,13 @@
 // Each real operand x is split into hi = tf32(x) and lo = x - hi, and the tile accumulates
 // hi*hi + hi*lo + lo*hi in FP32 in tensor memory (the lo*lo term is below FP32 rounding).
 //
-// One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Its 512
-// threads load a K chunk of 16 complex columns (one 128-byte row per matrix row) from global
-// memory two chunks ahead into registers, split it and store it into shared memory in the
-// 128-byte-swizzled K-major layout the tensor core reads; one thread issues the 12 MMAs of the
-// chunk and commits them to the chunk's stage barrier, which the writers of that stage wait for
-// STAGES chunks later.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
+// One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Sixteen
+// operand warps load a K chunk of 16 complex columns (one 128-byte row per matrix row) from
+// global memory two chunks ahead into registers, split it and store it into shared memory in
+// the 128-byte-swizzled K-major layout the tensor core reads, and arrive on the stage's full
+// barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
+// them to the stage's empty barrier, which the operand warps wait for before they overwrite the
+// stage STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
 // 32 (w % 4) .. + 31, column part w / 4), adds C0 and writes C.
 #include <stdint.h>
 
@@ -30,7 +31,8 @@ namespace helm {
 
 namespace {
 
-constexpr int ZG_THREADS = 512;
+constexpr int ZG_PRODUCERS = 512;                 // threads of the 16 operand warps
+constexpr int ZG_THREADS = ZG_PRODUCERS + 32;     // + one warp that issues the MMAs
 constexpr int ZG_BM = 128;   // tile rows (tcgen05 M)
 constexpr int ZG_KC = 16;    // complex K per chunk: 32 floats = one 128-byte swizzle row
 
@@ -111,8 +113,8 @@ template <int NT> struct ZCfg {
     static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int STAGES = NT <= 64 ? 3 : 2;
     static constexpr int TMEM_COLS = NR < 32 ? 32 : NR;      // a power of two >= 32
-    static constexpr int A_V4 = ZG_BM * 8 / ZG_THREADS;      // float4 of the A chunk per thread
-    static constexpr int B_V4 = (NT * 8 + ZG_THREADS - 1) / ZG_THREADS;
+    static constexpr int A_V4 = ZG_BM * 8 / ZG_PRODUCERS;    // float4 of the A chunk per thread
+    static constexpr int B_V4 = (NT * 8 + ZG_PRODUCERS - 1) / ZG_PRODUCERS;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;   // + alignment slack
 };
 
@@ -120,7 +122,8 @@ template <int NT>
 __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     using Cfg = ZCfg<NT>;
     extern __shared__ uint8_t zg_smem_raw[];
-    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];
+    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (every producer arrives)
+    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];   // stage read by its MMAs (commit)
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -138,13 +141,17 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int nkc = (a.K + ZG_KC - 1) / ZG_KC;
     const int nchunks = nterms * nkc;
 
+    const bool mma_warp = warp == ZG_PRODUCERS / 32;
     if (tid == 0) {
-        for (int s = 0; s < Cfg::STAGES; ++s) mbar_init(&empty_bar[s], 1);
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+            mbar_init(&full_bar[s], ZG_PRODUCERS);
+            mbar_init(&empty_bar[s], 1);
+        }
         mbar_init(&done_bar, 1);
         fence_mbar_init_cluster();
         s_abort = 0;
     }
-    if (warp == 0) {
+    if (mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -211,21 +218,43 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     };
 
     constexpr uint32_t idesc = idesc_tf32(Cfg::NR);
-    // one chunk: wait for its stage, store it, fetch chunk c + 2 into the freed registers, hand
-    // the stage to the tensor core; false once a wait of the CTA has given up
-    auto step = [&](int c, RA &ra, RB &rb) -> bool {
-        const int s = c % Cfg::STAGES;
-        if (c >= Cfg::STAGES) {   // the MMAs that read this stage STAGES chunks ago are done
-            if (!mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
-                atomicOr(a.status, ST_TIMEOUT);
-                s_abort = 1;
+    auto give_up = [&]() {
+        atomicOr(a.status, ST_TIMEOUT);
+        s_abort = 1;
+    };
+    if (!mma_warp) {
+        // operand warps: chunk c waits for its stage to be free, is split and stored, chunk c + 2
+        // is fetched into the freed registers, and every thread arrives on the stage's full
+        // barrier; they run up to STAGES chunks ahead of the tensor core
+        auto pstep = [&](int c, RA &ra, RB &rb) -> bool {
+            const int s = c % Cfg::STAGES;
+            if (c >= Cfg::STAGES &&
+                !mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
+                give_up();
+                return false;
             }
+            store(c, s, ra, rb);
+            if (c + 2 < nchunks) fetch(c + 2, ra, rb);
+            fence_proxy_async_smem();   // the stores are visible to the tensor core's reads
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+            return !*(volatile int *)&s_abort;
+        };
+        float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
+        if (nchunks > 0) fetch(0, ra0, rb0);
+        if (nchunks > 1) fetch(1, ra1, rb1);
+        for (int c = 0; c < nchunks; c += 2) {
+            if (!pstep(c, ra0, rb0)) break;
+            if (c + 1 < nchunks && !pstep(c + 1, ra1, rb1)) break;
         }
-        if (!*(volatile int *)&s_abort) store(c, s, ra, rb);
-        if (c + 2 < nchunks) fetch(c + 2, ra, rb);
-        fence_proxy_async_smem();   // the stores are visible to the tensor core's reads
-        if (__syncthreads_or(*(volatile int *)&s_abort)) return false;
-        if (tid == 0) {
+    } else if (lane == 0) {
+        // MMA thread: 12 MMAs per chunk (3 split products x 4 K steps), committed to the stage's
+        // empty barrier; then one commit that covers every MMA issued
+        for (int c = 0; c < nchunks; ++c) {
+            const int s = c % Cfg::STAGES;
+            if (!mbar_wait_or_abort(&full_bar[s], (uint32_t)((c / Cfg::STAGES) & 1), a.tries, &s_abort)) {
+                give_up();
+                break;
+            }
             tc_fence_after();
             const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
             const uint32_t a_hi = base, a_lo = base + Cfg::A_BYTES;
@@ -240,21 +269,10 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             }
             tc_commit(&empty_bar[s]);
         }
-        return true;
-    };
-    float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
-    if (nchunks > 0) fetch(0, ra0, rb0);
-    if (nchunks > 1) fetch(1, ra1, rb1);
-    for (int c = 0; c < nchunks; c += 2) {
-        if (!step(c, ra0, rb0)) break;
-        if (c + 1 < nchunks && !step(c + 1, ra1, rb1)) break;
+        tc_commit(&done_bar);
     }
     // every MMA issued is complete before the accumulator is read or freed
-    if (tid == 0) tc_commit(&done_bar);
-    if (!mbar_wait_bounded(&done_bar, 0, a.tries)) {
-        atomicOr(a.status, ST_TIMEOUT);
-        s_abort = 1;
-    }
+    if (!mbar_wait_bounded(&done_bar, 0, a.tries)) give_up();
     tc_fence_after();
     const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
 
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (mma_warp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
 }
