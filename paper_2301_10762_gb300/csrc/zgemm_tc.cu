@@ -16,8 +16,8 @@
 // One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Sixteen
 // operand warps load a K chunk of 16 complex columns (one 128-byte row per matrix row) from
 // global memory two chunks ahead into registers, split it and store it into shared memory in
-// the 128-byte-swizzled K-major layout the tensor core reads, and arrive on the stage's full
-// barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
+// the 128-byte-swizzled K-major layout the tensor core reads, meet at a named barrier and hand
+// the stage over with one arrival on its full barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
 // them to the stage's empty barrier, which the operand warps wait for before they overwrite the
 // stage STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
 // 32 (w % 4) .. + 31, column part w / 4), adds C0 and writes C.
@@ -106,6 +106,17 @@ __device__ __forceinline__ long long zop_off(int idx, int div, long long stride,
     return div > 0 ? (long long)(idx / div) * stride_hi + (long long)(idx % div) * stride : (long long)idx * stride;
 }
 
+// named barrier 1 over the operand warps, with an OR of v across them (all get the result)
+__device__ __forceinline__ bool operands_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(ZG_PRODUCERS)
+        : "memory");
+    return r != 0;
+}
+
 template <int NT> struct ZCfg {
     static constexpr int NR = 2 * NT;                        // real columns of the tile (tcgen05 N)
     static constexpr int A_BYTES = ZG_BM * 128;              // one split of the A chunk
@@ -122,7 +133,7 @@ template <int NT>
 __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     using Cfg = ZCfg<NT>;
     extern __shared__ uint8_t zg_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (every producer arrives)
+    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (operand warps, one arrival)
     __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];   // stage read by its MMAs (commit)
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t s_tmem;
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const bool mma_warp = warp == ZG_PRODUCERS / 32;
     if (tid == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
-            mbar_init(&full_bar[s], ZG_PRODUCERS);
+            mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
@@ -228,16 +239,22 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         // barrier; they run up to STAGES chunks ahead of the tensor core
         auto pstep = [&](int c, RA &ra, RB &rb) -> bool {
             const int s = c % Cfg::STAGES;
+            bool bad = false;
             if (c >= Cfg::STAGES &&
                 !mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
                 give_up();
-                return false;
+                bad = true;
             }
-            store(c, s, ra, rb);
-            if (c + 2 < nchunks) fetch(c + 2, ra, rb);
-            fence_proxy_async_smem();   // the stores are visible to the tensor core's reads
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
-            return !*(volatile int *)&s_abort;
+            if (!bad) {   // a thread whose wait gave up must not write a stage the MMAs may read
+                store(c, s, ra, rb);
+                if (c + 2 < nchunks) fetch(c + 2, ra, rb);
+                fence_proxy_async_smem();   // visible to the tensor core's (async proxy) reads
+            }
+            // the operand warps meet (every store is complete) and decide together whether to
+            // go on; then one thread hands the stage to the MMA warp
+            if (operands_sync_or(bad || *(volatile int *)&s_abort)) return false;
+            if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+            return true;
         };
         float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
         if (nchunks > 0) fetch(0, ra0, rb0);
