@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int nkc = (a.K + ZG_KC - 1) / ZG_KC;
     const int nchunks = nterms * nkc;
 
-    const bool mma_warp = warp == ZG_PRODUCERS / 32;
+    const bool mma_warp = warp == 0;
+    const int ptid = tid - 32;   // operand-thread index (warps 1 .. 16)
     if (tid == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
@@ -184,14 +185,14 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         const float2 *B = a.B[u].base + zop_off(task[3 + u], a.B[u].div, a.B[u].stride, a.B[u].stride_hi);
 #pragma unroll
         for (int i = 0; i < Cfg::A_V4; ++i) {
-            const int e = tid + i * ZG_THREADS, r = e >> 3, k = k0 + 2 * (e & 7);
+            const int e = ptid + i * ZG_PRODUCERS, r = e >> 3, k = k0 + 2 * (e & 7);
             ra[i] = (m0 + r < a.M && k < a.K)
                         ? __ldg(reinterpret_cast<const float4 *>(A + (long long)(m0 + r) * a.A[u].ld + k))
                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < Cfg::B_V4; ++i) {
-            const int e = tid + i * ZG_THREADS, n = e >> 3, k = k0 + 2 * (e & 7);
+            const int e = ptid + i * ZG_PRODUCERS, n = e >> 3, k = k0 + 2 * (e & 7);
             rb[i] = (e < NT * 8 && n0 + n < a.N && k < a.K)
                         ? __ldg(reinterpret_cast<const float4 *>(B + (long long)(n0 + n) * a.B[u].ld + k))
                         : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         const uint32_t b_hi = base + 2 * Cfg::A_BYTES, b_lo = b_hi + Cfg::B_BYTES;
 #pragma unroll
         for (int i = 0; i < Cfg::A_V4; ++i) {
-            const int e = tid + i * ZG_THREADS, r = e >> 3, j = e & 7;
+            const int e = ptid + i * ZG_PRODUCERS, r = e >> 3, j = e & 7;
             float4 hi, lo;
             split4(ra[i], sg, hi, lo);
             st_shared_v4(a_hi + sw128(r, j), hi);
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         }
 #pragma unroll
         for (int i = 0; i < Cfg::B_V4; ++i) {
-            const int e = tid + i * ZG_THREADS, n = e >> 3, j = e & 7;
+            const int e = ptid + i * ZG_PRODUCERS, n = e >> 3, j = e & 7;
             if (e < NT * 8) {
                 const float4 v = rb[i];
                 float4 hi, lo;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             // the operand warps meet (every store is complete) and decide together whether to
             // go on; then one thread hands the stage to the MMA warp
             if (operands_sync_or(bad || *(volatile int *)&s_abort)) return false;
-            if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+            if (ptid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
             return true;
         };
         float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
@@ -293,10 +294,10 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     tc_fence_after();
     const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
 
-    if (ok && (warp >> 2) < (Cfg::NR >= 64 ? 4 : Cfg::NR / 16)) {
-        // warp w reads lanes 32 (w % 4) .. + 31 (rows), real columns of part w / 4
+    if (ok && !mma_warp && ((warp - 1) >> 2) < (Cfg::NR >= 64 ? 4 : Cfg::NR / 16)) {
+        // warp w reads lanes 32 (w % 4) .. + 31 (rows), real columns of part (w - 1) / 4
         constexpr int parts = Cfg::NR >= 64 ? 4 : Cfg::NR / 16, cpp = Cfg::NR / parts;
-        const int q = warp & 3, h = warp >> 2;
+        const int q = warp & 3, h = (warp - 1) >> 2;
         const int r = 32 * q + lane, m = m0 + r;
         const float2 *C0 =
             a.C0.base ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) : nullptr;
