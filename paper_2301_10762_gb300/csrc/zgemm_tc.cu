@@ -248,8 +248,11 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             }
             if (!bad) {   // a thread whose wait gave up must not write a stage the MMAs may read
                 store(c, s, ra, rb);
+                // the stores are made visible to the tensor core's (async proxy) reads before
+                // the next loads are issued: a proxy fence after them would wait for those
+                // loads as well and expose their latency on every chunk
+                fence_proxy_async_smem();
                 if (c + 2 < nchunks) fetch(c + 2, ra, rb);
-                fence_proxy_async_smem();   // visible to the tensor core's (async proxy) reads
             }
             // the operand warps meet (every store is complete) and decide together whether to
             // go on; then one thread hands the stage to the MMA warp
