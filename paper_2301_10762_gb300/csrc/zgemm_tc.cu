@@ -15,7 +15,7 @@
 //
 // One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Sixteen
 // operand warps load a K chunk of 16 complex columns (one 128-byte row per matrix row) from
-// global memory two chunks ahead into registers, split it and store it into shared memory in
+// global memory two chunks ahead into registers (three register sets), split it and store it into shared memory in
 // the 128-byte-swizzled K-major layout the tensor core reads, meet at a named barrier and hand
 // the stage over with one arrival on its full barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
 // them to the stage's empty barrier, which the operand warps wait for before they overwrite the
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         // operand warps: chunk c waits for its stage to be free, is split and stored, chunk c + 2
         // is fetched into the freed registers, and every thread arrives on the stage's full
         // barrier; they run up to STAGES chunks ahead of the tensor core
-        auto pstep = [&](int c, RA &ra, RB &rb) -> bool {
+        auto pstep = [&](int c, RA &ra, RB &rb, RA &na, RB &nb) -> bool {
             const int s = c % Cfg::STAGES;
             bool bad = false;
             if (c >= Cfg::STAGES &&
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                 // the next loads are issued: a proxy fence after them would wait for those
                 // loads as well and expose their latency on every chunk
                 fence_proxy_async_smem();
-                if (c + 2 < nchunks) fetch(c + 2, ra, rb);
+                if (c + 2 < nchunks) fetch(c + 2, na, nb);
             }
             // the operand warps meet (every store is complete) and decide together whether to
             // go on; then one thread hands the stage to the MMA warp
@@ -260,12 +260,16 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             if (ptid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
             return true;
         };
-        float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4];
+        // three register sets: chunk c is stored from set c mod 3 while chunk c + 2 is loaded
+        // into set (c + 2) mod 3, whose stores (chunk c - 1) have long been issued -- loading
+        // into the set being stored would wait for the stores to read their registers
+        float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4], ra2[Cfg::A_V4], rb2[Cfg::B_V4];
         if (nchunks > 0) fetch(0, ra0, rb0);
         if (nchunks > 1) fetch(1, ra1, rb1);
-        for (int c = 0; c < nchunks; c += 2) {
-            if (!pstep(c, ra0, rb0)) break;
-            if (c + 1 < nchunks && !pstep(c + 1, ra1, rb1)) break;
+        for (int c = 0; c < nchunks; c += 3) {
+            if (!pstep(c, ra0, rb0, ra2, rb2)) break;
+            if (c + 1 < nchunks && !pstep(c + 1, ra1, rb1, ra0, rb0)) break;
+            if (c + 2 < nchunks && !pstep(c + 2, ra2, rb2, ra1, rb1)) break;
         }
     } else if (lane == 0) {
         // MMA thread: 12 MMAs per chunk (3 split products x 4 K steps), committed to the stage's
