@@ -53,10 +53,13 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n_real) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
 }
 
+// x rounded to the TF32 grid (10 explicit mantissa bits), to nearest with ties away from zero:
+// add half a unit of the 11th bit to the magnitude bits and clear the 13 low bits.  Integer
+// operations at full rate (the conversion instruction runs on a low-rate pipe, and the operand
+// warps round every element of every chunk).  Finite inputs; a carry into the exponent gives the
+// correctly rounded next power of two.
 __device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, float4 v) {
