@@ -15,10 +15,11 @@ factors is the comparison the metric names; the per-frequency error of sampled c
 against the CPU oracle is reported for both.
 
 Also reported: per-solve latency (p50 / p99 of helm_solve calls on a resident factor, one
-right-hand side per frequency and the full 64), the bilevel-hypergradient step of the
-FWI-step geometry (128 x 128, omega in {5, 10, 15}, 16 sources, 32 receivers, ten PCG
-iterations) and a short solve-server session (Poisson arrivals, 64^2 .. 256^2, FP64 and
-mixed).
+right-hand side per frequency and the full 64), the tensor-core GEMM alone at the workload's
+product shapes, the bilevel-hypergradient step of the FWI-step geometry (128 x 128, omega in
+{5, 10, 15}, 16 sources, 32 receivers, ten PCG iterations), the batched hypergradient over the
+32 uneven training models (96^2 .. 256^2) and a short solve-server session (Poisson arrivals,
+64^2 .. 256^2, FP64 and mixed).
 
 Multi-GPU (torchrun): every rank solves its own velocity model (weak scaling); no collective
 touches the data path, only the timing max over ranks and the solve count.
@@ -427,6 +428,37 @@ def hypergrad_step(hm, torch, steps, warmup, rank):
     return out
 
 
+# ------------------------------------------------ batched hypergradient (C4)
+
+def hypergrad_batch(hm, torch, n_cg=20, concurrent=4):
+    """The batched bilevel hypergradient of Algorithm alg:box over the uneven training set: 32
+    layered-plus-inclusion models on grids n = 96 + 32 (k mod 6), omega in {3, 9, 18, 36}, 51
+    sources in the well at x = 0.05 (on each model's own grid), 24 receivers at x = 0.95, fixed
+    N_CG = 20, mixed, refined to 1e-10; models processed `concurrent` at a time (own streams).
+    One timed pass after a warm-up pass on two models."""
+    import workloads as W
+    ms = W.config_hypergrad()
+    grids = [(w.nx, w.nz, w.lx, w.lz) for w in ms]
+    mf = [torch.tensor(w.m, device="cuda") for w in ms]
+    mt = [torch.tensor(w.m_true, device="cuda") for w in ms]
+    acqs = [hm.Acq.from_workload(w.acq) for w in ms]
+    w0 = ms[0]
+    kw = dict(prec=hm.HELM_MIXED, cg_fixed_iters=n_cg, refine_rtol=REFINE_RTOL, concurrent_models=concurrent)
+    hm.bilevel_hypergrad(grids[:2], mf[:2], mt[:2], acqs[:2], w0.omegas, w0.alpha, w0.alpha, w0.mu, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = hm.bilevel_hypergrad(grids, mf, mt, acqs, w0.omegas, w0.alpha, w0.alpha, w0.mu, **kw)
+    e1.record()
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    solves = out["solves"] + out["data_solves"]
+    return {"workload": f"hypergrad_batch: {len(ms)} models, grids 96^2..256^2, omega {{3,9,18,36}}, "
+                        f"{w0.acq.n_src} sources, 24 receivers, N_CG={n_cg}, mixed",
+            "value": solves / dt, "unit": UNIT, "seconds": dt, "solves": solves, "concurrent_models": concurrent,
+            "max_refine_iters": out["max_refine_iters"]}
+
+
 # ------------------------------------------------------------------------ main
 
 def main():
@@ -635,6 +667,10 @@ def main():
     extras = {"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks)} if rank == 0 else {}
     if not args.no_extras and rank == 0:
         extras["hypergrad_step_128"] = hypergrad_step(hm, torch, 10, args.warmup, rank)
+        try:
+            extras["hypergrad_batch"] = hypergrad_batch(hm, torch)
+        except Exception as e:  # keep the main line if the batch fails
+            extras["hypergrad_batch"] = {"failed": str(e)[:300]}
         try:
             extras["server"] = server_run([64, 128, 256], 40, 3.0, (0.8,))
         except Exception as e:  # keep the main line if the session fails

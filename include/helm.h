@@ -124,8 +124,10 @@ void helm_op_destroy(helm_op_t *op);
  * level by level (log2(nx) levels), so that each level is a batch of independent dense block
  * inversions and block products over all lines and frequencies, run on the tensor cores
  * (complex products as real TF32 products with the 3xTF32 split, FP32 accumulation).  Its
- * storage is about 3 nx nz^2 complex FP32 entries per frequency.  HELM_FACTOR_AUTO: BCR where
- * it applies (unless the environment sets HELM_FACTOR=line), else the line recurrence. */
+ * storage is about 3 nx nz^2 complex FP32 entries per frequency.  HELM_FACTOR_AUTO (unless the
+ * environment sets HELM_FACTOR=line or =bcr): BCR for HELM_MIXED on lines of nz >= 192 nodes
+ * (where the line recurrence's chain of nx dependent line inversions dominates), else the line
+ * recurrence. */
 typedef enum { HELM_FACTOR_AUTO = 0, HELM_FACTOR_LINE = 1, HELM_FACTOR_BCR = 2 } helm_factor_method;
 typedef struct {
     int32_t method;       /* helm_factor_method */
@@ -154,6 +156,10 @@ void helm_factor_destroy(helm_factor_t *f);
  * cluster, leaves its outputs incomplete and the call returns HELM_ETIMEOUT; the context stays
  * usable and the next call starts clean.  Process-wide; meant for tests of that error path. */
 void helm_set_wait_tries(int64_t tries);
+
+/* helm_factor_get_method -- the method a factor was built with (HELM_FACTOR_LINE or
+ * HELM_FACTOR_BCR); -1 for NULL. */
+int32_t helm_factor_get_method(const helm_factor_t *f);
 
 /* helm_factor_fp64_blocks -- HELM_MIXED: number of 16 x 16 pivot blocks of the factor that
  * were flagged and inverted in FP64.  A block is flagged when its FP32 Gauss-Jordan inverse X

@@ -148,17 +148,23 @@ extern "C" void helm_op_destroy(helm_op_t *op) {
 
 // ------------------------------------------------------------------------ factor
 
-// Factor method of a mixed factor: the options, else HELM_FACTOR=line|bcr, else BCR where it
-// applies (an even n_z of at least 16) and the line recurrence otherwise.  FP64 factors are line
-// factors (the tensor cores have no FP64 path).
+// Factor method of a mixed factor: the options, else HELM_FACTOR=line|bcr, else BCR on lines of
+// at least kBcrMinNz nodes and the line recurrence below.  The line recurrence's dependent chain
+// (n_x line inversions, n_x line steps per solve) is what BCR removes; on short lines its
+// per-step cost is small and BCR's extra arithmetic and launches do not pay (measured: 128 x 128
+// with 16 right-hand sides per frequency favours the line factor, 256 x 256 with 64 favours BCR
+// by 2.5x).  FP64 factors are line factors (the tensor cores have no FP64 path).
+static constexpr int kBcrMinNz = 192;
 static bool pick_bcr(const helm_op *op, helm_prec prec, const helm_factor_opts *opts) {
     if (prec != HELM_MIXED || !bcr_supported(op->g)) return false;
     int m = opts ? opts->method : HELM_FACTOR_AUTO;
     if (m == HELM_FACTOR_AUTO) {
         const char *env = getenv("HELM_FACTOR");
         if (env && !strcmp(env, "line")) m = HELM_FACTOR_LINE;
+        else if (env && !strcmp(env, "bcr")) m = HELM_FACTOR_BCR;
+        else m = op->g.nz >= kBcrMinNz ? HELM_FACTOR_BCR : HELM_FACTOR_LINE;
     }
-    return m != HELM_FACTOR_LINE;
+    return m == HELM_FACTOR_BCR;
 }
 
 extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_factor_opts *opts, helm_factor_t **out) {
@@ -246,6 +252,10 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_fac
 }
 
 extern "C" int32_t helm_factor_fp64_blocks(const helm_factor_t *f) { return f ? f->fp64_blocks : -1; }
+
+extern "C" int32_t helm_factor_get_method(const helm_factor_t *f) {
+    return f ? (f->use_bcr ? HELM_FACTOR_BCR : HELM_FACTOR_LINE) : -1;
+}
 
 extern "C" void helm_factor_destroy(helm_factor_t *f) {
     if (!f) return;

@@ -92,7 +92,7 @@ class helm_trace_entry(C.Structure):
 
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
-            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_set_wait_tries",
+            "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_factor_get_method", "helm_set_wait_tries",
             # include/helm_blas.h
             "helm_zgemm_batched", "helm_zinv_batched", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
@@ -134,6 +134,8 @@ def load(path: str = LIB_PATH):
     lib.helm_zinv_batched.argtypes = [i32, i32, vp, C.c_int64, i32, vp, C.c_int64, i32, vp]
     lib.helm_set_wait_tries.restype = None
     lib.helm_set_wait_tries.argtypes = [C.c_int64]
+    lib.helm_factor_get_method.restype = i32
+    lib.helm_factor_get_method.argtypes = [vp]
     lib.helm_factor_fp64_blocks.restype = i32
     lib.helm_factor_fp64_blocks.argtypes = [vp]
     lib.helm_factor_destroy.restype = None
@@ -270,6 +272,11 @@ class Factor:
     def fp64_blocks(self) -> int:
         """Pivot blocks of a mixed factor that were flagged and inverted in FP64."""
         return int(load().helm_factor_fp64_blocks(self.handle))
+
+    @property
+    def method(self) -> int:
+        """HELM_FACTOR_LINE (1) or HELM_FACTOR_BCR (2): the method the factor was built with."""
+        return int(load().helm_factor_get_method(self.handle))
 
     def close(self):
         if self.handle:

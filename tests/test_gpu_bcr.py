@@ -78,7 +78,10 @@ def test_bcr_solve_matches_oracle(nx, nz, nrhs):
         assert ex <= 1e-8 and ey <= 1e-8, (q, ex, ey)
 
 
-def test_bcr_and_line_factors_agree_and_bcr_is_the_mixed_default():
+def test_bcr_and_line_factors_agree_and_the_automatic_choice():
+    """Both methods solve the same system to the refinement tolerance; the automatic choice is
+    the line recurrence on short lines and BCR from nz = 192 on (mixed), the line factor for
+    FP64, and BCR is refused for FP64."""
     nx, nz = 40, 36
     rng = np.random.default_rng(5)
     m = (1.0 / (1.0 + 0.4 * rng.uniform(0, 1, (nx, nz))) ** 2).reshape(-1)
@@ -86,11 +89,17 @@ def test_bcr_and_line_factors_agree_and_bcr_is_the_mixed_default():
     B = torch.tensor(rng.standard_normal((1, 4, nx * nz)) + 0j, device="cuda")
     op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
     X = {}
-    for meth in (hm.HELM_FACTOR_LINE, hm.HELM_FACTOR_BCR, hm.HELM_FACTOR_AUTO):
-        X[meth], _ = hm.helm_solve(hm.helm_factor(op, hm.HELM_MIXED, method=meth), B, rtol=1e-12, max_iter=20)
+    for meth in (hm.HELM_FACTOR_LINE, hm.HELM_FACTOR_BCR):
+        f = hm.helm_factor(op, hm.HELM_MIXED, method=meth)
+        assert f.method == meth
+        X[meth], _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=20)
     ref = X[hm.HELM_FACTOR_LINE]
-    for meth in (hm.HELM_FACTOR_BCR, hm.HELM_FACTOR_AUTO):
-        err = torch.linalg.vector_norm(X[meth] - ref, dim=-1) / torch.linalg.vector_norm(ref, dim=-1)
-        assert float(err.max()) <= 1e-10
+    err = torch.linalg.vector_norm(X[hm.HELM_FACTOR_BCR] - ref, dim=-1) / torch.linalg.vector_norm(ref, dim=-1)
+    assert float(err.max()) <= 1e-10
+    assert hm.helm_factor(op, hm.HELM_MIXED).method == hm.HELM_FACTOR_LINE
+    assert hm.helm_factor(op, hm.HELM_FP64).method == hm.HELM_FACTOR_LINE
     with pytest.raises(hm.HelmError):
         hm.helm_factor(op, hm.HELM_FP64, method=hm.HELM_FACTOR_BCR)   # no FP64 tensor path
+    m2 = np.full(20 * 192, 0.5)
+    op2 = hm.helm_assemble(20, 192, 1.0, 1.0, torch.tensor(m2, device="cuda"), om)
+    assert hm.helm_factor(op2, hm.HELM_MIXED).method == hm.HELM_FACTOR_BCR
