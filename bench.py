@@ -204,6 +204,36 @@ def tensor_peak(peaks, sustained=True):
     return (1700.0 if sustained else 1900.0) * TF32_PER_BF16, "fallback BF16 x 1.1/2.25 (of fallback)"
 
 
+def matmul_peaks(torch):
+    """cuBLAS dense matmul rates (2 n^3 flops per product) for the precisions the path touches:
+    FP32 operands with TF32 tensor cores allowed, plain FP32, and FP64; best of 10 products after
+    3 warm-up ones, CUDA events around each product."""
+    out = {}
+    cases = [("tf32", torch.float32, True, 8192), ("fp32", torch.float32, False, 8192),
+             ("fp64", torch.float64, False, 4096)]
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32, n in cases:
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            c = torch.empty(n, n, device="cuda", dtype=dt)
+            best = float("inf")
+            for it in range(13):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                if it >= 3:
+                    best = min(best, e0.elapsed_time(e1))
+            out[name] = {"n": n, "ms": best, "tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12}
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    return out
+
+
 def roofline(name, trace, breakdown, dims, peaks):
     """name: the dominant kernel; trace: the timed region's trace (that kernel timed on every
     launch); breakdown: one fully traced step outside the timed region (for the share)."""
@@ -476,6 +506,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the hypergradient step and the server session")
     ap.add_argument("--server", action="store_true", help="long solve-server session instead of the solve step")
     ap.add_argument("--gemm-only", action="store_true", help="time the tensor-core GEMM alone and exit")
+    ap.add_argument("--matmul-peaks", action="store_true",
+                    help="time torch.matmul (cuBLAS) in TF32, FP32 and FP64 and exit")
     ap.add_argument("--server-sizes", default="64,128,256")
     ap.add_argument("--server-seconds", type=float, default=10.0)
     ap.add_argument("--server-requests", type=int, default=200, help="requests of the capacity run")
@@ -516,6 +548,10 @@ def main():
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peaks = json.load(open(pp))
+    if args.matmul_peaks:
+        if rank == 0:
+            print(json.dumps({"matmul_peaks": matmul_peaks(torch)}), flush=True)
+        return
     if args.gemm_only:
         if rank == 0:
             print(json.dumps({"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks)}), flush=True)

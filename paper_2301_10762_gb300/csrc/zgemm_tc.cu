@@ -19,8 +19,9 @@
 // the 128-byte-swizzled K-major layout the tensor core reads, meet at a named barrier and hand
 // the stage over with one arrival on its full barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
 // them to the stage's empty barrier, which the operand warps wait for before they overwrite the
-// stage STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the accumulator with tcgen05.ld (warp w: lanes
-// 32 (w % 4) .. + 31, column part w / 4), adds C0 and writes C.
+// stage STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the
+// accumulator with tcgen05.ld into a padded tile in the (then idle) shared memory, from which
+// each warp writes whole rows (row-major C) or whole columns (column-major C), adding C0.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -304,31 +305,55 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     tc_fence_after();
     const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
 
-    if (ok && !mma_warp && ((warp - 1) >> 2) < (Cfg::NR >= 64 ? 4 : Cfg::NR / 16)) {
-        // warp w reads lanes 32 (w % 4) .. + 31 (rows), real columns of part (w - 1) / 4
-        constexpr int parts = Cfg::NR >= 64 ? 4 : Cfg::NR / 16, cpp = Cfg::NR / parts;
-        const int q = warp & 3, h = (warp - 1) >> 2;
-        const int r = 32 * q + lane, m = m0 + r;
+    if (ok && !mma_warp) {
+        // Epilogue through shared memory (free once every MMA is complete): the operand warps
+        // copy the accumulator tile from tensor memory (warp w: lanes 32 (w % 4) .. + 31, the
+        // real columns of part (w - 1) / 4) into a padded [128][NT + 1] complex tile, meet, and
+        // write C (adding C0) a row or a column per warp and step, so that every warp store
+        // covers consecutive addresses whether C is row- or column-major.
+        constexpr int parts = Cfg::NR >= 64 ? 4 : Cfg::NR / 16, cpp = Cfg::NR / parts, TS = NT + 1;
+        float2 *T = reinterpret_cast<float2 *>(zg_smem_raw + (smem0 - smem_u32(zg_smem_raw)));
+        const int q = warp & 3, h = (warp - 1) >> 2, pw = warp - 1;
+        if (h < parts) {
+            const int r = 32 * q + lane;
+            for (int col = h * cpp; col < (h + 1) * cpp; col += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) T[r * TS + col / 2 + i] = make_float2(v[2 * i], v[2 * i + 1]);
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(ZG_PRODUCERS) : "memory");
         const float2 *C0 =
             a.C0.base ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) : nullptr;
         float2 *C = a.C + zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi);
-        for (int col = h * cpp; col < (h + 1) * cpp; col += 16) {   // real columns of this warp's part
-            float v[16];
-            tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
-            if (m >= a.M) continue;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int n = n0 + col / 2 + i;
-                if (n >= a.N) break;
-                float2 out = make_float2(v[2 * i], v[2 * i + 1]);
-                const long long o0 = a.c_col ? (long long)n * a.C0.ld + m : (long long)m * a.C0.ld + n;
-                const long long o = a.c_col ? (long long)n * a.ldc + m : (long long)m * a.ldc + n;
-                if (C0) {
-                    const float2 b = C0[o0];
-                    out.x += b.x;
-                    out.y += b.y;
+        if (!a.c_col) {
+            for (int rr = pw; rr < ZG_BM; rr += ZG_PRODUCERS / 32) {   // row-major: a row per warp
+                const int m = m0 + rr;
+                if (m >= a.M) break;
+                for (int nn = lane; nn < NT && n0 + nn < a.N; nn += 32) {
+                    float2 out = T[rr * TS + nn];
+                    if (C0) {
+                        const float2 b = C0[(long long)m * a.C0.ld + n0 + nn];
+                        out.x += b.x;
+                        out.y += b.y;
+                    }
+                    C[(long long)m * a.ldc + n0 + nn] = out;
                 }
-                C[o] = out;
+            }
+        } else {
+            for (int nn = pw; nn < NT; nn += ZG_PRODUCERS / 32) {     // column-major: a column per warp
+                const int n = n0 + nn;
+                if (n >= a.N) break;
+                for (int rr = lane; rr < ZG_BM && m0 + rr < a.M; rr += 32) {
+                    float2 out = T[rr * TS + nn];
+                    if (C0) {
+                        const float2 b = C0[(long long)n * a.C0.ld + m0 + rr];
+                        out.x += b.x;
+                        out.y += b.y;
+                    }
+                    C[(long long)n * a.ldc + m0 + rr] = out;
+                }
             }
         }
     }
