@@ -16,7 +16,8 @@ interpolation.  Close to a minimiser the decrease of f per step falls to the rou
 itself (an FP64 objective cannot resolve ||g|| = 1e-10 through f), so a step is also accepted on
 the approximate Wolfe conditions of Hager & Zhang (2005):
     f(x + a p) <= f(x) + eps |f(x)|   and   c2 g.p <= g(x + a p).p <= (2 c1 - 1) g.p,
-which test the slope instead.  A trial point where the objective is not finite (a model with
+which test the slope instead; where f is flat in that sense the zoom also keeps the step
+bracketed by the sign of the slope rather than by comparing values of f (their interval update).  A trial point where the objective is not finite (a model with
 m <= 0, where sqrt(m) is undefined) is treated as a step that is too long.
 """
 from __future__ import annotations
@@ -94,6 +95,14 @@ def wolfe_line_search(fun, x, f0, g0, p, alpha0=1.0, c1=1e-4, c2=0.9, max_evals=
             f, g, dg = phi(a)
             if accept(a, f, dg):
                 return a, f, g
+            if math.isfinite(f) and f <= f0 + flat:
+                # f is flat to rounding here, so its comparisons carry no information: keep the
+                # minimiser bracketed by the sign of the slope (Hager & Zhang's interval update)
+                if dg * (hi - lo) >= 0.0:
+                    hi, f_hi, dg_hi = a, f, dg
+                else:
+                    lo, f_lo, dg_lo, g_lo = a, f, dg, g
+                continue
             if not math.isfinite(f) or f > f0 + c1 * a * dg0 or f >= f_lo:
                 hi, f_hi, dg_hi = a, f, dg
             else:
