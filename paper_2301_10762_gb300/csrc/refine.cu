@@ -28,6 +28,7 @@ namespace helm {
 namespace {
 
 constexpr int RF_THREADS = 256;
+constexpr int RF_NPT = 8;   // nodes per thread in the per-column kernels (a block covers 2048 nodes)
 
 // ---------------------------------------------------------------- FP32-pair arithmetic
 // The intrinsics keep the compiler from contracting or reassociating these sequences.
@@ -115,23 +116,33 @@ __global__ void split_diag_kernel(size_t n, const double2 *diag, float4 *diag2) 
     }
 }
 
-// grid: (node blocks, columns)
+// grid: (node blocks of RF_THREADS * RF_NPT, columns)
 __global__ void __launch_bounds__(RF_THREADS) refine_start_kernel(int N, int cols, const double2 *B, int conj,
                                                                   float4 *bd, float2 *r32, double *norms) {
     __shared__ double sh[RF_THREADS / 32];
     for (int c = blockIdx.y; c < cols; c += gridDim.y) {
-        const int k = blockIdx.x * RF_THREADS + threadIdx.x;
         double bb = 0.0;
-        if (k < N) {
-            const size_t e = (size_t)c * N + k;
-            double2 b = B[e];
-            if (conj) b.y = -b.y;
-            float4 v;
-            split_double(b.x, v.x, v.z);
-            split_double(b.y, v.y, v.w);
-            bd[e] = v;
-            r32[e] = make_float2(v.x, v.y);
-            bb = b.x * b.x + b.y * b.y;
+        const size_t base = (size_t)c * N;
+        const int k0 = blockIdx.x * RF_THREADS * RF_NPT + threadIdx.x;
+        double2 b[RF_NPT];
+#pragma unroll
+        for (int q = 0; q < RF_NPT; ++q) {   // all loads first: RF_NPT in flight per thread
+            const int k = k0 + q * RF_THREADS;
+            b[q] = k < N ? __ldcs(B + base + k) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < RF_NPT; ++q) {
+            const int k = k0 + q * RF_THREADS;
+            if (k < N) {
+                double2 v2 = b[q];
+                if (conj) v2.y = -v2.y;
+                float4 v;
+                split_double(v2.x, v.x, v.z);
+                split_double(v2.y, v.y, v.w);
+                bd[base + k] = v;
+                r32[base + k] = make_float2(v.x, v.y);
+                bb += v2.x * v2.x + v2.y * v2.y;
+            }
         }
         bb = block_sum(bb, sh);
         if (threadIdx.x == 0) {
@@ -186,7 +197,7 @@ __device__ void refine_stop_test(int cols, double *norms, RefineStop stop, Refin
     }
 }
 
-// grid: (node blocks, columns); norms[col][0] pre-zeroed, norms[col][1] = ||b||^2
+// grid: (node blocks of RF_THREADS * RF_NPT, columns); norms[col][0] pre-zeroed, norms[col][1] = ||b||^2
 __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, int nrhs, int cols, const float4 *diag2,
                                                                    const float4 *bd, const float4 *x_in,
                                                                    const float2 *delta, float4 *x_out, float2 *r32,
@@ -206,13 +217,16 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
         const int eb = (int)(((unsigned long long)__double_as_longlong(bb) >> 52) & 0x7FF);
         const int ks = bb > 0.0 ? max(-62, min(62, (eb - 1023) / 2)) : 0;
         const float scale = __uint_as_float((unsigned)(127 - ks) << 23);
-        const int k = blockIdx.x * RF_THREADS + threadIdx.x;
         float rr = 0.f;
-        if (k < N) {
+        const size_t base = (size_t)c * N;
+        const float4 *xc = x_in ? x_in + base : nullptr;
+        const float2 *dc = delta + base;
+        const int k0 = blockIdx.x * RF_THREADS * RF_NPT + threadIdx.x;
+#pragma unroll 2
+        for (int q = 0; q < RF_NPT; ++q) {
+            const int k = k0 + q * RF_THREADS;
+            if (k >= N) break;
             const int i = k / nz, j = k % nz;
-            const size_t base = (size_t)c * N;
-            const float4 *xc = x_in ? x_in + base : nullptr;
-            const float2 *dc = delta + base;
             const cff xk = iterate_at(xc, dc, k);
             cff sx = {{0.f, 0.f}, {0.f, 0.f}}, sz = sx;
             if (i > 0) sx = cff_add(sx, iterate_at(xc, dc, k - nz));
@@ -224,11 +238,11 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
             cff ax = cff_mul(cff_of(diag2[(size_t)sys * N + k]), xk);
             ax = cff_add(ax, cff_scale(sx, cxj));
             ax = cff_add(ax, cff_scale(sz, czi));
-            const cff r = cff_sub(cff_of(bd[base + k]), ax);
+            const cff r = cff_sub(cff_of(__ldcs(bd + base + k)), ax);
             x_out[base + k] = cff_pack(xk);
             r32[base + k] = make_float2(r.re.hi, r.im.hi);
             const float sr = r.re.hi * scale, si = r.im.hi * scale;
-            rr = sr * sr + si * si;
+            rr = fmaf(sr, sr, fmaf(si, si, rr));
         }
         rr = block_sum(rr, shf);
         if (threadIdx.x == 0) atomicAdd(norms + 2 * (size_t)c, ldexp((double)rr, 2 * ks));
@@ -261,7 +275,19 @@ __global__ void refine_accumulate_kernel(size_t n, const float2 *d, int conj, do
 __global__ void refine_finish_kernel(size_t n, const float4 *xa, const float4 *xb, const RefineState *st, int conj,
                                      double2 *X) {
     const float4 *x = (st->iters & 1) ? xa : xb;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; e + 3 * stride < n; e += 4 * stride) {   // four loads in flight per thread
+        float4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldcs(x + e + q * stride);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double re = (double)v[q].x + (double)v[q].z, im = (double)v[q].y + (double)v[q].w;
+            X[e + q * stride] = make_double2(re, conj ? -im : im);
+        }
+    }
+    for (; e < n; e += stride) {
         const float4 v = x[e];
         const double re = (double)v.x + (double)v.z, im = (double)v.y + (double)v.w;
         X[e] = make_double2(re, conj ? -im : im);
@@ -288,7 +314,7 @@ cudaError_t launch_refine_start(const GridGeom &g, int cols, const double2 *B, i
     const int N = g.nx * g.nz;
     cudaError_t e = cudaMemsetAsync(norms, 0, (size_t)cols * 2 * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    dim3 grid((N + RF_THREADS - 1) / RF_THREADS, std::min(cols, 65535));
+    dim3 grid((N + RF_THREADS * RF_NPT - 1) / (RF_THREADS * RF_NPT), std::min(cols, 65535));
     HELM_TRACED(K_REFSTART, st, (refine_start_kernel<<<grid, RF_THREADS, 0, st>>>(N, cols, B, conj, bd, r32, norms)));
     return cudaGetLastError();
 }
@@ -298,7 +324,7 @@ cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const f
                                  cudaStream_t st, RefineState *state, RefineStop stop) {
     const int N = g.nx * g.nz, cols = n_sys * nrhs;
     StencilPairs cp{pair_of(coup_x(g, 1)), pair_of(coup_x(g, 0)), pair_of(coup_z(g, 1)), pair_of(coup_z(g, 0))};
-    dim3 grid((N + RF_THREADS - 1) / RF_THREADS, std::min(cols, 65535));
+    dim3 grid((N + RF_THREADS * RF_NPT - 1) / (RF_THREADS * RF_NPT), std::min(cols, 65535));
     HELM_TRACED(K_REFUPDATE, st, (refine_update_kernel<<<grid, RF_THREADS, 0, st>>>(g, nrhs, cols, diag2, bd, x_in, delta,
                                                                                     x_out, r32, norms, cp, state, stop)));
     return cudaGetLastError();
