@@ -460,6 +460,49 @@ def hypergrad_step(hm, torch, steps, warmup, rank):
 
 # ------------------------------------------------ batched hypergradient (C4)
 
+def grid512_step(hm, torch, steps=2, warmup=1):
+    """The metric's step on the largest grid of the solve server's workload: 512 x 512, the
+    same 8 frequencies and 64 top-row sources, mixed (block cyclic reduction) refined to 1e-10,
+    factor included; RHS-solves/s, per-phase times and the refinement sweeps."""
+    import workloads as W
+    w = W.config_mixed(512)
+    acq = hm.Acq.from_workload(w.acq)
+    m = torch.tensor(w.m, device="cuda")
+    n_om, ns, N = len(w.omegas), w.acq.n_src, w.n_nodes
+    B = torch.empty((n_om, ns, N), dtype=torch.complex128, device="cuda")
+    X = torch.empty_like(B)
+
+    def step(ev=None):
+        op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, m, w.omegas)
+        f = hm.helm_factor(op, hm.HELM_MIXED)
+        if ev is not None:
+            ev.record()
+        hm.helm_sources(op, acq, B)
+        _, info = hm.helm_solve(f, B, X, rtol=REFINE_RTOL, max_iter=40)
+        f.close()
+        op.close()
+        return info
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ts, fs, its = [], [], []
+    for _ in range(steps):
+        e0, ef, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        info = step(ef)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+        fs.append(e0.elapsed_time(ef) / 1e3)
+        its.append(info["iters"])
+    t = statistics.median(ts)
+    return {"workload": "mixed_512: 512x512, omega {5, 10, ..., 40}, 64 top-row point sources, refined to 1e-10",
+            "value": n_om * ns / t, "unit": UNIT, "ms_per_step": 1e3 * t, "steps": steps,
+            "factor_ms": 1e3 * statistics.median(fs), "refinement_sweeps": max(its),
+            "max_relres": info["max_relres"]}
+
+
 def hypergrad_batch(hm, torch, n_cg=20, concurrent=4):
     """The batched bilevel hypergradient of Algorithm alg:box over the uneven training set: 32
     layered-plus-inclusion models on grids n = 96 + 32 (k mod 6), omega in {3, 9, 18, 36}, 51
@@ -707,6 +750,10 @@ def main():
             extras["hypergrad_batch"] = hypergrad_batch(hm, torch)
         except Exception as e:  # keep the main line if the batch fails
             extras["hypergrad_batch"] = {"failed": str(e)[:300]}
+        try:
+            extras["mixed_512"] = grid512_step(hm, torch)
+        except Exception as e:  # keep the main line if the large grid fails
+            extras["mixed_512"] = {"failed": str(e)[:300]}
         try:
             extras["server"] = server_run([64, 128, 256], 40, 3.0, (0.8,))
         except Exception as e:  # keep the main line if the session fails

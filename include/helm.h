@@ -157,6 +157,26 @@ void helm_factor_destroy(helm_factor_t *f);
  * usable and the next call starts clean.  Process-wide; meant for tests of that error path. */
 void helm_set_wait_tries(int64_t tries);
 
+/* helm_fault_mask -- host-side fault injection (no counterpart in the paper; for tests of the
+ * failure paths).  The environment variable HELM_FAULT, read at every call that can take the
+ * path, is a comma-separated list of:
+ *   alloc    every device allocation of the library fails (calls return HELM_ENOMEM);
+ *   pivot    helm_factor factors a copy of A's diagonal whose first entry the host set to NaN
+ *            (the factor kernels meet a non-finite pivot: HELM_ESINGULAR; the op is unchanged);
+ *   timeout  bounded device-side waits take a try limit of zero, as after
+ *            helm_set_wait_tries(0): the first wait that is not already complete gives up
+ *            (HELM_ETIMEOUT);
+ *   nan_rhs  helm_solve / helm_adjoint_solve solve a copy of B whose first entry is NaN (the
+ *            residual is not finite: HELM_ENOCONV).
+ * Returns the bits the current value selects (HELM_FAULT_UNKNOWN for unrecognised words).
+ * Nothing faults, traps or hangs the device. */
+#define HELM_FAULT_ALLOC 0x1u
+#define HELM_FAULT_PIVOT 0x2u
+#define HELM_FAULT_TIMEOUT 0x4u
+#define HELM_FAULT_NAN_RHS 0x8u
+#define HELM_FAULT_UNKNOWN 0x80000000u
+uint32_t helm_fault_mask(void);
+
 /* helm_factor_get_method -- the method a factor was built with (HELM_FACTOR_LINE or
  * HELM_FACTOR_BCR); -1 for NULL. */
 int32_t helm_factor_get_method(const helm_factor_t *f);
@@ -174,8 +194,8 @@ int32_t helm_factor_fp64_blocks(const helm_factor_t *f);
  * they may not alias.  rtol / max_iter drive the refinement of HELM_MIXED (ignored by
  * HELM_FP64 except that info->max_relres is computed when info != NULL).  The call
  * synchronises the op's stream.
- * Errors: EINVAL, ENOCONV (mixed: max_iter reached above rtol; X holds the last
- * iterate), ETIMEOUT (a bounded device-side wait of a sweep gave up; X is incomplete),
+ * Errors: EINVAL, ENOCONV (mixed: max_iter reached above rtol, or a non-finite residual;
+ * FP64 with info: a non-finite residual; X holds the last iterate), ETIMEOUT (a bounded device-side wait of a sweep gave up; X is incomplete),
  * ECUDA. */
 helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
                        double rtol, int32_t max_iter, helm_solve_info *info);

@@ -43,7 +43,37 @@ extern "C" const char *helm_last_error(void) { return g_last_error.c_str(); }
 
 static std::atomic<int64_t> g_wait_tries{-1};
 
+// Host-side fault injection, read from the environment at every call that can take the path.
+// HELM_FAULT is a comma-separated list of: alloc (every device allocation of the library
+// fails: ENOMEM), pivot (helm_factor factors a copy of A's diagonal with its first entry set
+// to NaN from the host, so the factor kernels meet a non-finite pivot: ESINGULAR), timeout
+// (the bounded device waits take a try limit of zero and give up at the first wait that is not
+// already complete: ETIMEOUT), nan_rhs (helm_solve / helm_adjoint_solve work on a copy of B whose first entry is
+// NaN: the residual is not finite, ENOCONV).  Unknown words set HELM_FAULT_UNKNOWN.  Nothing
+// here faults, traps or hangs the device.
+uint32_t helm::fault_flags() {
+    const char *env = getenv("HELM_FAULT");
+    uint32_t f = 0;
+    if (!env) return 0;
+    const char *p = env;
+    while (*p) {
+        const char *q = p;
+        while (*q && *q != ',') ++q;
+        const size_t n = (size_t)(q - p);
+        if (n == 5 && !strncmp(p, "alloc", 5)) f |= HELM_FAULT_ALLOC;
+        else if (n == 5 && !strncmp(p, "pivot", 5)) f |= HELM_FAULT_PIVOT;
+        else if (n == 7 && !strncmp(p, "timeout", 7)) f |= HELM_FAULT_TIMEOUT;
+        else if (n == 7 && !strncmp(p, "nan_rhs", 7)) f |= HELM_FAULT_NAN_RHS;
+        else if (n > 0) f |= HELM_FAULT_UNKNOWN;
+        p = *q ? q + 1 : q;
+    }
+    return f;
+}
+
+extern "C" uint32_t helm_fault_mask(void) { return helm::fault_flags(); }
+
 uint32_t helm::wait_tries() {
+    if (fault_flags() & HELM_FAULT_TIMEOUT) return 0;
     const int64_t v = g_wait_tries.load(std::memory_order_relaxed);
     return v < 0 ? kDefaultWaitTries : (uint32_t)std::min<int64_t>(v, 0xffffffffLL);
 }
@@ -66,6 +96,10 @@ void keep_pool_memory() {
 helm_status dev_alloc(void **p, size_t bytes, const char *what, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) return HELM_OK;
+    if (fault_flags() & HELM_FAULT_ALLOC) {
+        helm_set_msg((std::string(what) + ": allocation refused (HELM_FAULT=alloc)").c_str());
+        return HELM_ENOMEM;
+    }
     keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, st);
     if (e != cudaSuccess) {
@@ -195,9 +229,39 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_fac
         helm_factor_destroy(f);
         return HELM_ECUDA;
     }
+    // HELM_FAULT=pivot: the factor kernels read a copy of the diagonal whose first entry the host
+    // set to NaN; op keeps its own diagonal (restored below, before anything else reads it)
+    double2 *diag_saved = nullptr, *diag_bad = nullptr;
+    if (fault_flags() & HELM_FAULT_PIVOT) {
+        const size_t nd = (size_t)op->n_omega * g.nx * g.nz;
+        const double2 bad = make_double2(NAN, 0.0);
+        if ((s = dev_alloc((void **)&diag_bad, nd * sizeof(double2), "allocate(diag copy)", op->st)) != HELM_OK) {
+            helm_factor_destroy(f);
+            return s;
+        }
+        e = cudaMemcpyAsync(diag_bad, op->diag, nd * sizeof(double2), cudaMemcpyDeviceToDevice, op->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(diag_bad, &bad, sizeof(bad), cudaMemcpyHostToDevice, op->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);   // the host value is on the stack
+        if (e != cudaSuccess) {
+            helm_set_error("helm_factor: inject a NaN pivot", e);
+            dev_free(diag_bad, op->st);
+            helm_factor_destroy(f);
+            return HELM_ECUDA;
+        }
+        diag_saved = op->diag;
+        op->diag = diag_bad;
+    }
+    auto restore_diag = [&]() {
+        if (diag_bad) {
+            op->diag = diag_saved;
+            dev_free(diag_bad, op->st);
+            diag_bad = nullptr;
+        }
+    };
     if (f->use_bcr) {
         if ((s = bcr_factor(f)) != HELM_OK) {
             cudaStreamSynchronize(op->st);
+            restore_diag();
             helm_factor_destroy(f);
             return s;
         }
@@ -206,6 +270,7 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_fac
         if ((s = dev_alloc(&f->G, gelems * esz, "allocate(factor)", op->st)) != HELM_OK ||
             (s = dev_alloc(&f->xch, (size_t)op->n_omega * factor_xch_elems(g.nz) * esz, "allocate(exchange)",
                            op->st)) != HELM_OK) {
+            restore_diag();
             helm_factor_destroy(f);
             return s;
         }
@@ -219,6 +284,7 @@ extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_fac
     int st_host[2] = {0, 0};   // status bits, pivot blocks inverted in FP64
     if (e == cudaSuccess) e = cudaMemcpyAsync(st_host, op->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, op->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);
+    restore_diag();
     f->fp64_blocks = st_host[1];
     if (e != cudaSuccess) {
         helm_set_error("helm_factor: launch", e);
@@ -314,8 +380,10 @@ helm_status max_relres(const helm_op *op, size_t cols, const double *norms_dev, 
     double mx = 0.0;
     for (size_t c = 0; c < cols; ++c) {
         const double rr = norms_host[2 * c], bb = norms_host[2 * c + 1];
-        const double rel = bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0);
-        if (!(rel <= mx)) mx = rel;  // propagates NaN
+        // a non-finite right-hand side (bb NaN or inf) or residual gives NaN: not converged
+        const double rel = (isnan(rr) || !isfinite(bb)) ? NAN : (bb > 0 ? sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0));
+        if (isnan(mx) || isnan(rel)) mx = NAN;   // a NaN column stays visible in the maximum
+        else if (rel > mx) mx = rel;
     }
     *out = mx;
     return HELM_OK;
@@ -434,6 +502,7 @@ helm_status solve_impl(helm_factor_t *f, int nrhs, const double2 *B, double2 *X,
             if (e == cudaSuccess) e = launch_residual(g, n_sys, nrhs, op->diag, B, X, nullptr, f->norms, conj, op->st);
             if (e != cudaSuccess) { helm_set_error("residual", e); return HELM_ECUDA; }
             if ((s = max_relres(op, cols, f->norms, f->norms_host.data(), &info->max_relres)) != HELM_OK) return s;
+            if (!isfinite(info->max_relres)) { helm_set_msg("non-finite residual"); return HELM_ENOCONV; }
         }
         return HELM_OK;
     }
@@ -457,11 +526,34 @@ static helm_status check_solve_args(const char *who, helm_factor_t *f, int32_t n
     return HELM_OK;
 }
 
+// solve_impl, or (HELM_FAULT=nan_rhs) solve_impl on a copy of B whose first entry is NaN
+static helm_status solve_entry(helm_factor_t *f, int nrhs, const double2 *B, double2 *X, double rtol, int max_iter,
+                               helm_solve_info *info, int conj) {
+    if (!(fault_flags() & HELM_FAULT_NAN_RHS)) return solve_impl(f, nrhs, B, X, rtol, max_iter, info, conj);
+    const helm_op *op = f->op;
+    const size_t n = (size_t)op->n_omega * nrhs * op->g.nx * op->g.nz;
+    const double2 bad = make_double2(NAN, 0.0);
+    double2 *Bc = nullptr;
+    helm_status s = dev_alloc((void **)&Bc, n * sizeof(double2), "allocate(rhs copy)", op->st);
+    if (s != HELM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(Bc, B, n * sizeof(double2), cudaMemcpyDeviceToDevice, op->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Bc, &bad, sizeof(bad), cudaMemcpyHostToDevice, op->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(op->st);   // the host value is on the stack
+    if (e != cudaSuccess) {
+        helm_set_error("solve: inject a NaN right-hand side", e);
+        dev_free(Bc, op->st);
+        return HELM_ECUDA;
+    }
+    s = solve_impl(f, nrhs, Bc, X, rtol, max_iter, info, conj);
+    dev_free(Bc, op->st);
+    return s;
+}
+
 extern "C" helm_status helm_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev, helm_c128 *X_dev,
                                   double rtol, int32_t max_iter, helm_solve_info *info) {
     helm_status s = check_solve_args("helm_solve", f, nrhs, B_dev, X_dev);
     if (s != HELM_OK || nrhs == 0) return s;
-    return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 0);
+    return solve_entry(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 0);
 }
 
 extern "C" helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const helm_c128 *B_dev,
@@ -469,7 +561,7 @@ extern "C" helm_status helm_adjoint_solve(helm_factor_t *f, int32_t nrhs, const 
                                           helm_solve_info *info) {
     helm_status s = check_solve_args("helm_adjoint_solve", f, nrhs, B_dev, X_dev);
     if (s != HELM_OK || nrhs == 0) return s;
-    return solve_impl(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 1);
+    return solve_entry(f, nrhs, (const double2 *)B_dev, (double2 *)X_dev, rtol, max_iter, info, 1);
 }
 
 // ------------------------------------------------------------ acquisition helpers

@@ -177,6 +177,7 @@ __device__ __forceinline__ void abort_drain() {
 // limit, so this is seconds at worst); helm_set_wait_tries overrides it for later launches
 constexpr uint32_t kDefaultWaitTries = 1u << 22;
 uint32_t wait_tries();   // host: the try count the next launches take
+uint32_t fault_flags();  // host: HELM_FAULT_* bits of the HELM_FAULT environment variable
 // asynchronous store into another CTA's shared memory that completes `bytes` of the
 // transaction count of the mbarrier at remote shared address `rbar`
 __device__ __forceinline__ void st_async(uint32_t raddr, float2 v, uint32_t rbar) {

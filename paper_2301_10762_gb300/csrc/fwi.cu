@@ -395,6 +395,11 @@ struct Ws {
         void *p = nullptr;
         if (*s != HELM_OK) return nullptr;
         if (n == 0) n = 1;
+        if (fault_flags() & HELM_FAULT_ALLOC) {
+            helm_set_msg("workspace: allocation refused (HELM_FAULT=alloc)");
+            *s = HELM_ENOMEM;
+            return nullptr;
+        }
         cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), st);
         if (e != cudaSuccess) {
             cudaGetLastError();

@@ -165,20 +165,25 @@ __device__ __forceinline__ cff iterate_at(const float4 *x, const float2 *d, size
     return {ff_add1(xv.re, dv.x), ff_add1(xv.im, dv.y)};
 }
 
+// maximum in which a NaN operand wins (a column with a non-finite residual must not be hidden)
+__device__ __forceinline__ double nan_max(double a, double b) { return (isnan(a) || isnan(b)) ? NAN : fmax(a, b); }
+
 // Stopping test of the pair phase, one block: rel = max over columns of sqrt(rr / bb) (bb = 0: 0 if
-// rr = 0 else inf); record it and decide; rr = 0 again for the next update.  The norms were
-// accumulated by atomics of other blocks, so they are read from L2.
+// rr = 0 else inf; a non-finite bb or rr: NaN, which stops the loop unconverged); record it and
+// decide; rr = 0 again for the next update.  The norms were accumulated by atomics of other
+// blocks, so they are read from L2.
 __device__ void refine_stop_test(int cols, double *norms, RefineStop stop, RefineState *st, double *sh) {
     double mx = 0.0;
     for (int c = threadIdx.x; c < cols; c += blockDim.x) {
         const double rr = __ldcg(norms + 2 * (size_t)c), bb = __ldcg(norms + 2 * (size_t)c + 1);
-        const double rel = bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0);
-        if (!(rel <= mx)) mx = rel;   // propagates NaN
+        // a non-finite right-hand side (bb NaN or inf) or residual gives NaN: not converged
+        const double rel = (isnan(rr) || !isfinite(bb)) ? NAN : (bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0));
+        mx = nan_max(mx, rel);
         norms[2 * (size_t)c] = 0.0;
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double v = __shfl_down_sync(0xffffffffu, mx, o);
-        if (!(v <= mx)) mx = v;
+        mx = nan_max(mx, v);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) sh[wid] = mx;
@@ -186,7 +191,7 @@ __device__ void refine_stop_test(int cols, double *norms, RefineStop stop, Refin
     if (threadIdx.x == 0) {
         double rel = 0.0;
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
-            if (!(sh[w] <= rel)) rel = sh[w];
+            rel = nan_max(rel, sh[w]);
         const int it = st->iters + 1;
         const double prev = it > 1 ? st->rel : INFINITY;
         st->iters = it;

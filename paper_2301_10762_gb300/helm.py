@@ -93,6 +93,7 @@ class helm_trace_entry(C.Structure):
 
 EXPORTED = ["helm_status_string", "helm_last_error", "helm_assemble", "helm_op_destroy", "helm_factor",
             "helm_factor_destroy", "helm_factor_fp64_blocks", "helm_factor_get_method", "helm_set_wait_tries",
+            "helm_fault_mask",
             # include/helm_blas.h
             "helm_zgemm_batched", "helm_zinv_batched", "helm_solve", "helm_adjoint_solve", "helm_solve_noalloc", "helm_sources",
             "helm_restrict", "helm_restrict_adjoint", "helm_field_grad",
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
     lib.helm_zinv_batched.argtypes = [i32, i32, vp, C.c_int64, i32, vp, C.c_int64, i32, vp]
     lib.helm_set_wait_tries.restype = None
     lib.helm_set_wait_tries.argtypes = [C.c_int64]
+    lib.helm_fault_mask.restype = C.c_uint32
+    lib.helm_fault_mask.argtypes = []
     lib.helm_factor_get_method.restype = i32
     lib.helm_factor_get_method.argtypes = [vp]
     lib.helm_factor_fp64_blocks.restype = i32
@@ -304,6 +307,16 @@ def helm_set_wait_tries(tries=-1):
     """Polls of a bounded device-side wait before it gives up, for later launches (< 0: the
     library default; 0: give up at the first wait that is not already complete)."""
     load().helm_set_wait_tries(int(tries))
+
+
+HELM_FAULT_ALLOC, HELM_FAULT_PIVOT, HELM_FAULT_TIMEOUT, HELM_FAULT_NAN_RHS = 0x1, 0x2, 0x4, 0x8
+HELM_FAULT_UNKNOWN = 0x80000000
+
+
+def helm_fault_mask():
+    """The HELM_FAULT_* bits that the HELM_FAULT environment variable selects now (host-side
+    fault injection for tests: alloc, pivot, timeout, nan_rhs)."""
+    return int(load().helm_fault_mask())
 
 
 HELM_FACTOR_AUTO, HELM_FACTOR_LINE, HELM_FACTOR_BCR = 0, 1, 2

@@ -111,6 +111,23 @@ def test_invalid_arguments_return_einval_with_a_message():
 
 
 @pytest.mark.skipif(not os.path.exists(LIB), reason="libhelm.so not built (run __graft_entry__.build())")
+def test_fault_injection_words_are_parsed(monkeypatch):
+    """HELM_FAULT (host-side fault injection) is read at every call: each word selects its bit,
+    unknown words set HELM_FAULT_UNKNOWN, an unset or empty variable selects nothing.  A host
+    function: no GPU needed."""
+    lib = ctypes.CDLL(LIB)
+    lib.helm_fault_mask.restype = ctypes.c_uint32
+    cases = {"": 0, "alloc": 0x1, "pivot": 0x2, "timeout": 0x4, "nan_rhs": 0x8, "alloc,nan_rhs": 0x9,
+             "pivot,timeout,alloc,nan_rhs": 0xF, "bogus": 0x80000000, "timeout,bogus,": 0x80000004,
+             "allocx": 0x80000000}
+    for value, bits in cases.items():
+        monkeypatch.setenv("HELM_FAULT", value)
+        assert lib.helm_fault_mask() == bits, value
+    monkeypatch.delenv("HELM_FAULT")
+    assert lib.helm_fault_mask() == 0
+
+
+@pytest.mark.skipif(not os.path.exists(LIB), reason="libhelm.so not built (run __graft_entry__.build())")
 def test_library_was_built_from_the_current_sources():
     """A build that failed after a source change leaves the previous libhelm.so behind, and the
     ABI checks above would then test stale code.  The build records a digest of the sources it

@@ -4,7 +4,9 @@ zero (helm_set_wait_tries), so that it gives up at once; the kernel then stops e
 cluster, drains, returns, and the call reports HELM_ETIMEOUT.  The context stays usable: the
 next call with the default limit gives the same result as before.  A model with a NaN value
 (a corrupted input copy) makes a pivot non-finite, which the factor reports as
-HELM_ESINGULAR."""
+HELM_ESINGULAR.  The host-side fault injection (HELM_FAULT=alloc|pivot|timeout|nan_rhs) drives
+ENOMEM, ESINGULAR, ETIMEOUT and ENOCONV through the library's own paths, and the calls after it
+are unaffected."""
 import numpy as np
 import pytest
 import torch
@@ -13,7 +15,7 @@ hm = pytest.importorskip("paper_2301_10762_gb300.helm")
 
 pytestmark = pytest.mark.gpu
 
-ETIMEOUT, ESINGULAR = 6, 5
+ENOMEM, ENOCONV, ESINGULAR, ETIMEOUT = 2, 4, 5, 6
 
 
 @pytest.fixture(autouse=True)
@@ -99,3 +101,78 @@ def test_non_finite_model_value_is_reported_as_esingular(prec):
     # a clean model on the same context still factors
     op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
     hm.helm_factor(op, prec).close()
+
+
+def test_fault_alloc_gives_enomem_and_nothing_sticks(monkeypatch):
+    nx, nz, nrhs = 48, 40, 3
+    m, om, B = _case(nx, nz, nrhs)
+    md = torch.tensor(m, device="cuda")
+    op = hm.helm_assemble(nx, nz, 1.0, 1.0, md, om)
+    f = hm.helm_factor(op, hm.HELM_MIXED)
+    ref, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    monkeypatch.setenv("HELM_FAULT", "alloc")
+    assert hm.helm_fault_mask() == hm.HELM_FAULT_ALLOC
+    for call in (lambda: hm.helm_assemble(nx, nz, 1.0, 1.0, md, om), lambda: hm.helm_factor(op, hm.HELM_FP64),
+                 lambda: hm.helm_factor(op, hm.HELM_MIXED, method=hm.HELM_FACTOR_BCR)):
+        with pytest.raises(hm.HelmError) as e:
+            call()
+        assert e.value.status == ENOMEM
+    monkeypatch.delenv("HELM_FAULT")
+    X, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    _same(X, ref, hm.HELM_MIXED)
+
+
+@pytest.mark.parametrize("prec,method", [(hm.HELM_FP64, hm.HELM_FACTOR_AUTO), (hm.HELM_MIXED, hm.HELM_FACTOR_LINE),
+                                         (hm.HELM_MIXED, hm.HELM_FACTOR_BCR)])
+def test_fault_pivot_gives_esingular_and_leaves_the_op_intact(monkeypatch, prec, method):
+    nx, nz, nrhs = 48, 40, 3
+    m, om, B = _case(nx, nz, nrhs)
+    op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
+    f0 = hm.helm_factor(op, prec, method=method)
+    ref, _ = hm.helm_solve(f0, B, rtol=1e-12, max_iter=10)
+    f0.close()
+    monkeypatch.setenv("HELM_FAULT", "pivot")
+    with pytest.raises(hm.HelmError) as e:
+        hm.helm_factor(op, prec, method=method)
+    assert e.value.status == ESINGULAR
+    monkeypatch.delenv("HELM_FAULT")
+    f = hm.helm_factor(op, prec, method=method)
+    X, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    _same(X, ref, prec)
+
+
+def test_fault_timeout_gives_etimeout(monkeypatch):
+    nx, nz, nrhs = 64, 64, 8
+    m, om, B = _case(nx, nz, nrhs)
+    op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
+    f = hm.helm_factor(op, hm.HELM_FP64)
+    ref, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    monkeypatch.setenv("HELM_FAULT", "timeout")
+    with pytest.raises(hm.HelmError) as e:
+        hm.helm_factor(op, hm.HELM_FP64)
+    assert e.value.status == ETIMEOUT
+    with pytest.raises(hm.HelmError) as e:
+        hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    assert e.value.status == ETIMEOUT
+    monkeypatch.delenv("HELM_FAULT")
+    X, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    _same(X, ref, hm.HELM_FP64)
+
+
+@pytest.mark.parametrize("prec", [hm.HELM_FP64, hm.HELM_MIXED])
+def test_fault_nan_rhs_gives_enoconv_and_leaves_b_intact(monkeypatch, prec):
+    nx, nz, nrhs = 48, 40, 3
+    m, om, B = _case(nx, nz, nrhs)
+    op = hm.helm_assemble(nx, nz, 1.0, 1.0, torch.tensor(m, device="cuda"), om)
+    f = hm.helm_factor(op, prec)
+    ref, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    B0 = B.clone()
+    monkeypatch.setenv("HELM_FAULT", "nan_rhs")
+    for solve in (hm.helm_solve, hm.helm_adjoint_solve):
+        with pytest.raises(hm.HelmError) as e:
+            solve(f, B, rtol=1e-12, max_iter=10)
+        assert e.value.status == ENOCONV
+    monkeypatch.delenv("HELM_FAULT")
+    assert torch.equal(B, B0)
+    X, _ = hm.helm_solve(f, B, rtol=1e-12, max_iter=10)
+    _same(X, ref, prec)

@@ -59,6 +59,29 @@ def test_mixed_256_workload_sampled_frequencies(method):
         assert _colerr(Xc[q][sel], fo.solve(E[sel])) <= 1e-8
 
 
+@pytest.mark.parametrize("prec,tol", [(hm.HELM_MIXED, 1e-8), (hm.HELM_FP64, 1e-9)])
+def test_512_grid_sampled_columns(prec, tol):
+    """The largest grid of the solve server's workload: 512 x 512 (262144 unknowns per
+    system), the mixed workload's medium at omega = 5 and 40 with its 64 top-row sources; the
+    mixed path takes block cyclic reduction (n_z = 512), the FP64 path the line factor with
+    its panels outside shared memory.  Four sampled columns against the oracle's sparse LU."""
+    w = W.config_mixed(512)
+    om = np.array([w.omegas[0], w.omegas[-1]])
+    g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+    op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), om)
+    f = hm.helm_factor(op, prec)
+    assert f.method == (hm.HELM_FACTOR_BCR if prec == hm.HELM_MIXED else hm.HELM_FACTOR_LINE)
+    B = hm.helm_sources(op, hm.Acq.from_workload(w.acq))
+    X, info = hm.helm_solve(f, B, rtol=BENCH_RTOL, max_iter=40)
+    assert info["max_relres"] <= BENCH_RTOL
+    sel = np.array([0, 21, 42, 63])
+    E = H.source_vectors(g, w.acq.src_xz[sel])
+    Xc = X[:, sel].cpu().numpy()
+    for q, o in enumerate(om):
+        fo = H.Factor(H.helmholtz_matrix(g, w.m, o))
+        assert _colerr(Xc[q], fo.solve(E)) <= tol
+
+
 @pytest.mark.parametrize("method,pin2,pin3", [(1, 2e-10, 1e-12), (2, 2e-8, 5e-12)])
 def test_mixed_factor_accuracy_sets_the_refinement_sweeps(method, pin2, pin3):
     """The complex-FP32 factor's accuracy sets the refinement sweeps of every solve.  On the
