@@ -370,7 +370,7 @@ def pcg(apply_H, rhs, apply_Minv, x0, rtol, maxiter):
 
 def hypergradient(grid: Grid, m_fwi, m_true, omegas, src_xz, rec_xz, alpha, alpha0, mu,
                   rec_w=None, src_amp=None, cg_rtol=1e-13, cg_maxiter=500, cg_fixed_iters=None,
-                  x0=None):
+                  x0=None, data_grid=None, m_true_data=None):
     """Upper-level derivatives for one training model (Algorithm alg:box, Theorems
     sogradt1 and sogradta), evaluated at the given m_fwi:
         rho solves H rho = m' - m_fwi by PCG with P2 = Gamma(alpha0, mu) (Eq. (P2)),
@@ -384,11 +384,21 @@ def hypergradient(grid: Grid, m_fwi, m_true, omegas, src_xz, rec_xz, alpha, alph
         psi = 1/2 ||m' - m_fwi||^2 (Eq. (SOobj) for one model).
     Reading of Eq. (gradALT1): the conjugated form that the proof of Theorem sogradt1
     yields with the paper's inner product (f, delta_r) = f(r).
+    data_grid, m_true_data: the training data u' computed on another grid of the same domain
+    (Appendix, data generation: u(m) and u(m') on different grids against the inverse crime),
+    with m' given on it; the data and their receiver derivatives are then that grid's:
+    R(u - u') reads R u - R_d u'_d and dR_l(u - u') reads dR_l u - dR_{d,l} u'_d.  m_true
+    stays the model on this grid (psi and the right-hand side of the rho system).
     Returns a dict (the 1/N_m' average over models is left to the caller)."""
     m_fwi = np.asarray(m_fwi, dtype=np.float64)
     R, Rx, Rz = restriction(grid, rec_xz)
     w = np.ones(R.shape[0]) if rec_w is None else np.asarray(rec_w, dtype=np.float64)
-    data, Ut = synthetic_data(grid, m_true, omegas, src_xz, rec_xz, src_amp)
+    if data_grid is None:
+        data, Ut = synthetic_data(grid, m_true, omegas, src_xz, rec_xz, src_amp)
+    else:   # receiver values d and dR_l u' of the data grid's wavefields
+        Rd, Rdx, Rdz = restriction(data_grid, rec_xz)
+        data, Ud = synthetic_data(data_grid, m_true_data, omegas, src_xz, rec_xz, src_amp)
+        dRd = [np.einsum("rn,wsn->wsr", Rl.toarray(), Ud) for Rl in (Rdx, Rdz)]
     phi, grad, fields = fwi_objective_gradient(grid, m_fwi, omegas, src_xz, rec_xz, data, alpha, mu,
                                                rec_w=w, src_amp=src_amp, return_fields=True)
     U = fields["U"]
@@ -406,10 +416,15 @@ def hypergradient(grid: Grid, m_fwi, m_true, omegas, src_xz, rec_xz, alpha, alph
     for q, om in enumerate(omegas):
         gk = g_vec(grid, m_fwi, om)
         T = fields["facs"][q].solve(gk[None, :] * U[q] * rho[None, :])
-        du = U[q] - Ut[q]                        # u - u'
-        Rt, Rdu = (R @ T.T).T, (R @ du.T).T      # [n_src, n_rec]
+        Rt = (R @ T.T).T                         # [n_src, n_rec]
+        if data_grid is None:
+            du = U[q] - Ut[q]                    # u - u'
+            Rdu = (R @ du.T).T
+        else:
+            Rdu = (R @ U[q].T).T - data[q]
         for l, Rl in enumerate((Rx, Rz)):
-            Rlt, Rldu = (Rl @ T.T).T, (Rl @ du.T).T
+            Rlt = (Rl @ T.T).T
+            Rldu = (Rl @ du.T).T if data_grid is None else (Rl @ U[q].T).T - dRd[l][q]
             dp[:, l] += (w ** 2) * np.sum(np.real(np.conj(Rlt) * Rdu + np.conj(Rt) * Rldu), axis=0)
         dw += -2.0 * w * np.sum(np.real(np.conj(Rt) * (-Rdu)), axis=0)
     return {

@@ -461,6 +461,57 @@ def test_hypergradient_implicit_function_check():
     assert abs(fd_w - hg["dpsi_dw"][j]) <= 1e-5 * abs(fd_w)
 
 
+def _fine_setup(nx=7, nz=6, fx=13, fz=11, seed=7):
+    """The tiny over-determined problem with a smooth m' known everywhere, so that it can be
+    sampled on the inversion grid and on a finer data grid of the same domain."""
+    w = W.tiny_case(nx, nz, seed=seed, n_omega=3, n_src=4, n_rec=12)
+    w.alpha, w.mu = 1e-4, 1e-4
+    fn = lambda X, Z: 1.0 / (1.2 + 0.8 * Z + 0.3 * np.sin(3.0 * X) * Z) ** 2
+    g, gd = H.Grid(nx, nz, w.lx, w.lz), H.Grid(fx, fz, w.lx, w.lz)
+    m = W.sample_on_grid(fn, nx, nz, w.lx, w.lz)
+    md = W.sample_on_grid(fn, fx, fz, w.lx, w.lz)
+    return w, g, gd, m, md
+
+
+def _psi_fine(w, g, gd, m, md, alpha, rec_xz):
+    data, _ = H.synthetic_data(gd, md, w.omegas, w.acq.src_xz, rec_xz)
+    m_fwi, gn = D.lower_level_newton(g, m, w.omegas, w.acq.src_xz, rec_xz, data, alpha, w.mu)
+    assert gn < 1e-10
+    return 0.5 * np.sum((m - m_fwi) ** 2), m_fwi
+
+
+def test_hypergradient_with_data_from_a_finer_grid_implicit_function_check():
+    """Training data computed on a finer grid (u(m') on 13 x 11 nodes, the inversion on 7 x 6):
+    dpsi/dalpha and dpsi/dp against central differences of psi, the lower level re-solved
+    with the finer grid's data at every perturbed design.  The data no longer fit exactly at
+    m_FWI, so the Hessian's second-order part and the data-grid receiver derivatives both
+    enter."""
+    w, g, gd, m, md = _fine_setup()
+    rec = w.acq.rec_xz.copy()
+    psi0, m_fwi = _psi_fine(w, g, gd, m, md, w.alpha, rec)
+    hg = H.hypergradient(g, m_fwi, m, w.omegas, w.acq.src_xz, rec, w.alpha, w.alpha, w.mu, cg_rtol=1e-14,
+                         data_grid=gd, m_true_data=md)
+    assert np.isclose(hg["psi"], psi0, rtol=1e-12)
+    da = 1e-3 * w.alpha
+    fd_a = (_psi_fine(w, g, gd, m, md, w.alpha + da, rec)[0] - _psi_fine(w, g, gd, m, md, w.alpha - da, rec)[0]) / (2 * da)
+    assert abs(fd_a - hg["dpsi_dalpha"]) <= 1e-5 * abs(fd_a)
+    for j, l in ((0, 0), (1, 1), (2, 0)):
+        dp = 1e-5
+        rp, rm = rec.copy(), rec.copy()
+        rp[j, l] += dp
+        rm[j, l] -= dp
+        fd_p = (_psi_fine(w, g, gd, m, md, w.alpha, rp)[0] - _psi_fine(w, g, gd, m, md, w.alpha, rm)[0]) / (2 * dp)
+        assert abs(fd_p - hg["dpsi_dp"][j, l]) <= 1e-5 * max(abs(fd_p), 1e-3 * np.abs(hg["dpsi_dp"]).max())
+    # the same-grid data through the data-grid branch reproduce the default branch
+    ref = H.hypergradient(g, m_fwi, m, w.omegas, w.acq.src_xz, rec, w.alpha, w.alpha, w.mu, cg_rtol=1e-14)
+    same = H.hypergradient(g, m_fwi, m, w.omegas, w.acq.src_xz, rec, w.alpha, w.alpha, w.mu, cg_rtol=1e-14,
+                           data_grid=g, m_true_data=m)
+    assert np.allclose(same["dpsi_dp"], ref["dpsi_dp"], rtol=1e-10, atol=1e-12 * np.abs(ref["dpsi_dp"]).max())
+    assert np.isclose(same["dpsi_dalpha"], ref["dpsi_dalpha"], rtol=1e-12)
+    # and the finer data are not the same-grid data: the terms differ
+    assert not np.allclose(hg["dpsi_dp"], ref["dpsi_dp"], rtol=1e-3)
+
+
 def test_unconjugated_gradALT1_fails_the_pin():
     """Eq. (gradALT1) as printed (no conjugates) disagrees with the differences of psi."""
     w, g = _hyper_setup(seed=8)
