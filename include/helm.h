@@ -305,9 +305,17 @@ helm_status fwi_hessian_vec(helm_factor_t *f, const helm_acq *acq, const helm_c1
  *   vectors of length nx*nz of that model's grid; each model's own sources, and receivers in
  *   the same number for all models, since dpsi_dp and dpsi_dw are per receiver); omega is
  *   shared by all models.
+ *   data_grids[n_models], m_data[n_models]: both NULL (the data u' = A(m')^{-1} e_s on the
+ *   model's grid, from m_true) or both given: the data computed on another grid of the same
+ *   domain (same lx, lz; the Appendix's data generation against the inverse crime), from m'
+ *   sampled on it (device, length nx*nz of that grid); then d = R' u' and the receiver
+ *   derivatives dR'_l u' are that grid's and R(u - u') above reads R u - R' u' (likewise for
+ *   dR_l).  m_true stays the model on the inversion grid (psi and the rho system).
  *   Outputs are host scalars / arrays (the call synchronises).  dpsi_dw may be NULL. */
 helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grids, const double *const *m_fwi,
                               const double *const *m_true, const helm_acq *acq /* [n_models] */,
+                              const helm_grid *data_grids /* [n_models] or NULL */,
+                              const double *const *m_data /* [n_models] or NULL */,
                               const double *omega, int32_t n_omega, double alpha, double alpha0,
                               double mu, helm_prec prec, const helm_pcg_opts *pcg, void *stream,
                               double *psi, double *dpsi_dalpha, double *dpsi_dp, double *dpsi_dw,

@@ -129,10 +129,13 @@ class GpuBilevelProblem:
     guess shared by all models; src_xz: [n_src][2]; alpha0, mu: P2 = Gamma(alpha0, mu) and the
     Tikhonov mu; prec: factor precision of every solve.  cg_rtol: the PCG tolerance for rho; the
     paper's 1e-15 lies below what FP64 PCG reaches on an ill-conditioned Hessian (the library then
-    reports non-convergence), so the default is 1e-13."""
+    reports non-convergence), so the default is 1e-13.  train_data_models: None (training data
+    from m_true on the inversion grid), or per training model (nx_d, nz_d, m_d): the data computed
+    from m_d on an nx_d x nz_d grid of the same domain, in the lower level and in the
+    hypergradient alike (the Appendix generates u(m') on another grid than u(m))."""
 
     def __init__(self, nx, nz, lx, lz, m_true, m0, src_xz, rec_x, alpha0, mu, prec=None, refine_rtol=1e-10,
-                 lower_gtol=1e-10, lower_max_iter=500, cg_rtol=1e-13, cg_max_iter=500):
+                 lower_gtol=1e-10, lower_max_iter=500, cg_rtol=1e-13, cg_max_iter=500, train_data_models=None):
         import torch
 
         from . import helm as hm
@@ -146,6 +149,13 @@ class GpuBilevelProblem:
         self.prec = hm.HELM_MIXED if prec is None else prec
         self.refine_rtol, self.lower_gtol, self.lower_max_iter = refine_rtol, lower_gtol, lower_max_iter
         self.cg_rtol, self.cg_max_iter = cg_rtol, cg_max_iter
+        self.train_data = None
+        if train_data_models is not None:
+            if len(train_data_models) != len(m_true):
+                raise ValueError("one data model per training model")
+            self.train_data = [((int(a), int(b), float(lx), float(lz)),
+                                torch.tensor(np.asarray(md, dtype=np.float64), device="cuda"))
+                               for (a, b, md) in train_data_models]
         self.evaluations = 0
 
     def acquisition(self, z):
@@ -210,15 +220,23 @@ class GpuBilevelProblem:
         m_fwi = []
         for k, mt in enumerate(self.m_true):
             prob = HelmholtzProblem(*self.grid, omegas, acq=acq, prec=self.prec, rtol=self.refine_rtol)
-            res = fwi_lower_level(prob, self.data(omegas, acq, mt), alpha, self.mu, self.warm[k],
+            if self.train_data is None:
+                d = self.data(omegas, acq, mt)
+            else:
+                dg, md = self.train_data[k]
+                d = self.data(omegas, acq, md, grid=dg[:2])
+            res = fwi_lower_level(prob, d, alpha, self.mu, self.warm[k],
                                   gtol=self.lower_gtol, max_iter=self.lower_max_iter)
             if not res["converged"]:
                 raise RuntimeError(f"lower level of model {k} stopped at ||grad phi|| = {res['gnorm']:.3e} "
                                    f"({res['message']})")
             self.warm[k] = res["x"]
             m_fwi.append(torch.tensor(res["x"], device="cuda"))
+        dgs = None if self.train_data is None else [dg for dg, _ in self.train_data]
+        mds = None if self.train_data is None else [md for _, md in self.train_data]
         out = hm.bilevel_hypergrad([self.grid] * len(self.m_true), m_fwi, self.m_true, acq, omegas, alpha,
                                    self.alpha0, self.mu, prec=self.prec, cg_rtol=self.cg_rtol,
-                                   cg_max_iter=self.cg_max_iter, refine_rtol=self.refine_rtol)
+                                   cg_max_iter=self.cg_max_iter, refine_rtol=self.refine_rtol,
+                                   data_grids=dgs, m_data=mds)
         self.evaluations += 1
         return out["psi"], out["dpsi_dp"][:, 1].copy(), out["dpsi_dalpha"]

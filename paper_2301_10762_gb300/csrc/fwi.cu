@@ -234,27 +234,34 @@ __global__ void hess_finish_kernel(GridGeom g, int n_chunks, const double *part,
 // Hypergradient receiver terms for one model, accumulated into dp[r][2], dw[r]:
 //   dp_{r,l} += w_r^2 Re[conj(dR_l tau) R(u - u') + conj(R tau) dR_l(u - u')],
 //   dw_r    += -2 w_r Re[conj(R tau) R(u' - u)],
+// with R(u - u') = R u - d and dR_l(u - u') = dR_l u - d_l, where d = R' u', d_l = dR'_l u' are
+// the data and their receiver derivatives on the data's own grid (R' its restriction; the
+// model's grid when the data come from it);
 // scaled by inv_models; block per receiver, threads over (w, s) columns, fixed order.
 __global__ void hyper_terms_kernel(int N, int n_cols, int n_rec, const int *idx, const double *tw,
                                    const double *twx, const double *twz, const double *rec_w, const double2 *T,
-                                   const double2 *U, const double2 *Ut, double inv_models, double *dp, double *dw) {
+                                   const double2 *U, const double2 *d, const double2 *dx, const double2 *dz,
+                                   double inv_models, double *dp, double *dw) {
     __shared__ double sh[32];
     const int r = blockIdx.x;
     double ax = 0.0, az = 0.0, aw = 0.0;
     for (int col = threadIdx.x; col < n_cols; col += blockDim.x) {
-        double2 Rt = make_double2(0, 0), Rxt = Rt, Rzt = Rt, Rd = Rt, Rxd = Rt, Rzd = Rt;
+        double2 Rt = make_double2(0, 0), Rxt = Rt, Rzt = Rt, Ru = Rt, Rxu = Rt, Rzu = Rt;
         for (int t = 0; t < 16; ++t) {
             const int ti = r * 16 + t;
             const size_t o = (size_t)col * N + idx[ti];
-            const double2 tv = T[o];
-            const double2 dv = make_double2(U[o].x - Ut[o].x, U[o].y - Ut[o].y);
+            const double2 tv = T[o], uv = U[o];
             Rt.x += tw[ti] * tv.x;   Rt.y += tw[ti] * tv.y;
             Rxt.x += twx[ti] * tv.x; Rxt.y += twx[ti] * tv.y;
             Rzt.x += twz[ti] * tv.x; Rzt.y += twz[ti] * tv.y;
-            Rd.x += tw[ti] * dv.x;   Rd.y += tw[ti] * dv.y;
-            Rxd.x += twx[ti] * dv.x; Rxd.y += twx[ti] * dv.y;
-            Rzd.x += twz[ti] * dv.x; Rzd.y += twz[ti] * dv.y;
+            Ru.x += tw[ti] * uv.x;   Ru.y += tw[ti] * uv.y;
+            Rxu.x += twx[ti] * uv.x; Rxu.y += twx[ti] * uv.y;
+            Rzu.x += twz[ti] * uv.x; Rzu.y += twz[ti] * uv.y;
         }
+        const size_t q = (size_t)col * n_rec + r;
+        const double2 Rd = make_double2(Ru.x - d[q].x, Ru.y - d[q].y);      // R(u - u')
+        const double2 Rxd = make_double2(Rxu.x - dx[q].x, Rxu.y - dx[q].y);  // dR_x(u - u')
+        const double2 Rzd = make_double2(Rzu.x - dz[q].x, Rzu.y - dz[q].y);  // dR_z(u - u')
         ax += (Rxt.x * Rd.x + Rxt.y * Rd.y) + (Rt.x * Rxd.x + Rt.y * Rxd.y);
         az += (Rzt.x * Rd.x + Rzt.y * Rd.y) + (Rt.x * Rzd.x + Rt.y * Rzd.y);
         aw += Rt.x * Rd.x + Rt.y * Rd.y;   // Re[conj(R tau) R(u - u')]
@@ -761,14 +768,16 @@ struct ModelState {
 };
 
 // one training model: accumulate psi, dpsi/dalpha, dp, dw (device, scaled by 1/n_models)
-helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const double *m_true, const helm_acq *acq,
+helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const double *m_true,
+                            const helm_grid *data_grid, const double *m_data, const helm_acq *acq,
                             const double *omega, int n_omega, double alpha, double alpha0, double mu,
                             helm_prec prec, const helm_pcg_opts *po, cudaStream_t st, double inv_models,
                             double *acc_dev /*[2]: psi, dalpha*/, double *dp_dev, double *dw_dev,
                             helm_hyper_info *info) {
-    // the data branch (A(m') assembled, factored, u' = A(m')^{-1} e_s, d = R u') runs on
-    // its own stream from a second host thread, concurrently with A(m_fwi) and u; the stream
-    // outlives the handles allocated on it (declared first, destroyed last)
+    // the data branch (A(m') assembled on the data's grid, factored, u' = A(m')^{-1} e_s, the
+    // data d = R' u' and their receiver derivatives dR'_x u', dR'_z u') runs on its own stream
+    // from a second host thread, concurrently with A(m_fwi) and u; the stream outlives the
+    // handles allocated on it (declared first, destroyed last)
     const helm_factor_opts fopts{po->factor_method};
     cudaStream_t st2 = nullptr;
     HK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
@@ -781,24 +790,28 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     int max_it = 0, max_it2 = 0;
     DevAcq da2;
     struct AcqGuard2 { DevAcq *d; ~AcqGuard2() { acq_free(d); } } ag2{&da2};
-    double2 *Ut = nullptr, *dtmp = nullptr;
+    double2 *dtmp = nullptr, *ddx = nullptr, *ddz = nullptr;
     helm_status s2 = HELM_OK;
     std::string msg2;   // error text of the data branch (set in its own thread)
     std::thread data_branch([&]() {
         auto run = [&]() {
-            s2 = helm_assemble(grid, m_true, omega, n_omega, st2, &ms.op_t);
+            s2 = helm_assemble(data_grid, m_data, omega, n_omega, st2, &ms.op_t);
             if (s2 == HELM_OK) s2 = helm_factor(ms.op_t, prec, &fopts, &ms.fac_t);
             if (s2 == HELM_OK) s2 = acq_upload(ms.op_t, acq, &da2);
             if (s2 != HELM_OK) return;
             const GridGeom &gt = ms.op_t->g;
             const size_t ct = (size_t)n_omega * da2.n_src;
             double2 *Et = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
-            Ut = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
+            double2 *Ut = ws2.get<double2>(ct * gt.nx * gt.nz, &s2);
             dtmp = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
+            ddx = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
+            ddz = ws2.get<double2>(ct * std::max(1, da2.n_rec), &s2);
             if (s2 != HELM_OK) return;
             s2 = forward_fields(ms.fac_t, da2, po->refine_rtol, Et, Ut, &dcount, &max_it2);
             if (s2 != HELM_OK) return;
             cudaError_t e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_w, Ut, dtmp, st2);
+            if (e == cudaSuccess) e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_wx, Ut, ddx, st2);
+            if (e == cudaSuccess) e = launch_restrict(gt, (int)ct, da2.n_rec, da2.tap_idx, da2.tap_wz, Ut, ddz, st2);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st2);
             if (e != cudaSuccess) { helm_set_error("data branch", e); s2 = HELM_ECUDA; }
         };
@@ -910,7 +923,7 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
     HL();
     HS(run_solve(ms.fac_f, ns, E, V, rtol, 0, &count, &max_it));
     HELM_TRACED(K_HYPER, st, (hyper_terms_kernel<<<nr, 256, 0, st>>>(N, (int)cols, nr, da.tap_idx, da.tap_w, da.tap_wx, da.tap_wz, da.rec_w,
-                                           V, U, Ut, inv_models, dp_dev, dw_dev)));
+                                           V, U, dtmp, ddx, ddz, inv_models, dp_dev, dw_dev)));
     HL();
     // dpsi/dalpha += m_fwi^T R rho / n_models ; psi += ||m' - m_fwi||^2 / (2 n_models)
     HELM_TRACED(K_REGR, st, (regR_kernel<<<nblk(N), 256, 0, st>>>(g, x, zz)));
@@ -942,15 +955,23 @@ helm_status hyper_one_model(const helm_grid *grid, const double *m_fwi, const do
 }  // namespace
 
 extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grids, const double *const *m_fwi,
-                                         const double *const *m_true, const helm_acq *acq, const double *omega,
-                                         int32_t n_omega, double alpha, double alpha0, double mu, helm_prec prec,
-                                         const helm_pcg_opts *pcg, void *stream, double *psi, double *dpsi_dalpha,
-                                         double *dpsi_dp, double *dpsi_dw, helm_hyper_info *info) {
+                                         const double *const *m_true, const helm_acq *acq,
+                                         const helm_grid *data_grids, const double *const *m_data,
+                                         const double *omega, int32_t n_omega, double alpha, double alpha0,
+                                         double mu, helm_prec prec, const helm_pcg_opts *pcg, void *stream,
+                                         double *psi, double *dpsi_dalpha, double *dpsi_dp, double *dpsi_dw,
+                                         helm_hyper_info *info) {
     if (n_models < 1 || !grids || !m_fwi || !m_true || !acq || !omega || n_omega < 1 || !psi || !dpsi_dalpha ||
-        !dpsi_dp || acq[0].n_rec < 1) {
+        !dpsi_dp || acq[0].n_rec < 1 || (!data_grids) != (!m_data)) {
         helm_set_msg("bilevel_hypergrad: bad arguments");
         return HELM_EINVAL;
     }
+    // data from another grid: of the same domain (the sources and receivers are physical points)
+    for (int k = 0; data_grids && k < n_models; ++k)
+        if (!m_data[k] || data_grids[k].lx != grids[k].lx || data_grids[k].lz != grids[k].lz) {
+            helm_set_msg("bilevel_hypergrad: a data grid must cover its model's domain (same lx, lz)");
+            return HELM_EINVAL;
+        }
     // one acquisition per model: its own sources, the same receivers (the design P)
     for (int k = 0; k < n_models; ++k)
         if (acq[k].n_src < 1 || acq[k].n_rec != acq[0].n_rec) {
@@ -1008,8 +1029,9 @@ extern "C" helm_status bilevel_hypergrad(int32_t n_models, const helm_grid *grid
                 if (s == HELM_OK && e == cudaSuccess) e = cudaMemsetAsync(dw, 0, nr * sizeof(double), sw);
                 if (e != cudaSuccess) { helm_set_error("bilevel_hypergrad", e); s = HELM_ECUDA; }
                 if (s == HELM_OK)
-                    s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], &acq[k], omega, n_omega, alpha, alpha0, mu, prec,
-                                        &po, sw, 1.0 / n_models, acc, dp, dw, &infos[k]);
+                    s = hyper_one_model(&grids[k], m_fwi[k], m_true[k], data_grids ? &data_grids[k] : &grids[k],
+                                        data_grids ? m_data[k] : m_true[k], &acq[k], omega, n_omega, alpha, alpha0,
+                                        mu, prec, &po, sw, 1.0 / n_models, acc, dp, dw, &infos[k]);
                 if (s == HELM_OK || s == HELM_ENOCONV) {
                     e = cudaMemcpyAsync(&acc_h[2 * (size_t)k], acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, sw);
                     if (e == cudaSuccess)

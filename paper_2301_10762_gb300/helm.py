@@ -164,7 +164,7 @@ def load(path: str = LIB_PATH):
     lib.helm_gamma_solve.restype = C.c_int
     lib.helm_gamma_solve.argtypes = [P(helm_grid), dbl, dbl, i32, vp, vp, vp]
     lib.bilevel_hypergrad.restype = C.c_int
-    lib.bilevel_hypergrad.argtypes = [i32, P(helm_grid), P(vp), P(vp), P(helm_acq), P(dbl), i32, dbl, dbl,
+    lib.bilevel_hypergrad.argtypes = [i32, P(helm_grid), P(vp), P(vp), P(helm_acq), P(helm_grid), P(vp), P(dbl), i32, dbl, dbl,
                                       dbl, C.c_int, P(helm_pcg_opts), vp, P(dbl), P(dbl), P(dbl), P(dbl),
                                       P(helm_hyper_info)]
     lib.helm_trace_enable.restype = None
@@ -493,9 +493,11 @@ def helm_gamma_solve(nx, nz, alpha0, mu, R: torch.Tensor, Z: torch.Tensor | None
 
 def bilevel_hypergrad(grids, m_fwi, m_true, acq, omegas, alpha, alpha0, mu, prec=HELM_FP64,
                       cg_rtol=1e-13, cg_max_iter=500, cg_fixed_iters=0, x0=1.0, refine_rtol=1e-10,
-                      stream=None, concurrent_models=0, factor_method=0):
+                      stream=None, concurrent_models=0, factor_method=0, data_grids=None, m_data=None):
     """grids: list of (nx, nz, lx, lz); m_fwi, m_true: lists of CUDA float64 tensors; acq: one
-    Acq for every model, or a list with one per model (the same number of receivers)."""
+    Acq for every model, or a list with one per model (the same number of receivers).
+    data_grids, m_data: None, or per model the (nx, nz, lx, lz) of another grid of the same
+    domain and m' sampled on it, from which the training data are computed."""
     lib = load()
     n = len(grids)
     acqs = list(acq) if isinstance(acq, (list, tuple)) else [acq] * n
@@ -507,13 +509,22 @@ def bilevel_hypergrad(grids, m_fwi, m_true, acq, omegas, alpha, alpha0, mu, prec
     pf = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_fwi", (g[0] * g[1],)).value for t, g in zip(m_fwi, grids)])
     pt = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_true", (g[0] * g[1],)).value for t, g in zip(m_true, grids)])
     om, p_om = _dbuf(np.atleast_1d(omegas))
+    if (data_grids is None) != (m_data is None):
+        raise ValueError("data_grids and m_data go together")
+    DG = pd = None
+    if data_grids is not None:
+        if len(data_grids) != n or len(m_data) != n:
+            raise ValueError("one data grid and one m' per model")
+        DG = (helm_grid * n)(*[helm_grid(*g) for g in data_grids])
+        pd = (C.c_void_p * n)(*[_dev(t, torch.float64, "m_data", (g[0] * g[1],)).value
+                                for t, g in zip(m_data, data_grids)])
     opts = helm_pcg_opts(int(cg_max_iter), int(cg_fixed_iters), float(cg_rtol), float(x0), float(refine_rtol),
                          int(concurrent_models), int(factor_method))
     psi, dalpha = C.c_double(), C.c_double()
     dp = np.zeros((acq.n_rec, 2))
     dw = np.zeros(acq.n_rec)
     info = helm_hyper_info()
-    _check(lib.bilevel_hypergrad(n, G, pf, pt, A, p_om, len(om), float(alpha), float(alpha0),
+    _check(lib.bilevel_hypergrad(n, G, pf, pt, A, DG, pd, p_om, len(om), float(alpha), float(alpha0),
                                  float(mu), int(prec), C.byref(opts), _stream_ptr(stream), C.byref(psi),
                                  C.byref(dalpha), dp.ctypes.data_as(C.POINTER(C.c_double)),
                                  dw.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bilevel_hypergrad")

@@ -91,8 +91,8 @@ def test_invalid_arguments_return_einval_with_a_message():
                                                        None),
         "fwi_hessian_vec": lambda: lib.fwi_hessian_vec(None, None, None, None, None, d(0), d(0), d(1e-10), 0, None),
         "helm_gamma_solve": lambda: lib.helm_gamma_solve(None, d(1e-3), d(1e-6), 1, None, None, None),
-        "bilevel_hypergrad": lambda: lib.bilevel_hypergrad(0, None, None, None, None, None, 0, d(0), d(0), d(0), 0,
-                                                           None, None, None, None, None, None, None),
+        "bilevel_hypergrad": lambda: lib.bilevel_hypergrad(0, None, None, None, None, None, None, None, 0, d(0), d(0),
+                                                           d(0), 0, None, None, None, None, None, None, None),
         "helm_zgemm_batched": lambda: lib.helm_zgemm_batched(1, 0, 1, 2, None, ctypes.c_int64(0), 2, None,
                                                              ctypes.c_int64(0), 2, ctypes.c_float(1.0), None, None,
                                                              ctypes.c_int64(0), 1, None),
