@@ -532,6 +532,37 @@ def hypergrad_batch(hm, torch, n_cg=20, concurrent=4):
             "max_refine_iters": out["max_refine_iters"]}
 
 
+def hypergrad_lower(hm, torch, n_models=2, n_cg=20):
+    """The uneven set fed with true lower-level solutions: L-BFGS (Section 4, Wolfe line
+    search) to ||grad phi|| <= 1e-10 on the first n_models models (96^2, 128^2), every phi /
+    grad phi evaluation on the GPU (mixed, refined to 1e-12); then the hypergradient at those
+    m_FWI (N_CG fixed).  Times the lower level (its evaluations are the method's dominant
+    cost at this stage) and the hypergradient pass."""
+    import workloads as W
+    from paper_2301_10762_gb300 import bilevel as B
+    ms = W.config_hypergrad()[:n_models]
+    res = B.lower_level_set(ms)
+    w0 = ms[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = hm.bilevel_hypergrad([(w.nx, w.nz, w.lx, w.lz) for w in ms], [torch.tensor(r["x"], device="cuda") for r in res],
+                               [torch.tensor(w.m_true, device="cuda") for w in ms],
+                               [hm.Acq.from_workload(w.acq) for w in ms], w0.omegas, w0.alpha, w0.alpha, w0.mu,
+                               prec=hm.HELM_MIXED, cg_fixed_iters=n_cg, refine_rtol=REFINE_RTOL)
+    e1.record()
+    e1.synchronize()
+    # one phi / grad phi evaluation: the forward and the adjoint solve of every (omega, source)
+    lower_solves = sum(r["evals"] * 2 * len(w.omegas) * w.acq.n_src for w, r in zip(ms, res))
+    lower_s = sum(r["seconds"] for r in res)
+    return {"workload": f"hypergrad_lower: models 0..{n_models - 1} of the uneven set ({', '.join(f'{w.nx}^2' for w in ms)}), "
+                        f"L-BFGS to ||grad phi|| <= 1e-10 from the smoothed model, then N_CG={n_cg}",
+            "lower_level": [{"n": w.nx, "iters": r["iters"], "evals": r["evals"], "gnorm": r["gnorm"],
+                             "seconds": r["seconds"]} for w, r in zip(ms, res)],
+            "lower_rhs_solves_per_s": lower_solves / lower_s, "lower_seconds": lower_s,
+            "hypergrad_seconds": e0.elapsed_time(e1) / 1e3, "unit": UNIT,
+            "dpsi_dalpha": out["dpsi_dalpha"]}
+
+
 # ------------------------------------------------------------------------ main
 
 def main():
@@ -750,6 +781,10 @@ def main():
             extras["hypergrad_batch"] = hypergrad_batch(hm, torch)
         except Exception as e:  # keep the main line if the batch fails
             extras["hypergrad_batch"] = {"failed": str(e)[:300]}
+        try:
+            extras["hypergrad_lower"] = hypergrad_lower(hm, torch)
+        except Exception as e:  # keep the main line if the lower level fails
+            extras["hypergrad_lower"] = {"failed": str(e)[:300]}
         try:
             extras["mixed_512"] = grid512_step(hm, torch)
         except Exception as e:  # keep the main line if the large grid fails

@@ -122,6 +122,42 @@ def run_protocol(problem, z0, alpha0, groups, z_bounds, m_tests, m0, alpha_bound
             "test_mre": (list(mre_init), list(mre_opt))}
 
 
+def lower_level_set(models, prec=None, refine_rtol=1e-12, gtol=1e-10, max_iter=5000, memory=10):
+    """m_FWI of the lower level (Section 4's L-BFGS to ||grad phi||_2 <= gtol) for a set of
+    training models, e.g. the uneven-grid set of workloads.config_hypergrad: each entry has
+    nx, nz, lx, lz, omegas, acq (workloads.Acquisition), m (the initial guess), m_true, alpha,
+    mu.  The data d = R u(m') come from FP64 factors of A(m'); every phi / grad phi evaluation
+    of the lower level is the library's (mixed by default, refined to refine_rtol, so that the
+    gradient stays accurate well below gtol).  Returns one dict per model: x (m_FWI, host),
+    gnorm, iters, evals, seconds, message."""
+    import time
+
+    import torch
+
+    from . import helm as hm
+    from .autograd import HelmholtzProblem
+    from .lbfgs import fwi_lower_level
+    prec = hm.HELM_MIXED if prec is None else prec
+    out = []
+    for w in models:
+        acq = hm.Acq.from_workload(w.acq)
+        op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m_true, device="cuda"), w.omegas)
+        f = hm.helm_factor(op, hm.HELM_FP64)
+        U, _ = hm.helm_solve(f, hm.helm_sources(op, acq), rtol=refine_rtol, max_iter=40)
+        d = hm.helm_restrict(op, acq, U)
+        f.close()
+        op.close()
+        prob = HelmholtzProblem(w.nx, w.nz, w.lx, w.lz, w.omegas, acq=acq, prec=prec, rtol=refine_rtol, max_iter=40)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fwi_lower_level(prob, d, w.alpha, w.mu, np.asarray(w.m, dtype=np.float64), gtol=gtol,
+                              max_iter=max_iter, memory=memory)
+        torch.cuda.synchronize()
+        res["seconds"] = time.perf_counter() - t0
+        out.append(res)
+    return out
+
+
 class GpuBilevelProblem:
     """Training models on one grid, fixed sources, receivers in a vertical borehole x = rec_x.
 

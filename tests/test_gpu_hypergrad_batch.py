@@ -44,3 +44,43 @@ def test_uneven_models_hypergradient_matches_oracle(two_models_oracle, prec, tol
     for k in ("dpsi_dp", "dpsi_dw"):
         err = np.linalg.norm(out[k] - ref[k]) / np.linalg.norm(ref[k])
         assert err <= tol, (k, err)
+
+
+@pytest.fixture(scope="module")
+def two_models_lower_level():
+    """The first two models' lower-level solutions: L-BFGS from the smoothed stand-in to
+    ||grad phi|| <= 1e-10 on the GPU (mixed factors, refinement to 1e-12)."""
+    from paper_2301_10762_gb300 import bilevel as B
+    ms = W.config_hypergrad()[:2]
+    return ms, B.lower_level_set(ms)
+
+
+def test_lower_level_solutions_feed_the_hypergradient(two_models_lower_level):
+    """Section 4's stopping rule on the uneven set: the L-BFGS iterates satisfy it on the
+    oracle's own gradient too, and the hypergradient at those m_FWI (converged PCG) matches the
+    oracle's at 1e-8 (mixed path)."""
+    ms, res = two_models_lower_level
+    ref = {"psi": 0.0, "dpsi_dalpha": 0.0, "dpsi_dp": 0.0, "dpsi_dw": 0.0}
+    for w, r in zip(ms, res):
+        assert r["converged"] and r["gnorm"] <= 1e-10
+        g = H.Grid(w.nx, w.nz, w.lx, w.lz)
+        data, _ = H.synthetic_data(g, w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz)
+        _, grad = H.fwi_objective_gradient(g, r["x"], w.omegas, w.acq.src_xz, w.acq.rec_xz, data, w.alpha, w.mu,
+                                           rec_w=w.acq.rec_w)
+        assert np.linalg.norm(grad) <= 2e-10
+        o = H.hypergradient(g, r["x"], w.m_true, w.omegas, w.acq.src_xz, w.acq.rec_xz, w.alpha, w.alpha, w.mu,
+                            rec_w=w.acq.rec_w, cg_rtol=1e-12, cg_maxiter=600)
+        assert o["cg_relres"] <= 1e-12
+        for k in ref:
+            ref[k] = ref[k] + o[k] / len(ms)
+    w0 = ms[0]
+    out = hm.bilevel_hypergrad([(w.nx, w.nz, w.lx, w.lz) for w in ms], [torch.tensor(r["x"], device="cuda") for r in res],
+                               [torch.tensor(w.m_true, device="cuda") for w in ms],
+                               [hm.Acq.from_workload(w.acq) for w in ms], w0.omegas, w0.alpha, w0.alpha, w0.mu,
+                               prec=hm.HELM_MIXED, cg_rtol=1e-12, cg_max_iter=600, refine_rtol=1e-10)
+    assert out["cg_relres"] <= 1e-12
+    assert abs(out["psi"] - ref["psi"]) <= 1e-12 * abs(ref["psi"])
+    assert abs(out["dpsi_dalpha"] - ref["dpsi_dalpha"]) <= 1e-8 * abs(ref["dpsi_dalpha"])
+    for k in ("dpsi_dp", "dpsi_dw"):
+        err = np.linalg.norm(out[k] - ref[k]) / np.linalg.norm(ref[k])
+        assert err <= 1e-8, (k, err)
