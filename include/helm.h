@@ -50,8 +50,19 @@ typedef enum {
 
 typedef struct { double re, im; } helm_c128;
 
-/* Uniform grid: nx x nz nodes (both >= 4) on [0, lx] x [0, lz]. */
-typedef struct { int32_t nx, nz; double lx, lz; } helm_grid;
+/* Uniform grid: nx x nz nodes (both >= 4) on [0, lx] x [0, lz].  lumping: the nodal quadrature
+ * of the mass term (Appendix "Numerical forward model"; the paper does not fix how the corner
+ * nodes of its triangulation are weighted): HELM_LUMP_TENSOR (0, the default of a
+ * zero-initialised struct) the tensor trapezoid hx hz q(i) q(j), q = 1/2 at the ends (every
+ * corner hx hz / 4); HELM_LUMP_UP / HELM_LUMP_DOWN (1 / 2) the vertex quadrature of the P1
+ * triangles cut along (i,j)-(i+1,j+1) / (i+1,j)-(i,j+1), a third of each triangle's area to each
+ * vertex: the same weights except at the four corners (hx hz / 3 where the diagonal ends,
+ * hx hz / 6 at the other two).  The stiffness of these right triangles does not depend on the
+ * orientation. */
+typedef struct { int32_t nx, nz; double lx, lz; int32_t lumping; } helm_grid;
+#define HELM_LUMP_TENSOR 0
+#define HELM_LUMP_UP 1
+#define HELM_LUMP_DOWN 2
 
 /* Precision of the line factors.  HELM_FP64: complex FP64 factors and sweeps.
  * HELM_MIXED: complex FP32 factors and sweeps, FP64 residuals and FP64 iterative

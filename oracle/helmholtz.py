@@ -86,16 +86,35 @@ def stiffness(nx, nz, lx, lz, diagonal="up"):
     return S
 
 
-def lumped_mass(nx, nz, lx, lz):
+def lumped_mass(nx, nz, lx, lz, lumping="tensor"):
     """d_k of M(m) = diag(d_k m_k) (Appendix 'Numerical forward model', nodal quadrature).
-    Reading: the orientation-free tensor trapezoid weights d = hx hz qx(i) qz(j), q = 1/2
-    at end nodes and 1 otherwise (interior hx hz, edges hx hz / 2, corners hx hz / 4)."""
+    lumping "tensor" (the default reading): the orientation-free tensor trapezoid weights
+    d = hx hz qx(i) qz(j), q = 1/2 at end nodes and 1 otherwise (interior hx hz, edges
+    hx hz / 2, corners hx hz / 4).  "up" / "down": the vertex quadrature of the P1 mass on the
+    triangles themselves, cut along the diagonal (i,j)-(i+1,j+1) ("up") or (i+1,j)-(i,j+1)
+    ("down"): every triangle gives a third of its area to each of its vertices (the four grid
+    corners then depend on the orientation)."""
     hx, hz = spacing(nx, nz, lx, lz)
-    qx = np.ones(nx)
-    qx[[0, -1]] = 0.5
-    qz = np.ones(nz)
-    qz[[0, -1]] = 0.5
-    return (hx * hz * np.outer(qx, qz)).reshape(-1)
+    if lumping == "tensor":
+        qx = np.ones(nx)
+        qx[[0, -1]] = 0.5
+        qz = np.ones(nz)
+        qz[[0, -1]] = 0.5
+        return (hx * hz * np.outer(qx, qz)).reshape(-1)
+    if lumping not in ("up", "down"):
+        raise ValueError(f"lumping {lumping!r}")
+    d = np.zeros(nx * nz)
+    xz = node_xz(nx, nz, lx, lz)
+    for i in range(nx - 1):
+        for j in range(nz - 1):
+            k00, k10, k01, k11 = i * nz + j, (i + 1) * nz + j, i * nz + j + 1, (i + 1) * nz + j + 1
+            tris = [(k00, k10, k11), (k00, k11, k01)] if lumping == "up" else [(k00, k10, k01), (k10, k11, k01)]
+            for t in tris:
+                (x0, z0), (x1, z1), (x2, z2) = xz[t[0]], xz[t[1]], xz[t[2]]
+                area = 0.5 * abs((x1 - x0) * (z2 - z0) - (x2 - x0) * (z1 - z0))
+                for k in t:
+                    d[k] += area / 3.0
+    return d
 
 
 def boundary_mass(nx, nz, lx, lz):
@@ -118,14 +137,14 @@ def boundary_mass(nx, nz, lx, lz):
 class Grid:
     """Grid plus the m-independent pieces of the operator."""
 
-    def __init__(self, nx, nz, lx=1.0, lz=1.0, diagonal="up"):
+    def __init__(self, nx, nz, lx=1.0, lz=1.0, diagonal="up", lumping="tensor"):
         if nx < 4 or nz < 4:
             raise ValueError("the sliding-cubic restriction needs at least 4 nodes per direction")
         self.nx, self.nz, self.lx, self.lz = int(nx), int(nz), float(lx), float(lz)
         self.hx, self.hz = spacing(nx, nz, lx, lz)
         self.N = self.nx * self.nz
         self.S = stiffness(nx, nz, lx, lz, diagonal)
-        self.d = lumped_mass(nx, nz, lx, lz)
+        self.d = lumped_mass(nx, nz, lx, lz, lumping)
         self.b = boundary_mass(nx, nz, lx, lz)
 
 

@@ -122,15 +122,16 @@ extern "C" helm_status helm_assemble(const helm_grid *grid, const double *m_dev,
     if (!out) { helm_set_msg("helm_assemble: NULL out"); return HELM_EINVAL; }
     *out = nullptr;
     if (!grid || !m_dev || !omega || n_omega < 1) { helm_set_msg("helm_assemble: NULL argument or n_omega < 1"); return HELM_EINVAL; }
-    if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0)) {
-        helm_set_msg("helm_assemble: need nx, nz >= 4 and positive lengths");
+    if (grid->nx < 4 || grid->nz < 4 || !(grid->lx > 0) || !(grid->lz > 0) || grid->lumping < HELM_LUMP_TENSOR ||
+        grid->lumping > HELM_LUMP_DOWN) {
+        helm_set_msg("helm_assemble: need nx, nz >= 4, positive lengths and a known lumping");
         return HELM_EINVAL;
     }
     for (int w = 0; w < n_omega; ++w)
         if (!isfinite(omega[w])) { helm_set_msg("helm_assemble: non-finite omega"); return HELM_EINVAL; }
     helm_op *op = new (std::nothrow) helm_op();
     if (!op) return HELM_ENOMEM;
-    op->g = GridGeom{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1)};
+    op->g = GridGeom{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1), grid->lumping};
     op->lx = grid->lx;
     op->lz = grid->lz;
     op->n_omega = n_omega;

@@ -9,7 +9,8 @@ namespace helm {
 // nodal quadrature).  Only the diagonal depends on (m, w); the off-diagonal couplings
 // are the grid constants coup_x / coup_z.  For node (i, j):
 //   S_kk = (hz/hx) w_z(j) [#x-neighbours] + (hx/hz) w_x(i) [#z-neighbours],
-//   d_k  = hx hz q(i) q(j)                      (tensor trapezoid, q = 1/2 at ends),
+//   d_k  = hx hz q(i) q(j)                      (tensor trapezoid, q = 1/2 at ends; or the
+//          triangles' vertex quadrature, lumped_mass),
 //   b_k  = hx q(i) [j on top/bottom] + hz q(j) [i on left/right]  (boundary length).
 __global__ void assemble_kernel(GridGeom g, const double *m, const double *omega, int n_omega, double2 *diag) {
     const int N = g.nx * g.nz;
@@ -19,7 +20,7 @@ __global__ void assemble_kernel(GridGeom g, const double *m, const double *omega
     const double qx = edge_w(i, g.nx), qz = edge_w(j, g.nz);
     const double skk = (g.hz / g.hx) * qz * ((i > 0) + (i < g.nx - 1)) +
                        (g.hx / g.hz) * qx * ((j > 0) + (j < g.nz - 1));
-    const double d = g.hx * g.hz * qx * qz;
+    const double d = lumped_mass(g, i, j);
     double b = 0.0;
     if (j == 0 || j == g.nz - 1) b += g.hx * qx;
     if (i == 0 || i == g.nx - 1) b += g.hz * qz;
@@ -48,7 +49,7 @@ __global__ void gcoef_kernel(GridGeom g, const double *m, const double *omega, i
     if (k >= N) return;
     const int i = k / g.nz, j = k % g.nz;
     const double qx = edge_w(i, g.nx), qz = edge_w(j, g.nz);
-    const double d = g.hx * g.hz * qx * qz;
+    const double d = lumped_mass(g, i, j);
     double b = 0.0;
     if (j == 0 || j == g.nz - 1) b += g.hx * qx;
     if (i == 0 || i == g.nx - 1) b += g.hz * qz;

@@ -48,9 +48,21 @@ template <> __device__ __forceinline__ float2 ldcg<float2>(const float2 *p) { re
 struct GridGeom {
     int nx, nz;
     double hx, hz;
+    int lump = 0;   // mass lumping: 0 tensor trapezoid, 1 / 2 triangles cut (i,j)-(i+1,j+1) / (i+1,j)-(i,j+1)
 };
 
 __host__ __device__ __forceinline__ double edge_w(int idx, int n) { return (idx == 0 || idx == n - 1) ? 0.5 : 1.0; }
+
+// lumped mass d_k of node (i, j) (Appendix "Numerical forward model", nodal quadrature): the tensor
+// trapezoid hx hz q(i) q(j), or the vertex quadrature of the triangles (a third of each adjacent
+// triangle's area), which differs from it only at the four grid corners: hx hz / 3 where the cutting
+// diagonal ends, hx hz / 6 at the other two
+__host__ __device__ __forceinline__ double lumped_mass(const GridGeom &g, int i, int j) {
+    const bool ci = i == 0 || i == g.nx - 1, cj = j == 0 || j == g.nz - 1;
+    if (g.lump == 0 || !(ci && cj)) return g.hx * g.hz * edge_w(i, g.nx) * edge_w(j, g.nz);
+    const bool diag_end = (i == 0) == (j == 0);   // (0,0) or (nx-1,nz-1): ends of the "up" diagonal
+    return g.hx * g.hz / ((diag_end == (g.lump == 1)) ? 3.0 : 6.0);
+}
 
 // coupling between line i-1 and line i at row j (i >= 1)
 __host__ __device__ __forceinline__ double coup_x(const GridGeom &g, int j) { return -(g.hz / g.hx) * edge_w(j, g.nz); }

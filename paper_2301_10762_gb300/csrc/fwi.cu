@@ -22,7 +22,7 @@ namespace helm {
 __device__ __forceinline__ void node_db(const GridGeom &g, int k, double &d, double &b) {
     const int i = k / g.nz, j = k % g.nz;
     const double qx = edge_w(i, g.nx), qz = edge_w(j, g.nz);
-    d = g.hx * g.hz * qx * qz;
+    d = lumped_mass(g, i, j);
     b = 0.0;
     if (j == 0 || j == g.nz - 1) b += g.hx * qx;
     if (i == 0 || i == g.nx - 1) b += g.hz * qz;
@@ -654,7 +654,7 @@ extern "C" helm_status helm_gamma_solve(const helm_grid *grid, double alpha0, do
     if (ncol == 0) return HELM_OK;
     keep_pool_memory();
     cudaStream_t st = (cudaStream_t)stream;
-    const GridGeom g{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1)};
+    const GridGeom g{grid->nx, grid->nz, grid->lx / (grid->nx - 1), grid->lz / (grid->nz - 1), grid->lumping};
     const size_t N = (size_t)g.nx * g.nz;
     helm_status s = HELM_OK;
     {

@@ -33,7 +33,11 @@ class HelmError(RuntimeError):
 
 
 class helm_grid(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("lx", C.c_double), ("lz", C.c_double)]
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("lx", C.c_double), ("lz", C.c_double),
+                ("lumping", C.c_int32)]
+
+
+HELM_LUMP_TENSOR, HELM_LUMP_UP, HELM_LUMP_DOWN = 0, 1, 2
 
 
 class helm_acq(C.Structure):
@@ -293,12 +297,14 @@ class Factor:
             pass
 
 
-def helm_assemble(nx, nz, lx, lz, m: torch.Tensor, omegas, stream=None) -> Op:
+def helm_assemble(nx, nz, lx, lz, m: torch.Tensor, omegas, stream=None, lumping=HELM_LUMP_TENSOR) -> Op:
+    """A(m, w) for every w; lumping: HELM_LUMP_TENSOR (tensor trapezoid) or HELM_LUMP_UP /
+    HELM_LUMP_DOWN (vertex quadrature of the triangles of that orientation; include/helm.h)."""
     lib = load()
     pm = _dev(m, torch.float64, "m", (nx * nz,))
     om, p_om = _dbuf(np.atleast_1d(omegas))
     h = C.c_void_p()
-    g = helm_grid(nx, nz, lx, lz)
+    g = helm_grid(nx, nz, lx, lz, int(lumping))
     _check(lib.helm_assemble(C.byref(g), pm, p_om, len(om), _stream_ptr(stream), C.byref(h)), "helm_assemble")
     return Op(h, nx, nz, lx, lz, om, stream)
 

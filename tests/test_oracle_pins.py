@@ -85,6 +85,40 @@ def test_stiffness_orientation_free_and_row_sums():
     assert np.count_nonzero(np.abs(S1[k]) > 1e-14) == 5
 
 
+@pytest.mark.parametrize("lumping", ["up", "down"])
+def test_triangle_lumping_closed_forms(lumping):
+    """Mass lumped on the triangles themselves (the orientation reading): the row sums of the
+    consistent P1 mass matrix (each triangle: area/12 (1 + delta_ab), a textbook closed form)
+    equal the lumped weights; interior and edge nodes keep the tensor trapezoid's weights, the
+    four corners get hx hz / 3 where the cutting diagonal ends and hx hz / 6 elsewhere; the
+    weights sum to the domain's area."""
+    nx, nz, lx, lz = 7, 6, 1.3, 0.8
+    hx, hz = lx / (nx - 1), lz / (nz - 1)
+    d = H.lumped_mass(nx, nz, lx, lz, lumping)
+    t = H.lumped_mass(nx, nz, lx, lz, "tensor")
+    M = np.zeros((nx * nz, nx * nz))
+    for i in range(nx - 1):
+        for j in range(nz - 1):
+            k00, k10, k01, k11 = i * nz + j, (i + 1) * nz + j, i * nz + j + 1, (i + 1) * nz + j + 1
+            tris = [(k00, k10, k11), (k00, k11, k01)] if lumping == "up" else [(k00, k10, k01), (k10, k11, k01)]
+            for tri in tris:
+                for a in tri:
+                    for b in tri:
+                        M[a, b] += (hx * hz / 2) / 12 * (2.0 if a == b else 1.0)
+    assert np.allclose(M.sum(axis=1), d, rtol=1e-13, atol=0)
+    corners = {(0, 0): 0, (nx - 1, 0): 1, (0, nz - 1): 2, (nx - 1, nz - 1): 3}
+    on_diag = {0, 3} if lumping == "up" else {1, 2}
+    for (i, j), c in corners.items():
+        assert np.isclose(d[i * nz + j], hx * hz / (3.0 if c in on_diag else 6.0), rtol=1e-14)
+    mask = np.ones(nx * nz, bool)
+    mask[[i * nz + j for (i, j) in corners]] = False
+    assert np.allclose(d[mask], t[mask], rtol=1e-14, atol=0)
+    assert np.isclose(d.sum(), lx * lz, rtol=1e-14)
+    # the two orientations are mirror images in x
+    other = H.lumped_mass(nx, nz, lx, lz, "down" if lumping == "up" else "up")
+    assert np.allclose(d.reshape(nx, nz)[::-1], other.reshape(nx, nz), rtol=1e-14, atol=0)
+
+
 def test_quadrature_weights_sum_to_area_and_perimeter():
     g = H.Grid(9, 6, 2.0, 0.75)
     assert np.isclose(g.d.sum(), 2.0 * 0.75)
