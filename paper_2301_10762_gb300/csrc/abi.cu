@@ -190,16 +190,19 @@ extern "C" void helm_op_destroy(helm_op_t *op) {
 // with 16 right-hand sides per frequency favours the line factor, 256 x 256 with 64 favours BCR
 // by 2.5x).  FP64 factors are line factors (the tensor cores have no FP64 path).
 static constexpr int kBcrMinNz = 192;
-static bool pick_bcr(const helm_op *op, helm_prec prec, const helm_factor_opts *opts) {
-    if (prec != HELM_MIXED || !bcr_supported(op->g)) return false;
-    int m = opts ? opts->method : HELM_FACTOR_AUTO;
+bool helm::factor_picks_bcr(const GridGeom &g, helm_prec prec, int method) {
+    if (prec != HELM_MIXED || !bcr_supported(g)) return false;
+    int m = method;
     if (m == HELM_FACTOR_AUTO) {
         const char *env = getenv("HELM_FACTOR");
         if (env && !strcmp(env, "line")) m = HELM_FACTOR_LINE;
         else if (env && !strcmp(env, "bcr")) m = HELM_FACTOR_BCR;
-        else m = op->g.nz >= kBcrMinNz ? HELM_FACTOR_BCR : HELM_FACTOR_LINE;
+        else m = g.nz >= kBcrMinNz ? HELM_FACTOR_BCR : HELM_FACTOR_LINE;
     }
     return m == HELM_FACTOR_BCR;
+}
+static bool pick_bcr(const helm_op *op, helm_prec prec, const helm_factor_opts *opts) {
+    return factor_picks_bcr(op->g, prec, opts ? opts->method : HELM_FACTOR_AUTO);
 }
 
 extern "C" helm_status helm_factor(helm_op_t *op, helm_prec prec, const helm_factor_opts *opts, helm_factor_t **out) {

@@ -103,6 +103,9 @@ helm_status acq_upload(const helm_op *op, const helm_acq *acq, DevAcq *d);
 // block cyclic reduction (bcr.cu)
 namespace helm {
 bool bcr_supported(const GridGeom &g);
+// whether helm_factor builds a block-cyclic-reduction factor for this grid and precision
+// (method: a helm_factor_method; HELM_FACTOR_AUTO follows HELM_FACTOR and the line length)
+bool factor_picks_bcr(const GridGeom &g, helm_prec prec, int method);
 helm_status bcr_factor(helm_factor_t *f);
 void bcr_free(helm_factor_t *f);
 helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip);

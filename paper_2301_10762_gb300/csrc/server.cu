@@ -84,7 +84,14 @@ struct helm_server {
 
     // device bytes as admission counts them (see helm_server.h)
     size_t factor_bytes(const helm_grid &g, int prec) const {
-        const size_t N = (size_t)g.nx * g.nz;
+        const size_t N = (size_t)g.nx * g.nz, blk = (size_t)g.nz * g.nz * 8;
+        const helm::GridGeom geom{g.nx, g.nz, g.lx / (g.nx - 1), g.lz / (g.nz - 1), g.lumping};
+        if (helm::factor_picks_bcr(geom, (helm_prec)prec, HELM_FACTOR_AUTO)) {
+            // block cyclic reduction: the inverses of every line and P, Q, W, V of the eliminated
+            // ones, and as much again of working blocks while it factors (counted throughout)
+            const size_t kept = ((size_t)g.nx + 4 * ((size_t)g.nx / 2 + 1)) * blk;
+            return 2 * kept + 96 * N + kMiB;
+        }
         return (size_t)g.nx * g.nz * g.nz * (prec == HELM_MIXED ? 8 : 16) + 96 * N + kMiB;
     }
     size_t scratch_bytes(const helm_grid &g, int prec, int nrhs) const {   // refinement scratch in the factor
