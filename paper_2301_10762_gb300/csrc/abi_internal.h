@@ -33,6 +33,8 @@ struct BcrData {
     int levels = 0, half = 0;
     float2 *Dinv = nullptr, *P = nullptr, *Q = nullptr, *W = nullptr, *V = nullptr;
     int *tasks = nullptr;
+    float2 *split = nullptr;     // partial tiles of the solve's split-K GEMM launches
+    size_t split_cap = 0;        // (complex elements)
     struct List {
         int first = 0, count = 0;   // tasks of one GEMM launch of the solve
         long long terms = 0;        // product terms over those tasks

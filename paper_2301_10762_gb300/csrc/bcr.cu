@@ -286,12 +286,25 @@ helm_status upload_ints(const std::vector<int> &h, TaskBuf &b, cudaStream_t st) 
 // A recorded sequence of launches: every task list goes into one host array, uploaded with a
 // single copy before the launches are enqueued (a copy from pageable host memory waits for the
 // stream, so one copy per launch would serialise the host with the GPU at every launch).
+// partial tiles of split-K GEMM launches: 64 MB for a factorisation (its deep levels: 8 tasks of
+// 256 x 256 split 16 ways), 32 MB kept with a factor for its solves (64 tasks of 256 x 64 split 8 ways)
+constexpr size_t kFactorSplitElems = (size_t)8 << 20, kSolveSplitElems = (size_t)4 << 20;
+
 struct Plan {
     cudaStream_t st;
     std::vector<int> ints;
     std::vector<std::function<helm_status(const int *)>> ops;
     std::vector<void *> scratch;   // device scratch of the launches, released after the last one
+    float2 *split = nullptr;       // split-K partial tiles shared by the plan's GEMM launches (one
+    size_t split_cap = 0;          // stream: each launch's reduction reads them before the next writes)
     explicit Plan(cudaStream_t s) : st(s) {}
+    helm_status with_split(size_t elems) {
+        helm_status s = dev_alloc((void **)&split, elems * sizeof(float2), "bcr: split-K tiles", st);
+        if (s != HELM_OK) return s;
+        scratch.push_back(split);
+        split_cap = elems;
+        return HELM_OK;
+    }
     ~Plan() {
         for (void *p : scratch) dev_free(p, st);
     }
@@ -338,6 +351,8 @@ helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, Plan &pl) {
     ZGemmArgs a = a0;
     a.tries = wait_tries();
     a.flops = 8.0 * a.M * a.N * a.K * (double)count_terms(tasks.data(), (size_t)n, a.nterms);
+    a.part = pl.split;
+    a.part_cap = pl.split_cap;
     const cudaStream_t st = pl.st;
     pl.ops.push_back([a, off, n, st](const int *dev) mutable -> helm_status {
         a.tasks = dev + off;
@@ -489,8 +504,12 @@ helm_status bcr_factor(helm_factor_t *f) {
         (s = dev_alloc((void **)&Uc, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK ||
         (s = dev_alloc((void **)&Un, (size_t)ns * half * blk, "bcr: work", st)) != HELM_OK)
         return s;
+    if ((s = dev_alloc((void **)&b.split, kSolveSplitElems * sizeof(float2), "bcr: split-K tiles", st)) != HELM_OK)
+        return s;
+    b.split_cap = kSolveSplitElems;
     cudaError_t e;
     Plan pl(st);
+    if ((s = pl.with_split(kFactorSplitElems)) != HELM_OK) return s;
     const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
     {
         const double2 *diag = op->diag;
@@ -667,6 +686,7 @@ void bcr_free(helm_factor_t *f) {
     dev_free(b.W, st);
     dev_free(b.V, st);
     dev_free(b.tasks, st);
+    dev_free(b.split, st);
     b = BcrData();
 }
 
@@ -690,6 +710,8 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     ga.status = op->status;
     ga.skip = skip;
     ga.tries = wait_tries();
+    ga.part = b.split;
+    ga.part_cap = b.split_cap;
     ga.c_stride = nz; ga.c_div = nx; ga.c_stride_hi = vhi; ga.ldc = N;
     cudaError_t e;
     auto launch = [&](ZGemmArgs a, const BcrData::List &lst) -> helm_status {
@@ -778,7 +800,8 @@ helm_status blas_zgemm(int batch, int M, int N, int K, const float2 *A, long lon
         tasks.insert(tasks.end(), v.begin(), v.end());
     }
     Plan pl(st);
-    helm_status s = gemm(a, tasks, pl);
+    helm_status s = pl.with_split(kFactorSplitElems);
+    if (s == HELM_OK) s = gemm(a, tasks, pl);
     return s == HELM_OK ? pl.run() : s;
 }
 
@@ -797,7 +820,8 @@ helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, 
     }
     const Fam f{X, sx, ldx};
     Plan pl(st);
-    helm_status s = invert_blocks(n, f, f, pairs, status, pl);
+    helm_status s = pl.with_split(kFactorSplitElems);
+    if (s == HELM_OK) s = invert_blocks(n, f, f, pairs, status, pl);
     return s == HELM_OK ? pl.run() : s;
 }
 

@@ -109,6 +109,13 @@ struct ZGemmArgs {
     const int *skip = nullptr;
     uint32_t tries = 0;
     double flops = 0.0;   // useful flops of the launch (8 M N K per complex term of every task), for tracing
+    // split-K: with part != nullptr a launch that fills less than a wave of CTAs splits each
+    // task's K chunks over ksplit CTAs, which write partial tiles into part (at most part_cap
+    // complex elements; laid out like C, without C0); a second kernel sums them in a fixed order
+    // and adds C0.  Set by launch_zgemm.
+    int ksplit = 1;
+    float2 *part = nullptr;
+    size_t part_cap = 0;
 };
 cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st);
 

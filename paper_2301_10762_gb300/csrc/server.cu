@@ -90,7 +90,7 @@ struct helm_server {
             // block cyclic reduction: the inverses of every line and P, Q, W, V of the eliminated
             // ones, and as much again of working blocks while it factors (counted throughout)
             const size_t kept = ((size_t)g.nx + 4 * ((size_t)g.nx / 2 + 1)) * blk;
-            return 2 * kept + 96 * N + kMiB;
+            return 2 * kept + 96 * N + 97 * kMiB;   // + the split-K tiles (32 MB kept, 64 MB while factoring)
         }
         return (size_t)g.nx * g.nz * g.nz * (prec == HELM_MIXED ? 8 : 16) + 96 * N + kMiB;
     }

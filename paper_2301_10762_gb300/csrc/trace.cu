@@ -15,6 +15,7 @@ static const char *kNames[K_COUNT] = {
     "fill", "sub", "regR", "dct_matrix", "p2_scale", "dgemm_dct", "line_gb_prepass", "split_diag", "refine_start", "refine_update",
     "refine_finish", "refine_accumulate", "field_grad", "g_coefficients", "hess_finish",
     "zgemm_tf32x3", "zinv_block", "ztranspose", "bcr_form_blocks", "bcr_level0_update", "bcr_solve_level0",
+    "zgemm_split_reduce",
 };
 
 namespace {

@@ -8,7 +8,7 @@ enum KernelId {
     K_ASSEMBLE, K_SOURCES, K_TAPS, K_RESTRICT, K_FACTOR64, K_FACTOR32, K_SWEEP64, K_SWEEP32, K_RESIDUAL,
     K_MISFIT, K_SCATTER, K_GRAD, K_GUP, K_ZBASE, K_HESS, K_HYPER, K_DOT, K_SUM, K_AXPBY, K_FILL, K_SUB,
     K_REGR, K_DCTMAT, K_P2SCALE, K_DGEMM, K_GBPRE, K_SPLITDIAG, K_REFSTART, K_REFUPDATE, K_REFFINISH, K_REFACCUM, K_FIELDGRAD, K_GCOEF, K_HESSFIN,
-    K_ZGEMM, K_ZINV, K_ZTRANS, K_BCR_FORM, K_BCR_L0, K_BCR_SOLVE_L0,
+    K_ZGEMM, K_ZINV, K_ZTRANS, K_BCR_FORM, K_BCR_L0, K_BCR_SOLVE_L0, K_ZSPLIT,
     K_COUNT
 };
 

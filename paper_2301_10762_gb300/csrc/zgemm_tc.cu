@@ -24,6 +24,8 @@
 // each warp writes whole rows (row-major C) or whole columns (column-major C), adding C0.
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "trace.h"
@@ -146,7 +148,8 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * ZG_BM, n0 = blockIdx.y * NT;
-    const int* task = a.tasks + (size_t)blockIdx.z * 8;
+    const int ks = a.ksplit, kpart = (int)(blockIdx.z % (unsigned)ks);   // split-K part of this CTA
+    const int* task = a.tasks + (size_t)(blockIdx.z / (unsigned)ks) * 8;
     const uint32_t smem0 = (smem_u32(zg_smem_raw) + 1023u) & ~1023u;
 
     // active terms (a term whose A index is negative is absent)
@@ -154,7 +157,10 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     for (int u = 0; u < a.nterms; ++u)
         if (task[u] >= 0) act[nterms++] = u;
     const int nkc = (a.K + ZG_KC - 1) / ZG_KC;
-    const int nchunks = nterms * nkc;
+    // this CTA's K chunks [cbase, cbase + nchunks) of the task's nterms * nkc (all of them
+    // unless split); the loops below count chunks locally from 0
+    const int cbase = (int)((long long)kpart * nterms * nkc / ks);
+    const int nchunks = (int)((long long)(kpart + 1) * nterms * nkc / ks) - cbase;
 
     const bool mma_warp = warp == 0;
     const int ptid = tid - 32;   // operand-thread index (warps 1 .. 16)
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     using RB = float4[Cfg::B_V4];
     auto term_of = [&](int c) { const int cu = c / nkc; return cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2]); };
     auto fetch = [&](int c, RA &ra, RB &rb) {
-        const int u = term_of(c), k0 = (c % nkc) * ZG_KC;
+        const int u = term_of(cbase + c), k0 = ((cbase + c) % nkc) * ZG_KC;
         const float2 *A = a.A[u].base + zop_off(task[u], a.A[u].div, a.A[u].stride, a.A[u].stride_hi);
         const float2 *B = a.B[u].base + zop_off(task[3 + u], a.B[u].div, a.B[u].stride, a.B[u].stride_hi);
 #pragma unroll
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     };
     // ---- split and store of a fetched chunk into stage s
     auto store = [&](int c, int s, const RA &ra, const RB &rb) {
-        const float sg = a.sign[term_of(c)];
+        const float sg = a.sign[term_of(cbase + c)];
         const uint32_t base = smem0 + (uint32_t)(s * Cfg::STAGE);
         const uint32_t a_hi = base, a_lo = base + Cfg::A_BYTES;
         const uint32_t b_hi = base + 2 * Cfg::A_BYTES, b_lo = b_hi + Cfg::B_BYTES;
@@ -303,9 +309,12 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     // every MMA issued is complete before the accumulator is read or freed
     if (!mbar_wait_bounded(&done_bar, 0, a.tries)) give_up();
     tc_fence_after();
-    const bool ok = !__syncthreads_or(*(volatile int *)&s_abort) && nchunks > 0;
+    const bool aborted = __syncthreads_or(*(volatile int *)&s_abort);
+    const bool ok = !aborted && nchunks > 0;
+    // a split part without chunks still owes its (zero) partial tile
+    const bool zero_part = !aborted && nchunks == 0 && ks > 1;
 
-    if (ok && !mma_warp) {
+    if ((ok || zero_part) && !mma_warp) {
         // Epilogue through shared memory (free once every MMA is complete): the operand warps
         // copy the accumulator tile from tensor memory (warp w: lanes 32 (w % 4) .. + 31, the
         // real columns of part (w - 1) / 4) into a padded [128][NT + 1] complex tile, meet, and
@@ -318,15 +327,25 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             const int r = 32 * q + lane;
             for (int col = h * cpp; col < (h + 1) * cpp; col += 16) {
                 float v[16];
-                tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+                if (ok) {
+                    tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
 #pragma unroll
                 for (int i = 0; i < 8; ++i) T[r * TS + col / 2 + i] = make_float2(v[2 * i], v[2 * i + 1]);
             }
         }
         asm volatile("bar.sync 1, %0;" ::"n"(ZG_PRODUCERS) : "memory");
-        const float2 *C0 =
-            a.C0.base ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) : nullptr;
-        float2 *C = a.C + zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi);
+        // split parts write their partial tile (C's layout, leading dimension M or N, no C0)
+        const bool split = ks > 1;
+        const float2 *C0 = (!split && a.C0.base)
+                               ? a.C0.base + zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi)
+                               : nullptr;
+        float2 *C = split ? a.part + (size_t)blockIdx.z * ((size_t)a.M * a.N)
+                          : a.C + zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi);
+        const long long ldc = split ? (a.c_col ? a.M : a.N) : a.ldc;
         if (!a.c_col) {
             for (int rr = pw; rr < ZG_BM; rr += ZG_PRODUCERS / 32) {   // row-major: a row per warp
                 const int m = m0 + rr;
@@ -338,7 +357,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                         out.x += b.x;
                         out.y += b.y;
                     }
-                    C[(long long)m * a.ldc + n0 + nn] = out;
+                    C[(long long)m * ldc + n0 + nn] = out;
                 }
             }
         } else {
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                         out.x += b.x;
                         out.y += b.y;
                     }
-                    C[(long long)n * a.ldc + m0 + rr] = out;
+                    C[(long long)n * ldc + m0 + rr] = out;
                 }
             }
         }
@@ -364,13 +383,70 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
                      : "memory");
 }
 
+// C_t = C0_t + sum over the ksplit partial tiles of task t, in part order; one thread per element
+// of C, consecutive threads along C's contiguous dimension
+__global__ void zsplit_reduce_kernel(ZGemmArgs a) {
+    if (a.skip && *a.skip) return;   // the GEMM itself was skipped
+    const int *task = a.tasks + (size_t)blockIdx.y * 8;
+    const long long mn = (long long)a.M * a.N;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= mn) return;
+    const int inner = a.c_col ? a.M : a.N;   // C's contiguous dimension
+    const int i = (int)(e / inner), o = (int)(e % inner);
+    const float2 *P = a.part + (size_t)blockIdx.y * a.ksplit * mn + e;
+    float2 v = P[0];
+    for (int p = 1; p < a.ksplit; ++p) {
+        const float2 w = P[(size_t)p * mn];
+        v.x += w.x;
+        v.y += w.y;
+    }
+    if (a.C0.base && task[6] >= 0) {
+        const float2 b = a.C0.base[zop_off(task[6], a.C0.div, a.C0.stride, a.C0.stride_hi) + (long long)i * a.C0.ld + o];
+        v.x += b.x;
+        v.y += b.y;
+    }
+    a.C[zop_off(task[7], a.c_div, a.c_stride, a.c_stride_hi) + (long long)i * a.ldc + o] = v;
+}
+
+// streaming multiprocessors of the current device (queried once)
+int num_sms() {
+    static const int n = []() {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            v = 0;
+        cudaGetLastError();
+        return v > 0 ? v : 148;
+    }();
+    return n;
+}
+
 template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
     using Cfg = ZCfg<NT>;
     const void *fn = (const void *)zgemm_tc_kernel<NT>;
     cudaError_t e = ensure_dyn_smem(fn, Cfg::SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((a.M + ZG_BM - 1) / ZG_BM), (unsigned)((a.N + NT - 1) / NT), (unsigned)n_tasks);
-    HELM_TRACED_W(K_ZGEMM, st, a.flops, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(a)));
+    // split-K where the launch fills at most half of the SMs: as many parts as keep it within one
+    // wave, at most one part per K chunk of a term, within the partial buffer
+    ZGemmArgs b = a;
+    b.ksplit = 1;
+    const long long tiles = (long long)((a.M + ZG_BM - 1) / ZG_BM) * ((a.N + NT - 1) / NT) * n_tasks;
+    const int kNumSMs = num_sms();
+    if (a.part && tiles * 2 <= kNumSMs) {
+        const int nkc = (a.K + ZG_KC - 1) / ZG_KC;
+        long long ks = std::min<long long>(nkc, kNumSMs / tiles);
+        ks = std::min<long long>(ks, (long long)(a.part_cap / ((size_t)a.M * a.N * n_tasks)));
+        ks = std::min<long long>(ks, 65535 / n_tasks);
+        if (ks >= 2) b.ksplit = (int)ks;
+    }
+    dim3 grid((unsigned)((a.M + ZG_BM - 1) / ZG_BM), (unsigned)((a.N + NT - 1) / NT), (unsigned)(n_tasks * b.ksplit));
+    HELM_TRACED_W(K_ZGEMM, st, a.flops, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(b)));
+    if (b.ksplit > 1) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long mn = (long long)a.M * a.N;
+        dim3 rg((unsigned)((mn + 255) / 256), (unsigned)n_tasks);
+        HELM_TRACED(K_ZSPLIT, st, (zsplit_reduce_kernel<<<rg, 256, 0, st>>>(b)));
+    }
     return cudaGetLastError();
 }
 
