@@ -15,11 +15,12 @@
 //
 // One CTA computes a 128 x NT complex tile (tcgen05 M = 128, N = 2 NT) of one task.  Sixteen
 // operand warps load a K chunk of 16 complex columns (one 128-byte row per matrix row) from
-// global memory two chunks ahead into registers (three register sets), split it and store it into shared memory in
-// the 128-byte-swizzled K-major layout the tensor core reads, meet at a named barrier and hand
-// the stage over with one arrival on its full barrier; a separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits
-// them to the stage's empty barrier, which the operand warps wait for before they overwrite the
-// stage STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the
+// global memory two chunks ahead into registers (three register sets), split it and store it
+// into shared memory in the 128-byte-swizzled K-major layout the tensor core reads; each warp
+// then arrives on the stage's full barrier on its own (sixteen arrivals complete it).  A
+// separate warp waits for it, issues the chunk's 12 MMAs from one thread and commits them to
+// the stage's empty barrier, which the operand warps wait for before they overwrite the stage
+// STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the
 // accumulator with tcgen05.ld into a padded tile in the (then idle) shared memory, from which
 // each warp writes whole rows (row-major C) or whole columns (column-major C), adding C0.
 #include <stdint.h>
@@ -112,17 +113,6 @@ __device__ __forceinline__ long long zop_off(int idx, int div, long long stride,
     return div > 0 ? (long long)(idx / div) * stride_hi + (long long)(idx % div) * stride : (long long)idx * stride;
 }
 
-// named barrier 1 over the operand warps, with an OR of v across them (all get the result)
-__device__ __forceinline__ bool operands_sync_or(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(ZG_PRODUCERS)
-        : "memory");
-    return r != 0;
-}
-
 template <int NT> struct ZCfg {
     static constexpr int NR = 2 * NT;                        // real columns of the tile (tcgen05 N)
     static constexpr int A_BYTES = ZG_BM * 128;              // one split of the A chunk
@@ -139,7 +129,7 @@ template <int NT>
 __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     using Cfg = ZCfg<NT>;
     extern __shared__ uint8_t zg_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (operand warps, one arrival)
+    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (one arrival per operand warp)
     __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];   // stage read by its MMAs (commit)
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t s_tmem;
@@ -166,7 +156,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int ptid = tid - 32;   // operand-thread index (warps 1 .. 16)
     if (tid == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
-            mbar_init(&full_bar[s], 1);
+            mbar_init(&full_bar[s], ZG_PRODUCERS / 32);   // one arrival per operand warp
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
@@ -246,29 +236,27 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     };
     if (!mma_warp) {
         // operand warps: chunk c waits for its stage to be free, is split and stored, chunk c + 2
-        // is fetched into the freed registers, and every thread arrives on the stage's full
-        // barrier; they run up to STAGES chunks ahead of the tensor core
+        // is fetched into the freed registers, and every warp arrives on the stage's full barrier
+        // (16 arrivals complete it) without waiting for the other warps; they run up to STAGES
+        // chunks ahead of the tensor core.  Decisions to stop are taken per warp (votes), so that
+        // no lane leaves the loop while its warp's other lanes go on
         auto pstep = [&](int c, RA &ra, RB &rb, RA &na, RB &nb) -> bool {
             const int s = c % Cfg::STAGES;
-            bool bad = false;
-            if (c >= Cfg::STAGES &&
-                !mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort)) {
-                give_up();
-                bad = true;
+            const bool bad = c >= Cfg::STAGES &&
+                             !mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort);
+            if (__any_sync(0xffffffffu, bad)) {   // a warp whose wait gave up writes no stage the MMAs may read
+                if (bad) give_up();
+                return false;
             }
-            if (!bad) {   // a thread whose wait gave up must not write a stage the MMAs may read
-                store(c, s, ra, rb);
-                // the stores are made visible to the tensor core's (async proxy) reads before
-                // the next loads are issued: a proxy fence after them would wait for those
-                // loads as well and expose their latency on every chunk
-                fence_proxy_async_smem();
-                if (c + 2 < nchunks) fetch(c + 2, na, nb);
-            }
-            // the operand warps meet (every store is complete) and decide together whether to
-            // go on; then one thread hands the stage to the MMA warp
-            if (operands_sync_or(bad || *(volatile int *)&s_abort)) return false;
-            if (ptid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
-            return true;
+            store(c, s, ra, rb);
+            // the stores are made visible to the tensor core's (async proxy) reads before the
+            // next loads are issued: a proxy fence after them would wait for those loads as well
+            // and expose their latency on every chunk
+            fence_proxy_async_smem();
+            if (c + 2 < nchunks) fetch(c + 2, na, nb);
+            __syncwarp();   // every lane's stores and fence before the warp's arrival
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+            return !__any_sync(0xffffffffu, *(volatile int *)&s_abort);
         };
         // three register sets: chunk c is stored from set c mod 3 while chunk c + 2 is loaded
         // into set (c + 2) mod 3, whose stores (chunk c - 1) have long been issued -- loading
