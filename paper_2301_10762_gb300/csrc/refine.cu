@@ -21,6 +21,7 @@
 // residuals on the FP64 iterate (residual_kernel, refine_accumulate_kernel).
 #include <math.h>
 #include "kernels.h"
+#include "pairsplit.h"
 #include "trace.h"
 
 namespace helm {
@@ -137,11 +138,12 @@ __global__ void __launch_bounds__(RF_THREADS) refine_start_kernel(int N, int col
                 double2 v2 = b[q];
                 if (conj) v2.y = -v2.y;
                 float4 v;
-                split_double(v2.x, v.x, v.z);
-                split_double(v2.y, v.y, v.w);
+                split_double_int(v2.x, v.x, v.z);   // the FP64 split's bits, from integer operations
+                split_double_int(v2.y, v.y, v.w);
                 bd[base + k] = v;
                 r32[base + k] = make_float2(v.x, v.y);
-                bb += v2.x * v2.x + v2.y * v2.y;
+                // (the zeros of point sources skip the FP64 arithmetic, tested on the bits)
+                if (((ps_bits64(v2.x) | ps_bits64(v2.y)) << 1) != 0) bb += v2.x * v2.x + v2.y * v2.y;
             }
         }
         bb = block_sum(bb, sh);
@@ -288,13 +290,13 @@ __global__ void refine_finish_kernel(size_t n, const float4 *xa, const float4 *x
         for (int q = 0; q < 4; ++q) v[q] = __ldcs(x + e + q * stride);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const double re = (double)v[q].x + (double)v[q].z, im = (double)v[q].y + (double)v[q].w;
+            const double re = pair_to_double(v[q].x, v[q].z), im = pair_to_double(v[q].y, v[q].w);
             X[e + q * stride] = make_double2(re, conj ? -im : im);
         }
     }
     for (; e < n; e += stride) {
         const float4 v = x[e];
-        const double re = (double)v.x + (double)v.z, im = (double)v.y + (double)v.w;
+        const double re = pair_to_double(v.x, v.z), im = pair_to_double(v.y, v.w);
         X[e] = make_double2(re, conj ? -im : im);
     }
 }
