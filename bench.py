@@ -419,6 +419,35 @@ def gemm_kernel_bench(hm, torch, peaks, reps=10):
     return out
 
 
+def zinv_kernel_bench(hm, torch, reps=10):
+    """The batched inversion alone at the 256^2 factor's shapes: the 1024 line blocks of level 0
+    (256 x 256, each through the 2 x 2 block inverse over two 128 x 128 base inversions and six
+    tensor-core products) and a deep level's 8 blocks (latency of one chain).  Complex
+    symmetric, diagonally dominant inputs; medians of `reps` calls, CUDA events."""
+    out = {}
+    g = torch.Generator(device="cuda").manual_seed(11)
+    for name, (b, n) in {"level0_1024x256": (1024, 256), "deep_8x256": (8, 256), "base_1024x128": (1024, 128)}.items():
+        A = torch.randn((b, n, n), dtype=torch.complex64, device="cuda", generator=g)
+        A = 0.5 * (A + A.transpose(1, 2)) + 3.0 * n ** 0.5 * torch.eye(n, dtype=torch.complex64, device="cuda")
+        X = torch.empty_like(A)
+        for _ in range(2):
+            hm.helm_zinv_batched(A, X)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hm.helm_zinv_batched(A, X)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        flops = 8.0 * n ** 3 * b   # Gauss-Jordan inverse: ~2 n^3 complex multiply-adds
+        out[name] = {"batch": b, "n": n, "us": t * 1e6, "tflops": flops / t / 1e12}
+        del A, X
+    return out
+
+
 # -------------------------------------------------------- hypergradient step
 
 def hypergrad_step(hm, torch, steps, warmup, rank):
@@ -580,6 +609,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the hypergradient step and the server session")
     ap.add_argument("--server", action="store_true", help="long solve-server session instead of the solve step")
     ap.add_argument("--gemm-only", action="store_true", help="time the tensor-core GEMM alone and exit")
+    ap.add_argument("--zinv-only", action="store_true", help="time the batched block inversion alone and exit")
     ap.add_argument("--matmul-peaks", action="store_true",
                     help="time torch.matmul (cuBLAS) in TF32, FP32 and FP64 and exit")
     ap.add_argument("--server-sizes", default="64,128,256")
@@ -625,6 +655,10 @@ def main():
     if args.matmul_peaks:
         if rank == 0:
             print(json.dumps({"matmul_peaks": matmul_peaks(torch)}), flush=True)
+        return
+    if args.zinv_only:
+        if rank == 0:
+            print(json.dumps({"kernel_zinv": zinv_kernel_bench(hm, torch)}), flush=True)
         return
     if args.gemm_only:
         if rank == 0:
@@ -774,7 +808,8 @@ def main():
 
     rl = roofline(dominant, trace, breakdown, (w.nx, w.nz, n_om, ns), peaks)
 
-    extras = {"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks)} if rank == 0 else {}
+    extras = {"kernel_zgemm": gemm_kernel_bench(hm, torch, peaks), "kernel_zinv": zinv_kernel_bench(hm, torch)} \
+        if rank == 0 else {}
     if not args.no_extras and rank == 0:
         extras["hypergrad_step_128"] = hypergrad_step(hm, torch, 10, args.warmup, rank)
         try:

@@ -810,9 +810,12 @@ helm_status blas_zinv(int batch, int n, const float2 *A, long long sa, int lda, 
     std::vector<int> pairs;
     for (int t = 0; t < batch; ++t) pairs.insert(pairs.end(), {t, t});
     if (A != X) {   // copy into X first: the recursion works in place on the output blocks
+        // blocks stacked without gaps on both sides are one 2D copy of batch * n rows
+        const bool stacked = sa == (long long)n * lda && sx == (long long)n * ldx;
         cudaError_t e = cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(float2), A, (size_t)lda * sizeof(float2),
-                                          (size_t)n * sizeof(float2), (size_t)n, cudaMemcpyDeviceToDevice, st);
-        for (int t = 1; t < batch && e == cudaSuccess; ++t)
+                                          (size_t)n * sizeof(float2), (size_t)n * (stacked ? batch : 1),
+                                          cudaMemcpyDeviceToDevice, st);
+        for (int t = 1; !stacked && t < batch && e == cudaSuccess; ++t)
             e = cudaMemcpy2DAsync(X + (long long)t * sx, (size_t)ldx * sizeof(float2), A + (long long)t * sa,
                                   (size_t)lda * sizeof(float2), (size_t)n * sizeof(float2), (size_t)n,
                                   cudaMemcpyDeviceToDevice, st);

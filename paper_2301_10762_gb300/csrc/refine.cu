@@ -205,9 +205,14 @@ __device__ void refine_stop_test(int cols, double *norms, RefineStop stop, Refin
 }
 
 // grid: (node blocks of RF_THREADS * RF_NPT, columns); norms[col][0] pre-zeroed, norms[col][1] = ||b||^2
-__global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, int nrhs, int cols, const float4 *diag2,
-                                                                   const float4 *bd, const float4 *x_in,
-                                                                   const float2 *delta, float4 *x_out, float2 *r32,
+// (the arrays are distinct: __restrict__ lets the loads of later nodes move above the stores of
+// earlier ones, so that several nodes' loads are in flight)
+__global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, int nrhs, int cols,
+                                                                   const float4 *__restrict__ diag2,
+                                                                   const float4 *__restrict__ bd,
+                                                                   const float4 *__restrict__ x_in,
+                                                                   const float2 *__restrict__ delta,
+                                                                   float4 *__restrict__ x_out, float2 *__restrict__ r32,
                                                                    double *norms, StencilPairs cp,
                                                                    RefineState *state, RefineStop stop) {
     __shared__ float shf[RF_THREADS / 32];
@@ -226,10 +231,10 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
         const float scale = __uint_as_float((unsigned)(127 - ks) << 23);
         float rr = 0.f;
         const size_t base = (size_t)c * N;
-        const float4 *xc = x_in ? x_in + base : nullptr;
-        const float2 *dc = delta + base;
+        const float4 *__restrict__ xc = x_in ? x_in + base : nullptr;
+        const float2 *__restrict__ dc = delta + base;
         const int k0 = blockIdx.x * RF_THREADS * RF_NPT + threadIdx.x;
-#pragma unroll 2
+#pragma unroll 4
         for (int q = 0; q < RF_NPT; ++q) {
             const int k = k0 + q * RF_THREADS;
             if (k >= N) break;
