@@ -369,7 +369,8 @@ helm_status factor_reserve(helm_factor_t *f, int nrhs) {
          (s = dev_alloc((void **)&f->xb, cols * N * sizeof(float4), "allocate(iterate)", st)) != HELM_OK ||
          (s = dev_alloc((void **)&f->r32, cols * N * sizeof(float2), "allocate(residual)", st)) != HELM_OK ||
          (s = dev_alloc((void **)&f->y, cols * N * sizeof(float2), "allocate(work)", st)) != HELM_OK ||
-         (s = dev_alloc((void **)&f->state, sizeof(RefineState), "allocate(refinement state)", st)) != HELM_OK))
+         (s = dev_alloc((void **)&f->state, refine_state_bytes(op->n_omega), "allocate(refinement state)", st)) !=
+             HELM_OK))
         return s;
     if ((s = dev_alloc((void **)&f->norms, cols * 2 * sizeof(double), "allocate(norms)", st)) != HELM_OK) return s;
     f->norms_host.assign(cols * 2, 0.0);
@@ -413,15 +414,18 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     const size_t n = (size_t)cols * g.nx * g.nz;
     const int rchunk = 16;
     if (max_iter < 1) max_iter = 1;
-    cudaError_t e = cudaMemsetAsync(w.state, 0, sizeof(RefineState), op->st);
+    cudaError_t e = cudaMemsetAsync(w.state, 0, refine_state_bytes(n_sys), op->st);
     if (e == cudaSuccess) e = launch_refine_start(g, cols, B, conj, w.bd, w.r32, w.norms, op->st);
     if (e != cudaSuccess) { helm_set_error("refinement start", e); return HELM_ECUDA; }
     const int *skip = &w.state->done;
     // the correction A~^{-1} r: line sweep, or the block-cyclic-reduction solve (which works in
     // place on r, recomputed before every correction)
+    // (in the pair phase a system whose columns are all at rtol is frozen: its solve products and
+    // updates are skipped; the FP64 phase corrects every column)
     auto sweep = [&](const int *skip_flag) -> cudaError_t {
         if (f->use_bcr) {
-            const helm_status bs = bcr_solve(f, nrhs, w.r32, w.y, skip_flag);
+            const int *frozen = skip_flag ? refine_sys(w.state) + 1 : nullptr;
+            const helm_status bs = bcr_solve(f, nrhs, w.r32, w.y, skip_flag, frozen);
             return bs == HELM_OK ? cudaSuccess : cudaErrorLaunchFailure;
         }
         return launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, w.r32, nullptr, w.y, 0, rchunk,
@@ -449,7 +453,7 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     int it = hs.iters;
     double rel = hs.rel;
     f->last_iters.store(std::max(1, it), std::memory_order_relaxed);
-    e = launch_refine_finish(n, w.xa, w.xb, w.state, conj, X, op->st);
+    e = launch_refine_finish(n, g.nx * g.nz, nrhs, w.xa, w.xb, w.state, conj, X, op->st);
     if (e != cudaSuccess) { helm_set_error("refinement finish", e); return HELM_ECUDA; }
     if (!(rel <= rtol) && it < max_iter && isfinite(rel)) {
         // FP64 phase: r = b - A x in FP64 on the FP64 iterate, correction conj?(A~^{-1} conj?(r))

@@ -110,7 +110,9 @@ bool bcr_supported(const GridGeom &g);
 bool factor_picks_bcr(const GridGeom &g, helm_prec prec, int method);
 helm_status bcr_factor(helm_factor_t *f);
 void bcr_free(helm_factor_t *f);
-helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip);
+// frozen: NULL, or the refinement's per-system flags (stride 2): columns of a set flag are skipped
+helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip,
+                      const int *frozen = nullptr);
 helm_status blas_zgemm(int batch, int M, int N, int K, const float2 *A, long long sa, int lda, const float2 *Bt,
                        long long sb, int ldb, float sign, const float2 *C0, float2 *C, long long sc, int ldc,
                        cudaStream_t st, int *status);

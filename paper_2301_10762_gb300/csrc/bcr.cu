@@ -233,13 +233,15 @@ __global__ void ztranspose_kernel(int n, const float2 *in, float2 *out, long lon
 // solve, level 0 of the forward pass: b_k -= C (y_{k-1} + y_{k+1}) for even k, y in x.  Thread:
 // two rows (one float4) of the line, for L0_COLS columns (frequency x right-hand side).
 constexpr int L0_COLS = 8;
-__global__ void bcr_solve_l0_fwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip) {
+__global__ void bcr_solve_l0_fwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip,
+                                        const int *frozen, int nrhs) {
     if (skip && *skip) return;
     const int nz = g.nz, nx = g.nx, N = nx * nz;
     const int k = 2 * blockIdx.y, r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (r >= nz) return;
     const float c0 = cp.cx(r, nz), c1 = cp.cx(r + 1, nz);
     for (int col = blockIdx.z * L0_COLS; col < min(cols, (int)(blockIdx.z + 1) * L0_COLS); ++col) {
+        if (frozen && frozen[2 * (col / nrhs)]) continue;   // a converged system's correction is not needed
         const size_t off = (size_t)col * N + (size_t)k * nz + r;
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k >= 1) { const float4 v = *reinterpret_cast<const float4 *>(x + off - nz); t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w; }
@@ -252,13 +254,15 @@ __global__ void bcr_solve_l0_fwd_kernel(GridGeom g, Coup cp, int cols, float2 *b
 }
 
 // solve, level 0 of the backward pass: b_j = C (x_{j-1} + x_{j+1}) for odd j
-__global__ void bcr_solve_l0_bwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip) {
+__global__ void bcr_solve_l0_bwd_kernel(GridGeom g, Coup cp, int cols, float2 *b, const float2 *x, const int *skip,
+                                        const int *frozen, int nrhs) {
     if (skip && *skip) return;
     const int nz = g.nz, nx = g.nx, N = nx * nz;
     const int j = 2 * blockIdx.y + 1, r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (r >= nz) return;
     const float c0 = cp.cx(r, nz), c1 = cp.cx(r + 1, nz);
     for (int col = blockIdx.z * L0_COLS; col < min(cols, (int)(blockIdx.z + 1) * L0_COLS); ++col) {
+        if (frozen && frozen[2 * (col / nrhs)]) continue;
         const size_t off = (size_t)col * N + (size_t)j * nz + r;
         float4 t = *reinterpret_cast<const float4 *>(x + off - nz);
         if (j + 1 < nx) { const float4 v = *reinterpret_cast<const float4 *>(x + off + nz); t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w; }
@@ -695,7 +699,7 @@ void bcr_free(helm_factor_t *f) {
 // x = A~^{-1} r for every system and right-hand side, complex FP32: r [n_sys][nrhs][N] is the
 // working vector (overwritten), x [n_sys][nrhs][N] the result.  skip: launches do nothing
 // while it is set (refinement finished).
-helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip) {
+helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, const int *skip, const int *frozen) {
     const helm_op *op = f->op;
     const GridGeom &g = op->g;
     const int nx = g.nx, nz = g.nz, ns = op->n_omega, N = nx * nz;
@@ -712,6 +716,8 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     ga.tries = wait_tries();
     ga.part = b.split;
     ga.part_cap = b.split_cap;
+    ga.sys_frozen = frozen;   // C index = system * nx + line
+    ga.sys_div = nx;
     ga.c_stride = nz; ga.c_div = nx; ga.c_stride_hi = vhi; ga.ldc = N;
     cudaError_t e;
     auto launch = [&](ZGemmArgs a, const BcrData::List &lst) -> helm_status {
@@ -735,7 +741,7 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
         a.C = x;
         if ((s = launch(a, b.fwd[0])) != HELM_OK) return s;
         HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_fwd_kernel<<<dim3(per, neven, colb), thr, 0, st>>>(
-                                            g, cp, cols, r, x, skip)));
+                                            g, cp, cols, r, x, skip, frozen, nrhs)));
         if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
     }
     for (int l = 1; l < b.levels; ++l) {   // b_k -= W_a b_a + V_c b_c
@@ -767,7 +773,7 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     {   // backward, level 0: t_j = C (x_{j-1} + x_{j+1}) into b_j, x_j = y_j - Dinv_j t_j
         if (nodd > 0) {
             HELM_TRACED(K_BCR_SOLVE_L0, st, (bcr_solve_l0_bwd_kernel<<<dim3(per, nodd, colb), thr, 0, st>>>(
-                                                g, cp, cols, r, x, skip)));
+                                                g, cp, cols, r, x, skip, frozen, nrhs)));
             if ((e = cudaGetLastError()) != cudaSuccess) { helm_set_error("bcr solve: level 0", e); return HELM_ECUDA; }
         }
         ZGemmArgs a = ga;

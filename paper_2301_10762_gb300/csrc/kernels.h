@@ -64,6 +64,19 @@ struct RefineState {
     double prev;     // the one before
     unsigned blocks; // update blocks finished in the current pass (the last one runs the test)
 };
+// The state is followed in memory by int sys[n_sys][2]: per system (frequency) the sweeps applied
+// to it and a frozen flag, set once all its columns are at rtol; later updates (and, on the
+// block-cyclic-reduction path, the solve's products) skip a frozen system, whose newest iterate
+// then stays in the buffer of its own last sweep.
+__host__ __device__ inline size_t refine_state_bytes(int n_sys) {
+    return ((sizeof(RefineState) + 15) / 16) * 16 + 2 * sizeof(int) * (size_t)(n_sys > 0 ? n_sys : 1);
+}
+__host__ __device__ inline int *refine_sys(RefineState *st) {
+    return reinterpret_cast<int *>(reinterpret_cast<char *>(st) + ((sizeof(RefineState) + 15) / 16) * 16);
+}
+__host__ __device__ inline const int *refine_sys(const RefineState *st) {
+    return reinterpret_cast<const int *>(reinterpret_cast<const char *>(st) + ((sizeof(RefineState) + 15) / 16) * 16);
+}
 struct RefineStop {  // stopping rule of the pair phase, applied on the device
     double rtol, floor_rel;
     int max_iter;
@@ -76,9 +89,10 @@ cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const f
                                  const float4 *x_in, const float2 *delta, float4 *x_out, float2 *r32, double *norms,
                                  cudaStream_t st, RefineState *state = nullptr, RefineStop stop = {});
 
-// X = conj?(hi + lo) in FP64 of the newest iterate: xa after an odd number of sweeps, else xb
-cudaError_t launch_refine_finish(size_t n, const float4 *xa, const float4 *xb, const RefineState *state, int conj,
-                                 double2 *X, cudaStream_t st);
+// X = conj?(hi + lo) in FP64 of each system's newest iterate: xa after an odd number of sweeps of
+// that system, else xb (columns of N nodes, nrhs columns per system)
+cudaError_t launch_refine_finish(size_t n, int N, int nrhs, const float4 *xa, const float4 *xb,
+                                 const RefineState *state, int conj, double2 *X, cudaStream_t st);
 // X += conj?(delta) in FP64 (refinement tail with FP64 residuals)
 cudaError_t launch_refine_accumulate(size_t n, const float2 *delta, int conj, double2 *X, cudaStream_t st);
 
@@ -116,6 +130,10 @@ struct ZGemmArgs {
     int ksplit = 1;
     float2 *part = nullptr;
     size_t part_cap = 0;
+    // per-system skip (refinement): a task whose system (C index / sys_div) has
+    // sys_frozen[2 * system] set does nothing
+    const int *sys_frozen = nullptr;
+    int sys_div = 1;
 };
 cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st);
 

@@ -174,14 +174,25 @@ __device__ __forceinline__ double nan_max(double a, double b) { return (isnan(a)
 // rr = 0 else inf; a non-finite bb or rr: NaN, which stops the loop unconverged); record it and
 // decide; rr = 0 again for the next update.  The norms were accumulated by atomics of other
 // blocks, so they are read from L2.
-__device__ void refine_stop_test(int cols, double *norms, RefineStop stop, RefineState *st, double *sh) {
+__device__ void refine_stop_test(int cols, int nrhs, double *norms, RefineStop stop, RefineState *st, double *sh) {
     double mx = 0.0;
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        const double rr = __ldcg(norms + 2 * (size_t)c), bb = __ldcg(norms + 2 * (size_t)c + 1);
-        // a non-finite right-hand side (bb NaN or inf) or residual gives NaN: not converged
-        const double rel = (isnan(rr) || !isfinite(bb)) ? NAN : (bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0));
-        mx = nan_max(mx, rel);
-        norms[2 * (size_t)c] = 0.0;
+    int *sys = refine_sys(st);
+    const int n_sys = cols / nrhs;
+    for (int q = threadIdx.x; q < n_sys; q += blockDim.x) {   // per system, over its columns
+        double ms = 0.0;
+        for (int j = 0; j < nrhs; ++j) {
+            const size_t c = (size_t)q * nrhs + j;
+            const double rr = __ldcg(norms + 2 * c), bb = __ldcg(norms + 2 * c + 1);
+            // a non-finite right-hand side (bb NaN or inf) or residual gives NaN: not converged
+            const double rel = (isnan(rr) || !isfinite(bb)) ? NAN : (bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? INFINITY : 0.0));
+            ms = nan_max(ms, rel);
+            norms[2 * c] = 0.0;
+        }
+        if (!sys[2 * q + 1]) {   // this pass updated the system: count it, freeze it once converged
+            sys[2 * q] += 1;
+            if (ms <= stop.rtol) sys[2 * q + 1] = 1;
+        }
+        mx = nan_max(mx, ms);   // (a frozen system's columns were not updated: 0)
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double v = __shfl_down_sync(0xffffffffu, mx, o);
@@ -220,8 +231,10 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
     __shared__ double shd[32];
     if (state && state->done) return;   // the refinement has stopped: later passes do nothing
     const int nx = g.nx, nz = g.nz, N = nx * nz;
+    const int *sysflags = state ? refine_sys(state) : nullptr;
     for (int c = blockIdx.y; c < cols; c += gridDim.y) {
         const int sys = c / nrhs;
+        if (sysflags && sysflags[2 * sys + 1]) continue;   // frozen: its iterate stays (whole block)
         const double bb = norms[2 * (size_t)c + 1];
         // power-of-two scale 2^-ks, ks about half the binary exponent of ||b||^2: keeps the FP32
         // squares of r 2^-ks in range; the sum is scaled back exactly by 2^(2 ks) (no FP64
@@ -268,7 +281,7 @@ __global__ void __launch_bounds__(RF_THREADS) refine_update_kernel(GridGeom g, i
         __syncthreads();
         if (s_last) {
             __threadfence();
-            refine_stop_test(cols, norms, stop, state, shd);
+            refine_stop_test(cols, nrhs, norms, stop, state, shd);
             if (threadIdx.x == 0) state->blocks = 0;
         }
     }
@@ -284,15 +297,19 @@ __global__ void refine_accumulate_kernel(size_t n, const float2 *d, int conj, do
     }
 }
 
-__global__ void refine_finish_kernel(size_t n, const float4 *xa, const float4 *xb, const RefineState *st, int conj,
-                                     double2 *X) {
-    const float4 *x = (st->iters & 1) ? xa : xb;
+__global__ void refine_finish_kernel(size_t n, int N, int nrhs, const float4 *xa, const float4 *xb,
+                                     const RefineState *st, int conj, double2 *X) {
+    const int *sys = refine_sys(st);
     const size_t stride = (size_t)gridDim.x * blockDim.x;
+    auto at = [&](size_t e) -> float4 {   // the newest iterate of this element's system
+        const int q = (int)(e / N) / nrhs;
+        return (sys[2 * q] & 1) ? __ldcs(xa + e) : __ldcs(xb + e);
+    };
     size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     for (; e + 3 * stride < n; e += 4 * stride) {   // four loads in flight per thread
         float4 v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldcs(x + e + q * stride);
+        for (int q = 0; q < 4; ++q) v[q] = at(e + q * stride);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const double re = pair_to_double(v[q].x, v[q].z), im = pair_to_double(v[q].y, v[q].w);
@@ -300,7 +317,7 @@ __global__ void refine_finish_kernel(size_t n, const float4 *xa, const float4 *x
         }
     }
     for (; e < n; e += stride) {
-        const float4 v = x[e];
+        const float4 v = at(e);
         const double re = pair_to_double(v.x, v.z), im = pair_to_double(v.y, v.w);
         X[e] = make_double2(re, conj ? -im : im);
     }
@@ -342,9 +359,9 @@ cudaError_t launch_refine_update(const GridGeom &g, int n_sys, int nrhs, const f
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_finish(size_t n, const float4 *xa, const float4 *xb, const RefineState *state, int conj,
-                                 double2 *X, cudaStream_t st) {
-    HELM_TRACED(K_REFFINISH, st, (refine_finish_kernel<<<flat_blocks(n), 256, 0, st>>>(n, xa, xb, state, conj, X)));
+cudaError_t launch_refine_finish(size_t n, int N, int nrhs, const float4 *xa, const float4 *xb,
+                                 const RefineState *state, int conj, double2 *X, cudaStream_t st) {
+    HELM_TRACED(K_REFFINISH, st, (refine_finish_kernel<<<flat_blocks(n), 256, 0, st>>>(n, N, nrhs, xa, xb, state, conj, X)));
     return cudaGetLastError();
 }
 

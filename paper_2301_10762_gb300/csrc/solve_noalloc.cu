@@ -103,10 +103,10 @@ extern "C" helm_status helm_solve_noalloc(helm_factor_t *f, int32_t nrhs, const 
     const size_t p_bytes = mixed ? align256(cols * N * sizeof(float4)) : 0;   // bd, xa, xb
     const size_t v_bytes = mixed ? align256(cols * N * sizeof(float2)) : 0;   // r32, y
     const size_t n_bytes = align256(cols * 2 * sizeof(double));
-    const size_t s_bytes = mixed ? align256(sizeof(RefineState)) : 0;
+    const size_t s_bytes = mixed ? align256(refine_state_bytes(n_sys)) : 0;
     if (cols > kMaxCols || 3 * p_bytes + 2 * v_bytes + n_bytes + s_bytes > kScratchBytes) {
         helm_set_msg("helm_solve_noalloc: problem larger than the fixed working array "
-                     "(32 MiB: n_omega*nrhs*N*64 bytes plus norms and 256 bytes, at most 16384 columns)");
+                     "(32 MiB: n_omega*nrhs*N*64 bytes plus norms and the refinement state, at most 16384 columns)");
         return HELM_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_mu);

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int m0 = blockIdx.x * ZG_BM, n0 = blockIdx.y * NT;
     const int ks = a.ksplit, kpart = (int)(blockIdx.z % (unsigned)ks);   // split-K part of this CTA
     const int* task = a.tasks + (size_t)(blockIdx.z / (unsigned)ks) * 8;
+    if (a.sys_frozen && a.sys_frozen[2 * (task[7] / a.sys_div)]) return;   // its system needs no correction
     const uint32_t smem0 = (smem_u32(zg_smem_raw) + 1023u) & ~1023u;
 
     // active terms (a term whose A index is negative is absent)
@@ -376,6 +377,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
 __global__ void zsplit_reduce_kernel(ZGemmArgs a) {
     if (a.skip && *a.skip) return;   // the GEMM itself was skipped
     const int *task = a.tasks + (size_t)blockIdx.y * 8;
+    if (a.sys_frozen && a.sys_frozen[2 * (task[7] / a.sys_div)]) return;
     const long long mn = (long long)a.M * a.N;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mn) return;
