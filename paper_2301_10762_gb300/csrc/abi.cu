@@ -423,13 +423,13 @@ helm_status mixed_refine(const helm_factor_t *f, int nrhs, const double2 *B, dou
     // (in the pair phase a system whose columns are all at rtol is frozen: its solve products and
     // updates are skipped; the FP64 phase corrects every column)
     auto sweep = [&](const int *skip_flag) -> cudaError_t {
+        const int *frozen = skip_flag ? refine_sys(w.state) + 1 : nullptr;
         if (f->use_bcr) {
-            const int *frozen = skip_flag ? refine_sys(w.state) + 1 : nullptr;
             const helm_status bs = bcr_solve(f, nrhs, w.r32, w.y, skip_flag, frozen);
             return bs == HELM_OK ? cudaSuccess : cudaErrorLaunchFailure;
         }
         return launch_line_sweep<float>(g, n_sys, nrhs, (const float2 *)f->G, w.r32, nullptr, w.y, 0, rchunk,
-                                        op->status, op->st, f->mid, skip_flag);
+                                        op->status, op->st, f->mid, skip_flag, frozen);
     };
     RefineState hs{};
     int enq = 0, batch = std::max(1, std::min(f->last_iters.load(std::memory_order_relaxed), max_iter));

@@ -30,10 +30,11 @@ cudaError_t launch_line_factor(const GridGeom &g, int n_sys, const double2 *diag
 // ---- sweep.cu
 // B in the working precision; TG = double writes X (conjugated if conj), TG = float writes Y.
 // skip (optional, device): nonzero when the launch runs makes it do nothing.
+// frozen (optional, device): frozen[2*sys] nonzero leaves system sys untouched (Y not written).
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
                               double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid,
-                              const int *skip = nullptr);
+                              const int *skip = nullptr, const int *frozen = nullptr);
 // FP64 residual B - A X (A^H X for conj), norms[col] += (||R||^2, ||B||^2); R32 = conj?(R) in FP32 if given
 cudaError_t launch_residual(const GridGeom &g, int n_sys, int nrhs, const double2 *diag, const double2 *B,
                             const double2 *X, float2 *R32, double *norms, int conj, cudaStream_t st);

@@ -41,6 +41,7 @@ template <typename TG> struct SweepArgs {
     int conj;            // FP64 path: B and X conjugated (adjoint solve)
     int *status;
     const int *skip;     // optional: nonzero -> the launch does nothing (refinement finished)
+    const int *frozen;   // optional: frozen[2*sys] nonzero -> system sys is left alone (converged)
     uint32_t tries;      // polls of a bounded mbarrier wait before it gives up
 };
 
@@ -143,7 +144,7 @@ constexpr int PP_KC = 32;      // K chunk
 template <typename TG>
 __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nrhs, const cx_t<TG> *G,
                                                              const cx_t<TG> *B, cx_t<TG> *Y, int conj,
-                                                             const int *skip) {
+                                                             const int *skip, const int *frozen) {
     using V = cx_t<TG>;
     if (skip && *skip) return;
     const int nx = g.nx, nz = g.nz, N = nx * nz;
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(128) line_gb_prepass_kernel(GridGeom g, int nr
     const int rt = bid % n_rt; bid /= n_rt;
     const int i = bid % nx;
     const int sys = bid / nx;
+    if (frozen && frozen[2 * sys]) return;
     const int q0 = ch * PP_RHS, Rc = min(PP_RHS, nrhs - q0);
     const int r0 = rt * PP_ROWS, nrows = min(PP_ROWS, nz - r0);
     constexpr int KP = PP_KC + 1;   // padded row stride (complex elements)
@@ -365,6 +367,8 @@ __global__ void __launch_bounds__(SW_THREADS) line_sweep_kernel(SweepArgs<TG> a)
     // a refinement that has already finished leaves the rest of its enqueued sweeps empty; every
     // CTA reads the same flag (written by an earlier launch) and leaves before any cluster sync
     if (a.skip && *a.skip) return;
+    // a converged system: every CTA of the cluster works on the same system and leaves together
+    if (a.frozen && a.frozen[2 * sys]) return;
     if (tid == 0) {
         for (int b = 0; b < 4; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init_cluster();
@@ -854,7 +858,7 @@ template <typename TG> SweepFn<TG> sweep_mma_fn(int MT, int KP, bool fm) {
 template <typename TG>
 cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t<TG> *G, const cx_t<TG> *B,
                               double2 *X, cx_t<TG> *Y, int conj, int rchunk, int *status, cudaStream_t st, int mid,
-                              const int *skip) {
+                              const int *skip, const int *frozen) {
     const int nz = g.nz;
     const size_t vsz = sizeof(cx_t<TG>);
     const int teams = (mid < g.nx - 1) ? 2 : 1;
@@ -948,12 +952,12 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
         }
         if (!mma) {   // CUDA-core sweep: Y_i = G_i b_i for all lines first
             const long blocks = (long)n_sys * g.nx * ((nz + PP_ROWS - 1) / PP_ROWS) * ((nrhs + PP_RHS - 1) / PP_RHS);
-            HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj, skip)));
+            HELM_TRACED(K_GBPRE, st, (line_gb_prepass_kernel<TG><<<(unsigned)blocks, 128, 0, st>>>(g, nrhs, G, B, Y, conj, skip, frozen)));
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
         const int n_chunks = (nrhs + R - 1) / R;
-        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status, skip, wait_tries()};
+        SweepArgs<TG> a{g, nrhs, R, cs, n_chunks, pf, tpo, mid, teams, G, B, X, Y, conj, status, skip, frozen, wait_tries()};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(n_sys * n_chunks * csz, 1, 1);
         cfg.blockDim = dim3(SW_THREADS, 1, 1);
@@ -974,9 +978,10 @@ cudaError_t launch_line_sweep(const GridGeom &g, int n_sys, int nrhs, const cx_t
 
 template cudaError_t launch_line_sweep<double>(const GridGeom &, int, int, const double2 *, const double2 *,
                                                double2 *, double2 *, int, int, int *, cudaStream_t, int,
-                                               const int *);
+                                               const int *, const int *);
 template cudaError_t launch_line_sweep<float>(const GridGeom &, int, int, const float2 *, const float2 *,
-                                              double2 *, float2 *, int, int, int *, cudaStream_t, int, const int *);
+                                              double2 *, float2 *, int, int, int *, cudaStream_t, int, const int *,
+                                              const int *);
 
 
 // ------------------------------------------------------------------ FP64 residual
