@@ -173,14 +173,16 @@ __device__ __forceinline__ double nan_max(double a, double b) { return (isnan(a)
 // Stopping test of the pair phase, one block: rel = max over columns of sqrt(rr / bb) (bb = 0: 0 if
 // rr = 0 else inf; a non-finite bb or rr: NaN, which stops the loop unconverged); record it and
 // decide; rr = 0 again for the next update.  The norms were accumulated by atomics of other
-// blocks, so they are read from L2.
+// blocks, so they are read from L2.  One warp per system, its lanes over the system's columns
+// (the test is the serial tail of the update, so its L2 reads are issued 32 at a time).
 __device__ void refine_stop_test(int cols, int nrhs, double *norms, RefineStop stop, RefineState *st, double *sh) {
     double mx = 0.0;
     int *sys = refine_sys(st);
     const int n_sys = cols / nrhs;
-    for (int q = threadIdx.x; q < n_sys; q += blockDim.x) {   // per system, over its columns
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, n_warps = (int)blockDim.x >> 5;
+    for (int q = wid; q < n_sys; q += n_warps) {
         double ms = 0.0;
-        for (int j = 0; j < nrhs; ++j) {
+        for (int j = lane; j < nrhs; j += 32) {
             const size_t c = (size_t)q * nrhs + j;
             const double rr = __ldcg(norms + 2 * c), bb = __ldcg(norms + 2 * c + 1);
             // a non-finite right-hand side (bb NaN or inf) or residual gives NaN: not converged
@@ -188,17 +190,13 @@ __device__ void refine_stop_test(int cols, int nrhs, double *norms, RefineStop s
             ms = nan_max(ms, rel);
             norms[2 * c] = 0.0;
         }
-        if (!sys[2 * q + 1]) {   // this pass updated the system: count it, freeze it once converged
+        for (int o = 16; o > 0; o >>= 1) ms = nan_max(ms, __shfl_xor_sync(0xffffffffu, ms, o));
+        if (lane == 0 && !sys[2 * q + 1]) {   // this pass updated the system: count it, freeze it once converged
             sys[2 * q] += 1;
             if (ms <= stop.rtol) sys[2 * q + 1] = 1;
         }
         mx = nan_max(mx, ms);   // (a frozen system's columns were not updated: 0)
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, mx, o);
-        mx = nan_max(mx, v);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) sh[wid] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
