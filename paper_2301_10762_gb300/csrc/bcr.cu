@@ -349,10 +349,28 @@ long long count_terms(const int *tasks, size_t n_tasks, int nterms) {
     return t;
 }
 
+// family counts of a launch's operands from its (host) task list, where not given
+void count_families(ZGemmArgs &a, const std::vector<int> &tasks) {
+    for (int u = 0; u < a.nterms; ++u) {
+        int ma = -1, mb = -1;
+        for (size_t t = 0; t < tasks.size(); t += 8)
+            if (tasks[t + u] >= 0) {
+                ma = std::max(ma, tasks[t + u]);
+                mb = std::max(mb, tasks[t + 3 + u]);
+            }
+        auto set = [](ZOperand &o, int mx) {
+            if (o.count == 0 && mx >= 0) o.count = o.div > 0 ? mx / o.div + 1 : mx + 1;
+        };
+        set(a.A[u], ma);
+        set(a.B[u], mb);
+    }
+}
+
 helm_status gemm(const ZGemmArgs &a0, const std::vector<int> &tasks, Plan &pl) {
     if (tasks.empty()) return HELM_OK;
     const int off = pl.add(tasks), n = (int)(tasks.size() / 8);
     ZGemmArgs a = a0;
+    count_families(a, tasks);
     a.tries = wait_tries();
     a.flops = 8.0 * a.M * a.N * a.K * (double)count_terms(tasks.data(), (size_t)n, a.nterms);
     a.part = pl.split;
@@ -707,7 +725,17 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     const BcrData &b = f->bcr;
     const cudaStream_t st = op->st;
     const long long vhi = (long long)nrhs * N;   // vectors: index system * nx + line
-    auto vec = [&](const float2 *base) { return zop(base, nz, N, nx, vhi); };
+    auto vec = [&](const float2 *base) {   // ns groups of nx line vectors
+        ZOperand o = zop(base, nz, N, nx, vhi);
+        o.count = ns;
+        return o;
+    };
+    const long long n_lines = (long long)ns * nx, n_half = (long long)ns * b.half;
+    auto blocks = [&](const float2 *base, long long count) {
+        ZOperand o = zop(base, nz2, nz);
+        o.count = count;
+        return o;
+    };
     ZGemmArgs ga;
     ga.M = nz; ga.N = nrhs; ga.K = nz;
     ga.c_col = 1;
@@ -736,7 +764,7 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     {
         ZGemmArgs a = ga;
         a.nterms = 1;
-        a.A[0] = zop(b.Dinv, nz2, nz);
+        a.A[0] = blocks(b.Dinv, n_lines);
         a.B[0] = vec(r);
         a.C = x;
         if ((s = launch(a, b.fwd[0])) != HELM_OK) return s;
@@ -747,8 +775,8 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     for (int l = 1; l < b.levels; ++l) {   // b_k -= W_a b_a + V_c b_c
         ZGemmArgs a = ga;
         a.nterms = 2;
-        a.A[0] = zop(b.W, nz2, nz); a.B[0] = vec(r); a.sign[0] = -1.f;
-        a.A[1] = zop(b.V, nz2, nz); a.B[1] = vec(r); a.sign[1] = -1.f;
+        a.A[0] = blocks(b.W, n_half); a.B[0] = vec(r); a.sign[0] = -1.f;
+        a.A[1] = blocks(b.V, n_half); a.B[1] = vec(r); a.sign[1] = -1.f;
         a.C0 = vec(r);
         a.C = r;
         if ((s = launch(a, b.fwd[l])) != HELM_OK) return s;
@@ -756,7 +784,7 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     {   // x_0 = Dinv_0 b_0
         ZGemmArgs a = ga;
         a.nterms = 1;
-        a.A[0] = zop(b.Dinv, nz2, nz);
+        a.A[0] = blocks(b.Dinv, n_lines);
         a.B[0] = vec(r);
         a.C = x;
         if ((s = launch(a, b.last)) != HELM_OK) return s;
@@ -764,9 +792,9 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
     for (int l = b.levels - 1; l >= 1; --l) {   // x_j = Dinv_j b_j - P_j x_{j-s} - Q_j x_{j+s}
         ZGemmArgs a = ga;
         a.nterms = 3;
-        a.A[0] = zop(b.Dinv, nz2, nz); a.B[0] = vec(r);
-        a.A[1] = zop(b.P, nz2, nz); a.B[1] = vec(x); a.sign[1] = -1.f;
-        a.A[2] = zop(b.Q, nz2, nz); a.B[2] = vec(x); a.sign[2] = -1.f;
+        a.A[0] = blocks(b.Dinv, n_lines); a.B[0] = vec(r);
+        a.A[1] = blocks(b.P, n_half); a.B[1] = vec(x); a.sign[1] = -1.f;
+        a.A[2] = blocks(b.Q, n_half); a.B[2] = vec(x); a.sign[2] = -1.f;
         a.C = x;
         if ((s = launch(a, b.bwd[l])) != HELM_OK) return s;
     }
@@ -778,7 +806,7 @@ helm_status bcr_solve(const helm_factor_t *f, int nrhs, float2 *r, float2 *x, co
         }
         ZGemmArgs a = ga;
         a.nterms = 1;
-        a.A[0] = zop(b.Dinv, nz2, nz); a.B[0] = vec(r); a.sign[0] = -1.f;
+        a.A[0] = blocks(b.Dinv, n_lines); a.B[0] = vec(r); a.sign[0] = -1.f;
         a.C0 = vec(x);
         a.C = x;
         if ((s = launch(a, b.bwd[0])) != HELM_OK) return s;

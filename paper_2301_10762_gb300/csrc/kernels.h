@@ -105,6 +105,9 @@ struct ZOperand {
     long long stride = 0, stride_hi = 0;
     int div = 0;
     int ld = 0;
+    // matrices of the family (div <= 0) or groups of div matrices (div > 0); 0 if not known.
+    // Launches whose operands all have a count stream them with tensor copies (narrow tiles).
+    long long count = 0;
 };
 // C_t = C0_t + sum_u sign_u A_{t,u} Bt_{t,u}^T for every task t of tasks[n_tasks][8]
 // (a_idx[3], b_idx[3], c0_idx, c_idx); a term with a negative A index is absent from its task.  A: M x K, Bt: N x K (row-major); C, C0: M x N, row-major or (c_col) column-major.

@@ -23,6 +23,7 @@
 // STAGES chunks later.  No CTA-wide barrier sits in the K loop.  The epilogue reads the
 // accumulator with tcgen05.ld into a padded tile in the (then idle) shared memory, from which
 // each warp writes whole rows (row-major C) or whole columns (column-major C), adding C0.
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is taken from the driver at run time)
 #include <stdint.h>
 
 #include <algorithm>
@@ -36,7 +37,6 @@ namespace helm {
 namespace {
 
 constexpr int ZG_PRODUCERS = 512;                 // threads of the 16 operand warps
-constexpr int ZG_THREADS = ZG_PRODUCERS + 32;     // + one warp that issues the MMAs
 constexpr int ZG_BM = 128;   // tile rows (tcgen05 M)
 constexpr int ZG_KC = 16;    // complex K per chunk: 32 floats = one 128-byte swizzle row
 
@@ -113,24 +113,69 @@ __device__ __forceinline__ long long zop_off(int idx, int div, long long stride,
     return div > 0 ? (long long)(idx / div) * stride_hi + (long long)(idx % div) * stride : (long long)idx * stride;
 }
 
-template <int NT> struct ZCfg {
+constexpr int ZG_SMEM_MAX = 232448;   // dynamic + static shared memory of one CTA (227 KB)
+
+// RING (tiles of N <= 64): a copy warp streams the raw rows of A and Bt (128 bytes of a row per
+// chunk) into a ring of SLOTS shared-memory slots with bulk copies, which complete on the slot's
+// mbarrier; the operand warps split from there.  Their proxy fence then orders their own stores
+// only: with register-held loads it also waits for every global load the warp has in flight,
+// which limits the loads to about one chunk ahead whatever the number of register sets.
+template <int NT, bool RING> struct ZCfg {
     static constexpr int NR = 2 * NT;                        // real columns of the tile (tcgen05 N)
     static constexpr int A_BYTES = ZG_BM * 128;              // one split of the A chunk
     static constexpr int B_BYTES = NR * 128;                 // one split of the expanded Bt chunk
     static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int STAGES = NT <= 64 ? 3 : 2;
+    static constexpr int STAGES = RING ? 2 : (NT <= 64 ? 3 : 2);
     static constexpr int TMEM_COLS = NR < 32 ? 32 : NR;      // a power of two >= 32
     static constexpr int A_V4 = ZG_BM * 8 / ZG_PRODUCERS;    // float4 of the A chunk per thread
     static constexpr int B_V4 = (NT * 8 + ZG_PRODUCERS - 1) / ZG_PRODUCERS;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024;   // + alignment slack
+    static constexpr int RAW_A = ZG_BM * 128;                // raw slot: A rows, then Bt rows
+    static constexpr int RAW = (ZG_BM + NT) * 128;
+    static constexpr int SLOTS_FIT = (ZG_SMEM_MAX - STAGES * STAGE - 2048) / RAW;
+    static constexpr int SLOTS = RING ? (SLOTS_FIT < 6 ? SLOTS_FIT : 6) : 1;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + (RING ? (size_t)SLOTS * RAW : 0) + 1024;   // + alignment slack
+    static constexpr int PW0 = RING ? 2 : 1;                 // first operand warp
+    static constexpr int THREADS = ZG_PRODUCERS + 32 * PW0;  // MMA warp [, copy warp], operand warps
+    // register sets of fetched chunks (register path): chunk c + NSETS - 1 is loaded while chunk
+    // c is stored
+    static constexpr int NSETS = 3;
 };
 
-template <int NT>
-__global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
-    using Cfg = ZCfg<NT>;
+// Tensor maps of the operands of a RING launch: each family of R x K complex matrices as a
+// rank-4 float tensor (2K floats of a row, then rows, matrices of a group and groups, ordered by
+// increasing stride); pos[u][role] is the dimension (1..3) of the row, in-group and group index.
+struct ZMaps {
+    CUtensorMap a[3], b[3];
+    int8_t apos[3][3], bpos[3][3];
+};
+
+// tiled tensor copy of one box into this CTA's shared memory, completing its bytes on the mbarrier
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+template <int NT, bool RING>
+__global__ void __launch_bounds__(ZCfg<NT, RING>::THREADS, 1)
+    zgemm_tc_kernel(ZGemmArgs a, const __grid_constant__ ZMaps maps) {
+    using Cfg = ZCfg<NT, RING>;
+    static_assert(!RING || Cfg::SLOTS >= 2, "the ring needs two slots");
     extern __shared__ uint8_t zg_smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];    // stage written (one arrival per operand warp)
     __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];   // stage read by its MMAs (commit)
+    __shared__ __align__(8) uint64_t raw_full[Cfg::SLOTS];     // ring slot's copies landed (RING)
+    __shared__ __align__(8) uint64_t raw_empty[Cfg::SLOTS];    // ring slot read by every operand warp (RING)
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -142,6 +187,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int* task = a.tasks + (size_t)(blockIdx.z / (unsigned)ks) * 8;
     if (a.sys_frozen && a.sys_frozen[2 * (task[7] / a.sys_div)]) return;   // its system needs no correction
     const uint32_t smem0 = (smem_u32(zg_smem_raw) + 1023u) & ~1023u;
+    const uint32_t ring0 = smem0 + (uint32_t)(Cfg::STAGES * Cfg::STAGE);   // raw slots (RING)
 
     // active terms (a term whose A index is negative is absent)
     int act[3] = {0, 0, 0}, nterms = 0;
@@ -154,12 +200,17 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     const int nchunks = (int)((long long)(kpart + 1) * nterms * nkc / ks) - cbase;
 
     const bool mma_warp = warp == 0;
-    const int ptid = tid - 32;   // operand-thread index (warps 1 .. 16)
+    const int ptid = tid - 32 * Cfg::PW0;   // operand-thread index (warps PW0 .. PW0 + 15)
     if (tid == 0) {
         for (int s = 0; s < Cfg::STAGES; ++s) {
             mbar_init(&full_bar[s], ZG_PRODUCERS / 32);   // one arrival per operand warp
             mbar_init(&empty_bar[s], 1);
         }
+        if (RING)
+            for (int q = 0; q < Cfg::SLOTS; ++q) {
+                mbar_init(&raw_full[q], 1);                     // the copy warp's expect_tx arrival
+                mbar_init(&raw_empty[q], ZG_PRODUCERS / 32);    // one arrival per operand warp
+            }
         mbar_init(&done_bar, 1);
         fence_mbar_init_cluster();
         s_abort = 0;
@@ -175,8 +226,8 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // ---- operand fetch of one chunk into registers (two register sets: chunk c + 2 is fetched
-    // while chunk c is stored, so that a load has two chunks of work to arrive in)
+    // ---- operand fetch of one chunk into registers (chunk c + NSETS - 1 is fetched while chunk c
+    // is stored, so that a load has NSETS - 1 chunks of work to arrive in)
     using RA = float4[Cfg::A_V4];
     using RB = float4[Cfg::B_V4];
     auto term_of = [&](int c) { const int cu = c / nkc; return cu == 0 ? act[0] : (cu == 1 ? act[1] : act[2]); };
@@ -230,12 +281,31 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         }
     };
 
+    // ---- RING: the chunk from its raw slot (rows of 128 bytes as copied) into registers
+    auto fetch_raw = [&](int c, RA &ra, RB &rb) {
+        const int k0 = ((cbase + c) % nkc) * ZG_KC;
+        const uint32_t slot = ring0 + (uint32_t)((c % Cfg::SLOTS) * Cfg::RAW);
+#pragma unroll
+        for (int i = 0; i < Cfg::A_V4; ++i) {
+            const int e = ptid + i * ZG_PRODUCERS, r = e >> 3, j = e & 7;
+            ra[i] = (m0 + r < a.M && k0 + 2 * j < a.K) ? ld_shared_v4(slot + (uint32_t)(r * 128 + j * 16))
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < Cfg::B_V4; ++i) {
+            const int e = ptid + i * ZG_PRODUCERS, n = e >> 3, j = e & 7;
+            rb[i] = (e < NT * 8 && n0 + n < a.N && k0 + 2 * j < a.K)
+                        ? ld_shared_v4(slot + (uint32_t)(Cfg::RAW_A + n * 128 + j * 16))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+
     constexpr uint32_t idesc = idesc_tf32(Cfg::NR);
     auto give_up = [&]() {
         atomicOr(a.status, ST_TIMEOUT);
         s_abort = 1;
     };
-    if (!mma_warp) {
+    if (warp >= Cfg::PW0 && !RING) {
         // operand warps: chunk c waits for its stage to be free, is split and stored, chunk c + 2
         // is fetched into the freed registers, and every warp arrives on the stage's full barrier
         // (16 arrivals complete it) without waiting for the other warps; they run up to STAGES
@@ -254,23 +324,88 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
             // next loads are issued: a proxy fence after them would wait for those loads as well
             // and expose their latency on every chunk
             fence_proxy_async_smem();
-            if (c + 2 < nchunks) fetch(c + 2, na, nb);
+            if (c + Cfg::NSETS - 1 < nchunks) fetch(c + Cfg::NSETS - 1, na, nb);
             __syncwarp();   // every lane's stores and fence before the warp's arrival
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
             return !__any_sync(0xffffffffu, *(volatile int *)&s_abort);
         };
-        // three register sets: chunk c is stored from set c mod 3 while chunk c + 2 is loaded
-        // into set (c + 2) mod 3, whose stores (chunk c - 1) have long been issued -- loading
+        // NSETS register sets: chunk c is stored from set c mod NSETS while chunk c + NSETS - 1 is
+        // loaded into set (c - 1) mod NSETS, whose stores (chunk c - 1) have been issued -- loading
         // into the set being stored would wait for the stores to read their registers
-        float4 ra0[Cfg::A_V4], rb0[Cfg::B_V4], ra1[Cfg::A_V4], rb1[Cfg::B_V4], ra2[Cfg::A_V4], rb2[Cfg::B_V4];
-        if (nchunks > 0) fetch(0, ra0, rb0);
-        if (nchunks > 1) fetch(1, ra1, rb1);
-        for (int c = 0; c < nchunks; c += 3) {
-            if (!pstep(c, ra0, rb0, ra2, rb2)) break;
-            if (c + 1 < nchunks && !pstep(c + 1, ra1, rb1, ra0, rb0)) break;
-            if (c + 2 < nchunks && !pstep(c + 2, ra2, rb2, ra1, rb1)) break;
+        constexpr int NS = Cfg::NSETS;
+        float4 ra[NS][Cfg::A_V4], rb[NS][Cfg::B_V4];
+#pragma unroll
+        for (int i = 0; i < NS - 1; ++i)
+            if (i < nchunks) fetch(i, ra[i], rb[i]);
+        bool go = true;
+        for (int c0 = 0; go && c0 < nchunks; c0 += NS) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+                if (go && c0 + i < nchunks) go = pstep(c0 + i, ra[i], rb[i], ra[(i + NS - 1) % NS], rb[(i + NS - 1) % NS]);
         }
-    } else if (lane == 0) {
+    } else if (warp >= Cfg::PW0) {
+        // RING operand warps: chunk c waits for its raw slot and its stage, is split from the
+        // slot into the stage, and the warp arrives on the stage's full barrier and on the slot's
+        // empty barrier (16 arrivals each), without waiting for the other warps
+        for (int c = 0; c < nchunks; ++c) {
+            const int s = c % Cfg::STAGES, q = c % Cfg::SLOTS;
+            bool bad = !mbar_wait_or_abort(&raw_full[q], (uint32_t)((c / Cfg::SLOTS) & 1), a.tries, &s_abort);
+            if (!bad && c >= Cfg::STAGES)
+                bad = !mbar_wait_or_abort(&empty_bar[s], (uint32_t)((c / Cfg::STAGES - 1) & 1), a.tries, &s_abort);
+            if (__any_sync(0xffffffffu, bad)) {
+                if (bad) give_up();
+                break;
+            }
+            float4 ra[Cfg::A_V4], rb[Cfg::B_V4];
+            fetch_raw(c, ra, rb);
+            store(c, s, ra, rb);
+            fence_proxy_async_smem();   // the stores, before the tensor core reads them
+            __syncwarp();               // every lane's slot reads, stores and fence before the arrivals
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&raw_empty[q])) : "memory");
+            }
+            if (__any_sync(0xffffffffu, *(volatile int *)&s_abort)) break;
+        }
+    } else if (RING && warp == 1) {
+        // RING copy warp: chunk c (a box of 128 rows of A and one of NT rows of Bt, 32 floats of K
+        // each, rows and K beyond the matrices filled with zeros) into slot c mod SLOTS once every
+        // operand warp has read the slot's previous chunk; the slot's mbarrier completes when both
+        // boxes have landed
+        int issued = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int q = c % Cfg::SLOTS;
+            if (__any_sync(0xffffffffu, *(volatile int *)&s_abort)) break;
+            if (c >= Cfg::SLOTS) {
+                const bool ok = mbar_wait_or_abort(&raw_empty[q], (uint32_t)((c / Cfg::SLOTS - 1) & 1), a.tries, &s_abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) give_up();
+                    break;
+                }
+            }
+            if (lane == 0) {
+                const int u = term_of(cbase + c), k0 = ((cbase + c) % nkc) * ZG_KC;
+                const uint32_t slot = ring0 + (uint32_t)(q * Cfg::RAW);
+                mbar_arrive_expect_tx(&raw_full[q], (uint32_t)Cfg::RAW);
+                int ca[4] = {2 * k0, 0, 0, 0}, cb[4] = {2 * k0, 0, 0, 0};
+                const int ia = task[u], ib = task[3 + u];
+                ca[maps.apos[u][0]] = m0;
+                ca[maps.apos[u][1]] = a.A[u].div > 0 ? ia % a.A[u].div : ia;
+                ca[maps.apos[u][2]] = a.A[u].div > 0 ? ia / a.A[u].div : 0;
+                cb[maps.bpos[u][0]] = n0;
+                cb[maps.bpos[u][1]] = a.B[u].div > 0 ? ib % a.B[u].div : ib;
+                cb[maps.bpos[u][2]] = a.B[u].div > 0 ? ib / a.B[u].div : 0;
+                tma_load_4d(slot, &maps.a[u], ca[0], ca[1], ca[2], ca[3], &raw_full[q]);
+                tma_load_4d(slot + Cfg::RAW_A, &maps.b[u], cb[0], cb[1], cb[2], cb[3], &raw_full[q]);
+            }
+            __syncwarp();
+            issued = c + 1;
+        }
+        // no copy may land in shared memory after the CTA has left: the last ones (one per slot)
+        // are waited for, also after an abort
+        for (int c = issued > Cfg::SLOTS ? issued - Cfg::SLOTS : 0; c < issued; ++c)
+            mbar_wait_bounded(&raw_full[c % Cfg::SLOTS], (uint32_t)((c / Cfg::SLOTS) & 1), a.tries);
+    } else if (warp == 0 && lane == 0) {
         // MMA thread: 12 MMAs per chunk (3 split products x 4 K steps), committed to the stage's
         // empty barrier; then one commit that covers every MMA issued
         for (int c = 0; c < nchunks; ++c) {
@@ -303,7 +438,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
     // a split part without chunks still owes its (zero) partial tile
     const bool zero_part = !aborted && nchunks == 0 && ks > 1;
 
-    if ((ok || zero_part) && !mma_warp) {
+    if ((ok || zero_part) && warp >= Cfg::PW0) {
         // Epilogue through shared memory (free once every MMA is complete): the operand warps
         // copy the accumulator tile from tensor memory (warp w: lanes 32 (w % 4) .. + 31, the
         // real columns of part (w - 1) / 4) into a padded [128][NT + 1] complex tile, meet, and
@@ -311,7 +446,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1) zgemm_tc_kernel(ZGemmArgs a) {
         // covers consecutive addresses whether C is row- or column-major.
         constexpr int parts = Cfg::NR >= 64 ? 4 : Cfg::NR / 16, cpp = Cfg::NR / parts, TS = NT + 1;
         float2 *T = reinterpret_cast<float2 *>(zg_smem_raw + (smem0 - smem_u32(zg_smem_raw)));
-        const int q = warp & 3, h = (warp - 1) >> 2, pw = warp - 1;
+        const int q = warp & 3, pw = warp - Cfg::PW0, h = pw >> 2;
         if (h < parts) {
             const int r = 32 * q + lane;
             for (int col = h * cpp; col < (h + 1) * cpp; col += 16) {
@@ -410,9 +545,68 @@ int num_sms() {
     return n;
 }
 
-template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
-    using Cfg = ZCfg<NT>;
-    const void *fn = (const void *)zgemm_tc_kernel<NT>;
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder (looked up once; null if the driver does not provide it)
+EncodeTiledFn tensor_map_encoder() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a family of R x K complex matrices (see ZMaps) with boxes of 32 floats x
+// box_rows rows; false if the family cannot be described (unknown count, strides that are not
+// multiples of 16 bytes) or the encoder refuses it.
+bool encode_family(CUtensorMap *m, int8_t pos[3], const ZOperand &o, int R, int K, int box_rows) {
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || !o.base || o.count <= 0 || o.ld < K) return false;
+    struct Dim { unsigned long long ext, stride; int role; };
+    Dim d[3];
+    d[0] = {(unsigned long long)R, (unsigned long long)o.ld * 8ull, 0};
+    if (o.div > 0) {
+        d[1] = {(unsigned long long)o.div, (unsigned long long)o.stride * 8ull, 1};
+        d[2] = {(unsigned long long)o.count, (unsigned long long)o.stride_hi * 8ull, 2};
+    } else {
+        d[1] = {(unsigned long long)o.count, (unsigned long long)o.stride * 8ull, 1};
+        d[2] = {1ull, 0ull, 2};
+    }
+    // dimensions of one element last, the others by increasing stride; a dimension of one
+    // element takes the stride that nests it after the previous one
+    std::stable_sort(d, d + 3, [](const Dim &x, const Dim &y) {
+        if ((x.ext == 1) != (y.ext == 1)) return y.ext == 1;
+        return x.stride < y.stride;
+    });
+    cuuint64_t dims[4] = {(cuuint64_t)2 * K, 0, 0, 0}, strides[3];
+    cuuint32_t box[4] = {32, 1, 1, 1}, estr[4] = {1, 1, 1, 1};
+    unsigned long long prev = (unsigned long long)2 * K * 4, prev_ext = 1;
+    for (int i = 0; i < 3; ++i) {
+        unsigned long long st = d[i].ext == 1 ? prev * prev_ext : d[i].stride;
+        if (st == 0 || (st & 15) || st >= (1ull << 40) || d[i].ext > (1ull << 32)) return false;
+        dims[i + 1] = d[i].ext;
+        strides[i] = st;
+        if (d[i].role == 0) box[i + 1] = (cuuint32_t)box_rows;
+        pos[d[i].role] = (int8_t)(i + 1);
+        prev = st;
+        prev_ext = d[i].ext;
+    }
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2 *>(o.base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT, bool RING> cudaError_t launch_nt(const ZGemmArgs &a, const ZMaps &maps, int n_tasks, cudaStream_t st) {
+    using Cfg = ZCfg<NT, RING>;
+    const void *fn = (const void *)zgemm_tc_kernel<NT, RING>;
     cudaError_t e = ensure_dyn_smem(fn, Cfg::SMEM);
     if (e != cudaSuccess) return e;
     // split-K where the launch fills at most half of the SMs: as many parts as keep it within one
@@ -429,7 +623,7 @@ template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStr
         if (ks >= 2) b.ksplit = (int)ks;
     }
     dim3 grid((unsigned)((a.M + ZG_BM - 1) / ZG_BM), (unsigned)((a.N + NT - 1) / NT), (unsigned)(n_tasks * b.ksplit));
-    HELM_TRACED_W(K_ZGEMM, st, a.flops, (zgemm_tc_kernel<NT><<<grid, ZG_THREADS, Cfg::SMEM, st>>>(b)));
+    HELM_TRACED_W(K_ZGEMM, st, a.flops, (zgemm_tc_kernel<NT, RING><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(b, maps)));
     if (b.ksplit > 1) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -438,6 +632,17 @@ template <int NT> cudaError_t launch_nt(const ZGemmArgs &a, int n_tasks, cudaStr
         HELM_TRACED(K_ZSPLIT, st, (zsplit_reduce_kernel<<<rg, 256, 0, st>>>(b)));
     }
     return cudaGetLastError();
+}
+
+// narrow tiles: the tensor-copy ring when every operand family has a tensor map, else the
+// register path
+template <int NT> cudaError_t launch_narrow(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
+    ZMaps maps{};
+    bool ring = true;
+    for (int u = 0; ring && u < a.nterms; ++u)
+        ring = encode_family(&maps.a[u], maps.apos[u], a.A[u], a.M, a.K, ZG_BM) &&
+               encode_family(&maps.b[u], maps.bpos[u], a.B[u], a.N, a.K, NT);
+    return ring ? launch_nt<NT, true>(a, maps, n_tasks, st) : launch_nt<NT, false>(a, maps, n_tasks, st);
 }
 
 }  // namespace
@@ -451,10 +656,10 @@ cudaError_t launch_zgemm(const ZGemmArgs &a, int n_tasks, cudaStream_t st) {
             (a.A[u].stride_hi & 1) || (a.B[u].stride_hi & 1) || ((uintptr_t)a.A[u].base & 15) ||
             ((uintptr_t)a.B[u].base & 15))
             return cudaErrorInvalidValue;
-    if (a.N <= 16) return launch_nt<16>(a, n_tasks, st);
-    if (a.N <= 32) return launch_nt<32>(a, n_tasks, st);
-    if (a.N <= 64) return launch_nt<64>(a, n_tasks, st);
-    return launch_nt<128>(a, n_tasks, st);
+    if (a.N <= 16) return launch_narrow<16>(a, n_tasks, st);
+    if (a.N <= 32) return launch_narrow<32>(a, n_tasks, st);
+    if (a.N <= 64) return launch_narrow<64>(a, n_tasks, st);
+    return launch_nt<128, false>(a, ZMaps{}, n_tasks, st);
 }
 
 }  // namespace helm

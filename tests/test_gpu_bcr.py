@@ -21,7 +21,8 @@ def _c64(rng, *shape):
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 128), (256, 256, 256), (96, 16, 160), (200, 40, 50), (130, 130, 34)])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 128), (256, 256, 256), (96, 16, 160), (200, 40, 50), (130, 130, 34),
+                                   (64, 24, 200)])
 def test_zgemm_matches_complex128_product(M, N, K):
     rng = np.random.default_rng(M + N + K)
     b = 3
