@@ -45,6 +45,7 @@
 
 #include "abi_internal.h"
 #include "kernels.h"
+#include "mma_tf32.cuh"
 #include "pivot16.cuh"
 #include "trace.h"
 
@@ -202,6 +203,133 @@ __global__ void __launch_bounds__(INV_THREADS, 1) zinv_base_kernel(InvArgs a) {
     for (int e = tid; e < n * n; e += INV_THREADS) {
         const int r = e / n, cc = e % n;
         X[(size_t)r * a.ldo + cc] = W[(size_t)r * ldw + cc];
+    }
+    if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
+}
+
+// X = M^{-1} of one 128 x 128 block per CTA: the block Gauss-Jordan of zinv_base_kernel with
+// the rank-16 update of each block step on the tensor pipe.  With R'[u][c] = (P W[K, :])[u][c]
+// off the pivot columns K and P[u][c - k0] on them, one product does the whole step:
+//     W <- W' + A' R',  W' = W with the rows and columns K zeroed,
+//     A'[r][u] = -W[r][k0 + u] off the pivot rows, delta(r - k0, u) on them,
+// as 3xTF32 mma.sync tiles (complex as real: an m16 x n8 tile for the real parts of eight
+// columns and one for the imaginary parts).  Warp w updates rows 16 (w mod 8) .. + 15, columns
+// 64 (w / 8) .. + 63.  Row strides keep the 16- and 8-byte fragment loads free of bank conflicts.
+constexpr int Z128_LDW = 136;   // W: rows g and g + 1 sixteen words apart
+constexpr int Z128_PS = 20;     // staged column panel U[r][u] and R'^T[c][u]
+size_t zinv128_smem_bytes() {
+    return sizeof(float2) * ((size_t)128 * Z128_LDW + 2 * (size_t)128 * Z128_PS + PIV * PIV);
+}
+
+__global__ void __launch_bounds__(INV_THREADS, 1) zinv128_kernel(InvArgs a) {
+    extern __shared__ __align__(16) unsigned char inv_smem[];
+    constexpr int n = 128, LDW = Z128_LDW, PS = Z128_PS;
+    float2 *W = reinterpret_cast<float2 *>(inv_smem);   // [128][LDW]
+    float2 *U = W + (size_t)n * LDW;                       // [128][PS]: column panel W[:, K]
+    float2 *RT = U + (size_t)n * PS;                       // [128][PS]: R'^T
+    float2 *P = RT + (size_t)n * PS;                       // [16][16]: pivot-block inverse
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int *ix = a.idx + 2 * (size_t)blockIdx.x;
+    const float2 *M = a.in.base + op_off(ix[0], a.in.div, a.in.stride, a.in.stride_hi);
+    float2 *X = a.out + op_off(ix[1], a.out_div, a.out_stride, a.out_stride_hi);
+    if (tid == 0) s_bad = 0;
+    for (int e = tid; e < n * n / 2; e += INV_THREADS) {   // two entries per float4
+        const int r = (2 * e) / n, c = (2 * e) % n;
+        *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) =
+            *reinterpret_cast<const float4 *>(M + (size_t)r * a.in.ld + c);
+    }
+    __syncthreads();
+    const int mw = warp & 7, cw = warp >> 3;
+    const int r0 = 16 * mw + g, r1 = r0 + 8;
+    for (int kb_i = 0; kb_i < n / PIV; ++kb_i) {
+        const int k0 = kb_i * PIV;
+        for (int e = tid; e < n * PIV; e += INV_THREADS) {
+            const int r = e >> 4, u = e & 15;
+            U[r * PS + u] = W[(size_t)r * LDW + k0 + u];
+        }
+        if (warp == 0 && !warp_invert16<float>(W + (size_t)k0 * LDW + k0, LDW, PIV, P) && lane == 0) s_bad = 1;
+        __syncthreads();
+        for (int e = tid; e < n * PIV; e += INV_THREADS) {   // R'^T[c][u], u = e / 128
+            const int u = e >> 7, c = e & 127;
+            float2 acc;
+            if (c >= k0 && c < k0 + PIV) {
+                acc = P[u * PIV + (c - k0)];
+            } else {
+                acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int v = 0; v < PIV; ++v) cfma(acc, P[u * PIV + v], W[(size_t)(k0 + v) * LDW + c]);
+            }
+            RT[c * PS + u] = acc;
+        }
+        __syncthreads();
+        // A' fragments of the warp's 16 rows for the four k-steps (four complex u each; slot t
+        // holds Re, slot t + 4 Im of column u = 4s + t)
+        const bool pivot_rows = mw == kb_i;
+        uint32_t ah[4][4], al[4][4];
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            const int u = 4 * st + t;
+            float2 x0, x1;
+            if (pivot_rows) {
+                x0 = make_float2(r0 - k0 == u ? 1.f : 0.f, 0.f);
+                x1 = make_float2(r1 - k0 == u ? 1.f : 0.f, 0.f);
+            } else {
+                x0 = U[r0 * PS + u];
+                x1 = U[r1 * PS + u];
+                x0 = make_float2(-x0.x, -x0.y);
+                x1 = make_float2(-x1.x, -x1.y);
+            }
+            split_tf32(x0.x, ah[st][0], al[st][0]);
+            split_tf32(x1.x, ah[st][1], al[st][1]);
+            split_tf32(x0.y, ah[st][2], al[st][2]);
+            split_tf32(x1.y, ah[st][3], al[st][3]);
+        }
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float re[4][4], im[4][4];   // [group of 8 columns][fragment]
+#pragma unroll
+            for (int gi = 0; gi < 4; ++gi) {
+                const int c = 64 * cw + 32 * half + 8 * gi + 2 * t;
+                const bool zero = pivot_rows || (c >= k0 && c < k0 + PIV);
+                const float4 w0 = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                       : *reinterpret_cast<const float4 *>(W + (size_t)r0 * LDW + c);
+                const float4 w1 = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                       : *reinterpret_cast<const float4 *>(W + (size_t)r1 * LDW + c);
+                re[gi][0] = w0.x; im[gi][0] = w0.y; re[gi][1] = w0.z; im[gi][1] = w0.w;
+                re[gi][2] = w1.x; im[gi][2] = w1.y; re[gi][3] = w1.z; im[gi][3] = w1.w;
+            }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+#pragma unroll
+                for (int gi = 0; gi < 4; ++gi) {
+                    // B: column g of the group, rows u = 4 st + t: Re tile (Re R', -Im R'),
+                    // Im tile (Im R', Re R')
+                    const float2 b = RT[(64 * cw + 32 * half + 8 * gi + g) * PS + 4 * st + t];
+                    uint32_t xr_h, xr_l, xi_h, xi_l;
+                    split_tf32(b.x, xr_h, xr_l);
+                    split_tf32(b.y, xi_h, xi_l);
+                    const uint32_t nxi_h = xi_h ^ 0x80000000u, nxi_l = xi_l ^ 0x80000000u;
+                    mma_tf32(re[gi], ah[st], xr_h, nxi_h);
+                    mma_tf32(re[gi], ah[st], xr_l, nxi_l);
+                    mma_tf32(re[gi], al[st], xr_h, nxi_h);
+                    mma_tf32(im[gi], ah[st], xi_h, xr_h);
+                    mma_tf32(im[gi], ah[st], xi_l, xr_l);
+                    mma_tf32(im[gi], al[st], xi_h, xr_h);
+                }
+            }
+#pragma unroll
+            for (int gi = 0; gi < 4; ++gi) {
+                const int c = 64 * cw + 32 * half + 8 * gi + 2 * t;
+                *reinterpret_cast<float4 *>(W + (size_t)r0 * LDW + c) = make_float4(re[gi][0], im[gi][0], re[gi][1], im[gi][1]);
+                *reinterpret_cast<float4 *>(W + (size_t)r1 * LDW + c) = make_float4(re[gi][2], im[gi][2], re[gi][3], im[gi][3]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n / 2; e += INV_THREADS) {
+        const int r = (2 * e) / n, c = (2 * e) % n;
+        *reinterpret_cast<float4 *>(X + (size_t)r * a.ldo + c) = *reinterpret_cast<const float4 *>(W + (size_t)r * LDW + c);
     }
     if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
 }
@@ -403,13 +531,19 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
     helm_status s;
     if (n <= INV_MAX) {
         const int off = pl.add(pairs);
-        const size_t smem = inv_smem_bytes(n);
-        cudaError_t e = ensure_dyn_smem((const void *)zinv_base_kernel, smem);
+        // 128 x 128 blocks on 16-byte boundaries (two complex entries per access): the kernel
+        // with the tensor-pipe update
+        const bool t128 = n == 128 && ((uintptr_t)in.base & 15) == 0 && ((uintptr_t)out.base & 15) == 0 &&
+                          (in.ld & 1) == 0 && (out.ld & 1) == 0 && (in.stride & 1) == 0 && (out.stride & 1) == 0;
+        const size_t smem = t128 ? zinv128_smem_bytes() : inv_smem_bytes(n);
+        const void *fn = t128 ? (const void *)zinv128_kernel : (const void *)zinv_base_kernel;
+        cudaError_t e = ensure_dyn_smem(fn, smem);
         if (e != cudaSuccess) { helm_set_error("bcr: block inversion", e); return HELM_ECUDA; }
         InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, nullptr, status};
-        pl.ops.push_back([a, off, count, smem, st](const int *dev) mutable -> helm_status {
+        pl.ops.push_back([a, off, count, smem, st, t128](const int *dev) mutable -> helm_status {
             a.idx = dev + off;
-            HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
+            if (t128) HELM_TRACED(K_ZINV, st, (zinv128_kernel<<<count, INV_THREADS, smem, st>>>(a)));
+            else HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
             const cudaError_t e2 = cudaGetLastError();
             if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
             return HELM_OK;

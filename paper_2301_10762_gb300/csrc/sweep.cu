@@ -20,6 +20,7 @@
 #include <mutex>
 #include <stdlib.h>
 #include "kernels.h"
+#include "mma_tf32.cuh"
 #include "trace.h"
 
 namespace helm {
@@ -226,23 +227,6 @@ __host__ __device__ __forceinline__ int padded_mma(int n) {
     while (p % 16 != 8) p += 2;
     return p;
 }
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
-}
-// d += A (16 x 8, row) * B (8 x 8, col), TF32 inputs, FP32 accumulate
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // FMA product of one lane: facc[q] += sum_p G(row, c_p) t_q(c_p) over its 4*KP complex columns
 // c_p = c0 .. c0 + 4*KP - 1 (held in g, two per float4), for the first NQ right-hand sides of
 // the line buffer tv ([rhs][nzp], complex FP32); rhs >= nq and columns >= nz read as zero.  The

@@ -51,6 +51,24 @@ def test_zinv_matches_numpy_inverse(n):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("n", [128, 256])
+def test_zinv_needs_pivoting(n):
+    """Complex symmetric blocks with a small shift (zero and tiny diagonal entries, so the
+    Gauss-Jordan pivots are chosen off the diagonal), against numpy's inverse; the bound scales
+    with the condition number."""
+    rng = np.random.default_rng(n + 7)
+    b = 3
+    M = _c64(rng, b, n, n)
+    M = ((M + np.transpose(M, (0, 2, 1))) / 2 + 0.5 * np.sqrt(n) * np.eye(n)).astype(np.complex64)
+    M[:, np.arange(0, n, 5), np.arange(0, n, 5)] = 0.0
+    M64 = M.astype(np.complex128)
+    X = hm.helm_zinv_batched(torch.tensor(M, device="cuda")).cpu().numpy().astype(np.complex128)
+    for i in range(b):
+        ref = np.linalg.inv(M64[i])
+        err = np.linalg.norm(X[i] - ref) / np.linalg.norm(ref)
+        assert err <= 2e-6 * np.linalg.cond(M64[i]), (i, err, np.linalg.cond(M64[i]))
+
+
 def _oracle_cols(nx, nz, m, om, B):
     g = H.Grid(nx, nz)
     return [H.Factor(H.helmholtz_matrix(g, m, w)).solve(B[q]) for q, w in enumerate(om)]
