@@ -338,6 +338,60 @@ size_t inv_smem_bytes(int n) {
     return sizeof(float2) * ((size_t)n * (n + 1) + (size_t)n * PIV + (size_t)PIV * (n + 1) + PIV * PIV);
 }
 
+// Inverse of complex symmetric tridiagonal blocks D (the level-0 line blocks) of size
+// n = n1 + n2 by the 2 x 2 block inverse, whose off-diagonal block D21 = c e_0 e_{n1-1}^T has a
+// single entry c = D[n1][n1 - 1]: with x = X11[:, n1 - 1] (X11 = D11^{-1}),
+//     S = D22 - c^2 X11[n1-1][n1-1] e_0 e_0^T,  X22 = S^{-1},
+//     X12 = -c x X22[0, :],  X21 = X12^T,  X11 <- X11 + c^2 X22[0][0] x x^T,
+// so that the four products of the general case are rank-one updates.  Blocks: in / out at
+// base + idx * stride, rows ld apart; pairs [count][2] (input index, output index).
+__global__ void tri_schur_kernel(int n, int n1, const float2 *in, float2 *out, long long stride, int ld,
+                                 const int *pairs) {
+    const float2 *D = in + (long long)pairs[2 * blockIdx.x] * stride;
+    float2 *X = out + (long long)pairs[2 * blockIdx.x + 1] * stride;
+    const int n2 = n - n1;
+    const float2 c = D[(long long)n1 * ld + n1 - 1];
+    const float2 x = X[(long long)(n1 - 1) * ld + n1 - 1];
+    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+        const int i = e / n2, j = e % n2;
+        float2 v = D[(long long)(n1 + i) * ld + n1 + j];
+        if (e == 0) {   // v -= c^2 x
+            const float2 c2 = cmul(c, c);
+            cfms(v, c2, x);
+        }
+        X[(long long)(n1 + i) * ld + n1 + j] = v;
+    }
+}
+
+__global__ void __launch_bounds__(512) tri_rank1_kernel(int n, int n1, const float2 *in, float2 *out, long long stride,
+                                                        int ld, const int *pairs) {
+    __shared__ float2 xs[INV_MAX], rs[INV_MAX];
+    const float2 *D = in + (long long)pairs[2 * blockIdx.x] * stride;
+    float2 *X = out + (long long)pairs[2 * blockIdx.x + 1] * stride;
+    const int n2 = n - n1;
+    const float2 c = D[(long long)n1 * ld + n1 - 1];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) xs[i] = X[(long long)i * ld + n1 - 1];
+    for (int j = threadIdx.x; j < n2; j += blockDim.x) rs[j] = X[(long long)n1 * ld + n1 + j];
+    __syncthreads();
+    const float2 c2d = cmul(cmul(c, c), rs[0]);           // c^2 X22[0][0]
+    const float2 mc = make_float2(-c.x, -c.y);
+    for (int e = threadIdx.x; e < n1 * n; e += blockDim.x) {   // rows 0 .. n1 - 1: X11 and X12
+        const int i = e / n, j = e % n;
+        float2 *w = X + (long long)i * ld + j;
+        if (j < n1) {
+            float2 v = *w;
+            cfma(v, cmul(c2d, xs[i]), xs[j]);
+            *w = v;
+        } else {
+            *w = cmul(cmul(mc, xs[i]), rs[j - n1]);
+        }
+    }
+    for (int e = threadIdx.x; e < n2 * n1; e += blockDim.x) {   // rows n1 .. n - 1, columns 0 .. n1 - 1: X21
+        const int i = e / n1, j = e % n1;
+        X[(long long)(n1 + i) * ld + j] = cmul(cmul(mc, rs[i]), xs[j]);
+    }
+}
+
 // out[idx_out] = in[idx_in]^T for n x n complex blocks (32 x 32 tiles through shared memory)
 __global__ void ztranspose_kernel(int n, const float2 *in, float2 *out, long long stride_in, long long stride_out,
                                   const int *idx) {
@@ -607,6 +661,42 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
     return HELM_OK;
 }
 
+// out[p.second] = in[p.first]^{-1} for complex symmetric tridiagonal n x n blocks, 128 < n <= 256
+// (in and out with the same stride and row length): two base inversions and two rank-one
+// kernels (tri_schur_kernel, tri_rank1_kernel)
+helm_status invert_tridiag_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl) {
+    const int count = (int)(pairs.size() / 2);
+    if (count == 0) return HELM_OK;
+    if (n <= INV_MAX || n > 2 * INV_MAX || in.stride != out.stride || in.ld != out.ld)
+        return invert_blocks(n, in, out, pairs, status, pl);
+    const int n1 = INV_MAX, n2 = n - n1;
+    const cudaStream_t st = pl.st;
+    helm_status s;
+    if ((s = invert_blocks(n1, in, out, pairs, status, pl)) != HELM_OK) return s;   // X11 = D11^{-1}
+    const int off = pl.add(pairs);
+    const float2 *ib = in.base;
+    float2 *ob = out.base;
+    const long long stride = in.stride;
+    const int ld = in.ld;
+    pl.ops.push_back([=](const int *dev) -> helm_status {   // S = D22 - c^2 X11[n1-1][n1-1] e0 e0^T
+        HELM_TRACED(K_ZINV, st, (tri_schur_kernel<<<count, 256, 0, st>>>(n, n1, ib, ob, stride, ld, dev + off)));
+        const cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
+        return HELM_OK;
+    });
+    std::vector<int> self(pairs.size());
+    for (int t = 0; t < count; ++t) self[2 * t] = self[2 * t + 1] = pairs[2 * t + 1];
+    const Fam X22 = out.sub(n1, n1);
+    if ((s = invert_blocks(n2, X22, X22, self, status, pl)) != HELM_OK) return s;
+    pl.ops.push_back([=](const int *dev) -> helm_status {   // X12, X21, X11 from rank-one updates
+        HELM_TRACED(K_ZINV, st, (tri_rank1_kernel<<<count, 512, 0, st>>>(n, n1, ib, ob, stride, ld, dev + off)));
+        const cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
+        return HELM_OK;
+    });
+    return HELM_OK;
+}
+
 helm_status transpose_blocks(int n, const float2 *in, float2 *out, long long stride, const std::vector<int> &pairs,
                              Plan &pl) {
     const int count = (int)(pairs.size() / 2);
@@ -685,7 +775,10 @@ helm_status bcr_factor(helm_factor_t *f) {
         std::vector<int> inv_pairs, tv, tw, tp, tq, td, tl, tu;
         for (int sy = 0; sy < ns; ++sy)
             for (int j = sp; j < nx; j += 2 * sp) inv_pairs.insert(inv_pairs.end(), {sy * nx + j, sy * nx + j});
-        if ((s = invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl)) != HELM_OK) return s;
+        // level 0: the line blocks are still tridiagonal
+        s = sp == 1 ? invert_tridiag_blocks(nz, fD, fDinv, inv_pairs, op->status, pl)
+                    : invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl);
+        if (s != HELM_OK) return s;
         if (sp == 1) {
             float2 *D0 = Dc, *Di = b.Dinv, *L1 = Ln, *U1 = Un;
             const Coup cp = coup_of(g);

@@ -74,7 +74,8 @@ def _oracle_cols(nx, nz, m, om, B):
     return [H.Factor(H.helmholtz_matrix(g, m, w)).solve(B[q]) for q, w in enumerate(om)]
 
 
-@pytest.mark.parametrize("nx,nz,nrhs", [(48, 40, 3), (64, 64, 8), (37, 32, 5), (33, 50, 2), (128, 128, 16)])
+@pytest.mark.parametrize("nx,nz,nrhs", [(48, 40, 3), (64, 64, 8), (37, 32, 5), (33, 50, 2), (128, 128, 16),
+                                          (20, 200, 2)])
 def test_bcr_solve_matches_oracle(nx, nz, nrhs):
     rng = np.random.default_rng(nx * nz)
     c = 1.0 + 0.5 * W.gaussian_smooth(rng.uniform(0, 1, (nx, nz)), 2.0)
