@@ -71,9 +71,10 @@ Coup coup_of(const GridGeom &g) {
 
 // dense D_i of every line and system: the diagonal of A and the vertical couplings next to it;
 // one float4 (two complex entries of a row) per thread and step
-__global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2 *D) {
+__global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2 *D, int even_only) {
     const int nz = g.nz, nx = g.nx;
     const int i = blockIdx.y, s = blockIdx.z;
+    if (even_only && (i & 1)) return;   // odd lines: inverted from the diagonal directly
     const float cz = cp.cz(i, nx);
     float4 *Di = reinterpret_cast<float4 *>(D + ((size_t)s * nx + i) * nz * nz);
     const double2 *dg = diag + ((size_t)s * nx + i) * nz;
@@ -117,6 +118,36 @@ __global__ void bcr_level0_kernel(GridGeom g, Coup cp, float2 *D, const float2 *
     }
 }
 
+// Implicit tridiagonal input of the block inversion (the level-0 line blocks, never formed in
+// memory): rows and columns row0 .. row0 + n - 1 of the block of line idx (input index = system
+// * nx + line) with A's diagonal diag[idx][.] and the line's vertical coupling; with corr, entry
+// (0, 0) less cz^2 X[corr_off] (X the output block: the Schur complement of the lower half).
+struct TriIn {
+    const double2 *diag = nullptr;   // [idx][nz]; nullptr: the input is a dense block
+    int nz = 0, nx = 0, row0 = 0;
+    float cz_in = 0.f, cz_edge = 0.f;
+    int corr = 0;
+    long long corr_off = 0;
+    __device__ __forceinline__ float cz(int idx) const {
+        const int line = idx % nx;
+        return (line == 0 || line == nx - 1) ? cz_edge : cz_in;
+    }
+    // entry (r, c) of the block of input idx; x: the output block (for the corrected corner)
+    __device__ __forceinline__ float2 entry(int idx, int r, int c, const float2 *x) const {
+        if (r == c) {
+            float2 v = to_c64(diag[(long long)idx * nz + row0 + r]);
+            if (corr && r == 0) {
+                const float c2 = cz(idx) * cz(idx);
+                const float2 w = x[corr_off];
+                v.x -= c2 * w.x;
+                v.y -= c2 * w.y;
+            }
+            return v;
+        }
+        return (r - c == 1 || c - r == 1) ? make_float2(cz(idx), 0.f) : make_float2(0.f, 0.f);
+    }
+};
+
 struct InvArgs {
     int n;
     ZOperand in;                 // row-major, ld = in.ld
@@ -125,6 +156,7 @@ struct InvArgs {
     int out_div, ldo;
     const int *idx;              // [count][2]: input index, output index
     int *status;
+    TriIn tri;                   // tri.diag set: implicit tridiagonal input instead of `in`
 };
 
 __device__ __forceinline__ long long op_off(int idx, int div, long long stride, long long stride_hi) {
@@ -148,7 +180,7 @@ __global__ void __launch_bounds__(INV_THREADS, 1) zinv_base_kernel(InvArgs a) {
     if (tid == 0) s_bad = 0;
     for (int e = tid; e < n * n; e += INV_THREADS) {
         const int r = e / n, c = e % n;
-        W[(size_t)r * ldw + c] = M[(size_t)r * a.in.ld + c];
+        W[(size_t)r * ldw + c] = a.tri.diag ? a.tri.entry(ix[0], r, c, X) : M[(size_t)r * a.in.ld + c];
     }
     __syncthreads();
     // update mapping: thread -> column c, row group rg (rows rg, rg + ng, ...)
@@ -236,8 +268,13 @@ __global__ void __launch_bounds__(INV_THREADS, 1) zinv128_kernel(InvArgs a) {
     if (tid == 0) s_bad = 0;
     for (int e = tid; e < n * n / 2; e += INV_THREADS) {   // two entries per float4
         const int r = (2 * e) / n, c = (2 * e) % n;
-        *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) =
-            *reinterpret_cast<const float4 *>(M + (size_t)r * a.in.ld + c);
+        if (a.tri.diag) {
+            const float2 v0 = a.tri.entry(ix[0], r, c, X), v1 = a.tri.entry(ix[0], r, c + 1, X);
+            *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else {
+            *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) =
+                *reinterpret_cast<const float4 *>(M + (size_t)r * a.in.ld + c);
+        }
     }
     __syncthreads();
     const int mw = warp & 7, cw = warp >> 3;
@@ -340,36 +377,18 @@ size_t inv_smem_bytes(int n) {
 
 // Inverse of complex symmetric tridiagonal blocks D (the level-0 line blocks) of size
 // n = n1 + n2 by the 2 x 2 block inverse, whose off-diagonal block D21 = c e_0 e_{n1-1}^T has a
-// single entry c = D[n1][n1 - 1]: with x = X11[:, n1 - 1] (X11 = D11^{-1}),
+// single entry, the line's vertical coupling c: with x = X11[:, n1 - 1] (X11 = D11^{-1}),
 //     S = D22 - c^2 X11[n1-1][n1-1] e_0 e_0^T,  X22 = S^{-1},
 //     X12 = -c x X22[0, :],  X21 = X12^T,  X11 <- X11 + c^2 X22[0][0] x x^T,
-// so that the four products of the general case are rank-one updates.  Blocks: in / out at
-// base + idx * stride, rows ld apart; pairs [count][2] (input index, output index).
-__global__ void tri_schur_kernel(int n, int n1, const float2 *in, float2 *out, long long stride, int ld,
-                                 const int *pairs) {
-    const float2 *D = in + (long long)pairs[2 * blockIdx.x] * stride;
-    float2 *X = out + (long long)pairs[2 * blockIdx.x + 1] * stride;
-    const int n2 = n - n1;
-    const float2 c = D[(long long)n1 * ld + n1 - 1];
-    const float2 x = X[(long long)(n1 - 1) * ld + n1 - 1];
-    for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
-        const int i = e / n2, j = e % n2;
-        float2 v = D[(long long)(n1 + i) * ld + n1 + j];
-        if (e == 0) {   // v -= c^2 x
-            const float2 c2 = cmul(c, c);
-            cfms(v, c2, x);
-        }
-        X[(long long)(n1 + i) * ld + n1 + j] = v;
-    }
-}
-
-__global__ void __launch_bounds__(512) tri_rank1_kernel(int n, int n1, const float2 *in, float2 *out, long long stride,
-                                                        int ld, const int *pairs) {
+// so that the four products of the general case are rank-one updates (the inversions read D11
+// and S implicitly, TriIn).  Output blocks at out + idx * stride, rows ld apart; pairs
+// [count][2] (input index = system * nx + line, output index).
+__global__ void __launch_bounds__(512) tri_rank1_kernel(int n, int n1, TriIn tri, float2 *out, long long stride, int ld,
+                                                        const int *pairs) {
     __shared__ float2 xs[INV_MAX], rs[INV_MAX];
-    const float2 *D = in + (long long)pairs[2 * blockIdx.x] * stride;
     float2 *X = out + (long long)pairs[2 * blockIdx.x + 1] * stride;
     const int n2 = n - n1;
-    const float2 c = D[(long long)n1 * ld + n1 - 1];
+    const float2 c = make_float2(tri.cz(pairs[2 * blockIdx.x]), 0.f);
     for (int i = threadIdx.x; i < n1; i += blockDim.x) xs[i] = X[(long long)i * ld + n1 - 1];
     for (int j = threadIdx.x; j < n2; j += blockDim.x) rs[j] = X[(long long)n1 * ld + n1 + j];
     __syncthreads();
@@ -578,7 +597,8 @@ struct Fam {
 };
 
 // out[p.second] = in[p.first]^{-1} for every index pair, n x n blocks (may be the same matrices)
-helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl) {
+helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl,
+                          const TriIn *tri = nullptr) {
     const int count = (int)(pairs.size() / 2);
     if (count == 0) return HELM_OK;
     const cudaStream_t st = pl.st;
@@ -593,7 +613,7 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
         const void *fn = t128 ? (const void *)zinv128_kernel : (const void *)zinv_base_kernel;
         cudaError_t e = ensure_dyn_smem(fn, smem);
         if (e != cudaSuccess) { helm_set_error("bcr: block inversion", e); return HELM_ECUDA; }
-        InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, nullptr, status};
+        InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, nullptr, status, tri ? *tri : TriIn{}};
         pl.ops.push_back([a, off, count, smem, st, t128](const int *dev) mutable -> helm_status {
             a.idx = dev + off;
             if (t128) HELM_TRACED(K_ZINV, st, (zinv128_kernel<<<count, INV_THREADS, smem, st>>>(a)));
@@ -604,6 +624,7 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
         });
         return HELM_OK;
     }
+    if (tri) return HELM_EINVAL;   // implicit input: base blocks only (invert_tridiag_blocks splits)
     const int n1 = INV_MAX * ((n / INV_MAX + 1) / 2), n2 = n - n1;
     // X11 = D11^{-1}
     if ((s = invert_blocks(n1, in, out, pairs, status, pl)) != HELM_OK) return s;
@@ -661,35 +682,34 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
     return HELM_OK;
 }
 
-// out[p.second] = in[p.first]^{-1} for complex symmetric tridiagonal n x n blocks, 128 < n <= 256
-// (in and out with the same stride and row length): two base inversions and two rank-one
-// kernels (tri_schur_kernel, tri_rank1_kernel)
-helm_status invert_tridiag_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl) {
+// out[p.second] = D^{-1} for the complex symmetric tridiagonal line blocks D given by `tri`
+// (input index = system * nx + line), n <= 256: one implicit base inversion for n <= 128; else
+// two and two rank-one kernels (tri_rank1_kernel)
+helm_status invert_tridiag_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs, int *status, Plan &pl,
+                                  const TriIn &tri) {
     const int count = (int)(pairs.size() / 2);
     if (count == 0) return HELM_OK;
-    if (n <= INV_MAX || n > 2 * INV_MAX || in.stride != out.stride || in.ld != out.ld)
-        return invert_blocks(n, in, out, pairs, status, pl);
+    if (n > 2 * INV_MAX) return HELM_EINVAL;
+    TriIn t0 = tri;
+    t0.row0 = 0;
+    t0.corr = 0;
+    if (n <= INV_MAX) return invert_blocks(n, in, out, pairs, status, pl, &t0);
     const int n1 = INV_MAX, n2 = n - n1;
     const cudaStream_t st = pl.st;
     helm_status s;
-    if ((s = invert_blocks(n1, in, out, pairs, status, pl)) != HELM_OK) return s;   // X11 = D11^{-1}
+    if ((s = invert_blocks(n1, in, out, pairs, status, pl, &t0)) != HELM_OK) return s;   // X11 = D11^{-1}
+    // X22 = S^{-1}, S read from the diagonal with the corner corrected by X11[n1-1][n1-1]
+    TriIn t1 = tri;
+    t1.row0 = n1;
+    t1.corr = 1;
+    t1.corr_off = -(long long)out.ld - 1;   // from X22's first entry to X11's last
+    if ((s = invert_blocks(n2, in, out.sub(n1, n1), pairs, status, pl, &t1)) != HELM_OK) return s;
     const int off = pl.add(pairs);
-    const float2 *ib = in.base;
     float2 *ob = out.base;
-    const long long stride = in.stride;
-    const int ld = in.ld;
-    pl.ops.push_back([=](const int *dev) -> helm_status {   // S = D22 - c^2 X11[n1-1][n1-1] e0 e0^T
-        HELM_TRACED(K_ZINV, st, (tri_schur_kernel<<<count, 256, 0, st>>>(n, n1, ib, ob, stride, ld, dev + off)));
-        const cudaError_t e2 = cudaGetLastError();
-        if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
-        return HELM_OK;
-    });
-    std::vector<int> self(pairs.size());
-    for (int t = 0; t < count; ++t) self[2 * t] = self[2 * t + 1] = pairs[2 * t + 1];
-    const Fam X22 = out.sub(n1, n1);
-    if ((s = invert_blocks(n2, X22, X22, self, status, pl)) != HELM_OK) return s;
+    const long long stride = out.stride;
+    const int ld = out.ld;
     pl.ops.push_back([=](const int *dev) -> helm_status {   // X12, X21, X11 from rank-one updates
-        HELM_TRACED(K_ZINV, st, (tri_rank1_kernel<<<count, 512, 0, st>>>(n, n1, ib, ob, stride, ld, dev + off)));
+        HELM_TRACED(K_ZINV, st, (tri_rank1_kernel<<<count, 512, 0, st>>>(n, n1, t0, ob, stride, ld, dev + off)));
         const cudaError_t e2 = cudaGetLastError();
         if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
         return HELM_OK;
@@ -757,13 +777,22 @@ helm_status bcr_factor(helm_factor_t *f) {
     Plan pl(st);
     if ((s = pl.with_split(kFactorSplitElems)) != HELM_OK) return s;
     const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
+    // level 0 inverts the odd lines' tridiagonal blocks straight from A's diagonal (n_z <= 256)
+    const bool tri_level0 = nz <= 2 * INV_MAX;
+    TriIn tri;
+    tri.diag = op->diag;
+    tri.nz = nz;
+    tri.nx = nx;
+    tri.cz_in = coup_of(g).cz_in;
+    tri.cz_edge = coup_of(g).cz_edge;
     {
         const double2 *diag = op->diag;
         float2 *D0 = Dc;
         const Coup cp = coup_of(g);
         const int perq = (int)std::min<long long>(64, (nz2 / 2 + 255) / 256);
         pl.ops.push_back([=](const int *) -> helm_status {
-            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(perq, nx, ns), 256, 0, st>>>(g, cp, diag, D0)));
+            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(perq, nx, ns), 256, 0, st>>>(g, cp, diag, D0,
+                                                                                           tri_level0 ? 1 : 0)));
             const cudaError_t e2 = cudaGetLastError();
             if (e2 != cudaSuccess) { helm_set_error("bcr: form blocks", e2); return HELM_ECUDA; }
             return HELM_OK;
@@ -776,8 +805,8 @@ helm_status bcr_factor(helm_factor_t *f) {
         for (int sy = 0; sy < ns; ++sy)
             for (int j = sp; j < nx; j += 2 * sp) inv_pairs.insert(inv_pairs.end(), {sy * nx + j, sy * nx + j});
         // level 0: the line blocks are still tridiagonal
-        s = sp == 1 ? invert_tridiag_blocks(nz, fD, fDinv, inv_pairs, op->status, pl)
-                    : invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl);
+        s = (sp == 1 && tri_level0) ? invert_tridiag_blocks(nz, fD, fDinv, inv_pairs, op->status, pl, tri)
+                                    : invert_blocks(nz, fD, fDinv, inv_pairs, op->status, pl);
         if (s != HELM_OK) return s;
         if (sp == 1) {
             float2 *D0 = Dc, *Di = b.Dinv, *L1 = Ln, *U1 = Un;
