@@ -69,12 +69,11 @@ Coup coup_of(const GridGeom &g) {
     return Coup{(float)coup_x(g, 1), (float)coup_x(g, 0), (float)coup_z(g, 1), (float)coup_z(g, 0)};
 }
 
-// dense D_i of every line and system: the diagonal of A and the vertical couplings next to it;
-// one float4 (two complex entries of a row) per thread and step
-__global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2 *D, int even_only) {
+// dense D_i of every line and system (n_z > 256): the diagonal of A and the vertical couplings
+// next to it; one float4 (two complex entries of a row) per thread and step
+__global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2 *D) {
     const int nz = g.nz, nx = g.nx;
     const int i = blockIdx.y, s = blockIdx.z;
-    if (even_only && (i & 1)) return;   // odd lines: inverted from the diagonal directly
     const float cz = cp.cz(i, nx);
     float4 *Di = reinterpret_cast<float4 *>(D + ((size_t)s * nx + i) * nz * nz);
     const double2 *dg = diag + ((size_t)s * nx + i) * nz;
@@ -93,8 +92,10 @@ __global__ void bcr_form_kernel(GridGeom g, Coup cp, const double2 *diag, float2
 
 // level 0 (couplings C = diag(cx)): kept line k (even) with eliminated neighbours k - 1, k + 1:
 //   D_k -= C Dinv_{k-1} C + C Dinv_{k+1} C,  L_k = -C Dinv_{k-1} C,  U_k = -C Dinv_{k+1} C
+// implicit (diag != nullptr): D_k is not in memory yet and is taken from A's diagonal and the
+// line's vertical coupling (the tridiagonal line block) before the update
 __global__ void bcr_level0_kernel(GridGeom g, Coup cp, float2 *D, const float2 *Dinv, float2 *Lnew, float2 *Unew,
-                                  int half) {
+                                  int half, const double2 *diag) {
     const int nz = g.nz, nx = g.nx, nz2 = nz * nz;
     const int k = 2 * blockIdx.y, s = blockIdx.z;
     const bool ha = k >= 1, hc = k + 1 < nx;
@@ -109,7 +110,14 @@ __global__ void bcr_level0_kernel(GridGeom g, Coup cp, float2 *D, const float2 *
         float2 ta = make_float2(0.f, 0.f), tc = ta;
         if (ha) { const float2 v = Da[e]; ta = make_float2(sc * v.x, sc * v.y); }
         if (hc) { const float2 v = Dc[e]; tc = make_float2(sc * v.x, sc * v.y); }
-        float2 d = Dk[e];
+        float2 d;
+        if (diag) {
+            const float cz = cp.cz(k, nx);
+            d = r == c ? to_c64(diag[((size_t)s * nx + k) * nz + r])
+                       : ((r - c == 1 || c - r == 1) ? make_float2(cz, 0.f) : make_float2(0.f, 0.f));
+        } else {
+            d = Dk[e];
+        }
         d.x -= ta.x + tc.x;
         d.y -= ta.y + tc.y;
         Dk[e] = d;
@@ -777,8 +785,10 @@ helm_status bcr_factor(helm_factor_t *f) {
     Plan pl(st);
     if ((s = pl.with_split(kFactorSplitElems)) != HELM_OK) return s;
     const int per = (int)std::min<long long>(64, (nz2 + 255) / 256);
-    // level 0 inverts the odd lines' tridiagonal blocks straight from A's diagonal (n_z <= 256)
+    // n_z <= 256: no line block is formed in memory before level 0, which inverts the odd lines'
+    // tridiagonal blocks and updates the even lines' straight from A's diagonal and couplings
     const bool tri_level0 = nz <= 2 * INV_MAX;
+    const double2 *tri_diag = tri_level0 ? op->diag : nullptr;
     TriIn tri;
     tri.diag = op->diag;
     tri.nz = nz;
@@ -790,9 +800,8 @@ helm_status bcr_factor(helm_factor_t *f) {
         float2 *D0 = Dc;
         const Coup cp = coup_of(g);
         const int perq = (int)std::min<long long>(64, (nz2 / 2 + 255) / 256);
-        pl.ops.push_back([=](const int *) -> helm_status {
-            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(perq, nx, ns), 256, 0, st>>>(g, cp, diag, D0,
-                                                                                           tri_level0 ? 1 : 0)));
+        if (!tri_level0) pl.ops.push_back([=](const int *) -> helm_status {
+            HELM_TRACED(K_BCR_FORM, st, (bcr_form_kernel<<<dim3(perq, nx, ns), 256, 0, st>>>(g, cp, diag, D0)));
             const cudaError_t e2 = cudaGetLastError();
             if (e2 != cudaSuccess) { helm_set_error("bcr: form blocks", e2); return HELM_ECUDA; }
             return HELM_OK;
@@ -813,7 +822,7 @@ helm_status bcr_factor(helm_factor_t *f) {
             const Coup cp = coup_of(g);
             pl.ops.push_back([=](const int *) -> helm_status {
                 HELM_TRACED(K_BCR_L0, st, (bcr_level0_kernel<<<dim3(per, (nx + 1) / 2, ns), 256, 0, st>>>(
-                                              g, cp, D0, Di, L1, U1, half)));
+                                              g, cp, D0, Di, L1, U1, half, tri_diag)));
                 const cudaError_t e2 = cudaGetLastError();
                 if (e2 != cudaSuccess) { helm_set_error("bcr: level 0", e2); return HELM_ECUDA; }
                 return HELM_OK;
