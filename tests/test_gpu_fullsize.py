@@ -2,8 +2,8 @@
 
 The FWI-step workload (128 x 128, omega in {5, 10, 15}, 16 sources) is solved with the
 same factor precision and refinement tolerance as the benchmark step, and every column is
-compared with the CPU oracle; the 256 x 256 mixed-precision workload (8 frequencies, 64
-sources) is compared on sampled frequencies.  Tolerances: 1e-9 (FP64 path), 1e-8 (mixed
+compared with the CPU oracle; so is the 256 x 256 mixed-precision workload (8 frequencies, 64
+sources).  Tolerances: 1e-9 (FP64 path), 1e-8 (mixed
 path), relative error per column."""
 import numpy as np
 import pytest
@@ -43,7 +43,7 @@ def test_fwi_step_workload_every_column(prec, tol, method):
 
 
 @pytest.mark.parametrize("method", [2, 1])
-def test_mixed_256_workload_sampled_frequencies(method):
+def test_mixed_256_workload_every_column(method):
     w = W.config_mixed(256)
     g = H.Grid(w.nx, w.nz, w.lx, w.lz)
     op = hm.helm_assemble(w.nx, w.nz, w.lx, w.lz, torch.tensor(w.m, device="cuda"), w.omegas)
@@ -53,10 +53,13 @@ def test_mixed_256_workload_sampled_frequencies(method):
     assert info["max_relres"] <= 1e-10
     E = H.source_vectors(g, w.acq.src_xz)
     Xc = X.cpu().numpy()
-    for q in (0, len(w.omegas) - 1):
+    # the metric's claim: every column of every frequency within 1e-8 of the oracle
+    errs = []
+    for q in range(len(w.omegas)):
         fo = H.Factor(H.helmholtz_matrix(g, w.m, w.omegas[q]))
-        sel = np.arange(0, w.acq.n_src, 7)
-        assert _colerr(Xc[q][sel], fo.solve(E[sel])) <= 1e-8
+        errs.append(_colerr(Xc[q], fo.solve(E)))
+    print("mixed 256^2 error per frequency:", ["%.2e" % e for e in errs])
+    assert max(errs) <= 1e-8, errs
 
 
 @pytest.mark.parametrize("prec,tol", [(hm.HELM_MIXED, 1e-8), (hm.HELM_FP64, 1e-9)])
