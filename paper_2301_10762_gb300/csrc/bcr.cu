@@ -45,8 +45,8 @@
 
 #include "abi_internal.h"
 #include "kernels.h"
-#include "mma_tf32.cuh"
 #include "pivot16.cuh"
+#include "tcgen05.cuh"
 #include "trace.h"
 
 namespace helm {
@@ -165,6 +165,7 @@ struct InvArgs {
     const int *idx;              // [count][2]: input index, output index
     int *status;
     TriIn tri;                   // tri.diag set: implicit tridiagonal input instead of `in`
+    uint32_t tries = 0;          // polls of a bounded mbarrier wait before it gives up
 };
 
 __device__ __forceinline__ long long op_off(int idx, int div, long long stride, long long stride_hi) {
@@ -247,136 +248,207 @@ __global__ void __launch_bounds__(INV_THREADS, 1) zinv_base_kernel(InvArgs a) {
     if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
 }
 
-// X = M^{-1} of one 128 x 128 block per CTA: the block Gauss-Jordan of zinv_base_kernel with
-// the rank-16 update of each block step on the tensor pipe.  With R'[u][c] = (P W[K, :])[u][c]
-// off the pivot columns K and P[u][c - k0] on them, one product does the whole step:
-//     W <- W' + A' R',  W' = W with the rows and columns K zeroed,
-//     A'[r][u] = -W[r][k0 + u] off the pivot rows, delta(r - k0, u) on them,
-// as 3xTF32 mma.sync tiles (complex as real: an m16 x n8 tile for the real parts of eight
-// columns and one for the imaginary parts).  Warp w updates rows 16 (w mod 8) .. + 15, columns
-// 64 (w / 8) .. + 63.  Row strides keep the 16- and 8-byte fragment loads free of bank conflicts.
-constexpr int Z128_LDW = 136;   // W: rows g and g + 1 sixteen words apart
-constexpr int Z128_PS = 20;     // staged column panel U[r][u] and R'^T[c][u]
-size_t zinv128_smem_bytes() {
-    return sizeof(float2) * ((size_t)128 * Z128_LDW + 2 * (size_t)128 * Z128_PS + PIV * PIV);
-}
+// X = M^{-1} of one 128 x 128 block per CTA with the block in tensor memory: lane r holds row r,
+// 256 FP32 columns (column 2c the real, 2c + 1 the imaginary part of entry c).  Each
+// Gauss-Jordan step (16 pivot columns K = k0 .. k0 + 15) is
+//     W <- W' + A' R'  (W' = W with the rows and columns K zeroed in tensor memory;
+//                       A'[r][u] = -W[r][k0 + u] off the pivot rows, delta(r - k0, u) on them;
+//                       R' = P W[K, :] off the pivot columns, P on them, P = W[K, K]^{-1}),
+// one tcgen05 3xTF32 product of M = 128, N = 256 (R' expanded to real rows as in the GEMM),
+// K = 32, accumulated into W itself.  Shared memory holds only the product's operands, the
+// pivot rows and the 16 x 16 blocks (~103 KB), so that two CTAs share an SM and one's pivot
+// chain (one warp) overlaps the other's work.  Warp w owns tensor-memory lanes 32 (w mod 4) ..
+// + 31 and columns 128 (w / 4) .. + 127.
+constexpr int ZT_THREADS = 256;
+constexpr int ZT_WS = 129;   // pivot rows W[K, :] in shared memory: row stride (complex)
+constexpr int ZT_PS = 17;    // padded copy of P
+constexpr uint32_t ZT_A = 0, ZT_B = 32768, ZT_PK = 98304, ZT_P = ZT_PK + 2048, ZT_PPAD = ZT_P + 2048;
+size_t zinv128_tm_smem_bytes() { return (size_t)ZT_PPAD + sizeof(float2) * PIV * ZT_PS + 1024; }
 
-__global__ void __launch_bounds__(INV_THREADS, 1) zinv128_kernel(InvArgs a) {
-    extern __shared__ __align__(16) unsigned char inv_smem[];
-    constexpr int n = 128, LDW = Z128_LDW, PS = Z128_PS;
-    float2 *W = reinterpret_cast<float2 *>(inv_smem);   // [128][LDW]
-    float2 *U = W + (size_t)n * LDW;                       // [128][PS]: column panel W[:, K]
-    float2 *RT = U + (size_t)n * PS;                       // [128][PS]: R'^T
-    float2 *P = RT + (size_t)n * PS;                       // [16][16]: pivot-block inverse
+__global__ void __launch_bounds__(ZT_THREADS, 2) zinv128_tm_kernel(InvArgs a) {
+    extern __shared__ __align__(16) unsigned char zt_smem[];
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t s_tmem;
     __shared__ int s_bad;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    constexpr int n = 128;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hh = warp >> 2, r = 32 * q + lane;
+    const uint32_t base = (smem_u32(zt_smem) + 1023u) & ~1023u;
+    unsigned char *gbase = zt_smem + (base - smem_u32(zt_smem));
+    float2 *Wk = reinterpret_cast<float2 *>(gbase + ZT_A);      // [16][ZT_WS], aliases the A tiles
+    float2 *Pk = reinterpret_cast<float2 *>(gbase + ZT_PK);     // [16][16]: the pivot block
+    float2 *P = reinterpret_cast<float2 *>(gbase + ZT_P);       // [16][16]: its inverse
+    float2 *Ps = reinterpret_cast<float2 *>(gbase + ZT_PPAD);   // [16][ZT_PS]: padded copy
+    const uint32_t a_hi = base + ZT_A, a_lo = a_hi + 16384, b_hi = base + ZT_B, b_lo = b_hi + 32768;
     const int *ix = a.idx + 2 * (size_t)blockIdx.x;
     const float2 *M = a.in.base + op_off(ix[0], a.in.div, a.in.stride, a.in.stride_hi);
     float2 *X = a.out + op_off(ix[1], a.out_div, a.out_stride, a.out_stride_hi);
-    if (tid == 0) s_bad = 0;
-    for (int e = tid; e < n * n / 2; e += INV_THREADS) {   // two entries per float4
-        const int r = (2 * e) / n, c = (2 * e) % n;
-        if (a.tri.diag) {
-            const float2 v0 = a.tri.entry(ix[0], r, c, X), v1 = a.tri.entry(ix[0], r, c + 1, X);
-            *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) = make_float4(v0.x, v0.y, v1.x, v1.y);
-        } else {
-            *reinterpret_cast<float4 *>(W + (size_t)r * LDW + c) =
-                *reinterpret_cast<const float4 *>(M + (size_t)r * a.in.ld + c);
-        }
+    if (tid == 0) {
+        s_bad = 0;
+        mbar_init(&mma_bar, 1);
+        fence_mbar_init_cluster();
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(256u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
-    const int mw = warp & 7, cw = warp >> 3;
-    const int r0 = 16 * mw + g, r1 = r0 + 8;
-    for (int kb_i = 0; kb_i < n / PIV; ++kb_i) {
-        const int k0 = kb_i * PIV;
-        for (int e = tid; e < n * PIV; e += INV_THREADS) {
-            const int r = e >> 4, u = e & 15;
-            U[r * PS + u] = W[(size_t)r * LDW + k0 + u];
-        }
-        if (warp == 0 && !warp_invert16<float>(W + (size_t)k0 * LDW + k0, LDW, PIV, P) && lane == 0) s_bad = 1;
-        __syncthreads();
-        for (int e = tid; e < n * PIV; e += INV_THREADS) {   // R'^T[c][u], u = e / 128
-            const int u = e >> 7, c = e & 127;
-            float2 acc;
-            if (c >= k0 && c < k0 + PIV) {
-                acc = P[u * PIV + (c - k0)];
-            } else {
-                acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int v = 0; v < PIV; ++v) cfma(acc, P[u * PIV + v], W[(size_t)(k0 + v) * LDW + c]);
-            }
-            RT[c * PS + u] = acc;
-        }
-        __syncthreads();
-        // A' fragments of the warp's 16 rows for the four k-steps (four complex u each; slot t
-        // holds Re, slot t + 4 Im of column u = 4s + t)
-        const bool pivot_rows = mw == kb_i;
-        uint32_t ah[4][4], al[4][4];
-#pragma unroll
-        for (int st = 0; st < 4; ++st) {
-            const int u = 4 * st + t;
-            float2 x0, x1;
-            if (pivot_rows) {
-                x0 = make_float2(r0 - k0 == u ? 1.f : 0.f, 0.f);
-                x1 = make_float2(r1 - k0 == u ? 1.f : 0.f, 0.f);
-            } else {
-                x0 = U[r0 * PS + u];
-                x1 = U[r1 * PS + u];
-                x0 = make_float2(-x0.x, -x0.y);
-                x1 = make_float2(-x1.x, -x1.y);
-            }
-            split_tf32(x0.x, ah[st][0], al[st][0]);
-            split_tf32(x1.x, ah[st][1], al[st][1]);
-            split_tf32(x0.y, ah[st][2], al[st][2]);
-            split_tf32(x1.y, ah[st][3], al[st][3]);
-        }
+    tc_fence_after();
+    const uint32_t trow = s_tmem + ((uint32_t)(32 * q) << 16);   // this warp's lanes, column 0
+    // the block into tensor memory: lane r, columns 128 hh .. + 127
 #pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            float re[4][4], im[4][4];   // [group of 8 columns][fragment]
+    for (int ch = 0; ch < 8; ++ch) {
+        const int col = 128 * hh + 16 * ch, c0 = col / 2;
+        float v[16];
 #pragma unroll
-            for (int gi = 0; gi < 4; ++gi) {
-                const int c = 64 * cw + 32 * half + 8 * gi + 2 * t;
-                const bool zero = pivot_rows || (c >= k0 && c < k0 + PIV);
-                const float4 w0 = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                       : *reinterpret_cast<const float4 *>(W + (size_t)r0 * LDW + c);
-                const float4 w1 = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                       : *reinterpret_cast<const float4 *>(W + (size_t)r1 * LDW + c);
-                re[gi][0] = w0.x; im[gi][0] = w0.y; re[gi][1] = w0.z; im[gi][1] = w0.w;
-                re[gi][2] = w1.x; im[gi][2] = w1.y; re[gi][3] = w1.z; im[gi][3] = w1.w;
+        for (int i = 0; i < 8; ++i) {
+            const float2 e = a.tri.diag ? a.tri.entry(ix[0], r, c0 + i, X) : M[(size_t)r * a.in.ld + c0 + i];
+            v[2 * i] = e.x;
+            v[2 * i + 1] = e.y;
+        }
+        tc_st16(trow + (uint32_t)col, v);
+    }
+    tc_wait_st();
+    constexpr uint32_t idesc = idesc_tf32(256);
+    int phase = 0;
+    bool aborted = false;
+#pragma unroll 1
+    for (int kb = 0; kb < n / PIV; ++kb) {
+        const int k0 = kb * PIV, qk = k0 >> 5, rk0 = k0 & 31;
+        const bool krow = q == qk && lane >= rk0 && lane < rk0 + PIV;   // this lane's row is a pivot row
+        tc_fence_before();
+        __syncthreads();   // the previous step's tensor-memory reads and shared-memory reads are done
+        tc_fence_after();
+        // (a) the column panel W[r][k0 + u], u = 8 hh .. 8 hh + 7 (kept for A'); the pivot block
+        float uf[16];
+        tc_ld16(trow + (uint32_t)(2 * k0 + 16 * hh), uf);
+        if (krow) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Pk[(lane - rk0) * PIV + 8 * hh + i] = make_float2(uf[2 * i], uf[2 * i + 1]);
+        }
+        // (b) the pivot rows' quarter: rows K to shared memory, then W' (rows K and columns K
+        // zeroed) back; (c) the other quarters: columns K zeroed
+        if (q == qk) {
+#pragma unroll 1
+            for (int ch = 0; ch < 8; ++ch) {
+                const int col = 128 * hh + 16 * ch;
+                float v[16];
+                tc_ld16(trow + (uint32_t)col, v);
+                if (krow) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) Wk[(lane - rk0) * ZT_WS + col / 2 + i] = make_float2(v[2 * i], v[2 * i + 1]);
+                }
+                const bool kcol = col >= 2 * k0 && col < 2 * k0 + 2 * PIV;
+                if (krow || kcol) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
+                tc_st16(trow + (uint32_t)col, v);
             }
+        } else {
+            float z[16];
 #pragma unroll
-            for (int st = 0; st < 4; ++st) {
+            for (int i = 0; i < 16; ++i) z[i] = 0.f;
+            tc_st16(trow + (uint32_t)(2 * k0 + 16 * hh), z);
+        }
+        tc_wait_st();
+        __syncthreads();
+        // (d) the pivot block's inverse (one warp), and its padded copy
+        if (warp == 0) {
+            if (!warp_invert16<float>(Pk, PIV, PIV, P) && lane == 0) s_bad = 1;
+            __syncwarp();
+            for (int e = lane; e < PIV * PIV; e += 32) Ps[(e >> 4) * ZT_PS + (e & 15)] = P[e];
+        }
+        __syncthreads();
+        // (e) R' and the expanded B tiles: item (c, j), u = 2j, 2j + 1; B row 2c = (Re, -Im),
+        // row 2c + 1 = (Im, Re) of R'[u][c], split into hi and lo
+#pragma unroll 1
+        for (int it = tid; it < n * 8; it += ZT_THREADS) {
+            const int c = it >> 3, j = it & 7, u0 = 2 * j, u1 = u0 + 1;
+            float2 r0, r1;
+            if (c >= k0 && c < k0 + PIV) {
+                r0 = Ps[u0 * ZT_PS + (c - k0)];
+                r1 = Ps[u1 * ZT_PS + (c - k0)];
+            } else {
+                r0 = make_float2(0.f, 0.f);
+                r1 = r0;
 #pragma unroll
-                for (int gi = 0; gi < 4; ++gi) {
-                    // B: column g of the group, rows u = 4 st + t: Re tile (Re R', -Im R'),
-                    // Im tile (Im R', Re R')
-                    const float2 b = RT[(64 * cw + 32 * half + 8 * gi + g) * PS + 4 * st + t];
-                    uint32_t xr_h, xr_l, xi_h, xi_l;
-                    split_tf32(b.x, xr_h, xr_l);
-                    split_tf32(b.y, xi_h, xi_l);
-                    const uint32_t nxi_h = xi_h ^ 0x80000000u, nxi_l = xi_l ^ 0x80000000u;
-                    mma_tf32(re[gi], ah[st], xr_h, nxi_h);
-                    mma_tf32(re[gi], ah[st], xr_l, nxi_l);
-                    mma_tf32(re[gi], al[st], xr_h, nxi_h);
-                    mma_tf32(im[gi], ah[st], xi_h, xr_h);
-                    mma_tf32(im[gi], ah[st], xi_l, xr_l);
-                    mma_tf32(im[gi], al[st], xi_h, xr_h);
+                for (int v = 0; v < PIV; ++v) {
+                    const float2 w = Wk[v * ZT_WS + c];
+                    cfma(r0, Ps[u0 * ZT_PS + v], w);
+                    cfma(r1, Ps[u1 * ZT_PS + v], w);
                 }
             }
-#pragma unroll
-            for (int gi = 0; gi < 4; ++gi) {
-                const int c = 64 * cw + 32 * half + 8 * gi + 2 * t;
-                *reinterpret_cast<float4 *>(W + (size_t)r0 * LDW + c) = make_float4(re[gi][0], im[gi][0], re[gi][1], im[gi][1]);
-                *reinterpret_cast<float4 *>(W + (size_t)r1 * LDW + c) = make_float4(re[gi][2], im[gi][2], re[gi][3], im[gi][3]);
-            }
+            float4 hi, lo;
+            split4(make_float4(r0.x, -r0.y, r1.x, -r1.y), 1.f, hi, lo);
+            st_shared_v4(b_hi + sw128(2 * c, j), hi);
+            st_shared_v4(b_lo + sw128(2 * c, j), lo);
+            split4(make_float4(r0.y, r0.x, r1.y, r1.x), 1.f, hi, lo);
+            st_shared_v4(b_hi + sw128(2 * c + 1, j), hi);
+            st_shared_v4(b_lo + sw128(2 * c + 1, j), lo);
         }
+        __syncthreads();   // the pivot rows read: their storage becomes the A tiles
+        // (f) A' row r, chunks j = 4 hh .. 4 hh + 3 (u = 2j, 2j + 1 of this thread's panel part)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * hh + jj, u0 = 2 * j;
+            float4 v;
+            if (krow) {
+                v = make_float4(r - k0 == u0 ? 1.f : 0.f, 0.f, r - k0 == u0 + 1 ? 1.f : 0.f, 0.f);
+            } else {
+                v = make_float4(-uf[4 * jj], -uf[4 * jj + 1], -uf[4 * jj + 2], -uf[4 * jj + 3]);
+            }
+            float4 hi, lo;
+            split4(v, 1.f, hi, lo);
+            st_shared_v4(a_hi + sw128(r, j), hi);
+            st_shared_v4(a_lo + sw128(r, j), lo);
+        }
+        fence_proxy_async_smem();   // the operand tiles, before the tensor core reads them
+        tc_fence_before();
         __syncthreads();
+        // (g) W' + A' R' into tensor memory
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {   // hi*hi, hi*lo, lo*hi
+                const uint32_t aa = p == 2 ? a_lo : a_hi, bb = p == 1 ? b_lo : b_hi;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(s_tmem, desc_sw128(aa + 32 * kk), desc_sw128(bb + 32 * kk), idesc, 1u);
+            }
+            tc_commit(&mma_bar);
+        }
+        const bool done = mbar_wait_bounded(&mma_bar, (uint32_t)phase, a.tries);
+        if (__syncthreads_or(!done)) {   // uniform: every thread leaves the loop
+            if (tid == 0) atomicOr(a.status, ST_TIMEOUT);
+            aborted = true;
+            break;
+        }
+        phase ^= 1;
+        tc_fence_after();
     }
-    for (int e = tid; e < n * n / 2; e += INV_THREADS) {
-        const int r = (2 * e) / n, c = (2 * e) % n;
-        *reinterpret_cast<float4 *>(X + (size_t)r * a.ldo + c) = *reinterpret_cast<const float4 *>(W + (size_t)r * LDW + c);
+    // the inverse out of tensor memory: lane r, columns 128 hh .. + 127
+    if (!aborted) {
+#pragma unroll 1
+        for (int ch = 0; ch < 8; ++ch) {
+            const int col = 128 * hh + 16 * ch;
+            float v[16];
+            tc_ld16(trow + (uint32_t)col, v);
+            float4 *xr = reinterpret_cast<float4 *>(X + (size_t)r * a.ldo + col / 2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xr[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        }
+    } else {
+        mbar_wait_bounded(&mma_bar, (uint32_t)phase, a.tries);   // an MMA that may still be in flight
     }
     if (tid == 0 && s_bad) atomicOr(a.status, ST_SINGULAR);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(256u) : "memory");
 }
 
 size_t inv_smem_bytes(int n) {
@@ -614,17 +686,18 @@ helm_status invert_blocks(int n, Fam in, Fam out, const std::vector<int> &pairs,
     if (n <= INV_MAX) {
         const int off = pl.add(pairs);
         // 128 x 128 blocks on 16-byte boundaries (two complex entries per access): the kernel
-        // with the tensor-pipe update
+        // with the block in tensor memory
         const bool t128 = n == 128 && ((uintptr_t)in.base & 15) == 0 && ((uintptr_t)out.base & 15) == 0 &&
                           (in.ld & 1) == 0 && (out.ld & 1) == 0 && (in.stride & 1) == 0 && (out.stride & 1) == 0;
-        const size_t smem = t128 ? zinv128_smem_bytes() : inv_smem_bytes(n);
-        const void *fn = t128 ? (const void *)zinv128_kernel : (const void *)zinv_base_kernel;
+        const size_t smem = t128 ? zinv128_tm_smem_bytes() : inv_smem_bytes(n);
+        const void *fn = t128 ? (const void *)zinv128_tm_kernel : (const void *)zinv_base_kernel;
         cudaError_t e = ensure_dyn_smem(fn, smem);
         if (e != cudaSuccess) { helm_set_error("bcr: block inversion", e); return HELM_ECUDA; }
         InvArgs a{n, in.op(), out.base, out.stride, 0, 0, out.ld, nullptr, status, tri ? *tri : TriIn{}};
+        a.tries = wait_tries();
         pl.ops.push_back([a, off, count, smem, st, t128](const int *dev) mutable -> helm_status {
             a.idx = dev + off;
-            if (t128) HELM_TRACED(K_ZINV, st, (zinv128_kernel<<<count, INV_THREADS, smem, st>>>(a)));
+            if (t128) HELM_TRACED(K_ZINV, st, (zinv128_tm_kernel<<<count, ZT_THREADS, smem, st>>>(a)));
             else HELM_TRACED(K_ZINV, st, (zinv_base_kernel<<<count, INV_THREADS, smem, st>>>(a)));
             const cudaError_t e2 = cudaGetLastError();
             if (e2 != cudaSuccess) { helm_set_error("bcr: block inversion", e2); return HELM_ECUDA; }
